@@ -1,0 +1,166 @@
+"""FP64 CPU oracle for the muSR fit objective (test infrastructure only).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline leg may import this package.  The GPU library never does, and
+this package never imports the GPU library: the two share no code.
+
+The arithmetic lives in ``musr_oracle.c`` (plain C, FP64, Neumaier sums),
+built on demand with gcc into ``liboracle.so`` beside it.  Each wrapper below
+states the passage of the paper it follows; see the C file's header for the
+readings taken where the paper is silent or garbled.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "musr_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOMEM, ENONFINITE, EDOMAIN, ENOCONV = 0, -1, -2, -4, -5, -7
+CHI2, POISSON = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile musr_oracle.c with gcc (OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int32)
+            lp = ctypes.POINTER(ctypes.c_int64)
+            layout = [ctypes.c_int, lp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                      ctypes.c_double, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip]
+            lib.orc_model.argtypes = layout + [dp, dp]
+            lib.orc_objective.argtypes = layout + [dp, dp, ctypes.c_int, dp]
+            lib.orc_gradient.argtypes = layout + [dp, dp, ctypes.c_int, dp, dp, dp]
+            lib.orc_gradient_fd.argtypes = layout + [dp, dp, ctypes.c_int, ctypes.c_double, dp]
+            lib.orc_fit.argtypes = layout + [dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_uint8),
+                                             ctypes.c_int, ctypes.c_double, dp, dp]
+            for f in (lib.orc_model, lib.orc_objective, lib.orc_gradient, lib.orc_gradient_fd,
+                      lib.orc_fit):
+                f.restype = ctypes.c_int
+            lib.orc_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _layout_args(lay):
+    nb = np.ascontiguousarray(lay.n_bins, dtype=np.int64)
+    mp = np.ascontiguousarray(lay.map, dtype=np.int32)
+    cp = np.ascontiguousarray(lay.comp, dtype=np.int32)
+    keep = (nb, mp, cp)
+    args = [lay.n_hist, nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), lay.t0_us, lay.dt_us,
+            lay.tau_us, lay.gamma, lay.n_params, lay.map_width,
+            mp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), lay.n_comp,
+            cp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))]
+    return args, keep
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle status {code}")
+        self.code = code
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def model(lay, theta) -> np.ndarray:
+    """Eq. 1 theory N^j(t_n) for every bin of every histogram (FP64)."""
+    lib = _load()
+    args, keep = _layout_args(lay)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = np.zeros(lay.total_bins)
+    st = lib.orc_model(*args, _dp(th), _dp(out))
+    if st:
+        raise OracleError(st)
+    return out
+
+
+def objective(lay, data, theta, obj=CHI2, raise_on_error=True):
+    """Eq. 3 chi2 (sigma^2 = max(d, 1)) or Eq. 4 Poisson deviance, FP64 compensated."""
+    lib = _load()
+    args, keep = _layout_args(lay)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    d = np.ascontiguousarray(data, dtype=np.float64)
+    v = np.zeros(1)
+    st = lib.orc_objective(*args, _dp(d), _dp(th), int(obj), _dp(v))
+    if st and raise_on_error:
+        raise OracleError(st)
+    return (float(v[0]), st) if not raise_on_error else float(v[0])
+
+
+def gradient(lay, data, theta, obj=CHI2, with_gn=True):
+    """Value, analytic gradient and Gauss-Newton matrix (FP64)."""
+    lib = _load()
+    args, keep = _layout_args(lay)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    d = np.ascontiguousarray(data, dtype=np.float64)
+    P = lay.n_params
+    v = np.zeros(1)
+    g = np.zeros(P)
+    H = np.zeros((P, P)) if with_gn else None
+    st = lib.orc_gradient(*args, _dp(d), _dp(th), int(obj), _dp(v), _dp(g),
+                          _dp(H) if with_gn else None)
+    if st:
+        raise OracleError(st)
+    return float(v[0]), g, H
+
+
+def gradient_fd(lay, data, theta, obj=CHI2, rel_h=1e-6):
+    """Central finite differences of the objective, h = rel_h * max(|theta_j|, 1)."""
+    lib = _load()
+    args, keep = _layout_args(lay)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    d = np.ascontiguousarray(data, dtype=np.float64)
+    g = np.zeros(lay.n_params)
+    st = lib.orc_gradient_fd(*args, _dp(d), _dp(th), int(obj), float(rel_h), _dp(g))
+    if st:
+        raise OracleError(st)
+    return g
+
+
+def fit(lay, data, theta0, obj=CHI2, free=None, max_iter=500, edm_tol=1e-8):
+    """Levenberg-Marquardt fit over the free parameters (FP64).
+
+    Returns (theta, stats dict, covariance of the free parameters).
+    """
+    lib = _load()
+    args, keep = _layout_args(lay)
+    th = np.ascontiguousarray(theta0, dtype=np.float64).copy()
+    d = np.ascontiguousarray(data, dtype=np.float64)
+    fm = np.ascontiguousarray(lay.free if free is None else free, dtype=np.uint8)
+    nf = int(fm.sum())
+    stats = np.zeros(8)
+    cov = np.zeros((nf, nf))
+    st = lib.orc_fit(*args, _dp(d), int(obj), _dp(th),
+                     fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), int(max_iter),
+                     float(edm_tol), _dp(stats), _dp(cov))
+    info = {"value": stats[0], "ndf": stats[1], "iters": int(stats[2]), "evals": int(stats[3]),
+            "edm": stats[4], "mu": stats[5], "status": int(st)}
+    return th, info, cov

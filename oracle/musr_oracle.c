@@ -1,0 +1,589 @@
+/*
+ * Plain FP64 CPU oracle for the muSR fit objective.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * statement of what the GPU library computes.  Only the test-suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header or constant with the CUDA library: every formula
+ * here is written directly from the paper.
+ *
+ *   Sec. 4.1, Eq. 1  N^j(t) = N0^j exp(-t/tau_mu) [1 + A^j(p, t)] + Nbkg^j,
+ *                    t = n * dt  (n = 0, 1, 2, ...; a start offset t0 is
+ *                    allowed, t = t0 + n * dt, with t0 = 0 reproducing Eq. 1)
+ *   Sec. 4.1, Eq. 2  per-histogram parameter set {N0, Nbkg, p}; the map array
+ *                    of Sec. 4.2.1 (Listing 3) gives the indirect addressing
+ *                    from a histogram's slots to the global parameter vector.
+ *   Sec. 4.1, Eq. 3  chi2 = sum_j sum_n (d - N)^2 / d_err^2, d_err^2 = d;
+ *                    reading: d_err^2 = max(d, 1) so that empty bins are
+ *                    defined.
+ *   Sec. 4.1, Eq. 4  L = 2 sum_j sum_n [(N - d) + d ln(d / N)]; reading: the
+ *                    log term sits inside the bracket (Poisson deviance,
+ *                    -2 ln of the likelihood ratio), it is minimised, and a
+ *                    bin with d = 0 contributes 2N.
+ *   Sec. 4.2.1, Listing 2 predefined functions:
+ *                    se(t, l)  = exp(-l t)
+ *                    sg(t, s)  = exp(-(s t)^2 / 2)
+ *                    stg(t, s) = 1/3 + 2/3 (1 - (s t)^2) exp(-(s t)^2 / 2)
+ *                    (the listing's integer 1/3 and 2/3 are read as the real
+ *                    fractions of the static Gaussian Kubo-Toyabe function)
+ *   Sec. 4.3, Eq. 5  A = A0 sg(t, sigma) cos(gamma_mu B t + phi); the cosine
+ *                    "tf" of Listing 3 is cos(2 pi gamma B t + phi) with gamma
+ *                    in MHz/G, t in us, phi in radians.
+ *
+ * Component kinds (columns are indices into the histogram's map row; a map
+ * entry of -1 stands for the constant 0):
+ *   0  TF_EXP   a * se(t, rate) * cos(2 pi gamma (B + B2) t + phi)
+ *   1  TF_GAUSS a * sg(t, rate) * cos(2 pi gamma (B + B2) t + phi)
+ *   2  KT_SG    a * stg(t, rate)
+ *
+ * Every sum over bins uses Neumaier-compensated FP64 summation, so the value
+ * returned is the exact sum of the FP64 per-bin terms to within a few ulp.
+ *
+ * Gradients: analytic chain rule (Sec. 4.1 objectives differentiated by
+ * hand) and, independently, FP64 central finite differences.  The
+ * Gauss-Newton matrix is H = sum c J J^T with c = 2 / max(d, 1) for chi2 and
+ * c = 2 / N (expected information, Fisher scoring) for the deviance.
+ *
+ * The fit is a Levenberg-Marquardt minimiser (the paper drives the same
+ * objective with Minuit2, Sec. 4.1) over the free parameters.
+ *
+ * Parity status: every function here is pinned by closed forms, invariants,
+ * library routines or brute force in tests/test_oracle_pins.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_OK 0
+#define ORC_EINVAL -1
+#define ORC_ENOMEM -2
+#define ORC_ENONFINITE -4
+#define ORC_EDOMAIN -5
+#define ORC_ENOCONV -7
+
+#define ORC_TF_EXP 0
+#define ORC_TF_GAUSS 1
+#define ORC_KT_SG 2
+
+#define ORC_CHI2 0
+#define ORC_POISSON 1
+
+static const double ORC_PI = 3.14159265358979323846264338327950288;
+
+/* ------------------------------------------------------------------------ */
+/* Neumaier compensated summation                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    double s, c;
+} orc_acc;
+
+static void acc_add(orc_acc* a, double x) {
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double acc_val(const orc_acc* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------ */
+/* Layout                                                                    */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int n_hist;
+    const int64_t* n_bins;
+    double t0, dt, tau, gamma;
+    int n_params, map_width;
+    const int32_t* map;
+    int n_comp;
+    const int32_t* comp; /* n_comp x 6: kind, amp, rate, field, field2, phase */
+} orc_layout;
+
+static int64_t hist_offset(const orc_layout* L, int k) {
+    int64_t off = 0;
+    for (int j = 0; j < k; ++j) off += L->n_bins[j];
+    return off;
+}
+
+static int64_t total_bins(const orc_layout* L) { return hist_offset(L, L->n_hist); }
+
+/* theta index of map column col for histogram k, or -1 */
+static int map_index(const orc_layout* L, int k, int col) {
+    if (col < 0) return -1;
+    return L->map[(int64_t)k * L->map_width + col];
+}
+
+static double map_value(const orc_layout* L, const double* theta, int k, int col) {
+    int i = map_index(L, k, col);
+    return i < 0 ? 0.0 : theta[i];
+}
+
+static int check_layout(const orc_layout* L) {
+    if (L->n_hist < 0 || L->n_params < 0 || L->map_width < 2 || L->n_comp < 0) return ORC_EINVAL;
+    if (!(L->dt > 0.0) || !(L->tau > 0.0)) return ORC_EINVAL;
+    for (int k = 0; k < L->n_hist; ++k) {
+        if (L->n_bins[k] < 0) return ORC_EINVAL;
+        for (int c = 0; c < L->map_width; ++c) {
+            int i = L->map[(int64_t)k * L->map_width + c];
+            if (i < -1 || i >= L->n_params) return ORC_EINVAL;
+        }
+    }
+    for (int c = 0; c < L->n_comp; ++c) {
+        const int32_t* d = L->comp + 6 * c;
+        if (d[0] < 0 || d[0] > 2) return ORC_EINVAL;
+        for (int s = 1; s < 6; ++s)
+            if (d[s] < -1 || d[s] >= L->map_width) return ORC_EINVAL;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Listing 2 predefined functions, written out                               */
+/* ------------------------------------------------------------------------ */
+static double fn_se(double t, double lambda) { return exp(-lambda * t); }
+
+static double fn_sg(double t, double sigma) {
+    double st = sigma * t;
+    return exp(-0.5 * st * st);
+}
+
+static double fn_stg(double t, double sigma) {
+    double x = (sigma * t) * (sigma * t);
+    return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - x) * exp(-0.5 * x);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 theory at one bin, plus its derivative with respect to every map    */
+/* column of the histogram (dcol may be NULL).                              */
+/* ------------------------------------------------------------------------ */
+static double theory_bin(const orc_layout* L, const double* theta, int k, double t, double* dcol) {
+    double n0 = map_value(L, theta, k, 0);
+    double bkg = map_value(L, theta, k, 1);
+    double life = exp(-t / L->tau);
+    double asym = 0.0;
+    /* dA/d(column value) accumulated per column */
+    double* dA = NULL;
+    double dA_local[64];
+    if (dcol) {
+        dA = dA_local;
+        for (int c = 0; c < L->map_width; ++c) dA[c] = 0.0;
+    }
+    for (int c = 0; c < L->n_comp; ++c) {
+        const int32_t* d = L->comp + 6 * c;
+        int kind = d[0];
+        double a = map_value(L, theta, k, d[1]);
+        double rate = map_value(L, theta, k, d[2]);
+        if (kind == ORC_KT_SG) {
+            double g = fn_stg(t, rate);
+            asym += a * g;
+            if (dA) {
+                if (d[1] >= 0) dA[d[1]] += g;
+                if (d[2] >= 0) {
+                    /* d stg / d sigma = (2/3) sigma t^2 ((sigma t)^2 - 3) exp(-(sigma t)^2/2) */
+                    double x = (rate * t) * (rate * t);
+                    dA[d[2]] += a * (2.0 / 3.0) * rate * t * t * (x - 3.0) * exp(-0.5 * x);
+                }
+            }
+            continue;
+        }
+        double field = map_value(L, theta, k, d[3]) + map_value(L, theta, k, d[4]);
+        double phi = map_value(L, theta, k, d[5]);
+        double arg = 2.0 * ORC_PI * L->gamma * field * t + phi;
+        double cs = cos(arg), sn = sin(arg);
+        double env, denv_drate;
+        if (kind == ORC_TF_EXP) {
+            env = fn_se(t, rate);
+            denv_drate = -t * env;
+        } else {
+            env = fn_sg(t, rate);
+            denv_drate = -rate * t * t * env;
+        }
+        asym += a * env * cs;
+        if (dA) {
+            if (d[1] >= 0) dA[d[1]] += env * cs;
+            if (d[2] >= 0) dA[d[2]] += a * denv_drate * cs;
+            double dphase = -a * env * sn;
+            if (d[3] >= 0) dA[d[3]] += dphase * 2.0 * ORC_PI * L->gamma * t;
+            if (d[4] >= 0) dA[d[4]] += dphase * 2.0 * ORC_PI * L->gamma * t;
+            if (d[5] >= 0) dA[d[5]] += dphase;
+        }
+    }
+    double n = n0 * life * (1.0 + asym) + bkg;
+    if (dcol) {
+        for (int c = 0; c < L->map_width; ++c) dcol[c] = n0 * life * dA[c];
+        dcol[0] += life * (1.0 + asym);
+        dcol[1] += 1.0;
+    }
+    return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-bin objective terms (Eq. 3 and Eq. 4)                                 */
+/* ------------------------------------------------------------------------ */
+static double chi2_term(double d, double n) {
+    double var = d > 1.0 ? d : 1.0;
+    double r = d - n;
+    return r * r / var;
+}
+
+/* returns 0 on success, ORC_EDOMAIN when the Poisson mean is invalid */
+static int deviance_term(double d, double n, double* out) {
+    if (n < 0.0 || (n == 0.0 && d > 0.0) || !(n == n)) return ORC_EDOMAIN;
+    if (d == 0.0) {
+        *out = 2.0 * n;
+        return 0;
+    }
+    *out = 2.0 * ((n - d) + d * log(d / n));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public entry points                                                       */
+/* ------------------------------------------------------------------------ */
+#define LAYOUT_ARGS                                                                         \
+    int n_hist, const int64_t *n_bins, double t0, double dt, double tau, double gamma,     \
+        int n_params, int map_width, const int32_t *map, int n_comp, const int32_t *comp
+#define MAKE_LAYOUT                                                                          \
+    orc_layout L = {n_hist, n_bins, t0, dt, tau, gamma, n_params, map_width, map, n_comp, comp}
+
+int orc_model(LAYOUT_ARGS, const double* theta, double* out) {
+    MAKE_LAYOUT;
+    int st = check_layout(&L);
+    if (st) return st;
+    if (L.map_width > 64) return ORC_EINVAL;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < L.n_hist; ++k) {
+        int64_t off = hist_offset(&L, k);
+        for (int64_t i = 0; i < L.n_bins[k]; ++i)
+            out[off + i] = theory_bin(&L, theta, k, L.t0 + (double)i * L.dt, NULL);
+    }
+    return ORC_OK;
+}
+
+static int objective_impl(const orc_layout* L, const double* data, const double* theta, int obj,
+                          double* value) {
+    int status = ORC_OK;
+    double* hsum = (double*)calloc((size_t)(L->n_hist > 0 ? L->n_hist : 1), sizeof(double));
+    int* hst = (int*)calloc((size_t)(L->n_hist > 0 ? L->n_hist : 1), sizeof(int));
+    if (!hsum || !hst) {
+        free(hsum);
+        free(hst);
+        return ORC_ENOMEM;
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < L->n_hist; ++k) {
+        int64_t off = hist_offset(L, k);
+        orc_acc a = {0.0, 0.0};
+        for (int64_t i = 0; i < L->n_bins[k]; ++i) {
+            double n = theory_bin(L, theta, k, L->t0 + (double)i * L->dt, NULL);
+            double d = data[off + i];
+            if (obj == ORC_CHI2) {
+                acc_add(&a, chi2_term(d, n));
+            } else {
+                double term;
+                if (deviance_term(d, n, &term)) {
+                    hst[k] = ORC_EDOMAIN;
+                    break;
+                }
+                acc_add(&a, term);
+            }
+        }
+        hsum[k] = acc_val(&a);
+    }
+    orc_acc tot = {0.0, 0.0};
+    for (int k = 0; k < L->n_hist; ++k) {
+        if (hst[k]) status = hst[k];
+        acc_add(&tot, hsum[k]);
+    }
+    free(hsum);
+    free(hst);
+    *value = status ? INFINITY : acc_val(&tot);
+    return status;
+}
+
+int orc_objective(LAYOUT_ARGS, const double* data, const double* theta, int obj, double* value) {
+    MAKE_LAYOUT;
+    int st = check_layout(&L);
+    if (st) return st;
+    if (L.map_width > 64 || (obj != ORC_CHI2 && obj != ORC_POISSON)) return ORC_EINVAL;
+    for (int j = 0; j < L.n_params; ++j)
+        if (!isfinite(theta[j])) return ORC_ENONFINITE;
+    return objective_impl(&L, data, theta, obj, value);
+}
+
+/*
+ * Analytic gradient and Gauss-Newton matrix over the full parameter vector.
+ * grad: n_params, gn: n_params x n_params row-major (either may be NULL).
+ */
+static int gradient_impl(const orc_layout* L, const double* data, const double* theta, int obj,
+                         double* value, double* grad, double* gn) {
+    int P = L->n_params, W = L->map_width, K = L->n_hist;
+    int status = ORC_OK;
+    size_t per = 1 + (size_t)P + (gn ? (size_t)P * P : 0);
+    /* per-histogram compensated accumulators: value, grad[P], gn[P*P] */
+    orc_acc* acc = (orc_acc*)calloc((size_t)(K > 0 ? K : 1) * per, sizeof(orc_acc));
+    int* hst = (int*)calloc((size_t)(K > 0 ? K : 1), sizeof(int));
+    if (!acc || !hst) {
+        free(acc);
+        free(hst);
+        return ORC_ENOMEM;
+    }
+#pragma omp parallel for schedule(dynamic)
+    for (int k = 0; k < K; ++k) {
+        orc_acc* a = acc + (size_t)k * per;
+        int64_t off = hist_offset(L, k);
+        double dcol[64];
+        int idx[64];
+        for (int c = 0; c < W; ++c) idx[c] = map_index(L, k, c);
+        for (int64_t i = 0; i < L->n_bins[k]; ++i) {
+            double t = L->t0 + (double)i * L->dt;
+            double n = theory_bin(L, theta, k, t, dcol);
+            double d = data[off + i];
+            double term, wg, wh;
+            if (obj == ORC_CHI2) {
+                double var = d > 1.0 ? d : 1.0;
+                term = (d - n) * (d - n) / var;
+                wg = -2.0 * (d - n) / var; /* d term / d N */
+                wh = 2.0 / var;
+            } else {
+                if (deviance_term(d, n, &term)) {
+                    hst[k] = ORC_EDOMAIN;
+                    break;
+                }
+                wg = 2.0 * (1.0 - d / n); /* d/dN of 2[(N-d) + d ln(d/N)] */
+                wh = 2.0 / n;
+            }
+            acc_add(&a[0], term);
+            /* chain rule through the map: dN/dtheta_j = sum over columns mapped to j */
+            for (int c = 0; c < W; ++c) {
+                if (idx[c] < 0) continue;
+                if (grad) acc_add(&a[1 + idx[c]], wg * dcol[c]);
+            }
+            if (gn) {
+                for (int c1 = 0; c1 < W; ++c1) {
+                    if (idx[c1] < 0) continue;
+                    for (int c2 = 0; c2 < W; ++c2) {
+                        if (idx[c2] < 0) continue;
+                        acc_add(&a[1 + P + (size_t)idx[c1] * P + idx[c2]], wh * dcol[c1] * dcol[c2]);
+                    }
+                }
+            }
+        }
+    }
+    orc_acc tot = {0.0, 0.0};
+    for (int k = 0; k < K; ++k) {
+        if (hst[k]) status = hst[k];
+        acc_add(&tot, acc_val(&acc[(size_t)k * per]));
+    }
+    if (value) *value = status ? INFINITY : acc_val(&tot);
+    if (grad) {
+        for (int j = 0; j < P; ++j) {
+            orc_acc s = {0.0, 0.0};
+            for (int k = 0; k < K; ++k) acc_add(&s, acc_val(&acc[(size_t)k * per + 1 + j]));
+            grad[j] = acc_val(&s);
+        }
+    }
+    if (gn) {
+        for (size_t e = 0; e < (size_t)P * P; ++e) {
+            orc_acc s = {0.0, 0.0};
+            for (int k = 0; k < K; ++k) acc_add(&s, acc_val(&acc[(size_t)k * per + 1 + P + e]));
+            gn[e] = acc_val(&s);
+        }
+    }
+    free(acc);
+    free(hst);
+    return status;
+}
+
+int orc_gradient(LAYOUT_ARGS, const double* data, const double* theta, int obj, double* value,
+                 double* grad, double* gn) {
+    MAKE_LAYOUT;
+    int st = check_layout(&L);
+    if (st) return st;
+    if (L.map_width > 32 || (obj != ORC_CHI2 && obj != ORC_POISSON)) return ORC_EINVAL;
+    for (int j = 0; j < L.n_params; ++j)
+        if (!isfinite(theta[j])) return ORC_ENONFINITE;
+    return gradient_impl(&L, data, theta, obj, value, grad, gn);
+}
+
+/* FP64 central finite differences, h_j = rel_h * max(|theta_j|, 1). */
+int orc_gradient_fd(LAYOUT_ARGS, const double* data, const double* theta, int obj, double rel_h,
+                    double* grad) {
+    MAKE_LAYOUT;
+    int st = check_layout(&L);
+    if (st) return st;
+    if (L.map_width > 64) return ORC_EINVAL;
+    double* th = (double*)malloc(sizeof(double) * (size_t)(L.n_params > 0 ? L.n_params : 1));
+    if (!th) return ORC_ENOMEM;
+    memcpy(th, theta, sizeof(double) * (size_t)L.n_params);
+    for (int j = 0; j < L.n_params; ++j) {
+        double h = rel_h * (fabs(theta[j]) > 1.0 ? fabs(theta[j]) : 1.0);
+        double fp, fm;
+        th[j] = theta[j] + h;
+        st = objective_impl(&L, data, th, obj, &fp);
+        if (st) break;
+        th[j] = theta[j] - h;
+        st = objective_impl(&L, data, th, obj, &fm);
+        if (st) break;
+        th[j] = theta[j];
+        grad[j] = (fp - fm) / (2.0 * h);
+    }
+    free(th);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Levenberg-Marquardt fit                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Cholesky solve of the n x n SPD system A x = b (A row-major, overwritten). */
+static int cholesky_solve(double* A, double* b, int n) {
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0)) return -1;
+        double ljj = sqrt(s);
+        A[j * n + j] = ljj;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[i * n + j];
+            for (int k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = v / ljj;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= A[i * n + k] * b[k];
+        b[i] = v / A[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double v = b[i];
+        for (int k = i + 1; k < n; ++k) v -= A[k * n + i] * b[k];
+        b[i] = v / A[i * n + i];
+    }
+    return 0;
+}
+
+/*
+ * stats (out, 8 doubles): [0] objective at the minimum, [1] ndf = bins - free,
+ * [2] iterations, [3] objective evaluations, [4] EDM, [5] final damping,
+ * [6] status, [7] 0.
+ * cov (out, n_free x n_free or NULL): 2 H^-1 over the free parameters.
+ */
+int orc_fit(LAYOUT_ARGS, const double* data, int obj, double* theta, const uint8_t* free_mask,
+            int max_iter, double edm_tol, double* stats, double* cov) {
+    MAKE_LAYOUT;
+    int st = check_layout(&L);
+    if (st) return st;
+    int P = L.n_params;
+    int nf = 0;
+    int fidx[512];
+    for (int j = 0; j < P; ++j)
+        if (free_mask[j]) {
+            if (nf >= 512) return ORC_EINVAL;
+            fidx[nf++] = j;
+        }
+    double* g = (double*)malloc(sizeof(double) * (size_t)P);
+    double* H = (double*)malloc(sizeof(double) * (size_t)P * P);
+    double* A = (double*)malloc(sizeof(double) * (size_t)nf * nf + 8);
+    double* b = (double*)malloc(sizeof(double) * (size_t)nf + 8);
+    double* trial = (double*)malloc(sizeof(double) * (size_t)P);
+    if (!g || !H || !A || !b || !trial) {
+        free(g); free(H); free(A); free(b); free(trial);
+        return ORC_ENOMEM;
+    }
+    double f;
+    int evals = 0, it = 0;
+    double mu = 1e-3, edm = INFINITY;
+    st = gradient_impl(&L, data, theta, obj, &f, g, H);
+    ++evals;
+    int result = ORC_ENOCONV;
+    if (st) result = st;
+    while (!st && it < max_iter) {
+        ++it;
+        /* EDM = 1/2 g^T H^-1 g over the free block */
+        for (int a = 0; a < nf; ++a) {
+            b[a] = -g[fidx[a]];
+            for (int c = 0; c < nf; ++c) A[a * nf + c] = H[fidx[a] * P + fidx[c]];
+        }
+        if (cholesky_solve(A, b, nf) == 0) {
+            double e = 0.0;
+            for (int a = 0; a < nf; ++a) e -= 0.5 * g[fidx[a]] * b[a];
+            edm = e;
+            if (edm < edm_tol) {
+                result = ORC_OK;
+                break;
+            }
+        }
+        /* damped step */
+        for (int a = 0; a < nf; ++a) {
+            b[a] = -g[fidx[a]];
+            for (int c = 0; c < nf; ++c) A[a * nf + c] = H[fidx[a] * P + fidx[c]];
+            A[a * nf + a] *= (1.0 + mu);
+        }
+        if (cholesky_solve(A, b, nf) != 0) {
+            mu *= 10.0;
+            if (mu > 1e20) break;
+            continue;
+        }
+        memcpy(trial, theta, sizeof(double) * (size_t)P);
+        for (int a = 0; a < nf; ++a) trial[fidx[a]] += b[a];
+        double ft;
+        int s2 = objective_impl(&L, data, trial, obj, &ft);
+        ++evals;
+        if (s2 == ORC_OK && ft < f) {
+            double rel = (f - ft) / (fabs(f) > 1e-300 ? fabs(f) : 1e-300);
+            memcpy(theta, trial, sizeof(double) * (size_t)P);
+            st = gradient_impl(&L, data, theta, obj, &f, g, H);
+            ++evals;
+            mu = mu * 0.1 > 1e-12 ? mu * 0.1 : 1e-12;
+            if (rel < 1e-15) {
+                result = ORC_OK;
+                break;
+            }
+        } else {
+            mu *= 10.0;
+            if (mu > 1e20) break;
+        }
+    }
+    if (st) result = st;
+    int64_t nb = total_bins(&L);
+    stats[0] = f;
+    stats[1] = (double)(nb - nf);
+    stats[2] = it;
+    stats[3] = evals;
+    stats[4] = edm;
+    stats[5] = mu;
+    stats[6] = result;
+    stats[7] = 0.0;
+    if (cov && !st) {
+        /* 2 H^-1 column by column */
+        for (int c = 0; c < nf; ++c) {
+            for (int a = 0; a < nf; ++a) {
+                for (int e = 0; e < nf; ++e) A[a * nf + e] = H[fidx[a] * P + fidx[e]];
+                b[a] = (a == c) ? 2.0 : 0.0;
+            }
+            if (cholesky_solve(A, b, nf) != 0) {
+                for (int a = 0; a < nf; ++a) cov[a * nf + c] = NAN;
+            } else {
+                for (int a = 0; a < nf; ++a) cov[a * nf + c] = b[a];
+            }
+        }
+    }
+    free(g); free(H); free(A); free(b); free(trial);
+    return result;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
