@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark: chi2 + gradient bin-evaluations per second on one GB300.
+
+Workload: 16 detector histograms x 65536 bins of 0.1953125 ns (12.8 us),
+theory = exponentially damped line + Gaussian-damped line (B1 + dB) + static
+Gaussian Kubo-Toyabe, 56 parameters (40 free), Poisson counts.  One step is
+one evaluation of chi2 and its gradient over every bin (objective kernel in
+adjoint mode), for a fresh parameter vector; L2 is flushed (256 MB write)
+between steps, outside the timed events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank runs an independent replica (the path has no
+exchange step); value = all ranks' bin-evaluations / max-over-ranks time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "chi2+grad bin-evals/s"
+UNIT = "bin-evals/s"
+WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi2 + gradient"
+
+# FP32-pipe FLOPs per bin of the adjoint (value + gradient) kernel for this
+# signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe), counted from
+# the kernel's per-bin arithmetic (FMA = 2 FLOPs); derivation in the design doc.
+FLOPS_PER_BIN_GRAD = 150
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+
+
+def fp32_peak_tflops(mhz=SM_MAX_MHZ):
+    return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed setup (replicas only)
+# --------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        if torch.cuda.is_available():
+            torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on a bounded sample
+# --------------------------------------------------------------------------
+SAMPLE_BINS = 8192  # leading bins of each of the 16 histograms
+
+
+def cpu_sample(lay, data):
+    offs = np.r_[0, np.cumsum(lay.n_bins)]
+    sub = W.multi_detector_layout(lay.n_hist, SAMPLE_BINS, window_us=lay.dt_us * SAMPLE_BINS)
+    sub.dt_us = lay.dt_us
+    d = np.concatenate([data[offs[k]:offs[k] + SAMPLE_BINS] for k in range(lay.n_hist)])
+    return sub, d
+
+
+def cpu_baseline(lay, data, thetas, seconds=12.0):
+    import oracle
+    sub, d = cpu_sample(lay, data)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.gradient(sub, d, thetas[n % len(thetas)], oracle.CHI2, with_gn=False)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and n >= 3:
+            break
+    return {"value": sub.total_bins * n / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{sub.n_hist} hist x {SAMPLE_BINS} leading bins of the workload, "
+                      f"{n} chi2+gradient evaluations in {el:.1f} s"}
+
+
+# --------------------------------------------------------------------------
+def make_workload():
+    lay, theta, seed = W.config_multi_detector()
+    return lay, theta, seed
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    lay, theta, seed = make_workload()
+    # Poisson data drawn from the oracle's own model (reference arm only)
+    data = W.poisson_counts(oracle.model(lay, theta), seed)
+    sub, d = cpu_sample(lay, data)
+    g = W.rng(seed + 11)
+    thetas = [W.perturb(theta, lay.free, 0.01, g) for _ in range(args.steps + args.warmup)]
+    for i in range(args.warmup):
+        oracle.gradient(sub, d, thetas[i], oracle.CHI2, with_gn=False)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        oracle.gradient(sub, d, thetas[args.warmup + i], oracle.CHI2, with_gn=False)
+    el = time.perf_counter() - t0
+    value = sub.total_bins * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "sample_bins_per_step": sub.total_bins},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{sub.n_hist} hist x {SAMPLE_BINS} leading bins per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    from paper_1604_02334_gb300 import MUSR_CHI2, MUSR_VALUE_GRAD, Run
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    lay, theta, seed = make_workload()
+    P = lay.n_params
+    # synthetic Poisson counts: mean from the library's model kernel, noise from numpy PCG64
+    with Run(lay) as mrun:
+        mean = mrun.model(theta).astype(np.float64)
+    data = W.poisson_counts(mean, seed + rank)
+    data_t = torch.tensor(data, dtype=torch.float32, device=dev)
+    run = Run(lay, data_t, stream="torch")
+    g = W.rng(seed + 11 + rank)
+    n_vec = args.steps + args.warmup
+    thetas = np.stack([W.perturb(theta, lay.free, 0.01, g) for _ in range(n_vec)])
+    thetas_t = torch.tensor(thetas, dtype=torch.float64, device=dev)
+    outs = torch.empty((n_vec, 1 + P), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        run.chi2_grad_device(thetas_t[i], outs[i], MUSR_CHI2, MUSR_VALUE_GRAD)
+
+    for i in range(args.warmup):
+        flush.fill_(i & 255)
+        step(i)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for j in range(args.steps):
+        flush.fill_((j + 1) & 255)
+        starts[j].record(stream)
+        step(args.warmup + j)
+        ends[j].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_total = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = world * lay.total_bins * args.steps / t_total
+    mean_ms = 1e3 * t_total / args.steps
+
+    # end to end through the C ABI with host buffers: per step, upload the
+    # histograms from pinned memory, evaluate chi2 + gradient, read them back
+    host_data = torch.tensor(data, dtype=torch.float32).pin_memory()
+    host_np = host_data.numpy()
+    e2e_steps = max(10, min(args.steps, 100))
+    run_h = Run(lay, host_np)
+    for i in range(3):
+        run_h.set_data(host_np)
+        run_h.chi2_grad(thetas[i], MUSR_CHI2)
+    barrier(world)
+    t0 = time.perf_counter()
+    for j in range(e2e_steps):
+        run_h.set_data(host_np)
+        run_h.chi2_grad(thetas[j % n_vec], MUSR_CHI2)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world)
+    run_h.close()
+    e2e = {"value": world * lay.total_bins * e2e_steps / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": lay.total_bins * 4 + P * 8, "d2h_bytes_per_step": (1 + P) * 8 + 4,
+           "steps": e2e_steps}
+
+    # sanity: results are finite
+    assert torch.isfinite(outs[args.warmup:]).all().item()
+
+    if rank != 0:
+        run.close()
+        return
+    peak = fp32_peak_tflops()
+    achieved = FLOPS_PER_BIN_GRAD * lay.total_bins / (mean_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 accumulate",
+        "data": "synthetic (Poisson counts of the model, numpy PCG64)",
+        "config": {"workload": WORKLOAD, "bins": lay.total_bins, "params": P,
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "eval_kernel<1,1,1,kGrad>",
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(lay, data, thetas)
+    print(json.dumps(line), flush=True)
+    run.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

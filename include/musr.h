@@ -1,0 +1,223 @@
+/*
+ * musr.h -- C ABI of the GB300 muSR fit-objective library (libmusr.so).
+ *
+ * The library evaluates, on one GPU, the objective a muSR fit minimises:
+ *
+ *   theory   (Sec. 4.1, Eq. 1)  N_k(t) = N0_k exp(-t/tau_mu) [1 + A_k(t)] + Nbkg_k,
+ *                               t = t0 + n * dt for bin n of histogram k;
+ *   chi2     (Sec. 4.1, Eq. 3)  sum_k sum_n (d - N)^2 / max(d, 1);
+ *   deviance (Sec. 4.1, Eq. 4)  2 sum_k sum_n [(N - d) + d ln(d / N)]  (2N where d = 0),
+ *
+ * over every bin of every histogram, for a parameter vector theta addressed
+ * through a per-histogram map (Sec. 4.1 Eq. 2; the parameter / map arrays of
+ * Sec. 4.2.1, Listing 3).  A_k(t) is a sum of the predefined components of
+ * Sec. 4.2.1 Listing 2 and Sec. 4.3 Eq. 5:
+ *
+ *   MUSR_TF_EXP          a exp(-lambda t)        cos(2 pi gamma (B + B2) t + phi)
+ *   MUSR_TF_GAUSS        a exp(-(sigma t)^2 / 2) cos(2 pi gamma (B + B2) t + phi)
+ *   MUSR_KT_STATIC_GAUSS a [1/3 + 2/3 (1 - (D t)^2) exp(-(D t)^2 / 2)]
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns MUSR_OK (0) or a negative status; none aborts.
+ *   - Host buffers belong to the caller.  musr_create_run copies the data
+ *     once (Sec. 4.2: data sets are uploaded once and reused for the whole
+ *     fit) and keeps no caller pointer afterwards.
+ *   - Host-pointer entry points are synchronous: results are in the caller's
+ *     buffers when they return.  Entry points named *_device are
+ *     asynchronous on the stream given (NULL = the run's own stream).
+ *   - One run handle may be used by one host thread at a time, and calls on
+ *     one run must not overlap on the GPU (they share the run's scratch).
+ *   - Units: t in microseconds, fields in gauss, gamma in MHz/G, phases in
+ *     radians, rates in 1/us.
+ *   - Limits: map_width <= 32, at most 2 precession components (TF_EXP or
+ *     TF_GAUSS) and at most one KT_STATIC_GAUSS per run, at most 2^24 bins per
+ *     histogram, at most 4096 parameters.  Other layouts return MUSR_ENOTSUP.
+ */
+#ifndef MUSR_H
+#define MUSR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MUSR_GAMMA_MU_MHZ_PER_G 0.013554 /* gamma_mu / 2 pi */
+#define MUSR_TAU_MU_US 2.197             /* muon lifetime */
+
+/* status codes */
+enum {
+    MUSR_OK = 0,
+    MUSR_EINVAL = -1,     /* bad argument or layout */
+    MUSR_ENOMEM = -2,     /* device or host allocation failed */
+    MUSR_ECUDA = -3,      /* a CUDA call failed (no device, launch error ...) */
+    MUSR_ENONFINITE = -4, /* theta holds NaN or Inf, or a result is not finite */
+    MUSR_EDOMAIN = -5,    /* deviance: a bin has N < 0, or N = 0 with d > 0 */
+    MUSR_ETIMEOUT = -6,   /* a bounded device wait ran out */
+    MUSR_ENOCONV = -7,    /* the minimiser stopped without meeting its tolerance */
+    MUSR_ENOTSUP = -8     /* layout outside the supported limits */
+};
+
+/* theory component kinds */
+enum { MUSR_TF_EXP = 0, MUSR_TF_GAUSS = 1, MUSR_KT_STATIC_GAUSS = 2 };
+/* objectives */
+enum { MUSR_CHI2 = 0, MUSR_POISSON = 1 };
+/* data element types */
+enum { MUSR_F32 = 0, MUSR_F64 = 1 };
+/* evaluation modes of musr_chi2_grad_device */
+enum { MUSR_VALUE = 0, MUSR_VALUE_GRAD = 1, MUSR_VALUE_GRAD_GN = 2 };
+
+/*
+ * One theory component.  Each field is a COLUMN of the histogram's map row
+ * (not a theta index); -1 means "not used" (the quantity is 0).
+ *   amp    amplitude a
+ *   rate   lambda (TF_EXP), sigma (TF_GAUSS) or Delta (KT_STATIC_GAUSS)
+ *   field  field B of the precession (TF only)
+ *   field2 a second field added to B, e.g. a line splitting dB (TF only)
+ *   phase  phase phi in radians (TF only)
+ */
+typedef struct {
+    int32_t kind, amp, rate, field, field2, phase;
+} musr_component;
+
+/*
+ * Run description (Sec. 4.1 Eq. 1-2).
+ *   n_hist, n_bins   K histograms with n_bins[k] bins each (uneven allowed).
+ *   t0_us, dt_us     time grid t = t0 + n dt (Eq. 1 has t0 = 0).
+ *   tau_us, gamma    muon lifetime and gamma_mu / 2 pi (MUSR_* defaults).
+ *   n_params         length P of theta.
+ *   map_width, map   K x map_width int32 row-major; map[k][c] is an index
+ *                    into theta or -1 (constant 0).  Column 0 is N0 and
+ *                    column 1 is Nbkg of histogram k.
+ *   n_comp, comp     the components of A_k(t); the same list for every
+ *                    histogram, each histogram reading its own map row.
+ *   data_dtype, data counts d, histogram-major, concatenated (sum n_bins
+ *                    values), MUSR_F32 or MUSR_F64.  The device keeps FP32
+ *                    (counts are exact in FP32 below 2^24).  May be NULL for
+ *                    a run used only to evaluate the model.
+ *   data_on_device   nonzero if data is a device pointer (copied D2D).
+ *   stream           cudaStream_t the run works on; NULL = the library
+ *                    creates one for the run.
+ */
+typedef struct {
+    int32_t n_hist;
+    const int64_t* n_bins;
+    double t0_us, dt_us, tau_us, gamma_mhz_per_g;
+    int32_t n_params, map_width;
+    const int32_t* map;
+    int32_t n_comp;
+    const musr_component* comp;
+    int32_t data_dtype;
+    const void* data;
+    int32_t data_on_device;
+    void* stream;
+} musr_run_desc;
+
+typedef struct musr_run_s* musr_run;
+
+/* Create a run: validates the layout, uploads the data once (Sec. 4.2) and
+ * allocates the run's device scratch.  *out receives the handle. */
+int musr_create_run(const musr_run_desc* desc, musr_run* out);
+
+/* Release a run and everything it owns.  NULL is allowed. */
+int musr_destroy_run(musr_run run);
+
+/* Number of parameters P / total bins of a run (for marshalling). */
+int musr_run_info(musr_run run, int32_t* n_params, int64_t* total_bins, int32_t* n_hist);
+
+/* Replace the run's data (same layout) without re-planning.  Host or device
+ * pointer as in the description; FP32 or FP64. */
+int musr_set_data(musr_run run, int32_t data_dtype, const void* data, int32_t data_on_device);
+
+/* Objective value (Eq. 3 if obj == MUSR_CHI2, Eq. 4 if MUSR_POISSON) at the
+ * host FP64 vector theta[P].  Synchronous.  MUSR_EDOMAIN for an invalid
+ * Poisson mean (value set to +inf), MUSR_ENONFINITE for non-finite theta. */
+int musr_chi2(musr_run run, int obj, const double* theta, double* value);
+
+/* Value, gradient d obj / d theta (grad[P], may be NULL) and Gauss-Newton
+ * matrix gn[P*P] row-major (may be NULL), computed in one adjoint pass.
+ * GN weights: 2 / max(d, 1) for chi2, 2 / N (Fisher scoring) for the
+ * deviance.  Synchronous, host buffers. */
+int musr_chi2_grad(musr_run run, int obj, const double* theta, double* value, double* grad,
+                   double* gn);
+
+/* Device variant: theta_dev[P] FP64 on the device; out_dev receives
+ * [value, grad[P] (mode >= 1), gn[P*P] (mode == 2)] FP64; status_dev (may be
+ * NULL) receives an int32 bit set: 1 = deviance domain error, 2 = non-finite
+ * value.  Asynchronous on stream (NULL = run stream). */
+int musr_chi2_grad_device(musr_run run, int obj, int mode, const double* theta_dev,
+                          double* out_dev, int32_t* status_dev, void* stream);
+
+/* Model N for every bin (FP32, histogram-major, total_bins values) into a
+ * host (out_on_device == 0) or device buffer. */
+int musr_model(musr_run run, const double* theta, float* out, int32_t out_on_device);
+
+/*
+ * Batched evaluation (many runs x many parameter vectors in one persistent
+ * launch under a CUDA graph).  runs[r] has n_vec[r] parameter vectors of its
+ * own length P_r, stored consecutively in thetas (run 0's vectors first);
+ * values receives sum n_vec values in the same order.  The one-shot form
+ * plans, evaluates and frees; musr_batch_* keep the plan for repeated use.
+ */
+int musr_chi2_batch(const musr_run* runs, int32_t n_runs, int obj, const double* thetas,
+                    const int32_t* n_vec, double* values);
+
+typedef struct musr_batch_s* musr_batch;
+/* Plan a batch over runs[n_runs] with at most max_vec[r] vectors per run.
+ * The runs must outlive the plan. */
+int musr_batch_create(const musr_run* runs, int32_t n_runs, const int32_t* max_vec,
+                      musr_batch* out);
+int musr_batch_destroy(musr_batch batch);
+/* Host-pointer evaluation with a plan (synchronous). */
+int musr_batch_eval(musr_batch batch, int obj, const double* thetas, const int32_t* n_vec,
+                    double* values);
+/* Device-pointer evaluation with a plan: thetas_dev as above, on the device,
+ * with every run's vector count fixed at its max_vec; values_dev FP64 on the
+ * device.  Asynchronous on the plan's stream. */
+int musr_batch_eval_device(musr_batch batch, int obj, const double* thetas_dev,
+                           double* values_dev);
+
+/* Fit options and result (the host minimiser that replaces Minuit2's role,
+ * Sec. 4.1). */
+enum {
+    MUSR_FIT_LM = 0,      /* Levenberg-Marquardt on the adjoint GN matrix */
+    MUSR_FIT_BFGS = 1,    /* quasi-Newton (BFGS) on the adjoint gradient */
+    MUSR_FIT_BFGS_FD = 2  /* BFGS on central differences from the batched kernel */
+};
+typedef struct {
+    int32_t method;   /* MUSR_FIT_* */
+    int32_t max_iter; /* <= 0: 500 */
+    double edm_tol;   /* <= 0: 1e-8; stop when 1/2 g^T H^-1 g < edm_tol */
+    double mu0;       /* <= 0: 1e-3; initial LM damping */
+    double fd_rel_h;  /* <= 0: 1e-6; relative step of MUSR_FIT_BFGS_FD */
+} musr_fit_opts;
+
+typedef struct {
+    double value;   /* objective at the returned theta */
+    double ndf;     /* total bins - free parameters */
+    double edm;     /* estimated distance to the minimum at exit */
+    double mu;      /* final LM damping */
+    int32_t iters;  /* minimiser iterations */
+    int32_t n_evals;/* objective / adjoint launches */
+    int32_t status; /* MUSR_OK or MUSR_ENOCONV / another error */
+    int32_t n_free;
+    double* cov;    /* caller buffer n_free x n_free (2 H^-1) or NULL */
+} musr_fit_result;
+
+/* Minimise obj over the parameters with free_mask[j] != 0 (NULL = all),
+ * starting from theta_inout, which receives the result.  opts may be NULL
+ * (defaults).  The return value equals out->status. */
+int musr_fit(musr_run run, int obj, double* theta_inout, const uint8_t* free_mask,
+             const musr_fit_opts* opts, musr_fit_result* out);
+
+/* Message for a status code (static string). */
+const char* musr_strerror(int code);
+
+/* Library version string. */
+const char* musr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MUSR_H */

@@ -1,0 +1,149 @@
+"""ctypes binding of libmusr.so: the C ABI of include/musr.h, same names.
+
+Argument marshalling only: every step of the evaluation runs in the
+library's CUDA kernels.  Importing this module fails loudly if libmusr.so
+has not been built (``python -m paper_1604_02334_gb300.build``); there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmusr.so")
+
+MUSR_OK = 0
+MUSR_EINVAL = -1
+MUSR_ENOMEM = -2
+MUSR_ECUDA = -3
+MUSR_ENONFINITE = -4
+MUSR_EDOMAIN = -5
+MUSR_ETIMEOUT = -6
+MUSR_ENOCONV = -7
+MUSR_ENOTSUP = -8
+
+MUSR_TF_EXP, MUSR_TF_GAUSS, MUSR_KT_STATIC_GAUSS = 0, 1, 2
+MUSR_CHI2, MUSR_POISSON = 0, 1
+MUSR_F32, MUSR_F64 = 0, 1
+MUSR_VALUE, MUSR_VALUE_GRAD, MUSR_VALUE_GRAD_GN = 0, 1, 2
+MUSR_FIT_LM, MUSR_FIT_BFGS, MUSR_FIT_BFGS_FD = 0, 1, 2
+MUSR_GAMMA_MU_MHZ_PER_G = 0.013554
+MUSR_TAU_MU_US = 2.197
+
+
+class musr_component(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("kind", "amp", "rate", "field", "field2", "phase")]
+
+
+class musr_run_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_hist", ctypes.c_int32),
+        ("n_bins", ctypes.POINTER(ctypes.c_int64)),
+        ("t0_us", ctypes.c_double),
+        ("dt_us", ctypes.c_double),
+        ("tau_us", ctypes.c_double),
+        ("gamma_mhz_per_g", ctypes.c_double),
+        ("n_params", ctypes.c_int32),
+        ("map_width", ctypes.c_int32),
+        ("map", ctypes.POINTER(ctypes.c_int32)),
+        ("n_comp", ctypes.c_int32),
+        ("comp", ctypes.POINTER(musr_component)),
+        ("data_dtype", ctypes.c_int32),
+        ("data", ctypes.c_void_p),
+        ("data_on_device", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class musr_fit_opts(ctypes.Structure):
+    _fields_ = [
+        ("method", ctypes.c_int32),
+        ("max_iter", ctypes.c_int32),
+        ("edm_tol", ctypes.c_double),
+        ("mu0", ctypes.c_double),
+        ("fd_rel_h", ctypes.c_double),
+    ]
+
+
+class musr_fit_result(ctypes.Structure):
+    _fields_ = [
+        ("value", ctypes.c_double),
+        ("ndf", ctypes.c_double),
+        ("edm", ctypes.c_double),
+        ("mu", ctypes.c_double),
+        ("iters", ctypes.c_int32),
+        ("n_evals", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("n_free", ctypes.c_int32),
+        ("cov", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_vp = ctypes.c_void_p
+_run = ctypes.c_void_p
+
+# name -> (restype, argtypes); the complete list of symbols include/musr.h declares
+SIGNATURES = {
+    "musr_create_run": (ctypes.c_int, [ctypes.POINTER(musr_run_desc), ctypes.POINTER(_run)]),
+    "musr_destroy_run": (ctypes.c_int, [_run]),
+    "musr_run_info": (ctypes.c_int, [_run, _i32p, ctypes.POINTER(ctypes.c_int64), _i32p]),
+    "musr_set_data": (ctypes.c_int, [_run, ctypes.c_int32, _vp, ctypes.c_int32]),
+    "musr_chi2": (ctypes.c_int, [_run, ctypes.c_int, _dp, _dp]),
+    "musr_chi2_grad": (ctypes.c_int, [_run, ctypes.c_int, _dp, _dp, _dp, _dp]),
+    "musr_chi2_grad_device": (ctypes.c_int, [_run, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "musr_model": (ctypes.c_int, [_run, _dp, _vp, ctypes.c_int32]),
+    "musr_chi2_batch": (ctypes.c_int, [ctypes.POINTER(_run), ctypes.c_int32, ctypes.c_int, _dp,
+                                       _i32p, _dp]),
+    "musr_batch_create": (ctypes.c_int, [ctypes.POINTER(_run), ctypes.c_int32, _i32p,
+                                         ctypes.POINTER(_vp)]),
+    "musr_batch_destroy": (ctypes.c_int, [_vp]),
+    "musr_batch_eval": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _i32p, _dp]),
+    "musr_batch_eval_device": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "musr_fit": (ctypes.c_int, [_run, ctypes.c_int, _dp, _u8p, ctypes.POINTER(musr_fit_opts),
+                                ctypes.POINTER(musr_fit_result)]),
+    "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "musr_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libmusr.so and declare every entry point (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_1604_02334_gb300.build` "
+                "(the library has no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class MusrError(RuntimeError):
+    def __init__(self, code: int, where: str = ""):
+        msg = load().musr_strerror(code).decode()
+        super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
+        self.code = code
+
+
+def check(code: int, where: str = "") -> int:
+    if code != MUSR_OK:
+        raise MusrError(code, where)
+    return code
+
+
+def __getattr__(name):
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(name)

@@ -1,0 +1,274 @@
+// Host minimiser driving the GPU objective (the role Minuit2 plays in the
+// paper, Sec. 4.1): Levenberg-Marquardt on the Gauss-Newton matrix that the
+// adjoint kernel returns, or BFGS on the adjoint (or central-difference)
+// gradient.  All linear algebra is FP64 on the host; each iteration costs one
+// kernel launch (value + gradient + GN at the trial point) and one small copy
+// back.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "musr.h"
+#include "musr_internal.h"
+#include "run_impl.h"
+
+namespace musr {
+int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
+                      double rel_h, double* value, double* grad);
+}
+
+using namespace musr;
+
+namespace {
+
+// Cholesky solve of the n x n SPD system A x = b (A overwritten).
+bool cholesky_solve(std::vector<double>& A, std::vector<double>& b, int n) {
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0)) return false;
+        const double l = sqrt(s);
+        A[j * n + j] = l;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[i * n + j];
+            for (int k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = v / l;
+        }
+    }
+    for (int i = 0; i < n; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= A[i * n + k] * b[k];
+        b[i] = v / A[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double v = b[i];
+        for (int k = i + 1; k < n; ++k) v -= A[k * n + i] * b[k];
+        b[i] = v / A[i * n + i];
+    }
+    return true;
+}
+
+struct Evaluator {
+    musr_run run;
+    int obj;
+    int P;
+    std::vector<double> buf;
+    int evals = 0;
+    // value (+grad, +GN) at theta; returns MUSR_OK, MUSR_EDOMAIN (value = inf) or an error
+    int operator()(const double* theta, int mode, double* value, double* grad, double* gn) {
+        buf.resize((size_t)run->n_out[mode] + 1);
+        int32_t flags = 0;
+        ++evals;
+        int st = run->eval_host(obj, mode, theta, buf.data(), &flags);
+        if (st != MUSR_OK) return st;
+        *value = (flags & 1) ? INFINITY : buf[0];
+        if (grad && mode >= kGrad) memcpy(grad, buf.data() + 1, sizeof(double) * P);
+        if (gn && mode == kGN) memcpy(gn, buf.data() + 1 + P, sizeof(double) * P * P);
+        if (flags & 1) return MUSR_EDOMAIN;
+        return isfinite(*value) ? MUSR_OK : MUSR_ENONFINITE;
+    }
+};
+
+int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
+           musr_fit_result* out) {
+    const int P = ev.P, nf = (int)fidx.size();
+    std::vector<double> g(P), H((size_t)P * P), gt(P), Ht((size_t)P * P), trial(P);
+    std::vector<double> A((size_t)nf * nf), b(nf);
+    double f;
+    int st = ev(theta, kGN, &f, g.data(), H.data());
+    if (st != MUSR_OK) return st;
+    double mu = o.mu0, edm = INFINITY;
+    int it = 0, result = MUSR_ENOCONV;
+    while (it < o.max_iter) {
+        ++it;
+        for (int a = 0; a < nf; ++a) {
+            b[a] = -g[fidx[a]];
+            for (int c = 0; c < nf; ++c) A[(size_t)a * nf + c] = H[(size_t)fidx[a] * P + fidx[c]];
+        }
+        if (cholesky_solve(A, b, nf)) {
+            double e = 0.0;
+            for (int a = 0; a < nf; ++a) e -= 0.5 * g[fidx[a]] * b[a];
+            edm = e;
+            if (edm < o.edm_tol) {
+                result = MUSR_OK;
+                break;
+            }
+        }
+        for (int a = 0; a < nf; ++a) {
+            b[a] = -g[fidx[a]];
+            for (int c = 0; c < nf; ++c) A[(size_t)a * nf + c] = H[(size_t)fidx[a] * P + fidx[c]];
+            A[(size_t)a * nf + a] *= (1.0 + mu);
+        }
+        if (!cholesky_solve(A, b, nf)) {
+            mu *= 10.0;
+            if (mu > 1e20) break;
+            continue;
+        }
+        memcpy(trial.data(), theta, sizeof(double) * P);
+        for (int a = 0; a < nf; ++a) trial[fidx[a]] += b[a];
+        double ft;
+        const int s2 = ev(trial.data(), kGN, &ft, gt.data(), Ht.data());
+        if (s2 != MUSR_OK && s2 != MUSR_EDOMAIN && s2 != MUSR_ENONFINITE) return s2;
+        if (s2 == MUSR_OK && ft < f) {
+            const double rel = (f - ft) / std::max(fabs(f), 1e-300);
+            memcpy(theta, trial.data(), sizeof(double) * P);
+            f = ft;
+            g.swap(gt);
+            H.swap(Ht);
+            mu = std::max(mu * 0.1, 1e-12);
+            if (rel < 1e-15) {
+                result = MUSR_OK;
+                break;
+            }
+        } else {
+            mu *= 10.0;
+            if (mu > 1e20) break;
+        }
+    }
+    out->value = f;
+    out->edm = edm;
+    out->mu = mu;
+    out->iters = it;
+    if (out->cov) {
+        for (int c = 0; c < nf; ++c) {
+            for (int a = 0; a < nf; ++a) {
+                for (int e = 0; e < nf; ++e) A[(size_t)a * nf + e] = H[(size_t)fidx[a] * P + fidx[e]];
+                b[a] = a == c ? 2.0 : 0.0;
+            }
+            const bool ok = cholesky_solve(A, b, nf);
+            for (int a = 0; a < nf; ++a) out->cov[(size_t)a * nf + c] = ok ? b[a] : NAN;
+        }
+    }
+    return result;
+}
+
+// BFGS on the inverse Hessian with a backtracking (Armijo) line search.
+// fd_h > 0: gradient by central differences from the batched kernel.
+int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
+             double fd_h, musr_fit_result* out) {
+    const int P = ev.P, nf = (int)fidx.size();
+    std::vector<double> g(P), gn_(P), x(P), Hi((size_t)nf * nf, 0.0), d(nf), s(nf), y(nf);
+    auto value_grad = [&](const double* th, double* f, double* gr) -> int {
+        if (fd_h > 0.0) {
+            ++ev.evals;
+            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr);
+        }
+        return ev(th, kGrad, f, gr, nullptr);
+    };
+    double f;
+    int st = value_grad(theta, &f, g.data());
+    if (st != MUSR_OK) return st;
+    // initial inverse Hessian: diagonal scaled by the gradient magnitude
+    double gnorm = 0.0;
+    for (int a = 0; a < nf; ++a) gnorm += g[fidx[a]] * g[fidx[a]];
+    gnorm = sqrt(gnorm);
+    for (int a = 0; a < nf; ++a) Hi[(size_t)a * nf + a] = 1.0 / std::max(gnorm, 1.0);
+    int it = 0, result = MUSR_ENOCONV;
+    double edm = INFINITY;
+    while (it < o.max_iter) {
+        ++it;
+        for (int a = 0; a < nf; ++a) {
+            double v = 0.0;
+            for (int c = 0; c < nf; ++c) v -= Hi[(size_t)a * nf + c] * g[fidx[c]];
+            d[a] = v;
+        }
+        double slope = 0.0;
+        for (int a = 0; a < nf; ++a) slope += g[fidx[a]] * d[a];
+        edm = -0.5 * slope;
+        if (edm < o.edm_tol) {
+            result = MUSR_OK;
+            break;
+        }
+        if (slope >= 0.0) {  // not a descent direction: reset
+            for (int a = 0; a < nf; ++a)
+                for (int c = 0; c < nf; ++c) Hi[(size_t)a * nf + c] = a == c ? 1.0 / std::max(gnorm, 1.0) : 0.0;
+            continue;
+        }
+        double step = 1.0, fn = INFINITY;
+        bool ok = false;
+        for (int ls = 0; ls < 40; ++ls) {
+            memcpy(x.data(), theta, sizeof(double) * P);
+            for (int a = 0; a < nf; ++a) x[fidx[a]] += step * d[a];
+            st = value_grad(x.data(), &fn, gn_.data());
+            if (st != MUSR_OK && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
+            if (st == MUSR_OK && fn <= f + 1e-4 * step * slope) {
+                ok = true;
+                break;
+            }
+            step *= 0.5;
+        }
+        if (!ok) break;
+        const double rel = (f - fn) / std::max(fabs(f), 1e-300);
+        double sy = 0.0;
+        for (int a = 0; a < nf; ++a) {
+            s[a] = step * d[a];
+            y[a] = gn_[fidx[a]] - g[fidx[a]];
+            sy += s[a] * y[a];
+        }
+        memcpy(theta, x.data(), sizeof(double) * P);
+        f = fn;
+        g.swap(gn_);
+        if (sy > 1e-300) {
+            // Hi <- (I - rho s y^T) Hi (I - rho y s^T) + rho s s^T
+            const double rho = 1.0 / sy;
+            std::vector<double> Hy(nf, 0.0);
+            for (int a = 0; a < nf; ++a)
+                for (int c = 0; c < nf; ++c) Hy[a] += Hi[(size_t)a * nf + c] * y[c];
+            double yHy = 0.0;
+            for (int a = 0; a < nf; ++a) yHy += y[a] * Hy[a];
+            for (int a = 0; a < nf; ++a)
+                for (int c = 0; c < nf; ++c)
+                    Hi[(size_t)a * nf + c] += (1.0 + rho * yHy) * rho * s[a] * s[c] -
+                                              rho * (Hy[a] * s[c] + s[a] * Hy[c]);
+        }
+        if (rel < 1e-15 && it > 1) {
+            result = MUSR_OK;
+            break;
+        }
+    }
+    out->value = f;
+    out->edm = edm;
+    out->mu = 0.0;
+    out->iters = it;
+    if (out->cov)
+        for (size_t e = 0; e < (size_t)nf * nf; ++e) out->cov[e] = 2.0 * Hi[e];
+    return result;
+}
+
+}  // namespace
+
+extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* free_mask,
+                        const musr_fit_opts* opts, musr_fit_result* out) {
+    if (!run || !theta || !out) return MUSR_EINVAL;
+    if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
+    musr_fit_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.max_iter <= 0) o.max_iter = 500;
+    if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
+    if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
+    if (!(o.fd_rel_h > 0.0)) o.fd_rel_h = 1e-6;
+    if (o.method < MUSR_FIT_LM || o.method > MUSR_FIT_BFGS_FD) return MUSR_EINVAL;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != run->device) cudaSetDevice(run->device);
+    std::vector<int> fidx;
+    for (int j = 0; j < run->P; ++j)
+        if (!free_mask || free_mask[j]) fidx.push_back(j);
+    Evaluator ev{run, obj, run->P, {}, 0};
+    musr_fit_result r = *out;
+    r.n_free = (int32_t)fidx.size();
+    r.ndf = (double)(run->total_bins - (int64_t)fidx.size());
+    int method = o.method;
+    if (method == MUSR_FIT_LM && run->P > musr::kMaxGnParams) method = MUSR_FIT_BFGS;
+    int st;
+    if (method == MUSR_FIT_LM) st = fit_lm(ev, theta, fidx, o, &r);
+    else st = fit_bfgs(ev, theta, fidx, o, method == MUSR_FIT_BFGS_FD ? o.fd_rel_h : 0.0, &r);
+    r.n_evals = ev.evals;
+    r.status = st;
+    *out = r;
+    if (cur != run->device) cudaSetDevice(cur);
+    return st;
+}

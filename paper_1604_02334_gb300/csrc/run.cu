@@ -1,0 +1,627 @@
+// Run handles and the single-run entry points of the C ABI (include/musr.h).
+//
+// A run owns the device copy of its histograms (uploaded once, Sec. 4.2), its
+// tiling plan, the role -> theta table derived from the map array (Sec. 4.2.1)
+// and the scratch of the fused reduction.  Host-pointer calls replay a CUDA
+// graph (theta upload -> objective kernel -> result download) so one call
+// costs one graph launch and one synchronisation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "musr_internal.h"
+#include "run_impl.h"
+
+namespace musr {
+
+cudaError_t launch_eval_mode0(const Signature&, int, int, cudaStream_t, const EvalParams&);
+cudaError_t launch_eval_mode1(const Signature&, int, int, cudaStream_t, const EvalParams&);
+cudaError_t launch_eval_mode2(const Signature&, int, int, cudaStream_t, const EvalParams&);
+cudaError_t launch_eval_mode3(const Signature&, int, int, cudaStream_t, const EvalParams&);
+
+cudaError_t launch_eval(const Signature& s, int mode, int threads, int n_tiles, cudaStream_t st,
+                        const EvalParams& p) {
+    switch (mode) {
+        case kValue: return launch_eval_mode0(s, threads, n_tiles, st, p);
+        case kGrad: return launch_eval_mode1(s, threads, n_tiles, st, p);
+        case kGN: return launch_eval_mode2(s, threads, n_tiles, st, p);
+        case kModel: return launch_eval_mode3(s, threads, n_tiles, st, p);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Copy concatenated counts (FP32 or FP64, device) into the padded FP32 layout.
+__global__ void pack_data_kernel(const void* src, int is_f64, const int64_t* src_off,
+                                 const int64_t* dst_off, const int32_t* nbins, int K, float* dst) {
+    const int k = blockIdx.y;
+    if (k >= K) return;
+    const int M = nbins[k];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+        const int64_t s = src_off[k] + i;
+        dst[dst_off[k] + i] = is_f64 ? (float)static_cast<const double*>(src)[s]
+                                     : static_cast<const float*>(src)[s];
+    }
+}
+
+}  // namespace musr
+
+using namespace musr;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MUSR_OK;
+    if (e == cudaErrorMemoryAllocation) return MUSR_ENOMEM;
+    return MUSR_ECUDA;
+}
+
+int map_col(const musr_run_s* r, int k, int col) {
+    if (col < 0) return -1;
+    return r->map[(size_t)k * r->W + col];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// plan construction
+// ---------------------------------------------------------------------------
+int musr_run_s::plan(const musr_run_desc* d) {
+    K = d->n_hist;
+    P = d->n_params;
+    W = d->map_width;
+    t0 = d->t0_us;
+    dt = d->dt_us;
+    tau = d->tau_us;
+    gamma = d->gamma_mhz_per_g;
+    if (K < 0 || P < 0 || P > kMaxParams || W < 2 || W > 32 || d->n_comp < 0) return MUSR_EINVAL;
+    if (!(dt > 0.0) || !(tau > 0.0) || !isfinite(t0) || !isfinite(gamma)) return MUSR_EINVAL;
+    if (K > 0 && (!d->n_bins || !d->map)) return MUSR_EINVAL;
+    if (d->n_comp > 0 && !d->comp) return MUSR_EINVAL;
+    n_bins.assign(d->n_bins, d->n_bins + K);
+    map.assign(d->map, d->map + (size_t)K * W);
+    comp.assign(d->comp, d->comp + d->n_comp);
+    total_bins = 0;
+    for (int k = 0; k < K; ++k) {
+        if (n_bins[k] < 0) return MUSR_EINVAL;
+        if (n_bins[k] > (int64_t(1) << 24)) return MUSR_ENOTSUP;
+        total_bins += n_bins[k];
+        for (int c = 0; c < W; ++c) {
+            const int i = map[(size_t)k * W + c];
+            if (i < -1 || i >= P) return MUSR_EINVAL;
+        }
+    }
+    // signature: exponential lines, Gaussian lines, Kubo-Toyabe
+    std::vector<int> exp_c, gau_c;
+    int kt_c = -1;
+    for (int c = 0; c < (int)comp.size(); ++c) {
+        const musr_component& m = comp[c];
+        const int cols[5] = {m.amp, m.rate, m.field, m.field2, m.phase};
+        for (int j = 0; j < 5; ++j)
+            if (cols[j] < -1 || cols[j] >= W) return MUSR_EINVAL;
+        if (m.kind == MUSR_TF_EXP) exp_c.push_back(c);
+        else if (m.kind == MUSR_TF_GAUSS) gau_c.push_back(c);
+        else if (m.kind == MUSR_KT_STATIC_GAUSS) {
+            if (kt_c >= 0) return MUSR_ENOTSUP;
+            kt_c = c;
+        } else return MUSR_EINVAL;
+    }
+    if (exp_c.size() + gau_c.size() > (size_t)kMaxOsc) return MUSR_ENOTSUP;
+    sig.ne = (int)exp_c.size();
+    sig.ng = (int)gau_c.size();
+    sig.kt = kt_c >= 0;
+    R = sig.roles();
+    // role -> theta table
+    role_theta.assign((size_t)K * kMaxRoles * 2, -1);
+    std::vector<int> osc = exp_c;
+    osc.insert(osc.end(), gau_c.begin(), gau_c.end());
+    for (int k = 0; k < K; ++k) {
+        int32_t* rt = role_theta.data() + (size_t)k * kMaxRoles * 2;
+        rt[0] = map_col(this, k, 0);
+        rt[2] = map_col(this, k, 1);
+        for (int s = 0; s < (int)osc.size(); ++s) {
+            const musr_component& m = comp[osc[s]];
+            int32_t* q = rt + 2 * (2 + 4 * s);
+            q[0] = map_col(this, k, m.amp);
+            q[2] = map_col(this, k, m.rate);
+            q[4] = map_col(this, k, m.field);
+            q[5] = map_col(this, k, m.field2);
+            q[6] = map_col(this, k, m.phase);
+        }
+        if (kt_c >= 0) {
+            const musr_component& m = comp[kt_c];
+            int32_t* q = rt + 2 * (2 + 4 * (int)osc.size());
+            q[0] = map_col(this, k, m.amp);
+            q[2] = map_col(this, k, m.rate);
+        }
+    }
+    // tiling: largest block that still gives >= 2 blocks per SM
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
+    threads = 32;
+    for (int t = kMaxThreads; t >= 32; t >>= 1) {
+        int64_t tiles = 0;
+        for (int k = 0; k < K; ++k)
+            tiles += std::max<int64_t>(1, (n_bins[k] + t * kBinsPerThread - 1) / (t * kBinsPerThread));
+        if (tiles >= 2 * dev_sms) {
+            threads = t;
+            break;
+        }
+    }
+    return build_tiles(threads);
+}
+
+int musr_run_s::build_tiles(int t) {
+    threads = t;
+    tile_bins = t * kBinsPerThread;
+    tile_hist.clear();
+    tile_start.clear();
+    hist_first_tile.assign(K, 0);
+    hist_ntiles.assign(K, 0);
+    hist_off.assign(K, 0);
+    model_off.assign(K, 0);
+    int64_t off = 0, moff = 0;
+    for (int k = 0; k < K; ++k) {
+        hist_off[k] = off;
+        model_off[k] = moff;
+        off += round_up(n_bins[k], 8);
+        moff += n_bins[k];
+        const int64_t nt = std::max<int64_t>(1, (n_bins[k] + tile_bins - 1) / tile_bins);
+        hist_first_tile[k] = (int32_t)tile_hist.size();
+        hist_ntiles[k] = (int32_t)nt;
+        for (int64_t j = 0; j < nt; ++j) {
+            tile_hist.push_back(k);
+            tile_start.push_back((int32_t)(j * tile_bins));
+        }
+    }
+    data_floats = (size_t)off + 8;
+    n_tiles = (int)tile_hist.size();
+    return MUSR_OK;
+}
+
+// CSR of output entry -> (histogram, accumulator) sources for one mode.
+void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const {
+    const int nacc = n_acc(mode, R);
+    const int64_t n_out = 1 + (mode >= kGrad ? P : 0) + (mode == kGN ? (int64_t)P * P : 0);
+    std::vector<std::pair<int64_t, int32_t>> e;
+    for (int k = 0; k < K; ++k) {
+        const int32_t* rt = role_theta.data() + (size_t)k * kMaxRoles * 2;
+        const int32_t base = k * nacc;
+        e.push_back({0, base});
+        if (mode >= kGrad) {
+            for (int r = 0; r < R; ++r)
+                for (int j = 0; j < 2; ++j)
+                    if (rt[2 * r + j] >= 0) e.push_back({1 + rt[2 * r + j], base + 1 + r});
+        }
+        if (mode == kGN) {
+            int a = 1 + R;
+            for (int r1 = 0; r1 < R; ++r1)
+                for (int r2 = r1; r2 < R; ++r2, ++a)
+                    for (int j1 = 0; j1 < 2; ++j1)
+                        for (int j2 = 0; j2 < 2; ++j2) {
+                            const int i = rt[2 * r1 + j1], jj = rt[2 * r2 + j2];
+                            if (i < 0 || jj < 0) continue;
+                            e.push_back({1 + P + (int64_t)i * P + jj, base + a});
+                            if (r1 != r2) e.push_back({1 + P + (int64_t)jj * P + i, base + a});
+                        }
+        }
+    }
+    std::stable_sort(e.begin(), e.end(),
+                     [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) {
+                         return x.first < y.first;
+                     });
+    ptr.assign(n_out + 1, 0);
+    src.resize(e.size());
+    for (size_t i = 0; i < e.size(); ++i) {
+        ptr[e[i].first + 1]++;
+        src[i] = e[i].second;
+    }
+    for (int64_t o = 0; o < n_out; ++o) ptr[o + 1] += ptr[o];
+}
+
+// One device allocation holds every per-run array; pieces are 256-byte aligned.
+struct Arena {
+    size_t size = 0;
+    template <class T>
+    size_t take(size_t n) {
+        size_t o = size;
+        size = round_up((int64_t)(size + n * sizeof(T)), 256);
+        return o;
+    }
+};
+
+int musr_run_s::allocate() {
+    const int nacc_max = n_acc(P <= kMaxGnParams ? kGN : kGrad, R);
+    std::vector<int32_t> ptr[3], src[3];
+    for (int m = 0; m < 3; ++m) {
+        if (m == kGN && P > kMaxGnParams) continue;
+        build_csr(m, ptr[m], src[m]);
+        n_out[m] = (int)ptr[m].size() - 1;
+    }
+    const int n_out_max = n_out[P <= kMaxGnParams ? kGN : kGrad];
+    Arena A;
+    const size_t o_data = A.take<float>(data_floats);
+    const size_t o_hoff = A.take<int64_t>(K + 1);
+    const size_t o_moff = A.take<int64_t>(K + 1);
+    const size_t o_nb = A.take<int32_t>(K + 1);
+    const size_t o_th = A.take<int32_t>(n_tiles);
+    const size_t o_ts = A.take<int32_t>(n_tiles);
+    const size_t o_hf = A.take<int32_t>(K + 1);
+    const size_t o_hn = A.take<int32_t>(K + 1);
+    const size_t o_rt = A.take<int32_t>(role_theta.size() + 1);
+    size_t o_ptr[3], o_src[3];
+    for (int m = 0; m < 3; ++m) {
+        o_ptr[m] = A.take<int32_t>(ptr[m].size() + 1);
+        o_src[m] = A.take<int32_t>(src[m].size() + 1);
+    }
+    const size_t o_part = A.take<double>((size_t)n_tiles * nacc_max);
+    const size_t o_hsum = A.take<double>((size_t)(K + 1) * nacc_max);
+    const size_t o_cnt = A.take<unsigned>(K + 2);
+    const size_t o_theta = A.take<double>(P + 1);
+    const size_t o_out = A.take<double>(n_out_max + 1);
+    const size_t o_status = A.take<int32_t>(2);
+    const size_t o_tmp = A.take<double>(P + 1);
+    if (cudaMalloc(&arena, A.size) != cudaSuccess) {
+        arena = nullptr;
+        return MUSR_ENOMEM;
+    }
+    char* b = static_cast<char*>(arena);
+    d_data = reinterpret_cast<float*>(b + o_data);
+    d_hist_off = reinterpret_cast<int64_t*>(b + o_hoff);
+    d_model_off = reinterpret_cast<int64_t*>(b + o_moff);
+    d_hist_nbins = reinterpret_cast<int32_t*>(b + o_nb);
+    d_tile_hist = reinterpret_cast<int32_t*>(b + o_th);
+    d_tile_start = reinterpret_cast<int32_t*>(b + o_ts);
+    d_hist_first_tile = reinterpret_cast<int32_t*>(b + o_hf);
+    d_hist_ntiles = reinterpret_cast<int32_t*>(b + o_hn);
+    d_role_theta = reinterpret_cast<int32_t*>(b + o_rt);
+    for (int m = 0; m < 3; ++m) {
+        d_csr_ptr[m] = reinterpret_cast<int32_t*>(b + o_ptr[m]);
+        d_csr_src[m] = reinterpret_cast<int32_t*>(b + o_src[m]);
+    }
+    d_partial = reinterpret_cast<double*>(b + o_part);
+    d_hist_sum = reinterpret_cast<double*>(b + o_hsum);
+    d_counters = reinterpret_cast<unsigned*>(b + o_cnt);
+    d_theta = reinterpret_cast<double*>(b + o_theta);
+    d_out = reinterpret_cast<double*>(b + o_out);
+    d_status = reinterpret_cast<int32_t*>(b + o_status);
+    d_theta_tmp = reinterpret_cast<double*>(b + o_tmp);
+
+    if (cudaMallocHost(&h_pinned, sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64) != cudaSuccess) {
+        h_pinned = nullptr;
+        return MUSR_ENOMEM;
+    }
+    h_theta = static_cast<double*>(h_pinned);
+    h_out = h_theta + P + 1;
+    h_status = reinterpret_cast<int32_t*>(h_out + n_out_max + 1);
+
+    // static tables
+    std::vector<int32_t> nb32(K);
+    for (int k = 0; k < K; ++k) nb32[k] = (int32_t)n_bins[k];
+    cudaError_t e = cudaSuccess;
+    auto up = [&](void* dst, const void* src_, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src_, bytes, cudaMemcpyHostToDevice, stream);
+    };
+    up(d_hist_off, hist_off.data(), sizeof(int64_t) * K);
+    up(d_model_off, model_off.data(), sizeof(int64_t) * K);
+    up(d_hist_nbins, nb32.data(), sizeof(int32_t) * K);
+    up(d_tile_hist, tile_hist.data(), sizeof(int32_t) * n_tiles);
+    up(d_tile_start, tile_start.data(), sizeof(int32_t) * n_tiles);
+    up(d_hist_first_tile, hist_first_tile.data(), sizeof(int32_t) * K);
+    up(d_hist_ntiles, hist_ntiles.data(), sizeof(int32_t) * K);
+    up(d_role_theta, role_theta.data(), sizeof(int32_t) * role_theta.size());
+    for (int m = 0; m < 3; ++m) {
+        up(d_csr_ptr[m], ptr[m].data(), sizeof(int32_t) * ptr[m].size());
+        up(d_csr_src[m], src[m].data(), sizeof(int32_t) * src[m].size());
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * (K + 2), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_data, 0, sizeof(float) * data_floats, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    return cuda_status(e);
+}
+
+int musr_run_s::upload(int dtype, const void* data, int on_device) {
+    if (!data) return MUSR_OK;
+    if (dtype != MUSR_F32 && dtype != MUSR_F64) return MUSR_EINVAL;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        // straight per-histogram copies into the padded layout (padding stays 0)
+        const float* src = static_cast<const float*>(data);
+        std::vector<float> conv;
+        if (dtype == MUSR_F64) {
+            conv.resize((size_t)total_bins);
+            const double* d64 = static_cast<const double*>(data);
+            for (int64_t i = 0; i < total_bins; ++i) conv[i] = (float)d64[i];
+            src = conv.data();
+        }
+        int64_t s = 0;
+        for (int k = 0; k < K && e == cudaSuccess; ++k) {
+            if (n_bins[k])
+                e = cudaMemcpyAsync(d_data + hist_off[k], src + s, sizeof(float) * n_bins[k],
+                                    cudaMemcpyHostToDevice, stream);
+            s += n_bins[k];
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        return cuda_status(e);
+    }
+    // device source: pack with a kernel (offsets staged through d_partial scratch)
+    std::vector<int64_t> src_off(K);
+    int64_t s = 0;
+    for (int k = 0; k < K; ++k) {
+        src_off[k] = s;
+        s += n_bins[k];
+    }
+    int64_t* d_src_off = nullptr;
+    e = cudaMalloc(&d_src_off, sizeof(int64_t) * (K + 1));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_src_off, src_off.data(), sizeof(int64_t) * K, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && K > 0) {
+        dim3 grid(64, K);
+        pack_data_kernel<<<grid, 256, 0, stream>>>(data, dtype == MUSR_F64, d_src_off, d_hist_off,
+                                                   d_hist_nbins, K, d_data);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (d_src_off) cudaFree(d_src_off);
+    return cuda_status(e);
+}
+
+EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double* out_dev,
+                              int32_t* status_dev) const {
+    EvalParams p;
+    memset(&p, 0, sizeof(p));
+    p.data = d_data;
+    p.hist_off = d_hist_off;
+    p.hist_nbins = d_hist_nbins;
+    p.tile_hist = d_tile_hist;
+    p.tile_start = d_tile_start;
+    p.hist_first_tile = d_hist_first_tile;
+    p.hist_ntiles = d_hist_ntiles;
+    p.role_theta = d_role_theta;
+    p.theta = theta_dev;
+    p.t0 = t0;
+    p.dt = dt;
+    p.inv_tau = 1.0 / tau;
+    p.gamma = gamma;
+    p.K = K;
+    p.P = P;
+    p.obj = obj;
+    p.partial = d_partial;
+    p.hist_sum = d_hist_sum;
+    p.hist_count = d_counters;
+    p.global_count = d_counters + K;
+    p.flags = d_counters + K + 1;
+    const int m = mode == kModel ? kValue : mode;
+    p.csr_ptr = d_csr_ptr[m];
+    p.csr_src = d_csr_src[m];
+    p.n_out = n_out[m];
+    p.out = out_dev;
+    p.status_out = status_dev;
+    p.model_off = d_model_off;
+    return p;
+}
+
+int musr_run_s::launch(int obj, int mode, const double* theta_dev, double* out_dev,
+                       int32_t* status_dev, cudaStream_t st, float* model_out) {
+    if (mode == kGN && P > kMaxGnParams) return MUSR_ENOTSUP;
+    if (K == 0) return MUSR_OK;
+    EvalParams p = params(obj, mode, theta_dev, out_dev, status_dev);
+    p.model_out = model_out;
+    return cuda_status(launch_eval(sig, mode, threads, n_tiles, st, p));
+}
+
+// Host-pointer evaluation through a cached CUDA graph.
+int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags) {
+    if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
+    if (mode < kValue || mode > kGN) return MUSR_EINVAL;
+    if (mode == kGN && P > kMaxGnParams) return MUSR_ENOTSUP;
+    for (int j = 0; j < P; ++j)
+        if (!isfinite(theta[j])) return MUSR_ENONFINITE;
+    const int nout = n_out[mode];
+    if (K == 0) {
+        memset(out_host, 0, sizeof(double) * nout);
+        *flags = 0;
+        return MUSR_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!graphs[obj][mode]) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * P, cudaMemcpyHostToDevice, cap_stream);
+            EvalParams p = params(obj, mode, d_theta, d_out, d_status);
+            launch_eval(sig, mode, threads, n_tiles, cap_stream, p);
+            cudaMemcpyAsync(h_out, d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, cap_stream);
+            cudaMemcpyAsync(h_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, cap_stream);
+            e = cudaStreamEndCapture(cap_stream, &g);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs[obj][mode], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            graphs[obj][mode] = nullptr;
+            return cuda_status(e);
+        }
+    }
+    memcpy(h_theta, theta, sizeof(double) * P);
+    e = cudaGraphLaunch(graphs[obj][mode], stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    memcpy(out_host, h_out, sizeof(double) * nout);
+    *flags = *h_status;
+    return MUSR_OK;
+}
+
+musr_run_s::~musr_run_s() {
+    for (int o = 0; o < 2; ++o)
+        for (int m = 0; m < 3; ++m)
+            if (graphs[o][m]) cudaGraphExecDestroy(graphs[o][m]);
+    if (arena) cudaFree(arena);
+    if (h_pinned) cudaFreeHost(h_pinned);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int musr_create_run(const musr_run_desc* desc, musr_run* out) {
+    if (!desc || !out) return MUSR_EINVAL;
+    *out = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return MUSR_ECUDA;
+    musr_run_s* r = new (std::nothrow) musr_run_s();
+    if (!r) return MUSR_ENOMEM;
+    r->device = dev;
+    int st = r->plan(desc);
+    if (st == MUSR_OK) {
+        if (desc->stream) {
+            r->stream = static_cast<cudaStream_t>(desc->stream);
+            r->own_stream = false;
+        } else {
+            st = cuda_status(cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking));
+            r->own_stream = true;
+        }
+    }
+    if (st == MUSR_OK) st = cuda_status(cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking));
+    if (st == MUSR_OK) st = r->allocate();
+    if (st == MUSR_OK) st = r->upload(desc->data_dtype, desc->data, desc->data_on_device);
+    if (st != MUSR_OK) {
+        delete r;
+        return st;
+    }
+    *out = r;
+    return MUSR_OK;
+}
+
+int musr_destroy_run(musr_run run) {
+    if (!run) return MUSR_OK;
+    DeviceGuard g(run->device);
+    cudaStreamSynchronize(run->stream);
+    delete run;
+    return MUSR_OK;
+}
+
+int musr_run_info(musr_run run, int32_t* n_params, int64_t* total_bins, int32_t* n_hist) {
+    if (!run) return MUSR_EINVAL;
+    if (n_params) *n_params = run->P;
+    if (total_bins) *total_bins = run->total_bins;
+    if (n_hist) *n_hist = run->K;
+    return MUSR_OK;
+}
+
+int musr_set_data(musr_run run, int32_t dtype, const void* data, int32_t on_device) {
+    if (!run || !data) return MUSR_EINVAL;
+    DeviceGuard g(run->device);
+    return run->upload(dtype, data, on_device);
+}
+
+int musr_chi2(musr_run run, int obj, const double* theta, double* value) {
+    if (!run || !theta || !value) return MUSR_EINVAL;
+    DeviceGuard g(run->device);
+    int32_t flags = 0;
+    int st = run->eval_host(obj, kValue, theta, value, &flags);
+    if (st != MUSR_OK) return st;
+    if (flags & 1) {
+        *value = INFINITY;
+        return MUSR_EDOMAIN;
+    }
+    return isfinite(*value) ? MUSR_OK : MUSR_ENONFINITE;
+}
+
+int musr_chi2_grad(musr_run run, int obj, const double* theta, double* value, double* grad,
+                   double* gn) {
+    if (!run || !theta) return MUSR_EINVAL;
+    DeviceGuard g(run->device);
+    const int mode = gn ? kGN : kGrad;
+    std::vector<double> out;
+    out.resize(run->n_out[mode == kGN && run->P > kMaxGnParams ? kGrad : mode] + 1);
+    int32_t flags = 0;
+    int st = run->eval_host(obj, mode, theta, out.data(), &flags);
+    if (st != MUSR_OK) return st;
+    if (value) *value = out[0];
+    if (grad) memcpy(grad, out.data() + 1, sizeof(double) * run->P);
+    if (gn) memcpy(gn, out.data() + 1 + run->P, sizeof(double) * run->P * run->P);
+    if (flags & 1) {
+        if (value) *value = INFINITY;
+        return MUSR_EDOMAIN;
+    }
+    return isfinite(out[0]) ? MUSR_OK : MUSR_ENONFINITE;
+}
+
+int musr_chi2_grad_device(musr_run run, int obj, int mode, const double* theta_dev, double* out_dev,
+                          int32_t* status_dev, void* stream) {
+    if (!run || !theta_dev || !out_dev) return MUSR_EINVAL;
+    if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
+    if (mode < MUSR_VALUE || mode > MUSR_VALUE_GRAD_GN) return MUSR_EINVAL;
+    DeviceGuard g(run->device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : run->stream;
+    if (run->K == 0) {
+        cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * run->n_out[mode], st);
+        if (e == cudaSuccess && status_dev) e = cudaMemsetAsync(status_dev, 0, sizeof(int32_t), st);
+        return cuda_status(e);
+    }
+    return run->launch(obj, mode, theta_dev, out_dev, status_dev, st, nullptr);
+}
+
+int musr_model(musr_run run, const double* theta, float* out, int32_t out_on_device) {
+    if (!run || !theta || !out) return MUSR_EINVAL;
+    DeviceGuard g(run->device);
+    for (int j = 0; j < run->P; ++j)
+        if (!isfinite(theta[j])) return MUSR_ENONFINITE;
+    if (run->K == 0 || run->total_bins == 0) return MUSR_OK;
+    cudaError_t e = cudaMemcpyAsync(run->d_theta_tmp, theta, sizeof(double) * run->P,
+                                    cudaMemcpyHostToDevice, run->stream);
+    float* dst = out;
+    float* tmp = nullptr;
+    if (e == cudaSuccess && !out_on_device) {
+        e = cudaMalloc(&tmp, sizeof(float) * run->total_bins);
+        dst = tmp;
+    }
+    int st = cuda_status(e);
+    if (st == MUSR_OK) st = run->launch(MUSR_CHI2, kModel, run->d_theta_tmp, nullptr, nullptr, run->stream, dst);
+    if (st == MUSR_OK && !out_on_device)
+        st = cuda_status(cudaMemcpyAsync(out, tmp, sizeof(float) * run->total_bins,
+                                         cudaMemcpyDeviceToHost, run->stream));
+    if (st == MUSR_OK) st = cuda_status(cudaStreamSynchronize(run->stream));
+    if (tmp) cudaFree(tmp);
+    return st;
+}
+
+const char* musr_strerror(int code) {
+    switch (code) {
+        case MUSR_OK: return "ok";
+        case MUSR_EINVAL: return "invalid argument or layout";
+        case MUSR_ENOMEM: return "out of memory";
+        case MUSR_ECUDA: return "CUDA error";
+        case MUSR_ENONFINITE: return "non-finite parameter or result";
+        case MUSR_EDOMAIN: return "Poisson mean outside its domain (N < 0, or N = 0 with d > 0)";
+        case MUSR_ETIMEOUT: return "bounded device wait timed out";
+        case MUSR_ENOCONV: return "minimiser did not converge";
+        case MUSR_ENOTSUP: return "layout outside the supported limits";
+    }
+    return "unknown status";
+}
+
+const char* musr_version(void) { return "musr-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,205 @@
+"""GPU parity: the CUDA objective / adjoint kernels against the FP64 oracle.
+
+Tolerances (stated for the FP32-evaluation / FP64-accumulation design):
+  * chi2 and the Poisson deviance: relative error <= 1e-6;
+  * gradient: ||g_gpu - g_oracle|| / ||g_oracle|| <= 1e-4 at a perturbed theta
+    (at the minimum g ~ 0 and a relative bound is meaningless);
+  * Gauss-Newton matrix: Frobenius relative error <= 1e-4;
+  * model N per bin: relative error <= 2e-6 (a few FP32 ulps);
+  * noise-free data: chi2_gpu <= sum (eps N)^2 / max(d, 1) with eps = 4e-7.
+All calls go through the C ABI (libmusr.so via ctypes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from _gpu_util import grad_rel_err, rel_err
+
+pytestmark = pytest.mark.gpu
+
+gpu = pytest.importorskip("paper_1604_02334_gb300")
+from paper_1604_02334_gb300 import MUSR_CHI2, MUSR_POISSON, Run  # noqa: E402
+from paper_1604_02334_gb300 import _lib  # noqa: E402
+
+OBJS = [(MUSR_CHI2, oracle.CHI2), (MUSR_POISSON, oracle.POISSON)]
+
+
+def poisson_data(lay, theta, seed):
+    return W.poisson_counts(oracle.model(lay, theta), seed)
+
+
+@pytest.fixture(scope="module")
+def md_small():
+    """16 detectors x 5000 bins: several tiles per histogram and a ragged tail."""
+    lay, theta, seed = W.config_multi_detector(16, 5000)
+    d = poisson_data(lay, theta, seed)
+    th = W.perturb(theta, lay.free, 0.01, W.rng(seed + 7))
+    return lay, theta, th, d
+
+
+@pytest.mark.parametrize("obj,oobj", OBJS)
+def test_single_histogram_objective(obj, oobj):
+    lay, theta, seed = W.config_single()
+    d = poisson_data(lay, theta, seed)  # FP64 counts
+    th = W.perturb(theta, lay.free, 0.05, W.rng(seed))
+    with Run(lay, d) as run:
+        for t in (theta, th):
+            v = run.chi2(t, obj)
+            ref = oracle.objective(lay, d, t, oobj)
+            assert rel_err(v, ref) <= 1e-6, (v, ref)
+
+
+@pytest.mark.parametrize("obj,oobj", OBJS)
+def test_multi_detector_value_grad_gn(md_small, obj, oobj):
+    lay, theta, th, d = md_small
+    with Run(lay, d.astype(np.float32)) as run:
+        v, g, H = run.chi2_grad(th, obj, gn=True)
+        v0 = run.chi2(th, obj)
+    rv, rg, rH = oracle.gradient(lay, d, th, oobj)
+    assert rel_err(v, rv) <= 1e-6
+    assert v0 == v  # value-only and adjoint launches agree bitwise
+    assert grad_rel_err(g, rg) <= 1e-4
+    assert np.linalg.norm(H - rH) / np.linalg.norm(rH) <= 1e-4
+
+
+def test_gradient_matches_oracle_central_differences(md_small):
+    """The adjoint gradient against FP64 central differences (h = 1e-6 relative)."""
+    lay, theta, th, d = md_small
+    with Run(lay, d) as run:
+        _, g, _ = run.chi2_grad(th, MUSR_CHI2)
+    gfd = oracle.gradient_fd(lay, d, th, oracle.CHI2, rel_h=1e-6)
+    assert grad_rel_err(g, gfd) <= 1e-4
+
+
+@pytest.mark.parametrize("obj,oobj", OBJS)
+def test_full_size_multi_detector(obj, oobj):
+    """16 x 65536 bins, the benchmark's workload, at the launch configuration it times."""
+    lay, theta, seed = W.config_multi_detector()
+    d = poisson_data(lay, theta, seed)
+    th = W.perturb(theta, lay.free, 0.01, W.rng(seed + 1))
+    with Run(lay, d.astype(np.float32)) as run:
+        v, g, _ = run.chi2_grad(th, obj)
+        vt = run.chi2(theta, obj)
+    rv, rg, _ = oracle.gradient(lay, d, th, oobj, with_gn=False)
+    assert rel_err(v, rv) <= 1e-6
+    assert grad_rel_err(g, rg) <= 1e-4
+    assert rel_err(vt, oracle.objective(lay, d, theta, oobj)) <= 1e-6
+
+
+def test_model_matches_oracle(md_small):
+    lay, theta, th, d = md_small
+    with Run(lay) as run:
+        n = run.model(th)
+    ref = oracle.model(lay, th)
+    np.testing.assert_allclose(n, ref, rtol=2e-6, atol=1e-6)
+
+
+def test_noise_free_chi2_bound():
+    lay, theta, _ = W.config_multi_detector(4, 3000)
+    ref = oracle.model(lay, theta)
+    d = ref.astype(np.float32).astype(np.float64)
+    with Run(lay, d) as run:
+        v = run.chi2(theta, MUSR_CHI2)
+    bound = np.sum((4e-7 * ref) ** 2 / np.maximum(d, 1.0)) + np.sum((d - ref) ** 2 / np.maximum(d, 1.0))
+    assert 0.0 <= v <= bound
+
+
+@pytest.mark.parametrize("nb", [[1], [7], [8], [9], [0, 5, 0, 2047, 2048, 2049, 13], [16385, 3]])
+def test_ragged_and_empty_histograms(nb):
+    lay = W.multi_detector_layout(len(nb), nb, window_us=12.8)
+    theta = W.multi_detector_theta(lay, W.rng(len(nb)))
+    d = poisson_data(lay, theta, 99)
+    th = W.perturb(theta, lay.free, 0.02, W.rng(5))
+    with Run(lay, d) as run:
+        for obj, oobj in OBJS:
+            v, g, H = run.chi2_grad(th, obj, gn=True)
+            rv, rg, rH = oracle.gradient(lay, d, th, oobj)
+            assert rel_err(v, rv) <= 1e-6
+            assert grad_rel_err(g, rg) <= 1e-4
+            assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
+
+
+def test_no_histograms():
+    lay = W.multi_detector_layout(1, [1])
+    lay.n_bins = np.zeros(0, dtype=np.int64)
+    lay.map = np.zeros((0, lay.map_width), dtype=np.int32)
+    with Run(lay, np.zeros(0)) as run:
+        v, g, _ = run.chi2_grad(np.ones(lay.n_params), MUSR_CHI2)
+    assert v == 0.0 and not g.any()
+
+
+def test_bitwise_repeatable(md_small):
+    lay, theta, th, d = md_small
+    with Run(lay, d) as run:
+        a = run.chi2_grad(th, MUSR_CHI2, gn=True)
+        b = run.chi2_grad(th, MUSR_CHI2, gn=True)
+    assert a[0] == b[0]
+    assert np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+def test_histogram_permutation(md_small):
+    lay, theta, th, d = md_small
+    perm = np.random.default_rng(3).permutation(lay.n_hist)
+    offs = np.r_[0, np.cumsum(lay.n_bins)]
+    dp = np.concatenate([d[offs[k]:offs[k + 1]] for k in perm])
+    with Run(lay, d) as r1, Run(lay.permuted(perm), dp) as r2:
+        for obj, _ in OBJS:
+            a, ga, _ = r1.chi2_grad(th, obj)
+            b, gb, _ = r2.chi2_grad(th, obj)
+            assert rel_err(a, b) <= 1e-6
+            assert grad_rel_err(ga, gb) <= 1e-4
+
+
+def test_poisson_domain_and_nonfinite():
+    lay, theta, seed = W.config_single()
+    d = poisson_data(lay, theta, seed)
+    with Run(lay, d) as run:
+        bad = theta.copy()
+        bad[0] = -100.0  # N < 0 with d > 0
+        v, st = run.chi2(bad, MUSR_POISSON, raise_on_error=False)
+        assert st == _lib.MUSR_EDOMAIN and v == math.inf
+        # chi2 is defined for any N
+        assert math.isfinite(run.chi2(bad, MUSR_CHI2))
+        nan = theta.copy()
+        nan[3] = float("nan")
+        _, st = run.chi2(nan, MUSR_CHI2, raise_on_error=False)
+        assert st == _lib.MUSR_ENONFINITE
+        # the run stays usable after errors
+        assert rel_err(run.chi2(theta, MUSR_POISSON), oracle.objective(lay, d, theta, oracle.POISSON)) <= 1e-6
+
+
+def test_device_path_and_autograd(md_small):
+    torch = pytest.importorskip("torch")
+    from paper_1604_02334_gb300 import Chi2
+    lay, theta, th, d = md_small
+    dev = torch.device("cuda:0")
+    data_t = torch.tensor(d, dtype=torch.float32, device=dev)
+    with Run(lay, data_t, stream="torch") as run:
+        v_host, g_host, _ = run.chi2_grad(th, MUSR_CHI2)
+        t = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
+        v = Chi2.apply(t, run, MUSR_CHI2)
+        (gt,) = torch.autograd.grad(v * 3.0, t)
+        torch.cuda.synchronize()
+        assert float(v) == v_host
+        np.testing.assert_array_equal(gt.cpu().numpy(), 3.0 * g_host)
+        out = torch.empty(1 + lay.n_params + lay.n_params ** 2, dtype=torch.float64, device=dev)
+        st = torch.zeros(1, dtype=torch.int32, device=dev)
+        run.chi2_grad_device(t.detach(), out, MUSR_POISSON, 2, st)
+        torch.cuda.synchronize()
+        rv, rg, rH = oracle.gradient(lay, d, th, oracle.POISSON)
+        o = out.cpu().numpy()
+        assert rel_err(o[0], rv) <= 1e-6 and int(st.item()) == 0
+        assert grad_rel_err(o[1:1 + lay.n_params], rg) <= 1e-4
+
+
+def test_set_data_from_device_fp64(md_small):
+    torch = pytest.importorskip("torch")
+    lay, theta, th, d = md_small
+    with Run(lay, d) as run:
+        a = run.chi2(th, MUSR_CHI2)
+        run.set_data(torch.tensor(d, dtype=torch.float64, device="cuda:0"))
+        b = run.chi2(th, MUSR_CHI2)
+    assert a == b
