@@ -189,7 +189,8 @@ typedef struct {
     int32_t max_iter; /* <= 0: 500 */
     double edm_tol;   /* <= 0: 1e-8; stop when 1/2 g^T H^-1 g < edm_tol */
     double mu0;       /* <= 0: 1e-3; initial LM damping */
-    double fd_rel_h;  /* <= 0: 1e-6; relative step of MUSR_FIT_BFGS_FD */
+    double fd_rel_h;  /* <= 0: 1e-4; relative step of MUSR_FIT_BFGS_FD (the FP32
+                         evaluation noise makes smaller steps noise-dominated) */
 } musr_fit_opts;
 
 typedef struct {

@@ -165,7 +165,7 @@ class Run:
 
     # -- fit ----------------------------------------------------------------
     def fit(self, theta0, obj=MUSR_CHI2, free=None, method=MUSR_FIT_LM, max_iter=500,
-            edm_tol=1e-8, mu0=1e-3, fd_rel_h=1e-6):
+            edm_tol=1e-8, mu0=1e-3, fd_rel_h=0.0):
         th = np.ascontiguousarray(theta0, dtype=np.float64).copy()
         fm = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
         nf = self.P if fm is None else int(fm.sum())
@@ -217,3 +217,70 @@ class _LazyChi2:
 
 
 Chi2 = _LazyChi2()
+
+
+class Batch:
+    """A batched-evaluation plan over several runs (musr_batch_*).
+
+    ``max_vec[r]`` parameter vectors of run r are evaluated per launch; the
+    first evaluation autotunes the launch shape.
+    """
+
+    def __init__(self, runs, max_vec):
+        lib = _lib.load()
+        self.runs = list(runs)
+        self.max_vec = np.ascontiguousarray(max_vec, dtype=np.int32)
+        handles = (ctypes.c_void_p * len(self.runs))(*[r.handle.value for r in self.runs])
+        h = ctypes.c_void_p()
+        check(lib.musr_batch_create(handles, len(self.runs),
+                                    self.max_vec.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                    ctypes.byref(h)), "musr_batch_create")
+        self.handle = h
+        self.n_values = int(self.max_vec.sum())
+        self.n_theta = int(sum(int(v) * r.P for v, r in zip(self.max_vec, self.runs)))
+
+    def eval(self, thetas, obj=MUSR_CHI2, n_vec=None):
+        th = np.ascontiguousarray(thetas, dtype=np.float64).ravel()
+        nv = self.max_vec if n_vec is None else np.ascontiguousarray(n_vec, dtype=np.int32)
+        out = np.zeros(int(nv.sum()))
+        check(_lib.load().musr_batch_eval(self.handle, int(obj), _dptr(th),
+                                          nv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(out)),
+              "musr_batch_eval")
+        return out
+
+    def eval_device(self, thetas_dev, values_dev, obj=MUSR_CHI2):
+        """thetas_dev / values_dev: CUDA FP64 tensors (every run at max_vec vectors)."""
+        check(_lib.load().musr_batch_eval_device(self.handle, int(obj),
+                                                 ctypes.c_void_p(thetas_dev.data_ptr()),
+                                                 ctypes.c_void_p(values_dev.data_ptr())),
+              "musr_batch_eval_device")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            _lib.load().musr_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def chi2_batch(runs, thetas, n_vec, obj=MUSR_CHI2):
+    """One-shot musr_chi2_batch: plan, evaluate, free."""
+    lib = _lib.load()
+    handles = (ctypes.c_void_p * len(runs))(*[r.handle.value for r in runs])
+    nv = np.ascontiguousarray(n_vec, dtype=np.int32)
+    th = np.ascontiguousarray(thetas, dtype=np.float64).ravel()
+    out = np.zeros(int(nv.sum()))
+    check(lib.musr_chi2_batch(handles, len(runs), int(obj), _dptr(th),
+                              nv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(out)),
+          "musr_chi2_batch")
+    return out

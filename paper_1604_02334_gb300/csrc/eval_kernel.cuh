@@ -86,26 +86,30 @@ __device__ __forceinline__ double role_value(const int32_t* rt, const double* th
 // Stage part `part` of histogram k's constants (part 0: N0, bkg, lifetime;
 // 1..NOSC: precession lines; NOSC+1: Kubo-Toyabe).  FP64 for every argument,
 // FP32 accurate functions for the small step factors.
+struct TimeGrid {
+    double t0, dt, inv_tau, gamma;
+};
+
 template <int NE, int NG, int KT>
-__device__ void stage_hist(int part, const EvalParams& p, int k, HistConst& hc) {
+__device__ void stage_hist(int part, const int32_t* rt, const double* theta, const TimeGrid& tg,
+                           HistConst& hc) {
     constexpr int NOSC = NE + NG;
     const double LOG2E = 1.4426950408889634074;
-    const int32_t* rt = p.role_theta + (size_t)k * kMaxRoles * 2;
-    const double dt = p.dt, t0 = p.t0, it = p.inv_tau;
+    const double dt = tg.dt, t0 = tg.t0, it = tg.inv_tau;
     if (part == 0) {
-        hc.n0 = (float)role_value(rt, p.theta, 0);
-        hc.bkg = (float)role_value(rt, p.theta, 1);
+        hc.n0 = (float)role_value(rt, theta, 0);
+        hc.bkg = (float)role_value(rt, theta, 1);
         split_hi_lo(dt * it * LOG2E, hc.aE_hi, hc.aE_lo);
         hc.qE = expm1f((float)(-dt * it));
         hc.cE = expf((float)(-t0 * it));
-        hc.kfreq = (float)(2.0 * 3.14159265358979323846 * p.gamma);
+        hc.kfreq = (float)(2.0 * 3.14159265358979323846 * tg.gamma);
     } else if (part <= NOSC) {
         const int c = part - 1;
         const int r = 2 + 4 * c;
-        const double amp = role_value(rt, p.theta, r);
-        const double rate = role_value(rt, p.theta, r + 1);
-        const double field = role_value(rt, p.theta, r + 2);
-        const double phi = role_value(rt, p.theta, r + 3);
+        const double amp = role_value(rt, theta, r);
+        const double rate = role_value(rt, theta, r + 1);
+        const double field = role_value(rt, theta, r + 2);
+        const double phi = role_value(rt, theta, r + 3);
         OscConst& o = hc.osc[c];
         o.amp = (float)amp;
         o.rate = (float)rate;
@@ -122,7 +126,7 @@ __device__ void stage_hist(int part, const EvalParams& p, int k, HistConst& hc) 
             o.q = 0.f;
             o.cenv = expf((float)(-t0 * it - 0.5 * s2 * t0 * t0));
         }
-        const double f = p.gamma * field;  // turns per microsecond
+        const double f = tg.gamma * field;  // turns per microsecond
         o.ph0 = turns_to_fixed(f * t0 + phi * 0.15915494309189533577);
         const double stp = f * dt;          // turns per bin
         o.step = turns_to_fixed(stp);
@@ -132,8 +136,8 @@ __device__ void stage_hist(int part, const EvalParams& p, int k, HistConst& hc) 
         o.sn = sinpif(2.f * red);             // sin(step)
     } else if (KT && part == NOSC + 1) {
         const int r = 2 + 4 * NOSC;
-        const double amp = role_value(rt, p.theta, r);
-        const double dl = role_value(rt, p.theta, r + 1);
+        const double amp = role_value(rt, theta, r);
+        const double dl = role_value(rt, theta, r + 1);
         const double s2 = dl * dl;
         hc.kt_amp = (float)amp;
         hc.kt_rate = (float)dl;
@@ -149,6 +153,150 @@ __device__ __forceinline__ void warp_sum(float (&v)[NACC]) {
     for (int a = 0; a < NACC; ++a) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[a] += __shfl_xor_sync(0xffffffffu, v[a], o);
+    }
+}
+
+// One thread's chunk of kBinsPerThread consecutive bins starting at bin n0 of a
+// histogram with M bins: theory (Eq. 1), objective term (Eq. 3 / Eq. 4) and,
+// by mode, the role partials accumulated into the gradient and GN matrix.
+template <int NE, int NG, int KT, int MODE, int NACC>
+__device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
+                                           const float (&d)[kBinsPerThread], int obj, float dtf,
+                                           float t0f, float (&acc)[NACC], bool& bad,
+                                           float* model_dst) {
+    constexpr int NOSC = NE + NG;
+    constexpr int R = 2 + 4 * NOSC + 2 * KT;
+    constexpr int G = kBinsPerThread;
+    const float nf0 = (float)n0;
+    const float n0p = hc.n0, bkg = hc.bkg;
+    float E = hc.cE * ex2_approx(-fmaf(nf0, hc.aE_hi, nf0 * hc.aE_lo));
+    float env[NOSC > 0 ? NOSC : 1], cs[NOSC > 0 ? NOSC : 1], sn[NOSC > 0 ? NOSC : 1];
+#pragma unroll
+    for (int c = 0; c < NOSC; ++c) {
+        const OscConst& o = hc.osc[c];
+        if (c < NE) env[c] = o.cenv * ex2_approx(-fmaf(nf0, o.a_hi, nf0 * o.a_lo));
+        const unsigned long long ph = o.ph0 + (unsigned long long)n0 * o.step;
+        const float x = (float)(int)(ph >> 32) * 2.3283064365386963e-10f;  // turns in [-1/2, 1/2)
+        __sincosf(6.28318530717958647692f * x, &sn[c], &cs[c]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        const float nf = nf0 + (float)g;
+        const float t = fmaf(nf, dtf, t0f);
+        const float nn = nf * nf;
+        float S = E;
+#pragma unroll
+        for (int c = 0; c < NOSC; ++c) {
+            const OscConst& o = hc.osc[c];
+            if (c >= NE)
+                env[c] = o.cenv * ex2_approx(-fmaf(nn, o.b_hi, fmaf(nf, o.a_hi, fmaf(nn, o.b_lo, nf * o.a_lo))));
+            S = fmaf(o.amp * env[c], cs[c], S);
+        }
+        float envk = 0.f, xk = 0.f, GE = 0.f;
+        if (KT) {
+            envk = hc.kt_cenv *
+                   ex2_approx(-fmaf(nn, hc.kt_b_hi, fmaf(nf, hc.kt_a_hi, fmaf(nn, hc.kt_b_lo, nf * hc.kt_a_lo))));
+            const float dtk = hc.kt_rate * t;
+            xk = dtk * dtk;
+            GE = fmaf(0.666666667f * (1.f - xk), envk, 0.333333333f * E);
+            S = fmaf(hc.kt_amp, GE, S);
+        }
+        const float N = fmaf(n0p, S, bkg);
+
+        if (MODE == kModel) {
+            if (n0 + g < M) model_dst[n0 + g] = N;
+        } else if (n0 + g < M) {
+            const float dv = d[g];
+            float term, wg, wh;
+            if (obj == MUSR_CHI2) {
+                const float w = rcp_approx(fmaxf(dv, 1.f));
+                const float r = dv - N;
+                term = r * r * w;
+                wg = -2.f * r * w;
+                wh = 2.f * w;
+            } else {
+                if (dv > 0.f) {
+                    if (!(N > 0.f)) {
+                        bad = true;
+                        term = wg = wh = 0.f;
+                    } else {
+                        const float rN = rcp_approx(N);
+                        const float rho = (dv - N) * rN;
+                        float h;
+                        if (fabsf(rho) < 0.125f) {
+                            // sum_{j>=2} (-1)^j rho^j / (j (j-1)), truncated after j = 9
+                            h = fmaf(rho, -1.f / 72.f, 1.f / 56.f);
+                            h = fmaf(rho, h, -1.f / 42.f);
+                            h = fmaf(rho, h, 1.f / 30.f);
+                            h = fmaf(rho, h, -1.f / 20.f);
+                            h = fmaf(rho, h, 1.f / 12.f);
+                            h = fmaf(rho, h, -1.f / 6.f);
+                            h = fmaf(rho, h, 0.5f);
+                            h = h * rho * rho;
+                        } else {
+                            const float u = log1pf(rho);
+                            h = fmaf(rho, u, u - rho);
+                        }
+                        term = 2.f * N * h;
+                        wg = -2.f * rho;
+                        wh = 2.f * rN;
+                    }
+                } else {
+                    if (!(N >= 0.f)) bad = true;
+                    term = 2.f * N;
+                    wg = 2.f;
+                    wh = N > 0.f ? 2.f * rcp_approx(N) : 0.f;
+                }
+            }
+            acc[0] += term;
+            if (MODE >= kGrad) {
+                float pr[R];
+                pr[0] = S;
+                pr[1] = 1.f;
+#pragma unroll
+                for (int c = 0; c < NOSC; ++c) {
+                    const OscConst& o = hc.osc[c];
+                    const float m = n0p * env[c];
+                    const float pa = m * cs[c];
+                    const float q = o.amp * pa;
+                    pr[2 + 4 * c] = pa;
+                    pr[2 + 4 * c + 1] = (c < NE) ? -t * q : -o.rate * t * t * q;
+                    const float ps = -o.amp * m * sn[c];
+                    pr[2 + 4 * c + 2] = ps * t * hc.kfreq;
+                    pr[2 + 4 * c + 3] = ps;
+                }
+                if (KT) {
+                    pr[2 + 4 * NOSC] = n0p * GE;
+                    pr[2 + 4 * NOSC + 1] =
+                        n0p * hc.kt_amp * 0.666666667f * hc.kt_rate * t * t * (xk - 3.f) * envk;
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[1 + r] = fmaf(wg, pr[r], acc[1 + r]);
+                if (MODE == kGN) {
+                    int a = 1 + R;
+#pragma unroll
+                    for (int r1 = 0; r1 < R; ++r1) {
+                        const float qv = wh * pr[r1];
+#pragma unroll
+                        for (int r2 = r1; r2 < R; ++r2) {
+                            acc[a] = fmaf(qv, pr[r2], acc[a]);
+                            ++a;
+                        }
+                    }
+                }
+            }
+        }
+        // step the recurrences to the next bin
+        E = fmaf(E, hc.qE, E);
+#pragma unroll
+        for (int c = 0; c < NOSC; ++c) {
+            const OscConst& o = hc.osc[c];
+            if (c < NE) env[c] = fmaf(env[c], o.q, env[c]);
+            const float c2 = fmaf(cs[c], o.cm1, fmaf(-sn[c], o.sn, cs[c]));
+            const float s2 = fmaf(sn[c], o.cm1, fmaf(cs[c], o.sn, sn[c]));
+            cs[c] = c2;
+            sn[c] = s2;
+        }
     }
 }
 
@@ -181,7 +329,10 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalParams p) {
         for (int g = 0; g < G; ++g) d[g] = 0.f;
     }
 
-    if (threadIdx.x < 2 + NOSC) stage_hist<NE, NG, KT>(threadIdx.x, p, k, hc);
+    if (threadIdx.x < 2 + NOSC) {
+        const TimeGrid tg{p.t0, p.dt, p.inv_tau, p.gamma};
+        stage_hist<NE, NG, KT>(threadIdx.x, p.role_theta + (size_t)k * kMaxRoles * 2, p.theta, tg, hc);
+    }
     __syncthreads();
 
     float acc[NACC];
@@ -189,140 +340,9 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalParams p) {
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
     bool bad = false;
 
-    if (active) {
-        const float nf0 = (float)n0;
-        const float dtf = (float)p.dt, t0f = (float)p.t0;
-        const float n0p = hc.n0, bkg = hc.bkg;
-        float E = hc.cE * ex2_approx(-fmaf(nf0, hc.aE_hi, nf0 * hc.aE_lo));
-        float env[NOSC > 0 ? NOSC : 1], cs[NOSC > 0 ? NOSC : 1], sn[NOSC > 0 ? NOSC : 1];
-#pragma unroll
-        for (int c = 0; c < NOSC; ++c) {
-            const OscConst& o = hc.osc[c];
-            if (c < NE) env[c] = o.cenv * ex2_approx(-fmaf(nf0, o.a_hi, nf0 * o.a_lo));
-            const unsigned long long ph = o.ph0 + (unsigned long long)n0 * o.step;
-            const float x = (float)(int)(ph >> 32) * 2.3283064365386963e-10f;  // turns in [-1/2, 1/2)
-            __sincosf(6.28318530717958647692f * x, &sn[c], &cs[c]);
-        }
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const float nf = nf0 + (float)g;
-            const float t = fmaf(nf, dtf, t0f);
-            const float nn = nf * nf;
-            float S = E;
-#pragma unroll
-            for (int c = 0; c < NOSC; ++c) {
-                const OscConst& o = hc.osc[c];
-                if (c >= NE)
-                    env[c] = o.cenv * ex2_approx(-fmaf(nn, o.b_hi, fmaf(nf, o.a_hi, fmaf(nn, o.b_lo, nf * o.a_lo))));
-                S = fmaf(o.amp * env[c], cs[c], S);
-            }
-            float envk = 0.f, xk = 0.f, GE = 0.f;
-            if (KT) {
-                envk = hc.kt_cenv *
-                       ex2_approx(-fmaf(nn, hc.kt_b_hi, fmaf(nf, hc.kt_a_hi, fmaf(nn, hc.kt_b_lo, nf * hc.kt_a_lo))));
-                const float dtk = hc.kt_rate * t;
-                xk = dtk * dtk;
-                GE = fmaf(0.666666667f * (1.f - xk), envk, 0.333333333f * E);
-                S = fmaf(hc.kt_amp, GE, S);
-            }
-            const float N = fmaf(n0p, S, bkg);
-
-            if (MODE == kModel) {
-                if (n0 + g < M) p.model_out[p.model_off[k] + n0 + g] = N;
-            } else if (n0 + g < M) {
-                const float dv = d[g];
-                float term, wg, wh;
-                if (p.obj == MUSR_CHI2) {
-                    const float w = rcp_approx(fmaxf(dv, 1.f));
-                    const float r = dv - N;
-                    term = r * r * w;
-                    wg = -2.f * r * w;
-                    wh = 2.f * w;
-                } else {
-                    if (dv > 0.f) {
-                        if (!(N > 0.f)) {
-                            bad = true;
-                            term = wg = wh = 0.f;
-                        } else {
-                            const float rN = rcp_approx(N);
-                            const float rho = (dv - N) * rN;
-                            float h;
-                            if (fabsf(rho) < 0.125f) {
-                                // sum_{j>=2} (-1)^j rho^j / (j (j-1)), truncated after j = 9
-                                h = fmaf(rho, -1.f / 72.f, 1.f / 56.f);
-                                h = fmaf(rho, h, -1.f / 42.f);
-                                h = fmaf(rho, h, 1.f / 30.f);
-                                h = fmaf(rho, h, -1.f / 20.f);
-                                h = fmaf(rho, h, 1.f / 12.f);
-                                h = fmaf(rho, h, -1.f / 6.f);
-                                h = fmaf(rho, h, 0.5f);
-                                h = h * rho * rho;
-                            } else {
-                                const float u = log1pf(rho);
-                                h = fmaf(rho, u, u - rho);
-                            }
-                            term = 2.f * N * h;
-                            wg = -2.f * rho;
-                            wh = 2.f * rN;
-                        }
-                    } else {
-                        if (!(N >= 0.f)) bad = true;
-                        term = 2.f * N;
-                        wg = 2.f;
-                        wh = N > 0.f ? 2.f * rcp_approx(N) : 0.f;
-                    }
-                }
-                acc[0] += term;
-                if (MODE >= kGrad) {
-                    float pr[R];
-                    pr[0] = S;
-                    pr[1] = 1.f;
-#pragma unroll
-                    for (int c = 0; c < NOSC; ++c) {
-                        const OscConst& o = hc.osc[c];
-                        const float m = n0p * env[c];
-                        const float pa = m * cs[c];
-                        const float q = o.amp * pa;
-                        pr[2 + 4 * c] = pa;
-                        pr[2 + 4 * c + 1] = (c < NE) ? -t * q : -o.rate * t * t * q;
-                        const float ps = -o.amp * m * sn[c];
-                        pr[2 + 4 * c + 2] = ps * t * hc.kfreq;
-                        pr[2 + 4 * c + 3] = ps;
-                    }
-                    if (KT) {
-                        pr[2 + 4 * NOSC] = n0p * GE;
-                        pr[2 + 4 * NOSC + 1] =
-                            n0p * hc.kt_amp * 0.666666667f * hc.kt_rate * t * t * (xk - 3.f) * envk;
-                    }
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[1 + r] = fmaf(wg, pr[r], acc[1 + r]);
-                    if (MODE == kGN) {
-                        int a = 1 + R;
-#pragma unroll
-                        for (int r1 = 0; r1 < R; ++r1) {
-                            const float qv = wh * pr[r1];
-#pragma unroll
-                            for (int r2 = r1; r2 < R; ++r2) {
-                                acc[a] = fmaf(qv, pr[r2], acc[a]);
-                                ++a;
-                            }
-                        }
-                    }
-                }
-            }
-            // step the recurrences to the next bin
-            E = fmaf(E, hc.qE, E);
-#pragma unroll
-            for (int c = 0; c < NOSC; ++c) {
-                const OscConst& o = hc.osc[c];
-                if (c < NE) env[c] = fmaf(env[c], o.q, env[c]);
-                const float c2 = fmaf(cs[c], o.cm1, fmaf(-sn[c], o.sn, cs[c]));
-                const float s2 = fmaf(sn[c], o.cm1, fmaf(cs[c], o.sn, sn[c]));
-                cs[c] = c2;
-                sn[c] = s2;
-            }
-        }
-    }
+    if (active)
+        eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
+                                           MODE == kModel ? p.model_out + p.model_off[k] : nullptr);
     if (MODE == kModel) return;
 
     // ---- block reduction: FP32 within the warp, FP64 across warps ----
@@ -385,9 +405,11 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const EvalParams p) {
         for (int j = p.csr_ptr[o]; j < e; ++j) s += __ldcg(p.hist_sum + p.csr_src[j]);
         p.out[o] = s;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         *p.global_count = 0u;
-        const unsigned f = atomicExch(p.flags, 0u);
+        unsigned f = atomicExch(p.flags, 0u);
+        if (!isfinite(p.out[0])) f |= 2u;
         if (p.status_out) *p.status_out = (int32_t)f;
     }
 }

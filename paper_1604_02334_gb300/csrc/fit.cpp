@@ -71,6 +71,24 @@ struct Evaluator {
     }
 };
 
+// EDM = 1/2 g^T H^-1 g over the free block (inf if H is not positive definite).
+double edm_of(const std::vector<double>& g, const std::vector<double>& H, const std::vector<int>& fidx,
+              int P, std::vector<double>& A, std::vector<double>& b) {
+    const int nf = (int)fidx.size();
+    for (int a = 0; a < nf; ++a) {
+        b[a] = -g[fidx[a]];
+        for (int c = 0; c < nf; ++c) A[(size_t)a * nf + c] = H[(size_t)fidx[a] * P + fidx[c]];
+    }
+    if (!cholesky_solve(A, b, nf)) return INFINITY;
+    double e = 0.0;
+    for (int a = 0; a < nf; ++a) e -= 0.5 * g[fidx[a]] * b[a];
+    return e;
+}
+
+// Relative resolution of objective values computed with FP32 evaluation and
+// FP64 accumulation: below it, value comparisons are decided by rounding.
+constexpr double kValueNoise = 1e-6;
+
 int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
            musr_fit_result* out) {
     const int P = ev.P, nf = (int)fidx.size();
@@ -81,20 +99,12 @@ int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const mus
     if (st != MUSR_OK) return st;
     double mu = o.mu0, edm = INFINITY;
     int it = 0, result = MUSR_ENOCONV;
+    edm = edm_of(g, H, fidx, P, A, b);
     while (it < o.max_iter) {
         ++it;
-        for (int a = 0; a < nf; ++a) {
-            b[a] = -g[fidx[a]];
-            for (int c = 0; c < nf; ++c) A[(size_t)a * nf + c] = H[(size_t)fidx[a] * P + fidx[c]];
-        }
-        if (cholesky_solve(A, b, nf)) {
-            double e = 0.0;
-            for (int a = 0; a < nf; ++a) e -= 0.5 * g[fidx[a]] * b[a];
-            edm = e;
-            if (edm < o.edm_tol) {
-                result = MUSR_OK;
-                break;
-            }
+        if (edm < o.edm_tol) {
+            result = MUSR_OK;
+            break;
         }
         for (int a = 0; a < nf; ++a) {
             b[a] = -g[fidx[a]];
@@ -106,19 +116,39 @@ int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const mus
             if (mu > 1e20) break;
             continue;
         }
+        // predicted decrease of the quadratic model
+        double pred = 0.0;
+        for (int a = 0; a < nf; ++a) {
+            double hb = 0.0;
+            for (int c = 0; c < nf; ++c) hb += H[(size_t)fidx[a] * P + fidx[c]] * b[c];
+            pred -= g[fidx[a]] * b[a] + 0.5 * b[a] * hb;
+        }
         memcpy(trial.data(), theta, sizeof(double) * P);
         for (int a = 0; a < nf; ++a) trial[fidx[a]] += b[a];
         double ft;
         const int s2 = ev(trial.data(), kGN, &ft, gt.data(), Ht.data());
         if (s2 != MUSR_OK && s2 != MUSR_EDOMAIN && s2 != MUSR_ENONFINITE) return s2;
-        if (s2 == MUSR_OK && ft < f) {
+        bool accept = false;
+        double edm_t = INFINITY;
+        if (s2 == MUSR_OK) {
+            const double noise = kValueNoise * fabs(f);
+            if (ft < f) {
+                accept = true;
+            } else if (pred < noise && ft - f < noise) {
+                // the change is below the value resolution: let the gradient decide
+                edm_t = edm_of(gt, Ht, fidx, P, A, b);
+                accept = edm_t < edm;
+            }
+        }
+        if (accept) {
             const double rel = (f - ft) / std::max(fabs(f), 1e-300);
             memcpy(theta, trial.data(), sizeof(double) * P);
             f = ft;
             g.swap(gt);
             H.swap(Ht);
+            edm = std::isfinite(edm_t) ? edm_t : edm_of(g, H, fidx, P, A, b);
             mu = std::max(mu * 0.1, 1e-12);
-            if (rel < 1e-15) {
+            if (rel >= 0.0 && rel < 1e-15 && edm < 1e3 * o.edm_tol) {
                 result = MUSR_OK;
                 break;
             }
@@ -197,6 +227,20 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
                 ok = true;
                 break;
             }
+            if (st == MUSR_OK && -step * slope < kValueNoise * fabs(f) &&
+                fn - f < kValueNoise * fabs(f)) {
+                // below the value resolution: accept if the gradient shrinks in the Hi metric
+                double e_new = 0.0;
+                for (int a = 0; a < nf; ++a) {
+                    double v = 0.0;
+                    for (int c = 0; c < nf; ++c) v += Hi[(size_t)a * nf + c] * gn_[fidx[c]];
+                    e_new += 0.5 * gn_[fidx[a]] * v;
+                }
+                if (e_new < edm) {
+                    ok = true;
+                    break;
+                }
+            }
             step *= 0.5;
         }
         if (!ok) break;
@@ -223,7 +267,7 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
                     Hi[(size_t)a * nf + c] += (1.0 + rho * yHy) * rho * s[a] * s[c] -
                                               rho * (Hy[a] * s[c] + s[a] * Hy[c]);
         }
-        if (rel < 1e-15 && it > 1) {
+        if (rel >= 0.0 && rel < 1e-15 && it > 1) {
             result = MUSR_OK;
             break;
         }
@@ -249,7 +293,7 @@ extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* fre
     if (o.max_iter <= 0) o.max_iter = 500;
     if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
     if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
-    if (!(o.fd_rel_h > 0.0)) o.fd_rel_h = 1e-6;
+    if (!(o.fd_rel_h > 0.0)) o.fd_rel_h = 1e-4;
     if (o.method < MUSR_FIT_LM || o.method > MUSR_FIT_BFGS_FD) return MUSR_EINVAL;
     int cur = 0;
     cudaGetDevice(&cur);

@@ -470,6 +470,7 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
 }
 
 musr_run_s::~musr_run_s() {
+    if (fd_batch) musr_batch_destroy(fd_batch);
     for (int o = 0; o < 2; ++o)
         for (int m = 0; m < 3; ++m)
             if (graphs[o][m]) cudaGraphExecDestroy(graphs[o][m]);

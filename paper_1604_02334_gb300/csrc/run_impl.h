@@ -52,6 +52,9 @@ struct musr_run_s {
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     bool own_stream = false;
     cudaGraphExec_t graphs[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    // batched plan over this run alone, used by the central-difference fit
+    musr_batch fd_batch = nullptr;
+    int fd_batch_vec = 0;
 
     int plan(const musr_run_desc* d);
     int build_tiles(int threads);
