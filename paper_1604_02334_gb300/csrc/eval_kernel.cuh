@@ -41,7 +41,7 @@ struct OscConst {
 };
 
 struct HistConst {
-    float n0, bkg, cE, aE_hi, aE_lo, qE;
+    float n0, n0_lo, bkg, cE, aE_hi, aE_lo, qE;  // N0 = n0 + n0_lo (FP32 pair)
     float kfreq;  // 2 pi gamma: dN/dB = dN/d(omega) * 2 pi gamma
     OscConst osc[kMaxOsc];
     float kt_amp, kt_rate, kt_cenv, kt_a_hi, kt_a_lo, kt_b_hi, kt_b_lo;
@@ -97,7 +97,7 @@ __device__ void stage_hist(int part, const int32_t* rt, const double* theta, con
     const double LOG2E = 1.4426950408889634074;
     const double dt = tg.dt, t0 = tg.t0, it = tg.inv_tau;
     if (part == 0) {
-        hc.n0 = (float)role_value(rt, theta, 0);
+        split_hi_lo(role_value(rt, theta, 0), hc.n0, hc.n0_lo);
         hc.bkg = (float)role_value(rt, theta, 1);
         split_hi_lo(dt * it * LOG2E, hc.aE_hi, hc.aE_lo);
         hc.qE = expm1f((float)(-dt * it));
@@ -168,7 +168,7 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
     constexpr int R = 2 + 4 * NOSC + 2 * KT;
     constexpr int G = kBinsPerThread;
     const float nf0 = (float)n0;
-    const float n0p = hc.n0, bkg = hc.bkg;
+    const float n0p = hc.n0, n0lo = hc.n0_lo, bkg = hc.bkg;
     float E = hc.cE * ex2_approx(-fmaf(nf0, hc.aE_hi, nf0 * hc.aE_lo));
     float env[NOSC > 0 ? NOSC : 1], cs[NOSC > 0 ? NOSC : 1], sn[NOSC > 0 ? NOSC : 1];
 #pragma unroll
@@ -201,7 +201,8 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
             GE = fmaf(0.666666667f * (1.f - xk), envk, 0.333333333f * E);
             S = fmaf(hc.kt_amp, GE, S);
         }
-        const float N = fmaf(n0p, S, bkg);
+        // N0 carried as an FP32 pair so its rounding does not bias every bin
+        const float N = fmaf(n0p, S, fmaf(n0lo, S, bkg));
 
         if (MODE == kModel) {
             if (n0 + g < M) model_dst[n0 + g] = N;
