@@ -223,17 +223,20 @@ def run_ours(args):
         mean = mrun.model(theta).astype(np.float64)
     data = W.poisson_counts(mean, seed + rank)
     data_t = torch.tensor(data, dtype=torch.float32, device=dev)
-    run = Run(lay, data_t, stream="torch")
+    run = Run(lay, data_t)
     g = W.rng(seed + 11 + rank)
     n_vec = args.steps + args.warmup
     thetas = np.stack([W.perturb(theta, lay.free, 0.01, g) for _ in range(n_vec)])
     thetas_t = torch.tensor(thetas, dtype=torch.float64, device=dev)
     outs = torch.empty((n_vec, 1 + P), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    # one explicit (non-default) stream carries the flush, the events and the kernel
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
 
     def step(i):
-        run.chi2_grad_device(thetas_t[i], outs[i], MUSR_CHI2, MUSR_VALUE_GRAD)
+        run.chi2_grad_device(thetas_t[i], outs[i], MUSR_CHI2, MUSR_VALUE_GRAD, stream=sptr)
 
     for i in range(args.warmup):
         flush.fill_(i & 255)

@@ -217,6 +217,10 @@ const char* musr_strerror(int code);
 /* Library version string. */
 const char* musr_version(void);
 
+/* Name of the CUDA error behind the most recent MUSR_ECUDA / MUSR_ENOMEM
+ * returned on the calling host thread ("none" if there was none). */
+const char* musr_last_cuda_error(void);
+
 #ifdef __cplusplus
 }
 #endif

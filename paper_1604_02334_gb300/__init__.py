@@ -156,7 +156,7 @@ class Run:
     def chi2_grad_device(self, theta_dev, out_dev, obj=MUSR_CHI2, mode=MUSR_VALUE_GRAD,
                          status_dev=None, stream=None):
         """theta_dev: CUDA FP64 tensor [P]; out_dev: CUDA FP64 tensor, 1 (+P (+P*P)) long."""
-        st = stream if stream is not None else _torch_stream_ptr()
+        st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
         check(_lib.load().musr_chi2_grad_device(
             self.handle, int(obj), int(mode), ctypes.c_void_p(theta_dev.data_ptr()),
             ctypes.c_void_p(out_dev.data_ptr()),

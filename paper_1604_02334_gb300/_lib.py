@@ -108,6 +108,7 @@ SIGNATURES = {
                                 ctypes.POINTER(musr_fit_result)]),
     "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "musr_version": (ctypes.c_char_p, []),
+    "musr_last_cuda_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -133,6 +134,8 @@ def load():
 class MusrError(RuntimeError):
     def __init__(self, code: int, where: str = ""):
         msg = load().musr_strerror(code).decode()
+        if code in (MUSR_ECUDA, MUSR_ENOMEM):
+            msg += " [" + load().musr_last_cuda_error().decode() + "]"
         super().__init__(f"{where}: {msg} ({code})" if where else f"{msg} ({code})")
         self.code = code
 

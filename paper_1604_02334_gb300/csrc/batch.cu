@@ -55,6 +55,7 @@ struct BatchParams {
     const int32_t* block_ptr;
     const int32_t* block_items;
     const int32_t* run_items;
+    const int64_t* item_slot;  // [n_items] partial offset of each item
     const double* thetas;
     int obj;
     double* partial;
@@ -66,7 +67,7 @@ struct BatchParams {
 template <int NE, int NG, int KT>
 __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p) {
     constexpr int NOSC = NE + NG;
-    constexpr int NPART = 2 + NOSC;
+    constexpr int NPART = stage_parts<NE, NG, KT>();
     constexpr int G = kBinsPerThread;
     extern __shared__ unsigned char smem_raw[];
     HistConst* hcs = reinterpret_cast<HistConst*>(smem_raw);
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
             const int32_t* rt = R.role_theta + (size_t)k * kMaxRoles * 2;
             for (int q = threadIdx.x; q < V * NPART; q += blockDim.x) {
                 const int v = q / NPART, part = q % NPART;
-                stage_hist<NE, NG, KT>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, tg, hcs[v]);
+                stage_hist<NE, NG, KT, false>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, tg, hcs[v]);
             }
         }
         for (int v = threadIdx.x; v < V; v += blockDim.x)
@@ -142,9 +143,18 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
             __threadfence();
             for (int v = threadIdx.x; v < V; v += blockDim.x) {
                 double s = 0.0;
-                for (int j = 0; j < R.n_items; ++j) {
-                    const BatchItem& o = p.items[p.run_items[R.item_first + j]];
-                    s += __ldcg(p.partial + o.slot + v);
+                for (int j0 = 0; j0 < R.n_items; j0 += 8) {
+                    // eight item partials in flight, then added in order
+                    int64_t slot[8];
+                    double x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        slot[u] = j0 + u < R.n_items ? p.item_slot[p.run_items[R.item_first + j0 + u]] : -1;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) x[u] = slot[u] >= 0 ? __ldcg(p.partial + slot[u] + v) : 0.0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (slot[u] >= 0) s += x[u];
                 }
                 const unsigned f = atomicExch(&p.flags[R.val_off + v], 0u);
                 p.values[R.val_off + v] = f ? (double)INFINITY : s;
@@ -158,8 +168,17 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
 template <int NE, int NG, int KT>
 cudaError_t launch_batch_sig(int blocks, int threads, size_t smem, cudaStream_t st, const BatchParams& p) {
     auto kern = batch_kernel<NE, NG, KT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // per-kernel attribute shared by every plan: raise it once to the opt-in maximum
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
     kern<<<blocks, threads, smem, st>>>(p);
     return cudaGetLastError();
 }
@@ -183,11 +202,6 @@ cudaError_t launch_batch(const Signature& s, int blocks, int threads, size_t sme
 using namespace musr;
 
 namespace {
-int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return MUSR_OK;
-    if (e == cudaErrorMemoryAllocation) return MUSR_ENOMEM;
-    return MUSR_ECUDA;
-}
 }  // namespace
 
 // Launch shape chosen by the autotuner.
@@ -215,6 +229,7 @@ struct musr_batch_s {
     BatchRunRef* d_runs = nullptr;
     BatchItem* d_items = nullptr;
     int32_t *d_block_ptr = nullptr, *d_block_items = nullptr, *d_run_items = nullptr;
+    int64_t* d_item_slot = nullptr;
     double *d_partial = nullptr, *d_thetas = nullptr, *d_values = nullptr;
     unsigned *d_run_count = nullptr, *d_flags = nullptr;
     void* h_pinned = nullptr;
@@ -322,6 +337,7 @@ int musr_batch_s::plan(const BatchShape& sh) {
     const size_t o_bp = off; off += al(sizeof(int32_t) * block_ptr.size());
     const size_t o_bi = off; off += al(sizeof(int32_t) * block_items.size() + 4);
     const size_t o_ri = off; off += al(sizeof(int32_t) * run_items.size() + 4);
+    const size_t o_is = off; off += al(sizeof(int64_t) * items.size() + 8);
     const size_t o_part = off; off += al(sizeof(double) * (size_t)(partial_len + 1));
     const size_t o_rc = off; off += al(sizeof(unsigned) * (runs.size() + 1));
     const size_t o_fl = off; off += al(sizeof(unsigned) * (size_t)(total_vals + 1));
@@ -335,6 +351,7 @@ int musr_batch_s::plan(const BatchShape& sh) {
     d_block_ptr = reinterpret_cast<int32_t*>(b + o_bp);
     d_block_items = reinterpret_cast<int32_t*>(b + o_bi);
     d_run_items = reinterpret_cast<int32_t*>(b + o_ri);
+    d_item_slot = reinterpret_cast<int64_t*>(b + o_is);
     d_partial = reinterpret_cast<double*>(b + o_part);
     d_run_count = reinterpret_cast<unsigned*>(b + o_rc);
     d_flags = reinterpret_cast<unsigned*>(b + o_fl);
@@ -347,6 +364,9 @@ int musr_batch_s::plan(const BatchShape& sh) {
     up(d_block_ptr, block_ptr.data(), sizeof(int32_t) * block_ptr.size());
     up(d_block_items, block_items.data(), sizeof(int32_t) * block_items.size());
     up(d_run_items, run_items.data(), sizeof(int32_t) * run_items.size());
+    std::vector<int64_t> item_slot(items.size());
+    for (size_t i = 0; i < items.size(); ++i) item_slot[i] = items[i].slot;
+    up(d_item_slot, item_slot.data(), sizeof(int64_t) * item_slot.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(d_run_count, 0, sizeof(unsigned) * (runs.size() + 1), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_flags, 0, sizeof(unsigned) * (size_t)(total_vals + 1), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
@@ -365,6 +385,7 @@ BatchParams musr_batch_s::params(int obj, const double* thetas, double* values) 
     p.block_ptr = d_block_ptr;
     p.block_items = d_block_items;
     p.run_items = d_run_items;
+    p.item_slot = d_item_slot;
     p.thetas = thetas;
     p.obj = obj;
     p.partial = d_partial;

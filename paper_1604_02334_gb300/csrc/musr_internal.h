@@ -15,6 +15,22 @@ constexpr int kMaxRoles = 2 + 4 * kMaxOsc + 2;     // N0, bkg, 4 per line, 2 for
 constexpr int kBinsPerThread = 8;                  // consecutive bins per thread (2 x float4)
 constexpr int kMaxThreads = 256;                   // block size upper bound
 constexpr int kMaxWarps = kMaxThreads / 32;
+constexpr int kInlineHists = 32;                   // constants passed inside the launch parameters
+
+// Per-histogram constants of the theory, staged once per evaluation (the
+// paper's kernel keeps the parameter / map values in shared memory for the
+// same reason, Sec. 4.2.2: every thread reads them many times).
+struct OscConst {
+    float amp, rate, cenv, a_hi, a_lo, b_hi, b_lo, q, cm1, sn;
+    unsigned long long ph0, step;  // phase at bin 0 and per bin, 64-bit fixed-point turns
+};
+
+struct HistConst {
+    float n0, n0_lo, bkg, cE, aE_hi, aE_lo, qE;  // N0 = n0 + n0_lo (FP32 pair)
+    float kfreq;  // 2 pi gamma: dN/dB = dN/d(omega) * 2 pi gamma
+    OscConst osc[kMaxOsc];
+    float kt_amp, kt_rate, kt_cenv, kt_a_hi, kt_a_lo, kt_b_hi, kt_b_lo;
+};
 
 // Kernel "signature": how many precession lines of each relaxation kind and
 // whether a static Gaussian Kubo-Toyabe term is present.  Exponential lines
@@ -40,23 +56,32 @@ struct EvalParams {
     const int32_t* hist_nbins;    // [K]
     const int32_t* tile_hist;     // [n_tiles]
     const int32_t* tile_start;    // [n_tiles] first bin of the tile
-    const int32_t* hist_first_tile;  // [K]
-    const int32_t* hist_ntiles;      // [K]
     const int32_t* role_theta;    // [K][kMaxRoles][2] theta indices (or -1) per role
-    const double* theta;          // [P]
+    const double* theta;          // [P] on the device (device calls)
     double t0, dt, inv_tau, gamma;
     int K, P, obj;
-    // reduction scratch
-    double* partial;              // [n_tiles][nacc]
-    double* hist_sum;             // [K][nacc]
-    unsigned* hist_count;         // [K]   (self-resetting)
+    // staged constants, reduction scratch
+    HistConst* hconst;            // [K] written by the stage kernel (device calls)
+    double* partial;              // [n_clusters][nacc] double-float pairs
+    double* hist_sum;             // [K][nacc] pairs (when they do not fit in shared memory)
     unsigned* global_count;       // [1]   (self-resetting)
     unsigned* flags;              // [1]   (self-resetting)
+    const int32_t* cluster_hist;        // [n_clusters]
+    const int32_t* hist_first_cluster;  // [K]
+    const int32_t* hist_nclusters;      // [K]
+    int n_clusters, cluster;      // clusters of `cluster` consecutive tiles of one histogram
     const int32_t* csr_ptr;       // [n_out + 1]
     const int32_t* csr_src;       // sources: k * nacc + acc
     int n_out;
+    int n_src;                    // csr_src length
+    int win_doubles;              // shared-memory window for cluster partials
+    int hsum_in_smem, csr_in_smem;
+    int smem_bytes;               // dynamic shared memory of the objective kernel
     double* out;                  // [n_out]
     int32_t* status_out;          // [1] or null
+    int hconst_ready;             // 1: hconst already holds this call's constants (host-staged)
+    int hconst_inline_n;          // > 0: hconst_inline holds the K histograms' constants
+    HistConst hconst_inline[kInlineHists];
     // model output (kModel)
     float* model_out;
     const int64_t* model_off;     // [K] offsets into model_out
@@ -65,5 +90,13 @@ struct EvalParams {
 // Launch the objective kernel for a signature / mode (eval_*.cu).
 cudaError_t launch_eval(const Signature& sig, int mode, int threads, int n_tiles,
                         cudaStream_t stream, const EvalParams& p);
+
+// Map a CUDA error to a status code, remembering its name for
+// musr_last_cuda_error() (per host thread).
+int cuda_status(cudaError_t e);
+
+// Stage every histogram's constants on the host (FP64), as the device would.
+void stage_host(const Signature& sig, int K, const int32_t* role_theta, const double* theta,
+                double t0, double dt, double inv_tau, double gamma, HistConst* out);
 
 }  // namespace musr

@@ -14,6 +14,7 @@
 #include <utility>
 #include <vector>
 
+#include "eval_kernel.cuh"
 #include "musr_internal.h"
 #include "run_impl.h"
 
@@ -33,6 +34,39 @@ cudaError_t launch_eval(const Signature& s, int mode, int threads, int n_tiles, 
         case kModel: return launch_eval_mode3(s, threads, n_tiles, st, p);
     }
     return cudaErrorInvalidValue;
+}
+
+template <int NE, int NG, int KT>
+void stage_host_sig(int K, const int32_t* role_theta, const double* theta, const TimeGrid& tg,
+                    HistConst* out) {
+    for (int k = 0; k < K; ++k) {
+        memset(&out[k], 0, sizeof(HistConst));
+        for (int part = 0; part < stage_parts<NE, NG, KT>(); ++part)
+            stage_hist<NE, NG, KT, true>(part, role_theta + (size_t)k * kMaxRoles * 2, theta, tg, out[k]);
+    }
+}
+
+void stage_host(const Signature& s, int K, const int32_t* role_theta, const double* theta, double t0,
+                double dt, double inv_tau, double gamma, HistConst* out) {
+    const TimeGrid tg{t0, dt, inv_tau, gamma};
+#define MUSR_CASE(NE, NG, KT) \
+    if (s.ne == NE && s.ng == NG && s.kt == KT) return stage_host_sig<NE, NG, KT>(K, role_theta, theta, tg, out);
+    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
+    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
+    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
+    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
+    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
+    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+#undef MUSR_CASE
+}
+
+thread_local const char* g_last_cuda_error = "none";
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MUSR_OK;
+    g_last_cuda_error = cudaGetErrorName(e);
+    if (e == cudaErrorMemoryAllocation) return MUSR_ENOMEM;
+    return MUSR_ECUDA;
 }
 
 // Copy concatenated counts (FP32 or FP64, device) into the padded FP32 layout.
@@ -68,11 +102,6 @@ struct DeviceGuard {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-int cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return MUSR_OK;
-    if (e == cudaErrorMemoryAllocation) return MUSR_ENOMEM;
-    return MUSR_ECUDA;
-}
 
 int map_col(const musr_run_s* r, int k, int col) {
     if (col < 0) return -1;
@@ -172,10 +201,28 @@ int musr_run_s::plan(const musr_run_desc* d) {
 int musr_run_s::build_tiles(int t) {
     threads = t;
     tile_bins = t * kBinsPerThread;
+    // cluster size: the largest of 8, 4, 2, 1 whose padding (every histogram's
+    // tiles rounded up to whole clusters) adds at most 25 % empty tiles
+    std::vector<int64_t> nt(K);
+    int64_t raw = 0;
+    for (int k = 0; k < K; ++k) {
+        nt[k] = std::max<int64_t>(1, (n_bins[k] + tile_bins - 1) / tile_bins);
+        raw += nt[k];
+    }
+    cluster = 1;
+    for (int c = 8; c >= 2; c >>= 1) {
+        int64_t padded = 0;
+        for (int k = 0; k < K; ++k) padded += (nt[k] + c - 1) / c * c;
+        if (padded * 4 <= raw * 5) {
+            cluster = c;
+            break;
+        }
+    }
     tile_hist.clear();
     tile_start.clear();
-    hist_first_tile.assign(K, 0);
-    hist_ntiles.assign(K, 0);
+    cluster_hist.clear();
+    hist_first_cluster.assign(K, 0);
+    hist_nclusters.assign(K, 0);
     hist_off.assign(K, 0);
     model_off.assign(K, 0);
     int64_t off = 0, moff = 0;
@@ -184,16 +231,18 @@ int musr_run_s::build_tiles(int t) {
         model_off[k] = moff;
         off += round_up(n_bins[k], 8);
         moff += n_bins[k];
-        const int64_t nt = std::max<int64_t>(1, (n_bins[k] + tile_bins - 1) / tile_bins);
-        hist_first_tile[k] = (int32_t)tile_hist.size();
-        hist_ntiles[k] = (int32_t)nt;
-        for (int64_t j = 0; j < nt; ++j) {
+        const int64_t ncl = (nt[k] + cluster - 1) / cluster;
+        hist_first_cluster[k] = (int32_t)cluster_hist.size();
+        hist_nclusters[k] = (int32_t)ncl;
+        for (int64_t j = 0; j < ncl * cluster; ++j) {
             tile_hist.push_back(k);
-            tile_start.push_back((int32_t)(j * tile_bins));
+            tile_start.push_back((int32_t)std::min<int64_t>(j * tile_bins, round_up(n_bins[k], 8)));
         }
+        for (int64_t c = 0; c < ncl; ++c) cluster_hist.push_back(k);
     }
     data_floats = (size_t)off + 8;
     n_tiles = (int)tile_hist.size();
+    n_clusters = (int)cluster_hist.size();
     return MUSR_OK;
 }
 
@@ -255,6 +304,16 @@ int musr_run_s::allocate() {
         if (m == kGN && P > kMaxGnParams) continue;
         build_csr(m, ptr[m], src[m]);
         n_out[m] = (int)ptr[m].size() - 1;
+        n_src[m] = (int)src[m].size();
+        // tail of the objective kernel: a window of cluster partials, the
+        // histogram sums and the CSR in shared memory when they fit
+        const int nacc = n_acc(m, R);
+        const int w = std::max(nacc, std::min(n_clusters * nacc, 4096 / nacc * nacc));
+        win_doubles[m] = w;
+        hsum_in_smem[m] = (size_t)K * nacc * 8 <= 64 * 1024;
+        csr_in_smem[m] = ((size_t)n_out[m] + 1 + n_src[m]) * 4 <= 64 * 1024;
+        smem_bytes[m] = (int)(8 * ((size_t)w + (hsum_in_smem[m] ? (size_t)K * nacc : 0)) +
+                              (csr_in_smem[m] ? 4 * ((size_t)n_out[m] + 1 + n_src[m]) : 0));
     }
     const int n_out_max = n_out[P <= kMaxGnParams ? kGN : kGrad];
     Arena A;
@@ -264,17 +323,19 @@ int musr_run_s::allocate() {
     const size_t o_nb = A.take<int32_t>(K + 1);
     const size_t o_th = A.take<int32_t>(n_tiles);
     const size_t o_ts = A.take<int32_t>(n_tiles);
+    const size_t o_ch = A.take<int32_t>(n_clusters + 1);
     const size_t o_hf = A.take<int32_t>(K + 1);
     const size_t o_hn = A.take<int32_t>(K + 1);
+    const size_t o_hc = A.take<HistConst>(K + 1);
     const size_t o_rt = A.take<int32_t>(role_theta.size() + 1);
     size_t o_ptr[3], o_src[3];
     for (int m = 0; m < 3; ++m) {
         o_ptr[m] = A.take<int32_t>(ptr[m].size() + 1);
         o_src[m] = A.take<int32_t>(src[m].size() + 1);
     }
-    const size_t o_part = A.take<double>((size_t)n_tiles * nacc_max);
+    const size_t o_part = A.take<double>((size_t)n_clusters * nacc_max);
     const size_t o_hsum = A.take<double>((size_t)(K + 1) * nacc_max);
-    const size_t o_cnt = A.take<unsigned>(K + 2);
+    const size_t o_cnt = A.take<unsigned>(4);
     const size_t o_theta = A.take<double>(P + 1);
     const size_t o_out = A.take<double>(n_out_max + 1);
     const size_t o_status = A.take<int32_t>(2);
@@ -290,8 +351,10 @@ int musr_run_s::allocate() {
     d_hist_nbins = reinterpret_cast<int32_t*>(b + o_nb);
     d_tile_hist = reinterpret_cast<int32_t*>(b + o_th);
     d_tile_start = reinterpret_cast<int32_t*>(b + o_ts);
-    d_hist_first_tile = reinterpret_cast<int32_t*>(b + o_hf);
-    d_hist_ntiles = reinterpret_cast<int32_t*>(b + o_hn);
+    d_cluster_hist = reinterpret_cast<int32_t*>(b + o_ch);
+    d_hist_first_cluster = reinterpret_cast<int32_t*>(b + o_hf);
+    d_hist_nclusters = reinterpret_cast<int32_t*>(b + o_hn);
+    d_hconst = reinterpret_cast<HistConst*>(b + o_hc);
     d_role_theta = reinterpret_cast<int32_t*>(b + o_rt);
     for (int m = 0; m < 3; ++m) {
         d_csr_ptr[m] = reinterpret_cast<int32_t*>(b + o_ptr[m]);
@@ -305,13 +368,22 @@ int musr_run_s::allocate() {
     d_status = reinterpret_cast<int32_t*>(b + o_status);
     d_theta_tmp = reinterpret_cast<double*>(b + o_tmp);
 
-    if (cudaMallocHost(&h_pinned, sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64) != cudaSuccess) {
+    // host staging, mapped so the kernel writes host-call results straight
+    // into it (no copy node after the kernel)
+    if (cudaHostAlloc(&h_pinned, sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64 +
+                                     sizeof(HistConst) * (size_t)(K + 1),
+                      cudaHostAllocMapped) != cudaSuccess) {
         h_pinned = nullptr;
         return MUSR_ENOMEM;
     }
     h_theta = static_cast<double*>(h_pinned);
     h_out = h_theta + P + 1;
     h_status = reinterpret_cast<int32_t*>(h_out + n_out_max + 1);
+    h_hconst = reinterpret_cast<HistConst*>(static_cast<char*>(h_pinned) +
+                                            ((sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64 + 15) / 16 * 16));
+    if (cudaHostGetDevicePointer((void**)&hd_out, h_out, 0) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&hd_status, h_status, 0) != cudaSuccess)
+        return MUSR_ECUDA;
 
     // static tables
     std::vector<int32_t> nb32(K);
@@ -325,14 +397,21 @@ int musr_run_s::allocate() {
     up(d_hist_nbins, nb32.data(), sizeof(int32_t) * K);
     up(d_tile_hist, tile_hist.data(), sizeof(int32_t) * n_tiles);
     up(d_tile_start, tile_start.data(), sizeof(int32_t) * n_tiles);
-    up(d_hist_first_tile, hist_first_tile.data(), sizeof(int32_t) * K);
-    up(d_hist_ntiles, hist_ntiles.data(), sizeof(int32_t) * K);
+    up(d_cluster_hist, cluster_hist.data(), sizeof(int32_t) * n_clusters);
+    up(d_hist_first_cluster, hist_first_cluster.data(), sizeof(int32_t) * K);
+    up(d_hist_nclusters, hist_nclusters.data(), sizeof(int32_t) * K);
     up(d_role_theta, role_theta.data(), sizeof(int32_t) * role_theta.size());
     for (int m = 0; m < 3; ++m) {
         up(d_csr_ptr[m], ptr[m].data(), sizeof(int32_t) * ptr[m].size());
         up(d_csr_src[m], src[m].data(), sizeof(int32_t) * src[m].size());
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * (K + 2), stream);
+    // opt the kernels whose reduction tail needs > 48 KB of shared memory in
+    for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
+        if (m == kGN && P > kMaxGnParams) continue;
+        EvalParams q = params(MUSR_CHI2, m, d_theta, d_out, d_status);
+        e = launch_eval(sig, m, threads, 0, stream, q);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_data, 0, sizeof(float) * data_floats, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     return cuda_status(e);
@@ -393,8 +472,6 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.hist_nbins = d_hist_nbins;
     p.tile_hist = d_tile_hist;
     p.tile_start = d_tile_start;
-    p.hist_first_tile = d_hist_first_tile;
-    p.hist_ntiles = d_hist_ntiles;
     p.role_theta = d_role_theta;
     p.theta = theta_dev;
     p.t0 = t0;
@@ -404,15 +481,25 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.K = K;
     p.P = P;
     p.obj = obj;
+    p.hconst = d_hconst;
     p.partial = d_partial;
     p.hist_sum = d_hist_sum;
-    p.hist_count = d_counters;
-    p.global_count = d_counters + K;
-    p.flags = d_counters + K + 1;
+    p.global_count = d_counters;
+    p.flags = d_counters + 1;
+    p.cluster_hist = d_cluster_hist;
+    p.hist_first_cluster = d_hist_first_cluster;
+    p.hist_nclusters = d_hist_nclusters;
+    p.n_clusters = n_clusters;
+    p.cluster = mode == kModel ? 1 : cluster;
     const int m = mode == kModel ? kValue : mode;
     p.csr_ptr = d_csr_ptr[m];
     p.csr_src = d_csr_src[m];
     p.n_out = n_out[m];
+    p.n_src = n_src[m];
+    p.win_doubles = win_doubles[m];
+    p.hsum_in_smem = hsum_in_smem[m];
+    p.csr_in_smem = csr_in_smem[m];
+    p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
     p.out = out_dev;
     p.status_out = status_dev;
     p.model_off = d_model_off;
@@ -441,27 +528,20 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
         *flags = 0;
         return MUSR_OK;
     }
+    // one launch: the histogram constants are staged here in FP64 and travel
+    // inline in the launch parameters (through device memory beyond
+    // kInlineHists histograms); results land in mapped host memory
+    EvalParams p = params(obj, mode, nullptr, hd_out, hd_status);
     cudaError_t e = cudaSuccess;
-    if (!graphs[obj][mode]) {
-        cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * P, cudaMemcpyHostToDevice, cap_stream);
-            EvalParams p = params(obj, mode, d_theta, d_out, d_status);
-            launch_eval(sig, mode, threads, n_tiles, cap_stream, p);
-            cudaMemcpyAsync(h_out, d_out, sizeof(double) * nout, cudaMemcpyDeviceToHost, cap_stream);
-            cudaMemcpyAsync(h_status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, cap_stream);
-            e = cudaStreamEndCapture(cap_stream, &g);
-        }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&graphs[obj][mode], g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
-            graphs[obj][mode] = nullptr;
-            return cuda_status(e);
-        }
+    if (K <= kInlineHists) {
+        stage_host(sig, K, role_theta.data(), theta, t0, dt, 1.0 / tau, gamma, p.hconst_inline);
+        p.hconst_inline_n = K;
+    } else {
+        stage_host(sig, K, role_theta.data(), theta, t0, dt, 1.0 / tau, gamma, h_hconst);
+        e = cudaMemcpyAsync(d_hconst, h_hconst, sizeof(HistConst) * K, cudaMemcpyHostToDevice, stream);
+        p.hconst_ready = 1;
     }
-    memcpy(h_theta, theta, sizeof(double) * P);
-    e = cudaGraphLaunch(graphs[obj][mode], stream);
+    if (e == cudaSuccess) e = launch_eval(sig, mode, threads, n_tiles, stream, p);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(e);
     memcpy(out_host, h_out, sizeof(double) * nout);
@@ -471,9 +551,6 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
 
 musr_run_s::~musr_run_s() {
     if (fd_batch) musr_batch_destroy(fd_batch);
-    for (int o = 0; o < 2; ++o)
-        for (int m = 0; m < 3; ++m)
-            if (graphs[o][m]) cudaGraphExecDestroy(graphs[o][m]);
     if (arena) cudaFree(arena);
     if (h_pinned) cudaFreeHost(h_pinned);
     if (cap_stream) cudaStreamDestroy(cap_stream);
@@ -624,5 +701,7 @@ const char* musr_strerror(int code) {
 }
 
 const char* musr_version(void) { return "musr-gb300 0.1 (sm_103a)"; }
+
+const char* musr_last_cuda_error(void) { return g_last_cuda_error; }
 
 }  // extern "C"

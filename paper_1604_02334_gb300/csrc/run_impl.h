@@ -28,7 +28,8 @@ struct musr_run_s {
     std::vector<int32_t> role_theta;  // [K][kMaxRoles][2]
     // tiling
     int threads = 256, tile_bins = 2048, n_tiles = 0;
-    std::vector<int32_t> tile_hist, tile_start, hist_first_tile, hist_ntiles;
+    int cluster = 1, n_clusters = 0;  // clusters of `cluster` consecutive tiles, one histogram each
+    std::vector<int32_t> tile_hist, tile_start, cluster_hist, hist_first_cluster, hist_nclusters;
     std::vector<int64_t> hist_off, model_off;
     size_t data_floats = 0;
     // device memory (one arena)
@@ -36,22 +37,30 @@ struct musr_run_s {
     float* d_data = nullptr;
     int64_t *d_hist_off = nullptr, *d_model_off = nullptr;
     int32_t *d_hist_nbins = nullptr, *d_tile_hist = nullptr, *d_tile_start = nullptr;
-    int32_t *d_hist_first_tile = nullptr, *d_hist_ntiles = nullptr, *d_role_theta = nullptr;
+    int32_t *d_cluster_hist = nullptr, *d_hist_first_cluster = nullptr, *d_hist_nclusters = nullptr;
+    int32_t* d_role_theta = nullptr;
+    musr::HistConst* d_hconst = nullptr;
+    musr::HistConst* h_hconst = nullptr;  // pinned
     int32_t* d_csr_ptr[3] = {nullptr, nullptr, nullptr};
     int32_t* d_csr_src[3] = {nullptr, nullptr, nullptr};
     int n_out[3] = {0, 0, 0};
+    int n_src[3] = {0, 0, 0};
+    // dynamic shared memory of the reduction tail per mode
+    int win_doubles[3] = {0, 0, 0}, hsum_in_smem[3] = {0, 0, 0}, csr_in_smem[3] = {0, 0, 0};
+    int smem_bytes[3] = {0, 0, 0};
     double *d_partial = nullptr, *d_hist_sum = nullptr;
-    unsigned* d_counters = nullptr;  // [K] per-histogram tickets, [1] global ticket, [1] flags
+    unsigned* d_counters = nullptr;  // [0] global ticket, [1] flags
     double *d_theta = nullptr, *d_out = nullptr, *d_theta_tmp = nullptr;
     int32_t* d_status = nullptr;
     // pinned staging for host-pointer calls
     void* h_pinned = nullptr;
     double *h_theta = nullptr, *h_out = nullptr;
     int32_t* h_status = nullptr;
-    // streams and cached graphs [objective][mode]
+    double* hd_out = nullptr;     // device view of h_out
+    int32_t* hd_status = nullptr; // device view of h_status
+    // streams
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     bool own_stream = false;
-    cudaGraphExec_t graphs[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     // batched plan over this run alone, used by the central-difference fit
     musr_batch fd_batch = nullptr;
     int fd_batch_vec = 0;

@@ -199,9 +199,15 @@ def test_device_path_and_autograd(md_small):
         t = torch.tensor(th, dtype=torch.float64, device=dev, requires_grad=True)
         v = Chi2.apply(t, run, MUSR_CHI2)
         (gt,) = torch.autograd.grad(v * 3.0, t)
+        ref = torch.empty(1 + lay.n_params, dtype=torch.float64, device=dev)
+        run.chi2_grad_device(t.detach(), ref, MUSR_CHI2, 1)
         torch.cuda.synchronize()
-        assert float(v) == v_host
-        np.testing.assert_array_equal(gt.cpu().numpy(), 3.0 * g_host)
+        # autograd plumbing is exact against the device entry point it wraps
+        assert float(v.detach()) == float(ref[0])
+        np.testing.assert_array_equal(gt.cpu().numpy(), 3.0 * ref[1:].cpu().numpy())
+        # device calls stage constants with FP32 functions, host calls in FP64
+        assert rel_err(float(v.detach()), v_host) <= 1e-7
+        assert grad_rel_err(ref[1:].cpu().numpy(), g_host) <= 1e-6
         out = torch.empty(1 + lay.n_params + lay.n_params ** 2, dtype=torch.float64, device=dev)
         st = torch.zeros(1, dtype=torch.int32, device=dev)
         run.chi2_grad_device(t.detach(), out, MUSR_POISSON, 2, st)
