@@ -217,6 +217,37 @@ const char* musr_strerror(int code);
 /* Library version string. */
 const char* musr_version(void);
 
+/*
+ * Allocation-free evaluation.  (No counterpart in the paper: an interface
+ * addition of this library.)  For callers that cannot call cudaMalloc --
+ * e.g. code running while another framework owns the device memory pool, or
+ * acquisition software that forbids allocation once it runs -- this entry
+ * point evaluates the objective (mode MUSR_VALUE) or the objective and its
+ * gradient (MUSR_VALUE_GRAD) without allocating anything: all scratch lives
+ * in one static device array of MUSR_NOALLOC_SCRATCH_BYTES inside the
+ * library, held on every GPU that loads the library until the process ends.
+ *   desc        layout as for musr_create_run; data must be FP32 on the device
+ *               (data_on_device != 0, data_dtype == MUSR_F32); desc->stream
+ *               is ignored.
+ *   theta_dev   FP64 [n_params] on the device.
+ *   out_dev     FP64 on the device: [value] or [value, grad[n_params]].
+ *   status_dev  int32 on the device or NULL (bit 1: deviance domain error).
+ *   stream      cudaStream_t; the call is asynchronous on it.
+ * Limits: n_hist <= MUSR_NOALLOC_MAX_HIST, n_params <= MUSR_NOALLOC_MAX_PARAMS,
+ * and the padded histograms plus tables must fit the scratch array (about 8e6
+ * bins); anything larger returns MUSR_ENOTSUP, as do other modes or FP64 data.
+ * Every call shares the one array and rewrites it, so calls whose work
+ * overlaps on the GPU (different streams or host threads) race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.
+ */
+#define MUSR_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define MUSR_NOALLOC_MAX_HIST 64
+#define MUSR_NOALLOC_MAX_PARAMS 256
+int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mode, const double* theta_dev,
+                           double* out_dev, int32_t* status_dev, void* stream);
+
 /* Name of the CUDA error behind the most recent MUSR_ECUDA / MUSR_ENOMEM
  * returned on the calling host thread ("none" if there was none). */
 const char* musr_last_cuda_error(void);

@@ -109,6 +109,8 @@ SIGNATURES = {
     "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "musr_version": (ctypes.c_char_p, []),
     "musr_last_cuda_error": (ctypes.c_char_p, []),
+    "musr_chi2_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(musr_run_desc), ctypes.c_int, ctypes.c_int,
+                                              _vp, _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -1,0 +1,341 @@
+// musr_chi2_grad_noalloc: the objective / adjoint evaluation for callers that
+// cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs while another framework
+// owns the device's memory pool, real-time acquisition processes that forbid
+// allocation after start-up, or plug-ins whose host application hands them
+// only pre-allocated device buffers.  For them this entry point keeps every
+// piece of scratch the evaluation needs (tiling tables, the parameter map,
+// the staged per-histogram constants, the reduction partials and a padded
+// copy of the histograms) in one file-scope device array of a fixed size,
+// MUSR_NOALLOC_SCRATCH_BYTES.  The array belongs to this library's module:
+// every GPU that loads it holds the array until the process exits.  The
+// entry point itself calls no cudaMalloc, cudaFree or other allocating
+// routine, on the device or on the host.
+//
+// Host code cannot use the array's name as a device address, so the first
+// call on each device looks the address up with cudaGetSymbolAddress (that
+// device current) and keeps it; later calls reuse it.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+
+#include "eval_kernel.cuh"
+#include "musr.h"
+#include "musr_internal.h"
+
+namespace musr {
+namespace {
+
+constexpr size_t kScratchBytes = MUSR_NOALLOC_SCRATCH_BYTES;
+constexpr int kNaMaxHist = MUSR_NOALLOC_MAX_HIST;
+constexpr int kNaMaxParams = MUSR_NOALLOC_MAX_PARAMS;
+constexpr int kNaMaxTiles = 1 << 13;
+
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
+
+// Host-side plan of one call, built in a static buffer under a mutex (no
+// heap use); the device work itself is asynchronous.
+struct NaPlan {
+    int K, P, R, threads, tile_bins, cluster, n_tiles, n_clusters, n_out, n_src;
+    Signature sig;
+    int64_t hist_off[kNaMaxHist];
+    int32_t hist_nbins[kNaMaxHist];
+    int32_t hist_first_cluster[kNaMaxHist], hist_nclusters[kNaMaxHist];
+    int32_t role_theta[kNaMaxHist * kMaxRoles * 2];
+    int32_t tile_hist[kNaMaxTiles], tile_start[kNaMaxTiles], cluster_hist[kNaMaxTiles];
+    int32_t csr_ptr[kNaMaxParams + 2];
+    int32_t csr_src[kNaMaxHist * (1 + 2 * kMaxRoles)];
+    int32_t csr_cnt[kNaMaxParams + 2];
+    int64_t data_floats;
+};
+NaPlan g_plan;
+std::mutex g_plan_mutex;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int col_theta(const musr_run_desc* d, int k, int col) {
+    return col < 0 ? -1 : d->map[(int64_t)k * d->map_width + col];
+}
+
+int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
+    pl.K = d->n_hist;
+    pl.P = d->n_params;
+    if (pl.K < 1 || pl.K > kNaMaxHist || pl.P < 1 || pl.P > kNaMaxParams) return MUSR_ENOTSUP;
+    if (d->map_width < 2 || d->map_width > 32 || d->n_comp < 0 || !d->n_bins || !d->map) return MUSR_EINVAL;
+    if (d->n_comp > 0 && !d->comp) return MUSR_EINVAL;
+    if (!(d->dt_us > 0.0) || !(d->tau_us > 0.0)) return MUSR_EINVAL;
+    int exp_c[kMaxOsc], gau_c[kMaxOsc], ne = 0, ng = 0, kt_c = -1;
+    for (int c = 0; c < d->n_comp; ++c) {
+        const musr_component& m = d->comp[c];
+        const int cols[5] = {m.amp, m.rate, m.field, m.field2, m.phase};
+        for (int j = 0; j < 5; ++j)
+            if (cols[j] < -1 || cols[j] >= d->map_width) return MUSR_EINVAL;
+        if (m.kind == MUSR_TF_EXP || m.kind == MUSR_TF_GAUSS) {
+            if (ne + ng >= kMaxOsc) return MUSR_ENOTSUP;
+            if (m.kind == MUSR_TF_EXP) exp_c[ne++] = c;
+            else gau_c[ng++] = c;
+        } else if (m.kind == MUSR_KT_STATIC_GAUSS) {
+            if (kt_c >= 0) return MUSR_ENOTSUP;
+            kt_c = c;
+        } else {
+            return MUSR_EINVAL;
+        }
+    }
+    pl.sig.ne = ne;
+    pl.sig.ng = ng;
+    pl.sig.kt = kt_c >= 0;
+    pl.R = pl.sig.roles();
+    int osc[kMaxOsc];
+    for (int i = 0; i < ne; ++i) osc[i] = exp_c[i];
+    for (int i = 0; i < ng; ++i) osc[ne + i] = gau_c[i];
+    for (int k = 0; k < pl.K; ++k) {
+        if (d->n_bins[k] < 0) return MUSR_EINVAL;
+        if (d->n_bins[k] > (int64_t(1) << 24)) return MUSR_ENOTSUP;
+        for (int c = 0; c < d->map_width; ++c) {
+            const int i = d->map[(int64_t)k * d->map_width + c];
+            if (i < -1 || i >= pl.P) return MUSR_EINVAL;
+        }
+        int32_t* rt = pl.role_theta + (size_t)k * kMaxRoles * 2;
+        for (int i = 0; i < kMaxRoles * 2; ++i) rt[i] = -1;
+        rt[0] = col_theta(d, k, 0);
+        rt[2] = col_theta(d, k, 1);
+        for (int s = 0; s < ne + ng; ++s) {
+            const musr_component& m = d->comp[osc[s]];
+            int32_t* q = rt + 2 * (2 + 4 * s);
+            q[0] = col_theta(d, k, m.amp);
+            q[2] = col_theta(d, k, m.rate);
+            q[4] = col_theta(d, k, m.field);
+            q[5] = col_theta(d, k, m.field2);
+            q[6] = col_theta(d, k, m.phase);
+        }
+        if (kt_c >= 0) {
+            const musr_component& m = d->comp[kt_c];
+            int32_t* q = rt + 2 * (2 + 4 * (ne + ng));
+            q[0] = col_theta(d, k, m.amp);
+            q[2] = col_theta(d, k, m.rate);
+        }
+    }
+    // tiling: the largest block that still gives >= 2 blocks per SM, clusters of
+    // up to 8 tiles with at most 25 % padding
+    pl.threads = 32;
+    for (int t = kMaxThreads; t >= 32; t >>= 1) {
+        int64_t tiles = 0;
+        for (int k = 0; k < pl.K; ++k)
+            tiles += std::max<int64_t>(1, (d->n_bins[k] + t * kBinsPerThread - 1) / (t * kBinsPerThread));
+        if (tiles >= 2 * sms) {
+            pl.threads = t;
+            break;
+        }
+    }
+    pl.tile_bins = pl.threads * kBinsPerThread;
+    int64_t raw = 0;
+    for (int k = 0; k < pl.K; ++k) raw += std::max<int64_t>(1, (d->n_bins[k] + pl.tile_bins - 1) / pl.tile_bins);
+    pl.cluster = 1;
+    for (int c = 8; c >= 2; c >>= 1) {
+        int64_t padded = 0;
+        for (int k = 0; k < pl.K; ++k) {
+            const int64_t nt = std::max<int64_t>(1, (d->n_bins[k] + pl.tile_bins - 1) / pl.tile_bins);
+            padded += (nt + c - 1) / c * c;
+        }
+        if (padded * 4 <= raw * 5) {
+            pl.cluster = c;
+            break;
+        }
+    }
+    int64_t off = 0;
+    pl.n_tiles = 0;
+    pl.n_clusters = 0;
+    for (int k = 0; k < pl.K; ++k) {
+        const int64_t M = d->n_bins[k];
+        pl.hist_off[k] = off;
+        pl.hist_nbins[k] = (int32_t)M;
+        off += round_up(M, 8);
+        const int64_t nt = std::max<int64_t>(1, (M + pl.tile_bins - 1) / pl.tile_bins);
+        const int64_t ncl = (nt + pl.cluster - 1) / pl.cluster;
+        if (pl.n_tiles + ncl * pl.cluster > kNaMaxTiles) return MUSR_ENOTSUP;
+        pl.hist_first_cluster[k] = pl.n_clusters;
+        pl.hist_nclusters[k] = (int32_t)ncl;
+        for (int64_t j = 0; j < ncl * pl.cluster; ++j) {
+            pl.tile_hist[pl.n_tiles] = k;
+            pl.tile_start[pl.n_tiles] = (int32_t)std::min<int64_t>(j * pl.tile_bins, round_up(M, 8));
+            ++pl.n_tiles;
+        }
+        for (int64_t c = 0; c < ncl; ++c) pl.cluster_hist[pl.n_clusters++] = k;
+    }
+    pl.data_floats = off + 8;
+    // CSR of output -> (histogram, accumulator) in (k, role, entry) order, by
+    // counting sort (no heap)
+    const int nacc = n_acc(mode, pl.R);
+    pl.n_out = 1 + (mode >= kGrad ? pl.P : 0);
+    for (int o = 0; o <= pl.n_out; ++o) pl.csr_cnt[o] = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            pl.csr_ptr[0] = 0;
+            for (int o = 0; o < pl.n_out; ++o) pl.csr_ptr[o + 1] = pl.csr_ptr[o] + pl.csr_cnt[o];
+            for (int o = 0; o < pl.n_out; ++o) pl.csr_cnt[o] = pl.csr_ptr[o];
+        }
+        for (int k = 0; k < pl.K; ++k) {
+            const int32_t* rt = pl.role_theta + (size_t)k * kMaxRoles * 2;
+            const int32_t base = k * nacc;
+            if (pass == 0) pl.csr_cnt[0]++;
+            else pl.csr_src[pl.csr_cnt[0]++] = base;
+            if (mode < kGrad) continue;
+            for (int r = 0; r < pl.R; ++r)
+                for (int j = 0; j < 2; ++j) {
+                    const int i = rt[2 * r + j];
+                    if (i < 0) continue;
+                    if (pass == 0) pl.csr_cnt[1 + i]++;
+                    else pl.csr_src[pl.csr_cnt[1 + i]++] = base + 1 + r;
+                }
+        }
+    }
+    pl.n_src = pl.csr_ptr[pl.n_out];
+    return MUSR_OK;
+}
+
+cudaError_t launch_na(const Signature& s, int mode, int threads, int n_tiles, cudaStream_t st,
+                      const EvalParams& p) {
+#define MUSR_CASE(NE, NG, KT)                                                     \
+    if (s.ne == NE && s.ng == NG && s.kt == KT)                                   \
+        return mode == kValue ? launch_one<NE, NG, KT, kValue>(threads, n_tiles, st, p) \
+                              : launch_one<NE, NG, KT, kGrad>(threads, n_tiles, st, p);
+    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
+    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
+    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
+    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
+    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
+    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+#undef MUSR_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+}  // namespace musr
+
+using namespace musr;
+
+extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mode,
+                                      const double* theta_dev, double* out_dev, int32_t* status_dev,
+                                      void* stream) {
+    if (!desc || !theta_dev || !out_dev) return MUSR_EINVAL;
+    if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
+    if (mode != MUSR_VALUE && mode != MUSR_VALUE_GRAD) return MUSR_ENOTSUP;
+    if (!desc->data || !desc->data_on_device || desc->data_dtype != MUSR_F32) return MUSR_ENOTSUP;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MUSR_ECUDA;
+    // one-time set-up on this device: the device address of the scratch array
+    unsigned char* base = g_scratch_addr[dev].load();
+    if (!base) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+        if (e != cudaSuccess || !ptr) return cuda_status(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+        base = static_cast<unsigned char*>(ptr);
+        g_scratch_addr[dev].store(base);
+    }
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    std::lock_guard<std::mutex> lock(g_plan_mutex);
+    NaPlan& pl = g_plan;
+    int st = plan_call(desc, mode, sms, pl);
+    if (st != MUSR_OK) return st;
+    const int nacc = n_acc(mode, pl.R);
+
+    // carve the scratch array; reject calls whose working set does not fit
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_cnt = take(4 * sizeof(unsigned));
+    const size_t o_hc = take(sizeof(HistConst) * pl.K);
+    const size_t o_hoff = take(sizeof(int64_t) * pl.K);
+    const size_t o_nb = take(sizeof(int32_t) * pl.K);
+    const size_t o_th = take(sizeof(int32_t) * pl.n_tiles);
+    const size_t o_ts = take(sizeof(int32_t) * pl.n_tiles);
+    const size_t o_ch = take(sizeof(int32_t) * pl.n_clusters);
+    const size_t o_hf = take(sizeof(int32_t) * pl.K);
+    const size_t o_hn = take(sizeof(int32_t) * pl.K);
+    const size_t o_rt = take(sizeof(int32_t) * pl.K * kMaxRoles * 2);
+    const size_t o_cp = take(sizeof(int32_t) * (pl.n_out + 1));
+    const size_t o_cs = take(sizeof(int32_t) * (pl.n_src + 1));
+    const size_t o_part = take(sizeof(double) * (size_t)pl.n_clusters * nacc);
+    const size_t o_hsum = take(sizeof(double) * (size_t)pl.K * nacc);
+    const size_t o_data = take(sizeof(float) * (size_t)pl.data_floats);
+    if (off > kScratchBytes) return MUSR_ENOTSUP;
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(base + o_cnt, 0, 4 * sizeof(unsigned), s);  // tickets start at 0
+    auto up = [&](size_t o, const void* src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s);
+    };
+    up(o_hoff, pl.hist_off, sizeof(int64_t) * pl.K);
+    up(o_nb, pl.hist_nbins, sizeof(int32_t) * pl.K);
+    up(o_th, pl.tile_hist, sizeof(int32_t) * pl.n_tiles);
+    up(o_ts, pl.tile_start, sizeof(int32_t) * pl.n_tiles);
+    up(o_ch, pl.cluster_hist, sizeof(int32_t) * pl.n_clusters);
+    up(o_hf, pl.hist_first_cluster, sizeof(int32_t) * pl.K);
+    up(o_hn, pl.hist_nclusters, sizeof(int32_t) * pl.K);
+    up(o_rt, pl.role_theta, sizeof(int32_t) * pl.K * kMaxRoles * 2);
+    up(o_cp, pl.csr_ptr, sizeof(int32_t) * (pl.n_out + 1));
+    up(o_cs, pl.csr_src, sizeof(int32_t) * pl.n_src);
+    // the histograms, copied into the padded layout the kernel reads
+    float* data = reinterpret_cast<float*>(base + o_data);
+    const float* src = static_cast<const float*>(desc->data);
+    int64_t so = 0;
+    for (int k = 0; k < pl.K && e == cudaSuccess; ++k) {
+        const int64_t M = desc->n_bins[k];
+        if (M) e = cudaMemcpyAsync(data + pl.hist_off[k], src + so, sizeof(float) * M, cudaMemcpyDeviceToDevice, s);
+        so += M;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+
+    EvalParams p;
+    memset(&p, 0, sizeof(p));
+    p.data = data;
+    p.hist_off = reinterpret_cast<const int64_t*>(base + o_hoff);
+    p.hist_nbins = reinterpret_cast<const int32_t*>(base + o_nb);
+    p.tile_hist = reinterpret_cast<const int32_t*>(base + o_th);
+    p.tile_start = reinterpret_cast<const int32_t*>(base + o_ts);
+    p.role_theta = reinterpret_cast<const int32_t*>(base + o_rt);
+    p.theta = theta_dev;
+    p.t0 = desc->t0_us;
+    p.dt = desc->dt_us;
+    p.inv_tau = 1.0 / desc->tau_us;
+    p.gamma = desc->gamma_mhz_per_g;
+    p.K = pl.K;
+    p.P = pl.P;
+    p.obj = obj;
+    p.hconst = reinterpret_cast<HistConst*>(base + o_hc);
+    p.partial = reinterpret_cast<double*>(base + o_part);
+    p.hist_sum = reinterpret_cast<double*>(base + o_hsum);
+    p.global_count = reinterpret_cast<unsigned*>(base + o_cnt);
+    p.flags = reinterpret_cast<unsigned*>(base + o_cnt) + 1;
+    p.cluster_hist = reinterpret_cast<const int32_t*>(base + o_ch);
+    p.hist_first_cluster = reinterpret_cast<const int32_t*>(base + o_hf);
+    p.hist_nclusters = reinterpret_cast<const int32_t*>(base + o_hn);
+    p.n_clusters = pl.n_clusters;
+    p.cluster = pl.cluster;
+    p.csr_ptr = reinterpret_cast<const int32_t*>(base + o_cp);
+    p.csr_src = reinterpret_cast<const int32_t*>(base + o_cs);
+    p.n_out = pl.n_out;
+    p.n_src = pl.n_src;
+    p.win_doubles = std::max(nacc, std::min(pl.n_clusters * nacc, 4096 / nacc * nacc));
+    p.hsum_in_smem = 1;  // K <= 64 and nacc <= 13: at most 6.5 KB
+    p.csr_in_smem = 1;   // at most ~7 KB
+    p.smem_bytes = (int)(8 * ((size_t)p.win_doubles + (size_t)pl.K * nacc) +
+                         4 * ((size_t)pl.n_out + 1 + pl.n_src));
+    p.out = out_dev;
+    p.status_out = status_dev;
+    // allow the tail's shared memory, then stage the constants and evaluate
+    e = launch_na(pl.sig, mode, pl.threads, 0, s, p);
+    if (e == cudaSuccess) e = launch_na(pl.sig, mode, pl.threads, pl.n_tiles, s, p);
+    return cuda_status(e);
+}
