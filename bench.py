@@ -209,6 +209,45 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def batched_throughput(dev, rank, reps=5):
+    """Value-only bin-evaluations per second of the batched persistent kernel on
+    64 uneven runs x (P+1) Jacobian vectors, device-resident (L2 flushed)."""
+    import torch
+    from paper_1604_02334_gb300 import Batch, Run
+    runs = W.config_batched()
+    gruns, vecs = [], []
+    for br in runs:
+        with Run(br.layout) as m:
+            mean = m.model(br.theta).astype(np.float64)
+        d = W.poisson_counts(mean, br.seed + rank).astype(np.float32)
+        gruns.append(Run(br.layout, torch.tensor(d, device=dev)))
+        vecs.append(W.jacobian_vectors(br.theta, br.layout.free, 1e-6))
+    mv = [v.shape[0] for v in vecs]
+    flat = np.concatenate([v.ravel() for v in vecs])
+    b = Batch(gruns, mv)
+    th = torch.tensor(flat, device=dev)
+    out = torch.empty(b.n_values, dtype=torch.float64, device=dev)
+    b.eval_device(th, out)  # autotunes on first use
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(reps):
+        flush.fill_(i & 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.eval_device(th, out)
+        torch.cuda.synchronize()
+        ms.append(1e3 * (time.perf_counter() - t0))
+    binevals = sum(br.layout.total_bins * m for br, m in zip(runs, mv))
+    med = float(np.median(ms))
+    b.close()
+    for g in gruns:
+        g.close()
+    return {"workload": "64 runs, K~U{1..32} x M~U[2^14,2^17] bins, P+1 vectors each",
+            "bins": int(sum(br.layout.total_bins for br in runs)), "bin_evals": int(binevals),
+            "ms": med, "value": binevals / (med * 1e-3), "unit": "bin-evals/s (chi2, value only)"}
+
+
 def run_ours(args):
     import torch
 
@@ -287,6 +326,7 @@ def run_ours(args):
 
     # sanity: results are finite
     assert torch.isfinite(outs[args.warmup:]).all().item()
+    batched = None if args.no_batched else batched_throughput(dev, rank)
 
     if rank != 0:
         run.close()
@@ -306,9 +346,11 @@ def run_ours(args):
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,  # stage kernel + objective kernel per step
         "wall_s": wall,
     }
+    if batched:
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lay, data, thetas)
     print(json.dumps(line), flush=True)
@@ -322,6 +364,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
