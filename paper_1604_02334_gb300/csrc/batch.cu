@@ -36,7 +36,8 @@ struct BatchRunRef {
     const int64_t* hist_off;
     const int32_t* hist_nbins;
     const int32_t* role_theta;
-    double t0, dt, inv_tau, gamma;
+    RunConst rc;
+    double t0, dt;
     int32_t P, V;           // parameters, vectors evaluated this launch
     int64_t theta_off;      // offset of the run's first vector in thetas
     int64_t val_off;        // offset of the run's first value
@@ -89,11 +90,10 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
 
         __syncthreads();  // the previous item is done with hcs / red
         {
-            const TimeGrid tg{R.t0, R.dt, R.inv_tau, R.gamma};
             const int32_t* rt = R.role_theta + (size_t)k * kMaxRoles * 2;
             for (int q = threadIdx.x; q < V * NPART; q += blockDim.x) {
                 const int v = q / NPART, part = q % NPART;
-                stage_hist<NE, NG, KT, false>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, tg, hcs[v]);
+                stage_part<NE, NG, KT>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, R.rc, hcs[v]);
             }
         }
         for (int v = threadIdx.x; v < V; v += blockDim.x)
@@ -317,10 +317,9 @@ int musr_batch_s::plan(const BatchShape& sh) {
         R.hist_off = run->d_hist_off;
         R.hist_nbins = run->d_hist_nbins;
         R.role_theta = run->d_role_theta;
+        R.rc = run->rc;
         R.t0 = run->t0;
         R.dt = run->dt;
-        R.inv_tau = 1.0 / run->tau;
-        R.gamma = run->gamma;
         R.P = run->P;
         R.V = max_vec[r];
         R.theta_off = theta_off[r];

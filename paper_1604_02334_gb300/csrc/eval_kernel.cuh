@@ -53,133 +53,17 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
-__host__ __device__ __forceinline__ void split_hi_lo(double v, float& hi, float& lo) {
-    hi = (float)v;
-    lo = (float)(v - (double)hi);
-}
-
-// x mod 1 as 64-bit fixed-point turns.
-__host__ __device__ __forceinline__ unsigned long long turns_to_fixed(double x) {
-    double y = x - floor(x);
-    if (!(y >= 0.0) || y >= 1.0) y = 0.0;
-    double s = y * 4294967296.0;  // exact scaling by 2^32
-    double hi = floor(s);
-    double lo = floor((s - hi) * 4294967296.0);
-    return ((unsigned long long)hi << 32) | (unsigned long long)lo;
-}
-
-// Sum of the (up to two) theta entries a role reads.
-__host__ __device__ __forceinline__ double role_value(const int32_t* rt, const double* theta, int r) {
-    int i0 = rt[2 * r], i1 = rt[2 * r + 1];
+// Sum of the (up to two) theta entries a role reads (at most one FP64 add).
+__device__ __forceinline__ double role_value(const int32_t* rt, const double* theta, int r) {
+    const int i0 = rt[2 * r], i1 = rt[2 * r + 1];
     double v = 0.0;
     if (i0 >= 0) v += theta[i0];
     if (i1 >= 0) v += theta[i1];
     return v;
 }
 
-// Per-histogram constants in NPART independent parts (so that different
-// threads can compute them concurrently):
-//   part 0        N0 (hi/lo), bkg, lifetime recurrence, 2 pi gamma
-//   part 1 + 2c   envelope of precession line c
-//   part 2 + 2c   phase of precession line c (64-bit fixed-point turns)
-//   part 1 + 2 NOSC  static Gaussian Kubo-Toyabe term
-// Every argument is formed in FP64.  PRECISE (host) evaluates the few
-// transcendental step factors in FP64 too; the device variant uses FP32
-// accurate functions of the FP64 arguments (FP64 functions are slow there).
-struct TimeGrid {
-    double t0, dt, inv_tau, gamma;
-};
-
-template <int NE, int NG, int KT>
-__host__ __device__ constexpr int stage_parts() {
-    return 2 + 2 * (NE + NG);
-}
-
-template <bool PRECISE>
-__host__ __device__ __forceinline__ float st_expm1(double x) {
-#ifdef __CUDA_ARCH__
-    if (!PRECISE) return expm1f((float)x);
-#endif
-    return (float)expm1(x);
-}
-template <bool PRECISE>
-__host__ __device__ __forceinline__ float st_exp(double x) {
-#ifdef __CUDA_ARCH__
-    if (!PRECISE) return expf((float)x);
-#endif
-    return (float)exp(x);
-}
-// sin(pi x) for x in [-1, 1]
-template <bool PRECISE>
-__host__ __device__ __forceinline__ float st_sinpi(double x) {
-#ifdef __CUDA_ARCH__
-    if (!PRECISE) return sinpif((float)x);
-#endif
-    return (float)sin(3.14159265358979323846 * x);
-}
-
-template <int NE, int NG, int KT, bool PRECISE>
-__host__ __device__ void stage_hist(int part, const int32_t* rt, const double* theta, const TimeGrid& tg,
-                                    HistConst& hc) {
-    constexpr int NOSC = NE + NG;
-    const double LOG2E = 1.4426950408889634074;
-    const double dt = tg.dt, t0 = tg.t0, it = tg.inv_tau;
-    if (part == 0) {
-        split_hi_lo(role_value(rt, theta, 0), hc.n0, hc.n0_lo);
-        hc.bkg = (float)role_value(rt, theta, 1);
-        split_hi_lo(dt * it * LOG2E, hc.aE_hi, hc.aE_lo);
-        hc.qE = st_expm1<PRECISE>(-dt * it);
-        hc.cE = st_exp<PRECISE>(-t0 * it);
-        hc.kfreq = (float)(2.0 * 3.14159265358979323846 * tg.gamma);
-    } else if (part <= 2 * NOSC) {
-        const int c = (part - 1) >> 1;
-        const int r = 2 + 4 * c;
-        OscConst& o = hc.osc[c];
-        if (part & 1) {  // envelope
-            const double amp = role_value(rt, theta, r);
-            const double rate = role_value(rt, theta, r + 1);
-            o.amp = (float)amp;
-            o.rate = (float)rate;
-            if (c < NE) {  // exp(-(1/tau + lambda) t)
-                const double rt_ = it + rate;
-                split_hi_lo(rt_ * dt * LOG2E, o.a_hi, o.a_lo);
-                o.b_hi = o.b_lo = 0.f;
-                o.q = st_expm1<PRECISE>(-rt_ * dt);
-                o.cenv = st_exp<PRECISE>(-rt_ * t0);
-            } else {  // exp(-t/tau - sigma^2 t^2 / 2), t = t0 + n dt
-                const double s2 = rate * rate;
-                split_hi_lo((it + s2 * t0) * dt * LOG2E, o.a_hi, o.a_lo);
-                split_hi_lo(0.5 * s2 * dt * dt * LOG2E, o.b_hi, o.b_lo);
-                o.q = 0.f;
-                o.cenv = st_exp<PRECISE>(-t0 * it - 0.5 * s2 * t0 * t0);
-            }
-        } else {  // phase
-            const double field = role_value(rt, theta, r + 2);
-            const double phi = role_value(rt, theta, r + 3);
-            const double f = tg.gamma * field;  // turns per microsecond
-            o.ph0 = turns_to_fixed(f * t0 + phi * 0.15915494309189533577);
-            const double stp = f * dt;  // turns per bin
-            o.step = turns_to_fixed(stp);
-            const double red = stp - rint(stp);  // in [-0.5, 0.5]
-            const float sh = st_sinpi<PRECISE>(red);
-            o.cm1 = -2.f * sh * sh;                  // cos(step) - 1
-            o.sn = st_sinpi<PRECISE>(2.0 * red);     // sin(step)
-        }
-    } else if (KT && part == 2 * NOSC + 1) {
-        const int r = 2 + 4 * NOSC;
-        const double amp = role_value(rt, theta, r);
-        const double dl = role_value(rt, theta, r + 1);
-        const double s2 = dl * dl;
-        hc.kt_amp = (float)amp;
-        hc.kt_rate = (float)dl;
-        split_hi_lo((it + s2 * t0) * dt * LOG2E, hc.kt_a_hi, hc.kt_a_lo);
-        split_hi_lo(0.5 * s2 * dt * dt * LOG2E, hc.kt_b_hi, hc.kt_b_lo);
-        hc.kt_cenv = st_exp<PRECISE>(-t0 * it - 0.5 * s2 * t0 * t0);
-    }
-}
-
-// Double-float (hi + lo) accumulation on the FP32 pipe: TwoSum of the high
-// parts, low parts added into the error, renormalised (Knuth / Dekker).
+// ---- double-float (hi + lo) arithmetic on the FP32 pipe (Knuth TwoSum,
+// Dekker TwoProd with FMA); about 44 significant bits ----
 struct DF {
     float hi, lo;
 };
@@ -191,6 +75,177 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
     const float h = __fadd_rn(s, e);
     return DF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = __fadd_rn(p, e);
+    return DF{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+__device__ __forceinline__ DF df_from(double x) {
+    const float hi = __double2float_rn(x);
+    return DF{hi, __double2float_rn(x - (double)hi)};
+}
+
+__device__ __forceinline__ DF df_of(const float2 v) { return DF{v.x, v.y}; }
+
+// frac(x * c) in 64-bit fixed-point turns, c = c.x + c.y * 2^-64 (unsigned
+// 64.64), by exact integer arithmetic on x's significand (truncated at
+// 2^-64 turns).  The phase of every precession line is formed this way, so it
+// is exact at any t without FP64 arithmetic.
+__device__ __forceinline__ unsigned long long fixmul(double x, ulonglong2 c) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0 || e == 0x7ff) return 0ull;  // zero / subnormal / non-finite
+    const unsigned long long m = (bits & 0xfffffffffffffull) | (1ull << 52);
+    // P = m * (c.x * 2^64 + c.y), 192 bits, in units of 2^-64 turns per 2^sh
+    const unsigned long long l1 = m * c.y, h1 = __umul64hi(m, c.y);
+    const unsigned long long l2 = m * c.x, h2 = __umul64hi(m, c.x);
+    const unsigned long long p0 = l1;
+    const unsigned long long p1 = h1 + l2;
+    const unsigned long long p2 = h2 + (p1 < h1 ? 1ull : 0ull);
+    const int sh = e - 1075;  // x = m * 2^sh
+    unsigned long long r;
+    if (sh >= 0) {
+        r = sh < 64 ? (p0 << sh) : 0ull;
+    } else {
+        const int s = -sh;
+        if (s < 64) r = (p0 >> s) | (p1 << (64 - s));
+        else if (s == 64) r = p1;
+        else if (s < 128) r = (p1 >> (s - 64)) | (p2 << (128 - s));
+        else if (s == 128) r = p2;
+        else if (s < 192) r = p2 >> (s - 128);
+        else r = 0ull;
+    }
+    return (bits >> 63) ? (0ull - r) : r;
+}
+
+// expm1(x) and sin(pi x): short Taylor series for the small per-bin step
+// arguments (|x| < 1/64, truncation below 3e-15 relative), the FP32 library
+// functions otherwise.
+__device__ __forceinline__ float step_expm1(float x) {
+    if (fabsf(x) >= 0.015625f) return expm1f(x);
+    float r = fmaf(x, 1.f / 6.f, 1.f);
+    r = fmaf(x * 0.2f, r, 1.f);
+    r = fmaf(x * 0.25f, r, 1.f);
+    r = fmaf(x * (1.f / 3.f), r, 1.f);
+    r = fmaf(x * 0.5f, r, 1.f);
+    return x * r;
+}
+
+__device__ __forceinline__ float step_sinpi(float x) {
+    if (fabsf(x) >= 0.03125f) return sinpif(x);
+    const float y = 3.14159265358979323846f * x, y2 = y * y;
+    float r = fmaf(-y2, 1.f / 42.f, 1.f);
+    r = fmaf(-y2 * 0.05f, r, 1.f);
+    r = fmaf(-y2 * (1.f / 6.f), r, 1.f);
+    return y * r;
+}
+
+// Per-histogram constants in NPART independent parts, each computed by lane 0
+// of its own warp so the parts overlap:
+//   part 0        N0 (hi/lo), bkg, lifetime recurrence
+//   part 1 + 2c   envelope of precession line c
+//   part 2 + 2c   phase of precession line c (64-bit fixed-point turns)
+//   part 1 + 2 NOSC  static Gaussian Kubo-Toyabe term
+// Only FP32 (double-float where precision matters), integer arithmetic and
+// FP32 accurate functions: no chains of FP64 operations.
+template <int NE, int NG, int KT>
+__host__ __device__ constexpr int stage_parts() {
+    return 2 + 2 * (NE + NG);
+}
+
+template <int NE, int NG, int KT>
+__device__ void stage_part(int part, const int32_t* rt, const double* theta, const RunConst& rc,
+                           HistConst& hc) {
+    constexpr int NOSC = NE + NG;
+    const DF it = df_of(rc.inv_tau), dtL = df_of(rc.dt_log2e), dt = df_of(rc.dt);
+    if (part == 0) {
+        const DF n0 = df_from(role_value(rt, theta, 0));
+        hc.n0 = n0.hi;
+        hc.n0_lo = n0.lo;
+        hc.bkg = __double2float_rn(role_value(rt, theta, 1));
+        hc.aE_hi = rc.aE_hi;
+        hc.aE_lo = rc.aE_lo;
+        hc.qE = rc.qE;
+        hc.cE = rc.cE;
+        hc.kfreq = rc.kfreq;
+    } else if (part <= 2 * NOSC) {
+        const int c = (part - 1) >> 1;
+        const int r = 2 + 4 * c;
+        OscConst& o = hc.osc[c];
+        if (part & 1) {  // envelope
+            const DF rate = df_from(role_value(rt, theta, r + 1));
+            o.amp = __double2float_rn(role_value(rt, theta, r));
+            o.rate = rate.hi;
+            if (c < NE) {  // exp(-(1/tau + lambda) t)
+                const DF rtot = df_add(it, rate);
+                const DF a = df_mul(rtot, dtL);
+                o.a_hi = a.hi;
+                o.a_lo = a.lo;
+                o.b_hi = o.b_lo = 0.f;
+                o.q = step_expm1(-df_mul(rtot, dt).hi);
+                o.cenv = rc.t0_zero ? 1.f : expf(-df_mul(rtot, df_of(rc.t0)).hi);
+            } else {  // exp(-t/tau - sigma^2 t^2 / 2), t = t0 + n dt
+                const DF s2 = df_mul(rate, rate);
+                const DF a = df_add(df_mul(it, dtL), df_mul(s2, df_of(rc.t0_dt_log2e)));
+                const DF b = df_mul(s2, df_of(rc.half_dt2_log2e));
+                o.a_hi = a.hi;
+                o.a_lo = a.lo;
+                o.b_hi = b.hi;
+                o.b_lo = b.lo;
+                o.q = 0.f;
+                if (rc.t0_zero) {
+                    o.cenv = 1.f;
+                } else {
+                    const DF t0 = df_of(rc.t0);
+                    const DF x = df_add(df_mul(t0, it), df_mul(df_mul(s2, t0), DF{0.5f * t0.hi, 0.5f * t0.lo}));
+                    o.cenv = expf(-x.hi);
+                }
+            }
+        } else {  // phase: sums of fixed-point products are exact mod 1 turn
+            const int i0 = rt[2 * (r + 2)], i1 = rt[2 * (r + 2) + 1], ip = rt[2 * (r + 3)];
+            unsigned long long step = 0ull, ph0 = 0ull;
+            if (i0 >= 0) {
+                step += fixmul(theta[i0], rc.turns_per_bin);
+                if (!rc.t0_zero) ph0 += fixmul(theta[i0], rc.turns_at_t0);
+            }
+            if (i1 >= 0) {
+                step += fixmul(theta[i1], rc.turns_per_bin);
+                if (!rc.t0_zero) ph0 += fixmul(theta[i1], rc.turns_at_t0);
+            }
+            if (ip >= 0) ph0 += fixmul(theta[ip], rc.inv_two_pi);
+            o.ph0 = ph0;
+            o.step = step;
+            const float red = (float)(long long)step * 5.42101086242752217e-20f;  // turns in [-1/2, 1/2)
+            const float sh = step_sinpi(red);
+            o.cm1 = -2.f * sh * sh;        // cos(step) - 1
+            o.sn = step_sinpi(2.f * red);  // sin(step)
+        }
+    } else if (KT && part == 2 * NOSC + 1) {
+        const int r = 2 + 4 * NOSC;
+        const DF dl = df_from(role_value(rt, theta, r + 1));
+        const DF s2 = df_mul(dl, dl);
+        hc.kt_amp = __double2float_rn(role_value(rt, theta, r));
+        hc.kt_rate = dl.hi;
+        const DF a = df_add(df_mul(it, dtL), df_mul(s2, df_of(rc.t0_dt_log2e)));
+        const DF b = df_mul(s2, df_of(rc.half_dt2_log2e));
+        hc.kt_a_hi = a.hi;
+        hc.kt_a_lo = a.lo;
+        hc.kt_b_hi = b.hi;
+        hc.kt_b_lo = b.lo;
+        if (rc.t0_zero) {
+            hc.kt_cenv = 1.f;
+        } else {
+            const DF t0 = df_of(rc.t0);
+            const DF x = df_add(df_mul(t0, it), df_mul(df_mul(s2, t0), DF{0.5f * t0.hi, 0.5f * t0.lo}));
+            hc.kt_cenv = expf(-x.hi);
+        }
+    }
 }
 
 // Block-wide copy of n elements from global (L2) to shared memory with eight
@@ -368,20 +423,6 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
 }
 
 
-// Device-path staging: one block per histogram; part q of its constants is
-// computed by lane 0 of warp q.  It lets the dependent objective kernel
-// launch at once (programmatic dependent launch); that kernel waits for the
-// staged constants before it reads them.
-template <int NE, int NG, int KT>
-__global__ void stage_kernel(const double* theta, const int32_t* role_theta, TimeGrid tg, HistConst* out) {
-    asm volatile("griddepcontrol.launch_dependents;");
-    constexpr int NPART = stage_parts<NE, NG, KT>();
-    const int k = blockIdx.x;
-    const int part = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0 && part < NPART)
-        stage_hist<NE, NG, KT, false>(part, role_theta + (size_t)k * kMaxRoles * 2, theta, tg, out[k]);
-}
-
 template <int NE, int NG, int KT, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant__ EvalParams p) {
     namespace cg = cooperative_groups;
@@ -392,7 +433,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 
     __shared__ HistConst hc;
     __shared__ float red[kMaxWarps][NACC];
-    __shared__ DF bpart[NACC];  // this block's sums; the cluster leader reads them
+    __shared__ DF cpart[8][NACC];  // the cluster leader's copy receives every block's sums
     __shared__ int s_last;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
@@ -401,13 +442,14 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     const int tile = blockIdx.x;
     const int k = p.tile_hist[tile];
     const int M = p.hist_nbins[k];
-    const int n0 = p.tile_start[tile] + (int)threadIdx.x * G;
-    const bool active = n0 < M;
+    const int stripe = (int)blockDim.x * G;  // a tile is p.chunks stripes of blockDim x 8 bins
+    int n0 = p.tile_start[tile] + (int)threadIdx.x * G;
+    const float* hdata = p.data + p.hist_off[k];
 
-    // issue the histogram loads first so their latency overlaps the staging
+    // issue the first chunk's loads so their latency overlaps the staging
     float d[G];
-    if (MODE != kModel && active) {
-        const float4* src = reinterpret_cast<const float4*>(p.data + p.hist_off[k] + n0);
+    if (MODE != kModel && n0 < M) {
+        const float4* src = reinterpret_cast<const float4*>(hdata + n0);
         float4 a = __ldg(src), b = __ldg(src + 1);
         d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
         d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w;
@@ -416,19 +458,32 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         for (int g = 0; g < G; ++g) d[g] = 0.f;
     }
 
-    // histogram k's constants: inline in the launch parameters (host calls) or
-    // written by the preceding stage kernel (device calls)
+    // stage histogram k's constants: one part per warp, so the parts' latency
+    // chains overlap (theta is inline in the launch parameters for host calls);
+    // warps not staging preload the tail's small tables (only the last block
+    // will read them, but no block knows yet whether it is last)
+    const int W = p.win_doubles;  // window of cluster partials, a multiple of NACC
+    int32_t* tbl = reinterpret_cast<int32_t*>(reinterpret_cast<DF*>(dyn_smem) + W +
+                                              (p.hsum_in_smem ? p.K * NACC : 0));
     {
-        const unsigned* src;
-        if (p.hconst_inline_n > 0) {
-            src = reinterpret_cast<const unsigned*>(&p.hconst_inline[k]);
-        } else {
-            asm volatile("griddepcontrol.wait;" ::: "memory");
-            src = reinterpret_cast<const unsigned*>(p.hconst + k);
+        constexpr int NPART = stage_parts<NE, NG, KT>();
+        if (MODE != kModel && p.preload && (int)threadIdx.x >= 32 * NPART) {
+            const int n1 = p.n_out + 1, n2 = p.n_src, n3 = p.n_clusters, n4 = p.K;
+            const int stride = (int)blockDim.x - 32 * NPART;
+            for (int i = (int)threadIdx.x - 32 * NPART; i < n1 + n2 + n3 + 2 * n4; i += stride) {
+                int32_t v;
+                if (i < n1) v = p.csr_ptr[i];
+                else if (i < n1 + n2) v = p.csr_src[i - n1];
+                else if (i < n1 + n2 + n3) v = p.cluster_hist[i - n1 - n2];
+                else if (i < n1 + n2 + n3 + n4) v = p.hist_first_cluster[i - n1 - n2 - n3];
+                else v = p.hist_nclusters[i - n1 - n2 - n3 - n4];
+                tbl[i] = v;
+            }
         }
-        unsigned* dst = reinterpret_cast<unsigned*>(&hc);
-        for (int i = threadIdx.x; i < (int)(sizeof(HistConst) / 4); i += blockDim.x)
-            dst[i] = p.hconst_inline_n > 0 ? src[i] : __ldcg(src + i);
+        const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
+        const int32_t* rt = p.role_theta + (size_t)k * kMaxRoles * 2;
+        for (int part = warp; part < NPART; part += nwarps)
+            if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, p.rc, hc);
     }
     __syncthreads();
 
@@ -437,9 +492,26 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
     bool bad = false;
 
-    if (active)
-        eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
-                                           MODE == kModel ? p.model_out + p.model_off[k] : nullptr);
+    for (int c = 0; c < p.chunks; ++c) {
+        // the next chunk's loads are in flight while this one is evaluated
+        const int n1 = n0 + stripe;
+        float dn[G];
+        if (MODE != kModel && c + 1 < p.chunks && n1 < M) {
+            const float4* src = reinterpret_cast<const float4*>(hdata + n1);
+            float4 a = __ldg(src), b = __ldg(src + 1);
+            dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
+            dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g) dn[g] = 0.f;
+        }
+        if (n0 < M)
+            eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
+                                               MODE == kModel ? p.model_out + p.model_off[k] : nullptr);
+#pragma unroll
+        for (int g = 0; g < G; ++g) d[g] = dn[g];
+        n0 = n1;
+    }
     if (MODE == kModel) return;
 
     // ---- block: FP32 warp sums, double-float across warps ----
@@ -449,33 +521,31 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
     }
     const int any_bad = __syncthreads_or(bad);
-    for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
-        DF v{red[0][a], 0.f};
-        for (int w = 1; w < nwarps; ++w) v = df_add(v, DF{red[w][a], 0.f});
-        bpart[a] = v;
-    }
     if (threadIdx.x == 0 && any_bad) atomicOr(p.flags, 1u);
 
-    // ---- cluster: the leader sums its blocks through distributed shared memory ----
+    // ---- cluster: every block pushes its sums into the leader's shared memory
+    // (distributed shared memory stores), one cluster barrier, the leader adds ----
     cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
     const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
+    {
+        DF* dst = &cl.map_shared_rank(&cpart[0][0], 0)[rank * NACC];
+        for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
+            DF v{red[0][a], 0.f};
+            for (int w = 1; w < nwarps; ++w) v = df_add(v, DF{red[w][a], 0.f});
+            dst[a] = v;
+        }
+    }
+    cl.sync();
+    if (rank != 0) return;
     DF* partial = reinterpret_cast<DF*>(p.partial);
-    if (rank == 0) {
+    {
         const int cidx = blockIdx.x / (int)csize;
         for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
-            DF rv[8];  // all remote reads in flight before the (ordered) adds
-#pragma unroll
-            for (unsigned r = 0; r < 8; ++r) rv[r] = r < csize ? cl.map_shared_rank(bpart, r)[a] : DF{0.f, 0.f};
-            DF v = rv[0];
-#pragma unroll
-            for (unsigned r = 1; r < 8; ++r)
-                if (r < csize) v = df_add(v, rv[r]);
+            DF v = cpart[0][a];
+            for (unsigned r = 1; r < csize; ++r) v = df_add(v, cpart[r][a]);
             partial[(size_t)cidx * NACC + a] = v;
         }
     }
-    cl.sync();  // keep every block's shared memory alive until the leader has read it
-    if (rank != 0) return;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -487,8 +557,12 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     __threadfence();
 
     // ---- last cluster leader: histogram sums (fixed order), then theta via the map ----
-    const int W = p.win_doubles;  // window of cluster partials, a multiple of NACC
     DF* win = reinterpret_cast<DF*>(dyn_smem);
+    const int32_t* t_cptr = p.preload ? tbl : p.csr_ptr;
+    const int32_t* t_csrc = p.preload ? tbl + p.n_out + 1 : p.csr_src;
+    const int32_t* t_chist = p.preload ? tbl + p.n_out + 1 + p.n_src : p.cluster_hist;
+    const int32_t* t_hfirst = p.preload ? t_chist + p.n_clusters : p.hist_first_cluster;
+    const int32_t* t_hncl = p.preload ? t_hfirst + p.K : p.hist_nclusters;
     DF* hsum = p.hsum_in_smem ? win + W : reinterpret_cast<DF*>(p.hist_sum);
     for (int i = threadIdx.x; i < p.K * NACC; i += blockDim.x) hsum[i] = DF{0.f, 0.f};
     const int total = p.n_clusters * NACC;
@@ -498,20 +572,20 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         copy_to_smem(reinterpret_cast<float2*>(win), reinterpret_cast<const float2*>(partial + i0), n);
         __syncthreads();
         const int c0 = i0 / NACC, c1 = c0 + n / NACC;
-        const int k0 = p.cluster_hist[c0], k1 = p.cluster_hist[c1 - 1];
+        const int k0 = t_chist[c0], k1 = t_chist[c1 - 1];
         for (int q = threadIdx.x; q < (k1 - k0 + 1) * NACC; q += blockDim.x) {
             const int kk = k0 + q / NACC, a = q % NACC;
-            const int first = p.hist_first_cluster[kk];
-            const int lo = max(first, c0), hi = min(first + p.hist_nclusters[kk], c1);
+            const int first = t_hfirst[kk];
+            const int lo = max(first, c0), hi = min(first + t_hncl[kk], c1);
             DF s = hsum[kk * NACC + a];
             for (int c = lo; c < hi; ++c) s = df_add(s, win[(c - c0) * NACC + a]);
             hsum[kk * NACC + a] = s;
         }
     }
     __syncthreads();
-    const int32_t* cptr = p.csr_ptr;
-    const int32_t* csrc = p.csr_src;
-    if (p.csr_in_smem) {
+    const int32_t* cptr = t_cptr;
+    const int32_t* csrc = t_csrc;
+    if (!p.preload && p.csr_in_smem) {
         int32_t* sp = reinterpret_cast<int32_t*>(win + W + (p.hsum_in_smem ? p.K * NACC : 0));
         copy_to_smem(sp, p.csr_ptr, p.n_out + 1);
         copy_to_smem(sp + p.n_out + 1, p.csr_src, p.n_src);
@@ -534,13 +608,20 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     }
 }
 
-// Launch the objective kernel in clusters of p.cluster blocks.  With the
-// constants not inline (device calls) the stage kernel runs first and the
-// objective kernel follows as its programmatic dependent.  n_tiles == 0 only
-// sets the kernel's shared-memory attribute (call it outside stream capture).
+// Launch the objective kernel in clusters of p.cluster blocks.  n_tiles == 0
+// only sets the kernel's shared-memory attribute (call it outside capture);
+// n_tiles < 0 only reports the kernel's resident blocks per SM.
 template <int NE, int NG, int KT, int MODE>
 cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const EvalParams& p) {
     const size_t smem = (size_t)p.smem_bytes;
+    if (n_tiles < 0) {
+        // occupancy query: resident blocks per SM written to p.status_out (host int)
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<NE, NG, KT, MODE>,
+                                                                      threads, smem);
+        *reinterpret_cast<int*>(p.status_out) = nb;
+        return e;
+    }
     if (n_tiles == 0) {
         // the attribute is per kernel, shared by every run: only ever raise it
         // (to the device's opt-in maximum), never lower it below another run's need
@@ -556,28 +637,18 @@ cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const Eval
         return cudaFuncSetAttribute(eval_kernel<NE, NG, KT, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
     }
-    const bool staged = p.hconst_inline_n == 0 && !p.hconst_ready;
-    if (staged) {
-        const TimeGrid tg{p.t0, p.dt, p.inv_tau, p.gamma};
-        stage_kernel<NE, NG, KT><<<p.K, 32 * stage_parts<NE, NG, KT>(), 0, stream>>>(
-            p.theta, p.role_theta, tg, p.hconst);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_tiles);
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = p.cluster;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = staged ? 2 : 1;
+    cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, eval_kernel<NE, NG, KT, MODE>, p);
 }
 

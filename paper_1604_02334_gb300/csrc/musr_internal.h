@@ -15,7 +15,7 @@ constexpr int kMaxRoles = 2 + 4 * kMaxOsc + 2;     // N0, bkg, 4 per line, 2 for
 constexpr int kBinsPerThread = 8;                  // consecutive bins per thread (2 x float4)
 constexpr int kMaxThreads = 256;                   // block size upper bound
 constexpr int kMaxWarps = kMaxThreads / 32;
-constexpr int kInlineHists = 32;                   // constants passed inside the launch parameters
+constexpr int kInlineParams = 256;                 // theta passed inside the launch parameters
 
 // Per-histogram constants of the theory, staged once per evaluation (the
 // paper's kernel keeps the parameter / map values in shared memory for the
@@ -30,6 +30,17 @@ struct HistConst {
     float kfreq;  // 2 pi gamma: dN/dB = dN/d(omega) * 2 pi gamma
     OscConst osc[kMaxOsc];
     float kt_amp, kt_rate, kt_cenv, kt_a_hi, kt_a_lo, kt_b_hi, kt_b_lo;
+};
+
+// Theta-independent constants of a run's time grid, prepared on the host in
+// FP64 / exact integer arithmetic (float2 = double-float hi, lo).
+struct RunConst {
+    float2 inv_tau, dt, dt_log2e, t0, t0_dt_log2e, half_dt2_log2e;
+    float aE_hi, aE_lo, qE, cE, kfreq;  // lifetime recurrence, 2 pi gamma
+    int t0_zero;
+    ulonglong2 turns_per_bin;  // gamma * dt as unsigned 64.64 fixed point (turns per gauss)
+    ulonglong2 turns_at_t0;    // gamma * t0
+    ulonglong2 inv_two_pi;     // 1 / (2 pi)
 };
 
 // Kernel "signature": how many precession lines of each relaxation kind and
@@ -58,10 +69,10 @@ struct EvalParams {
     const int32_t* tile_start;    // [n_tiles] first bin of the tile
     const int32_t* role_theta;    // [K][kMaxRoles][2] theta indices (or -1) per role
     const double* theta;          // [P] on the device (device calls)
+    RunConst rc;
     double t0, dt, inv_tau, gamma;
     int K, P, obj;
-    // staged constants, reduction scratch
-    HistConst* hconst;            // [K] written by the stage kernel (device calls)
+    // reduction scratch
     double* partial;              // [n_clusters][nacc] double-float pairs
     double* hist_sum;             // [K][nacc] pairs (when they do not fit in shared memory)
     unsigned* global_count;       // [1]   (self-resetting)
@@ -70,18 +81,19 @@ struct EvalParams {
     const int32_t* hist_first_cluster;  // [K]
     const int32_t* hist_nclusters;      // [K]
     int n_clusters, cluster;      // clusters of `cluster` consecutive tiles of one histogram
+    int chunks;                   // stripes of blockDim x 8 bins per tile
     const int32_t* csr_ptr;       // [n_out + 1]
     const int32_t* csr_src;       // sources: k * nacc + acc
     int n_out;
     int n_src;                    // csr_src length
     int win_doubles;              // shared-memory window for cluster partials
     int hsum_in_smem, csr_in_smem;
+    int preload;                  // 1: every block preloads the tail's tables (CSR, cluster tables)
     int smem_bytes;               // dynamic shared memory of the objective kernel
     double* out;                  // [n_out]
     int32_t* status_out;          // [1] or null
-    int hconst_ready;             // 1: hconst already holds this call's constants (host-staged)
-    int hconst_inline_n;          // > 0: hconst_inline holds the K histograms' constants
-    HistConst hconst_inline[kInlineHists];
+    int theta_inline_n;           // > 0: theta_inline holds theta (host calls)
+    double theta_inline[kInlineParams];
     // model output (kModel)
     float* model_out;
     const int64_t* model_off;     // [K] offsets into model_out
@@ -95,8 +107,7 @@ cudaError_t launch_eval(const Signature& sig, int mode, int threads, int n_tiles
 // musr_last_cuda_error() (per host thread).
 int cuda_status(cudaError_t e);
 
-// Stage every histogram's constants on the host (FP64), as the device would.
-void stage_host(const Signature& sig, int K, const int32_t* role_theta, const double* theta,
-                double t0, double dt, double inv_tau, double gamma, HistConst* out);
+// Theta-independent constants of a time grid (host, FP64 / integer).
+RunConst make_run_const(double t0, double dt, double tau, double gamma);
 
 }  // namespace musr

@@ -70,7 +70,8 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
     if (pl.K < 1 || pl.K > kNaMaxHist || pl.P < 1 || pl.P > kNaMaxParams) return MUSR_ENOTSUP;
     if (d->map_width < 2 || d->map_width > 32 || d->n_comp < 0 || !d->n_bins || !d->map) return MUSR_EINVAL;
     if (d->n_comp > 0 && !d->comp) return MUSR_EINVAL;
-    if (!(d->dt_us > 0.0) || !(d->tau_us > 0.0)) return MUSR_EINVAL;
+    if (!(d->dt_us > 0.0) || !(d->tau_us > 0.0) || !(d->t0_us >= 0.0) || !(d->gamma_mhz_per_g >= 0.0))
+        return MUSR_EINVAL;
     int exp_c[kMaxOsc], gau_c[kMaxOsc], ne = 0, ng = 0, kt_c = -1;
     for (int c = 0; c < d->n_comp; ++c) {
         const musr_component& m = d->comp[c];
@@ -255,7 +256,6 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
         return o;
     };
     const size_t o_cnt = take(4 * sizeof(unsigned));
-    const size_t o_hc = take(sizeof(HistConst) * pl.K);
     const size_t o_hoff = take(sizeof(int64_t) * pl.K);
     const size_t o_nb = take(sizeof(int32_t) * pl.K);
     const size_t o_th = take(sizeof(int32_t) * pl.n_tiles);
@@ -310,10 +310,10 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.dt = desc->dt_us;
     p.inv_tau = 1.0 / desc->tau_us;
     p.gamma = desc->gamma_mhz_per_g;
+    p.rc = make_run_const(desc->t0_us, desc->dt_us, desc->tau_us, desc->gamma_mhz_per_g);
     p.K = pl.K;
     p.P = pl.P;
     p.obj = obj;
-    p.hconst = reinterpret_cast<HistConst*>(base + o_hc);
     p.partial = reinterpret_cast<double*>(base + o_part);
     p.hist_sum = reinterpret_cast<double*>(base + o_hsum);
     p.global_count = reinterpret_cast<unsigned*>(base + o_cnt);
@@ -323,6 +323,8 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.hist_nclusters = reinterpret_cast<const int32_t*>(base + o_hn);
     p.n_clusters = pl.n_clusters;
     p.cluster = pl.cluster;
+    p.chunks = 1;
+    p.preload = 0;
     p.csr_ptr = reinterpret_cast<const int32_t*>(base + o_cp);
     p.csr_src = reinterpret_cast<const int32_t*>(base + o_cs);
     p.n_out = pl.n_out;

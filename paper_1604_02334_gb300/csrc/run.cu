@@ -36,28 +36,54 @@ cudaError_t launch_eval(const Signature& s, int mode, int threads, int n_tiles, 
     return cudaErrorInvalidValue;
 }
 
-template <int NE, int NG, int KT>
-void stage_host_sig(int K, const int32_t* role_theta, const double* theta, const TimeGrid& tg,
-                    HistConst* out) {
-    for (int k = 0; k < K; ++k) {
-        memset(&out[k], 0, sizeof(HistConst));
-        for (int part = 0; part < stage_parts<NE, NG, KT>(); ++part)
-            stage_hist<NE, NG, KT, true>(part, role_theta + (size_t)k * kMaxRoles * 2, theta, tg, out[k]);
-    }
+namespace {
+// |a * b| as unsigned 64.64 fixed point, exactly (truncated at 2^-64), from the
+// two doubles' significands; *neg receives the product's sign.
+ulonglong2 product_fixed(double a, double b, int* neg) {
+    *neg = 0;
+    if (a == 0.0 || b == 0.0 || !isfinite(a) || !isfinite(b)) return ulonglong2{0ull, 0ull};
+    *neg = (a < 0.0) != (b < 0.0);
+    int ea, eb;
+    const double fa = frexp(fabs(a), &ea), fb = frexp(fabs(b), &eb);  // [0.5, 1)
+    const unsigned long long ma = (unsigned long long)ldexp(fa, 53);
+    const unsigned long long mb = (unsigned long long)ldexp(fb, 53);
+    const unsigned __int128 P = (unsigned __int128)ma * mb;  // |ab| = P * 2^(ea + eb - 106)
+    const int sh = ea + eb - 106 + 64;                       // |ab| * 2^64 = P * 2^sh
+    unsigned __int128 V;
+    if (sh >= 0) V = sh < 22 ? P << sh : ~(unsigned __int128)0;  // |ab| < 2^64 in practice
+    else V = -sh < 128 ? P >> -sh : 0;
+    return ulonglong2{(unsigned long long)(V >> 64), (unsigned long long)V};
 }
 
-void stage_host(const Signature& s, int K, const int32_t* role_theta, const double* theta, double t0,
-                double dt, double inv_tau, double gamma, HistConst* out) {
-    const TimeGrid tg{t0, dt, inv_tau, gamma};
-#define MUSR_CASE(NE, NG, KT) \
-    if (s.ne == NE && s.ng == NG && s.kt == KT) return stage_host_sig<NE, NG, KT>(K, role_theta, theta, tg, out);
-    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
-    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
-    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
-    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
-    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
-    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
-#undef MUSR_CASE
+float2 df_split(double v) {
+    const float hi = (float)v;
+    return float2{hi, (float)(v - (double)hi)};
+}
+}  // namespace
+
+RunConst make_run_const(double t0, double dt, double tau, double gamma) {
+    const double LOG2E = 1.4426950408889634074;
+    RunConst rc;
+    memset(&rc, 0, sizeof(rc));
+    rc.inv_tau = df_split(1.0 / tau);
+    rc.dt = df_split(dt);
+    rc.dt_log2e = df_split(dt * LOG2E);
+    rc.t0 = df_split(t0);
+    rc.t0_dt_log2e = df_split(t0 * dt * LOG2E);
+    rc.half_dt2_log2e = df_split(0.5 * dt * dt * LOG2E);
+    const float2 aE = df_split(dt / tau * LOG2E);
+    rc.aE_hi = aE.x;
+    rc.aE_lo = aE.y;
+    rc.qE = (float)expm1(-dt / tau);
+    rc.cE = (float)exp(-t0 / tau);
+    rc.kfreq = (float)(2.0 * 3.14159265358979323846 * gamma);
+    rc.t0_zero = t0 == 0.0;
+    int neg = 0;
+    rc.turns_per_bin = product_fixed(gamma, dt, &neg);  // dt > 0; gamma >= 0 is checked at plan
+    rc.turns_at_t0 = product_fixed(gamma, t0, &neg);    // t0 >= 0 is checked at plan
+    // 1 / (2 pi) = 0.1591549430918953357688837633725143620344596457404564487476673440588967976342265350901138027662530859560728427267...
+    rc.inv_two_pi = ulonglong2{0ull, 2935890503282001226ull};
+    return rc;
 }
 
 thread_local const char* g_last_cuda_error = "none";
@@ -122,7 +148,10 @@ int musr_run_s::plan(const musr_run_desc* d) {
     tau = d->tau_us;
     gamma = d->gamma_mhz_per_g;
     if (K < 0 || P < 0 || P > kMaxParams || W < 2 || W > 32 || d->n_comp < 0) return MUSR_EINVAL;
-    if (!(dt > 0.0) || !(tau > 0.0) || !isfinite(t0) || !isfinite(gamma)) return MUSR_EINVAL;
+    if (!(dt > 0.0) || !(tau > 0.0) || !(t0 >= 0.0) || !isfinite(t0) || !(gamma >= 0.0) ||
+        !isfinite(gamma))
+        return MUSR_EINVAL;
+    rc = make_run_const(t0, dt, tau, gamma);
     if (K > 0 && (!d->n_bins || !d->map)) return MUSR_EINVAL;
     if (d->n_comp > 0 && !d->comp) return MUSR_EINVAL;
     n_bins.assign(d->n_bins, d->n_bins + K);
@@ -182,47 +211,7 @@ int musr_run_s::plan(const musr_run_desc* d) {
             q[2] = map_col(this, k, m.rate);
         }
     }
-    // tiling: largest block that still gives >= 2 blocks per SM
-    int dev_sms = 152;
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
-    threads = 32;
-    for (int t = kMaxThreads; t >= 32; t >>= 1) {
-        int64_t tiles = 0;
-        for (int k = 0; k < K; ++k)
-            tiles += std::max<int64_t>(1, (n_bins[k] + t * kBinsPerThread - 1) / (t * kBinsPerThread));
-        if (tiles >= 2 * dev_sms) {
-            threads = t;
-            break;
-        }
-    }
-    return build_tiles(threads);
-}
-
-int musr_run_s::build_tiles(int t) {
-    threads = t;
-    tile_bins = t * kBinsPerThread;
-    // cluster size: the largest of 8, 4, 2, 1 whose padding (every histogram's
-    // tiles rounded up to whole clusters) adds at most 25 % empty tiles
-    std::vector<int64_t> nt(K);
-    int64_t raw = 0;
-    for (int k = 0; k < K; ++k) {
-        nt[k] = std::max<int64_t>(1, (n_bins[k] + tile_bins - 1) / tile_bins);
-        raw += nt[k];
-    }
-    cluster = 1;
-    for (int c = 8; c >= 2; c >>= 1) {
-        int64_t padded = 0;
-        for (int k = 0; k < K; ++k) padded += (nt[k] + c - 1) / c * c;
-        if (padded * 4 <= raw * 5) {
-            cluster = c;
-            break;
-        }
-    }
-    tile_hist.clear();
-    tile_start.clear();
-    cluster_hist.clear();
-    hist_first_cluster.assign(K, 0);
-    hist_nclusters.assign(K, 0);
+    // data layout: every histogram at a multiple of 8 floats
     hist_off.assign(K, 0);
     model_off.assign(K, 0);
     int64_t off = 0, moff = 0;
@@ -231,19 +220,66 @@ int musr_run_s::build_tiles(int t) {
         model_off[k] = moff;
         off += round_up(n_bins[k], 8);
         moff += n_bins[k];
-        const int64_t ncl = (nt[k] + cluster - 1) / cluster;
-        hist_first_cluster[k] = (int32_t)cluster_hist.size();
-        hist_nclusters[k] = (int32_t)ncl;
-        for (int64_t j = 0; j < ncl * cluster; ++j) {
-            tile_hist.push_back(k);
-            tile_start.push_back((int32_t)std::min<int64_t>(j * tile_bins, round_up(n_bins[k], 8)));
-        }
-        for (int64_t c = 0; c < ncl; ++c) cluster_hist.push_back(k);
     }
     data_floats = (size_t)off + 8;
-    n_tiles = (int)tile_hist.size();
-    n_clusters = (int)cluster_hist.size();
     return MUSR_OK;
+}
+
+// Tiles of `chunks` stripes of t x 8 bins; cluster size the largest of 8, 4,
+// 2, 1 whose padding (every histogram's tiles rounded up to whole clusters)
+// adds at most 25 % empty tiles.
+void musr_run_s::build_tiles(Tiling& T, int t, int chunks) const {
+    T.threads = t;
+    T.chunks = chunks;
+    T.tile_bins = t * kBinsPerThread * chunks;
+    std::vector<int64_t> nt(K);
+    int64_t raw = 0;
+    for (int k = 0; k < K; ++k) {
+        nt[k] = std::max<int64_t>(1, (n_bins[k] + T.tile_bins - 1) / T.tile_bins);
+        raw += nt[k];
+    }
+    T.cluster = 1;
+    for (int c = 8; c >= 2; c >>= 1) {
+        int64_t padded = 0;
+        for (int k = 0; k < K; ++k) padded += (nt[k] + c - 1) / c * c;
+        if (padded * 4 <= raw * 5) {
+            T.cluster = c;
+            break;
+        }
+    }
+    T.tile_hist.clear();
+    T.tile_start.clear();
+    T.cluster_hist.clear();
+    T.hist_first_cluster.assign(K, 0);
+    T.hist_nclusters.assign(K, 0);
+    for (int k = 0; k < K; ++k) {
+        const int64_t ncl = (nt[k] + T.cluster - 1) / T.cluster;
+        T.hist_first_cluster[k] = (int32_t)T.cluster_hist.size();
+        T.hist_nclusters[k] = (int32_t)ncl;
+        for (int64_t j = 0; j < ncl * T.cluster; ++j) {
+            T.tile_hist.push_back(k);
+            T.tile_start.push_back((int32_t)std::min<int64_t>(j * T.tile_bins, round_up(n_bins[k], 8)));
+        }
+        for (int64_t c = 0; c < ncl; ++c) T.cluster_hist.push_back(k);
+    }
+    T.n_tiles = (int)T.tile_hist.size();
+    T.n_clusters = (int)T.cluster_hist.size();
+}
+
+// Dynamic shared memory of the objective kernel's tail for a mode / tiling: a
+// window of cluster partials, the histogram sums and the CSR when they fit.
+int musr_run_s::tail_smem(int mode, const Tiling& T, int* win, int* hsum_smem, int* csr_smem) const {
+    const int nacc = n_acc(mode, R);
+    const int w = std::max(nacc, std::min(T.n_clusters * nacc, 4096 / nacc * nacc));
+    const int hs = (size_t)K * nacc * 8 <= 64 * 1024;
+    const int cs = ((size_t)n_out[mode] + 1 + n_src[mode]) * 4 <= 64 * 1024;
+    if (win) *win = w;
+    if (hsum_smem) *hsum_smem = hs;
+    if (csr_smem) *csr_smem = cs;
+    // the CSR region doubles as the preloaded-table region (CSR + cluster tables)
+    const size_t tables = (size_t)n_out[mode] + 1 + n_src[mode] + T.n_clusters + 2 * (size_t)K;
+    const size_t csr_ints = cs ? std::max(tables, (size_t)n_out[mode] + 1 + n_src[mode]) : 0;
+    return (int)(8 * ((size_t)w + (hs ? (size_t)K * nacc : 0)) + 4 * csr_ints);
 }
 
 // CSR of output entry -> (histogram, accumulator) sources for one mode.
@@ -305,15 +341,38 @@ int musr_run_s::allocate() {
         build_csr(m, ptr[m], src[m]);
         n_out[m] = (int)ptr[m].size() - 1;
         n_src[m] = (int)src[m].size();
-        // tail of the objective kernel: a window of cluster partials, the
-        // histogram sums and the CSR in shared memory when they fit
-        const int nacc = n_acc(m, R);
-        const int w = std::max(nacc, std::min(n_clusters * nacc, 4096 / nacc * nacc));
-        win_doubles[m] = w;
-        hsum_in_smem[m] = (size_t)K * nacc * 8 <= 64 * 1024;
-        csr_in_smem[m] = ((size_t)n_out[m] + 1 + n_src[m]) * 4 <= 64 * 1024;
-        smem_bytes[m] = (int)(8 * ((size_t)w + (hsum_in_smem[m] ? (size_t)K * nacc : 0)) +
-                              (csr_in_smem[m] ? 4 * ((size_t)n_out[m] + 1 + n_src[m]) : 0));
+    }
+    // per-mode tiling: the largest block giving >= 2 blocks per SM at one
+    // stripe per tile, then enough stripes per tile that the whole grid is one
+    // wave of resident blocks (resident count from the kernel's occupancy)
+    int dev_sms = 152;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
+    for (int m = 0; m < 4; ++m) {
+        if (m == kGN && P > kMaxGnParams) continue;
+        int t = 32;
+        for (int c = kMaxThreads; c >= 32; c >>= 1) {
+            int64_t tiles = 0;
+            for (int k = 0; k < K; ++k)
+                tiles += std::max<int64_t>(1, (n_bins[k] + c * kBinsPerThread - 1) / (c * kBinsPerThread));
+            if (tiles >= 2 * dev_sms) {
+                t = c;
+                break;
+            }
+        }
+        build_tiles(tl[m], t, 1);
+        int per_sm = 0;
+        EvalParams q;
+        memset(&q, 0, sizeof(q));
+        q.smem_bytes = m == kModel ? 0 : tail_smem(m, tl[m], nullptr, nullptr, nullptr);
+        q.status_out = reinterpret_cast<int32_t*>(&per_sm);
+        if (launch_eval(sig, m, t, -1, stream, q) != cudaSuccess || per_sm < 1) per_sm = 1;
+        const int64_t resident = (int64_t)per_sm * dev_sms * 9 / 10;
+        int chunks = 1;
+        while (chunks < 8 && tl[m].n_tiles > resident) {
+            ++chunks;
+            build_tiles(tl[m], t, chunks);
+        }
+        if (m < 3) smem_bytes[m] = tail_smem(m, tl[m], &win_doubles[m], &hsum_in_smem[m], &csr_in_smem[m]);
     }
     const int n_out_max = n_out[P <= kMaxGnParams ? kGN : kGrad];
     Arena A;
@@ -321,19 +380,23 @@ int musr_run_s::allocate() {
     const size_t o_hoff = A.take<int64_t>(K + 1);
     const size_t o_moff = A.take<int64_t>(K + 1);
     const size_t o_nb = A.take<int32_t>(K + 1);
-    const size_t o_th = A.take<int32_t>(n_tiles);
-    const size_t o_ts = A.take<int32_t>(n_tiles);
-    const size_t o_ch = A.take<int32_t>(n_clusters + 1);
-    const size_t o_hf = A.take<int32_t>(K + 1);
-    const size_t o_hn = A.take<int32_t>(K + 1);
-    const size_t o_hc = A.take<HistConst>(K + 1);
+    size_t o_th[4], o_ts[4], o_ch[4], o_hf[4], o_hn[4];
+    int max_clusters = 1;
+    for (int m = 0; m < 4; ++m) {
+        o_th[m] = A.take<int32_t>(tl[m].n_tiles + 1);
+        o_ts[m] = A.take<int32_t>(tl[m].n_tiles + 1);
+        o_ch[m] = A.take<int32_t>(tl[m].n_clusters + 1);
+        o_hf[m] = A.take<int32_t>(K + 1);
+        o_hn[m] = A.take<int32_t>(K + 1);
+        if (m < 3) max_clusters = std::max(max_clusters, tl[m].n_clusters);
+    }
     const size_t o_rt = A.take<int32_t>(role_theta.size() + 1);
     size_t o_ptr[3], o_src[3];
     for (int m = 0; m < 3; ++m) {
         o_ptr[m] = A.take<int32_t>(ptr[m].size() + 1);
         o_src[m] = A.take<int32_t>(src[m].size() + 1);
     }
-    const size_t o_part = A.take<double>((size_t)n_clusters * nacc_max);
+    const size_t o_part = A.take<double>((size_t)max_clusters * nacc_max);
     const size_t o_hsum = A.take<double>((size_t)(K + 1) * nacc_max);
     const size_t o_cnt = A.take<unsigned>(4);
     const size_t o_theta = A.take<double>(P + 1);
@@ -349,12 +412,13 @@ int musr_run_s::allocate() {
     d_hist_off = reinterpret_cast<int64_t*>(b + o_hoff);
     d_model_off = reinterpret_cast<int64_t*>(b + o_moff);
     d_hist_nbins = reinterpret_cast<int32_t*>(b + o_nb);
-    d_tile_hist = reinterpret_cast<int32_t*>(b + o_th);
-    d_tile_start = reinterpret_cast<int32_t*>(b + o_ts);
-    d_cluster_hist = reinterpret_cast<int32_t*>(b + o_ch);
-    d_hist_first_cluster = reinterpret_cast<int32_t*>(b + o_hf);
-    d_hist_nclusters = reinterpret_cast<int32_t*>(b + o_hn);
-    d_hconst = reinterpret_cast<HistConst*>(b + o_hc);
+    for (int m = 0; m < 4; ++m) {
+        tl[m].d_tile_hist = reinterpret_cast<int32_t*>(b + o_th[m]);
+        tl[m].d_tile_start = reinterpret_cast<int32_t*>(b + o_ts[m]);
+        tl[m].d_cluster_hist = reinterpret_cast<int32_t*>(b + o_ch[m]);
+        tl[m].d_hist_first_cluster = reinterpret_cast<int32_t*>(b + o_hf[m]);
+        tl[m].d_hist_nclusters = reinterpret_cast<int32_t*>(b + o_hn[m]);
+    }
     d_role_theta = reinterpret_cast<int32_t*>(b + o_rt);
     for (int m = 0; m < 3; ++m) {
         d_csr_ptr[m] = reinterpret_cast<int32_t*>(b + o_ptr[m]);
@@ -370,8 +434,7 @@ int musr_run_s::allocate() {
 
     // host staging, mapped so the kernel writes host-call results straight
     // into it (no copy node after the kernel)
-    if (cudaHostAlloc(&h_pinned, sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64 +
-                                     sizeof(HistConst) * (size_t)(K + 1),
+    if (cudaHostAlloc(&h_pinned, sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64,
                       cudaHostAllocMapped) != cudaSuccess) {
         h_pinned = nullptr;
         return MUSR_ENOMEM;
@@ -379,8 +442,6 @@ int musr_run_s::allocate() {
     h_theta = static_cast<double*>(h_pinned);
     h_out = h_theta + P + 1;
     h_status = reinterpret_cast<int32_t*>(h_out + n_out_max + 1);
-    h_hconst = reinterpret_cast<HistConst*>(static_cast<char*>(h_pinned) +
-                                            ((sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64 + 15) / 16 * 16));
     if (cudaHostGetDevicePointer((void**)&hd_out, h_out, 0) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&hd_status, h_status, 0) != cudaSuccess)
         return MUSR_ECUDA;
@@ -395,11 +456,14 @@ int musr_run_s::allocate() {
     up(d_hist_off, hist_off.data(), sizeof(int64_t) * K);
     up(d_model_off, model_off.data(), sizeof(int64_t) * K);
     up(d_hist_nbins, nb32.data(), sizeof(int32_t) * K);
-    up(d_tile_hist, tile_hist.data(), sizeof(int32_t) * n_tiles);
-    up(d_tile_start, tile_start.data(), sizeof(int32_t) * n_tiles);
-    up(d_cluster_hist, cluster_hist.data(), sizeof(int32_t) * n_clusters);
-    up(d_hist_first_cluster, hist_first_cluster.data(), sizeof(int32_t) * K);
-    up(d_hist_nclusters, hist_nclusters.data(), sizeof(int32_t) * K);
+    for (int m = 0; m < 4; ++m) {
+        const Tiling& T = tl[m];
+        up(T.d_tile_hist, T.tile_hist.data(), sizeof(int32_t) * T.n_tiles);
+        up(T.d_tile_start, T.tile_start.data(), sizeof(int32_t) * T.n_tiles);
+        up(T.d_cluster_hist, T.cluster_hist.data(), sizeof(int32_t) * T.n_clusters);
+        up(T.d_hist_first_cluster, T.hist_first_cluster.data(), sizeof(int32_t) * K);
+        up(T.d_hist_nclusters, T.hist_nclusters.data(), sizeof(int32_t) * K);
+    }
     up(d_role_theta, role_theta.data(), sizeof(int32_t) * role_theta.size());
     for (int m = 0; m < 3; ++m) {
         up(d_csr_ptr[m], ptr[m].data(), sizeof(int32_t) * ptr[m].size());
@@ -409,7 +473,7 @@ int musr_run_s::allocate() {
     for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
         if (m == kGN && P > kMaxGnParams) continue;
         EvalParams q = params(MUSR_CHI2, m, d_theta, d_out, d_status);
-        e = launch_eval(sig, m, threads, 0, stream, q);
+        e = launch_eval(sig, m, tl[m].threads, 0, stream, q);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * 4, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_data, 0, sizeof(float) * data_floats, stream);
@@ -470,27 +534,29 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.data = d_data;
     p.hist_off = d_hist_off;
     p.hist_nbins = d_hist_nbins;
-    p.tile_hist = d_tile_hist;
-    p.tile_start = d_tile_start;
+    const Tiling& T = tl[mode];
+    p.tile_hist = T.d_tile_hist;
+    p.tile_start = T.d_tile_start;
     p.role_theta = d_role_theta;
     p.theta = theta_dev;
     p.t0 = t0;
     p.dt = dt;
     p.inv_tau = 1.0 / tau;
     p.gamma = gamma;
+    p.rc = rc;
     p.K = K;
     p.P = P;
     p.obj = obj;
-    p.hconst = d_hconst;
     p.partial = d_partial;
     p.hist_sum = d_hist_sum;
     p.global_count = d_counters;
     p.flags = d_counters + 1;
-    p.cluster_hist = d_cluster_hist;
-    p.hist_first_cluster = d_hist_first_cluster;
-    p.hist_nclusters = d_hist_nclusters;
-    p.n_clusters = n_clusters;
-    p.cluster = mode == kModel ? 1 : cluster;
+    p.cluster_hist = T.d_cluster_hist;
+    p.hist_first_cluster = T.d_hist_first_cluster;
+    p.hist_nclusters = T.d_hist_nclusters;
+    p.n_clusters = T.n_clusters;
+    p.cluster = mode == kModel ? 1 : T.cluster;
+    p.chunks = T.chunks;
     const int m = mode == kModel ? kValue : mode;
     p.csr_ptr = d_csr_ptr[m];
     p.csr_src = d_csr_src[m];
@@ -499,6 +565,10 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.win_doubles = win_doubles[m];
     p.hsum_in_smem = hsum_in_smem[m];
     p.csr_in_smem = csr_in_smem[m];
+    // small tables are preloaded by every block (overlapping its staging)
+    p.preload = mode != kModel && csr_in_smem[m] &&
+                (n_out[m] + 1 + n_src[m] + T.n_clusters + 2 * K) <= 1024 &&
+                T.threads > 32 * (2 + 2 * sig.n_osc());  // warps beyond the staging ones exist
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
     p.out = out_dev;
     p.status_out = status_dev;
@@ -512,7 +582,7 @@ int musr_run_s::launch(int obj, int mode, const double* theta_dev, double* out_d
     if (K == 0) return MUSR_OK;
     EvalParams p = params(obj, mode, theta_dev, out_dev, status_dev);
     p.model_out = model_out;
-    return cuda_status(launch_eval(sig, mode, threads, n_tiles, st, p));
+    return cuda_status(launch_eval(sig, mode, tl[mode].threads, tl[mode].n_tiles, st, p));
 }
 
 // Host-pointer evaluation through a cached CUDA graph.
@@ -528,20 +598,19 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
         *flags = 0;
         return MUSR_OK;
     }
-    // one launch: the histogram constants are staged here in FP64 and travel
-    // inline in the launch parameters (through device memory beyond
-    // kInlineHists histograms); results land in mapped host memory
+    // one launch: theta travels inline in the launch parameters (through device
+    // memory beyond kInlineParams), results land in mapped host memory
     EvalParams p = params(obj, mode, nullptr, hd_out, hd_status);
     cudaError_t e = cudaSuccess;
-    if (K <= kInlineHists) {
-        stage_host(sig, K, role_theta.data(), theta, t0, dt, 1.0 / tau, gamma, p.hconst_inline);
-        p.hconst_inline_n = K;
+    if (P <= kInlineParams) {
+        p.theta_inline_n = P;
+        memcpy(p.theta_inline, theta, sizeof(double) * P);
     } else {
-        stage_host(sig, K, role_theta.data(), theta, t0, dt, 1.0 / tau, gamma, h_hconst);
-        e = cudaMemcpyAsync(d_hconst, h_hconst, sizeof(HistConst) * K, cudaMemcpyHostToDevice, stream);
-        p.hconst_ready = 1;
+        memcpy(h_theta, theta, sizeof(double) * P);
+        e = cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * P, cudaMemcpyHostToDevice, stream);
+        p.theta = d_theta;
     }
-    if (e == cudaSuccess) e = launch_eval(sig, mode, threads, n_tiles, stream, p);
+    if (e == cudaSuccess) e = launch_eval(sig, mode, tl[mode].threads, tl[mode].n_tiles, stream, p);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(e);
     memcpy(out_host, h_out, sizeof(double) * nout);

@@ -22,25 +22,29 @@ struct musr_run_s {
     std::vector<int32_t> map;
     std::vector<musr_component> comp;
     double t0 = 0, dt = 0, tau = 0, gamma = 0;
+    musr::RunConst rc;  // theta-independent constants of the time grid
     int64_t total_bins = 0;
     musr::Signature sig;
     int R = 0;
     std::vector<int32_t> role_theta;  // [K][kMaxRoles][2]
-    // tiling
-    int threads = 256, tile_bins = 2048, n_tiles = 0;
-    int cluster = 1, n_clusters = 0;  // clusters of `cluster` consecutive tiles, one histogram each
-    std::vector<int32_t> tile_hist, tile_start, cluster_hist, hist_first_cluster, hist_nclusters;
+    // tiling, per mode (value, grad, GN, model): tiles of `chunks` stripes of
+    // threads x 8 bins, grouped in clusters of `cluster` tiles of one histogram,
+    // sized so a launch is one wave of resident blocks
+    struct Tiling {
+        int threads = 256, chunks = 1, tile_bins = 2048, cluster = 1, n_tiles = 0, n_clusters = 0;
+        std::vector<int32_t> tile_hist, tile_start, cluster_hist, hist_first_cluster, hist_nclusters;
+        int32_t *d_tile_hist = nullptr, *d_tile_start = nullptr, *d_cluster_hist = nullptr;
+        int32_t *d_hist_first_cluster = nullptr, *d_hist_nclusters = nullptr;
+    };
+    Tiling tl[4];
     std::vector<int64_t> hist_off, model_off;
     size_t data_floats = 0;
     // device memory (one arena)
     void* arena = nullptr;
     float* d_data = nullptr;
     int64_t *d_hist_off = nullptr, *d_model_off = nullptr;
-    int32_t *d_hist_nbins = nullptr, *d_tile_hist = nullptr, *d_tile_start = nullptr;
-    int32_t *d_cluster_hist = nullptr, *d_hist_first_cluster = nullptr, *d_hist_nclusters = nullptr;
+    int32_t* d_hist_nbins = nullptr;
     int32_t* d_role_theta = nullptr;
-    musr::HistConst* d_hconst = nullptr;
-    musr::HistConst* h_hconst = nullptr;  // pinned
     int32_t* d_csr_ptr[3] = {nullptr, nullptr, nullptr};
     int32_t* d_csr_src[3] = {nullptr, nullptr, nullptr};
     int n_out[3] = {0, 0, 0};
@@ -66,7 +70,8 @@ struct musr_run_s {
     int fd_batch_vec = 0;
 
     int plan(const musr_run_desc* d);
-    int build_tiles(int threads);
+    void build_tiles(Tiling& t, int threads, int chunks) const;
+    int tail_smem(int mode, const Tiling& t, int* win, int* hsum_smem, int* csr_smem) const;
     void build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const;
     int allocate();
     int upload(int dtype, const void* data, int on_device);

@@ -60,7 +60,7 @@ def test_multi_detector_value_grad_gn(md_small, obj, oobj):
         v0 = run.chi2(th, obj)
     rv, rg, rH = oracle.gradient(lay, d, th, oobj)
     assert rel_err(v, rv) <= 1e-6
-    assert rel_err(v0, v) <= 1e-9  # value-only and adjoint instantiations
+    assert rel_err(v0, v) <= 1e-7  # value-only and adjoint launches (tilings differ per mode)
     assert grad_rel_err(g, rg) <= 1e-4
     assert np.linalg.norm(H - rH) / np.linalg.norm(rH) <= 1e-4
 
