@@ -177,6 +177,29 @@ int musr_batch_eval(musr_batch batch, int obj, const double* thetas, const int32
 int musr_batch_eval_device(musr_batch batch, int obj, const double* thetas_dev,
                            double* values_dev);
 
+/*
+ * Synthetic data.  (The paper fits measured histograms; the learned start
+ * proposer is trained on histograms generated from the theory of Eq. 1.)
+ *
+ * musr_poisson_sample: counts_dev[i] ~ Poisson(mu_dev[i]) for n FP32 means on
+ * the device.  Random numbers: Philox4x32-10 keyed by seed, counter (attempt,
+ * i low, i high, 0xffffffff).  Inversion below mean 12, Hormann's PTRS above.
+ * Asynchronous on stream.
+ *
+ * musr_generate: for n_samples parameter vectors thetas_dev (FP64, n_samples x
+ * P, device) of the run's layout, the theory summed over groups of `rebin`
+ * consecutive bins (the last group of a histogram may be short), a Poisson
+ * count drawn for every group (counter (attempt, group, histogram,
+ * sample_offset + sample)), written to out_dev as FP32 counts, or log(1 + count)
+ * if log1p_out != 0; layout sample-major, then histogram, then group
+ * (sum_k ceil(n_bins[k] / rebin) values per sample).  mu_dev (may be NULL)
+ * receives the group means in the same layout.  The run's data are not used.
+ * Asynchronous on stream (NULL = run stream).
+ */
+int musr_poisson_sample(const float* mu_dev, int64_t n, uint64_t seed, int32_t* counts_dev, void* stream);
+int musr_generate(musr_run run, const double* thetas_dev, int32_t n_samples, int32_t rebin, uint64_t seed,
+                  uint64_t sample_offset, int32_t log1p_out, float* out_dev, float* mu_dev, void* stream);
+
 /* Fit options and result (the host minimiser that replaces Minuit2's role,
  * Sec. 4.1). */
 enum {

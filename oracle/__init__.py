@@ -56,8 +56,15 @@ def _load():
             lib.orc_gradient_fd.argtypes = layout + [dp, dp, ctypes.c_int, ctypes.c_double, dp]
             lib.orc_fit.argtypes = layout + [dp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_uint8),
                                              ctypes.c_int, ctypes.c_double, dp, dp]
+            u32p = ctypes.POINTER(ctypes.c_uint32)
+            lib.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+            lib.orc_philox4x32_10.restype = None
+            lib.orc_poisson.argtypes = [ctypes.POINTER(ctypes.c_float), ctypes.c_int64, ctypes.c_uint64,
+                                        ctypes.POINTER(ctypes.c_int32)]
+            lib.orc_poisson.restype = None
+            lib.orc_rebinned_mean.argtypes = layout + [dp, ctypes.c_int, ctypes.c_int, dp]
             for f in (lib.orc_model, lib.orc_objective, lib.orc_gradient, lib.orc_gradient_fd,
-                      lib.orc_fit):
+                      lib.orc_fit, lib.orc_rebinned_mean):
                 f.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             _lib = lib
@@ -164,3 +171,36 @@ def fit(lay, data, theta0, obj=CHI2, free=None, max_iter=500, edm_tol=1e-8):
     info = {"value": stats[0], "ndf": stats[1], "iters": int(stats[2]), "evals": int(stats[3]),
             "edm": stats[4], "mu": stats[5], "status": int(st)}
     return th, info, cov
+
+
+def philox4x32_10(counter, key):
+    """Philox4x32-10 block for a 4-word counter and 2-word key (Salmon et al. 2011)."""
+    lib = _load()
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xffffffff for x in counter])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xffffffff for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return [int(x) for x in o]
+
+
+def poisson(mu, seed):
+    """Poisson variates for FP32 means mu[i] (inversion below 12, PTRS above)."""
+    lib = _load()
+    m = np.ascontiguousarray(mu, dtype=np.float32)
+    out = np.zeros(m.shape[0], dtype=np.int32)
+    lib.orc_poisson(m.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), m.shape[0], int(seed),
+                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    return out
+
+
+def rebinned_mean(lay, thetas, rebin):
+    """Sums of the Eq. 1 theory over groups of `rebin` bins, per parameter vector (FP64)."""
+    lib = _load()
+    args, keep = _layout_args(lay)
+    th = np.ascontiguousarray(np.atleast_2d(thetas), dtype=np.float64)
+    per = int(sum((int(m) + rebin - 1) // rebin for m in lay.n_bins))
+    out = np.zeros(th.shape[0] * per)
+    st = lib.orc_rebinned_mean(*args, _dp(th), th.shape[0], int(rebin), _dp(out))
+    if st:
+        raise OracleError(st)
+    return out.reshape(th.shape[0], per)

@@ -587,3 +587,220 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ======================================================================== */
+/* Synthetic-data generator: Philox4x32-10 and a Poisson sampler             */
+/* ======================================================================== */
+/*
+ * Random numbers come from the counter-based generator Philox4x32-10
+ * (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+ * SC 2011): ten rounds of two 32x32->64 multiplications with the round
+ * multipliers 0xD2511F53 / 0xCD9E8D57, the key bumped by the Weyl constants
+ * 0x9E3779B9 / 0xBB67AE85 between rounds.
+ *
+ * Poisson variates: inversion by sequential search for mean < 12, and the
+ * transformed-rejection sampler PTRS of Hormann (1993, "The transformed
+ * rejection method for generating Poisson random variables") above.  The
+ * acceptance test of PTRS compares log(V * alpha^-1 / (a / us^2 + b)) with the
+ * log-probability log p(k; mu); for k >= 10 the latter is written with
+ * Stirling's series in the cancellation-free form
+ *     log p = -mu h(y) + 1/2 log1p(y) - 1/2 log(2 pi mu) - 1/(12 n) + 1/(360 n^3),
+ *     n = k + 1, y = (n - mu) / mu, h(y) = (1 + y) log1p(y) - y,
+ * so that it can be evaluated in FP32 at any mean.
+ *
+ * The sampler's floating-point decisions are taken in FP32, in the operation
+ * order of the GPU sampler, with logarithm and exponential built from IEEE
+ * basic operations (below), so both produce the same integers.  This file is
+ * compiled with -ffp-contract=off; fused multiply-adds appear only as fmaf().
+ */
+static void philox_round(uint32_t c[4], const uint32_t k[2]) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    const uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {key[0], key[1]};
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k[0] += 0x9E3779B9u;
+            k[1] += 0xBB67AE85u;
+        }
+        philox_round(c, k);
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* uniform in (0, 1): ((r >> 9) + 1/2) * 2^-23, exact in FP32, never 0 or 1 */
+static float u01(uint32_t r) { return ((float)(r >> 9) + 0.5f) * 1.1920928955078125e-07f; }
+
+static float f_from_bits(uint32_t b) {
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+static uint32_t bits_from_f(float f) {
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return b;
+}
+
+/* natural log of a positive normal float: x = m 2^e, m in [sqrt(1/2), sqrt(2)),
+ * log m = 2 atanh(s), s = (m - 1)/(m + 1), series to s^9 */
+static float s_log(float x) {
+    const uint32_t b = bits_from_f(x);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = f_from_bits((b & 0x7fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    const float s = (m - 1.0f) / (m + 1.0f);
+    const float s2 = s * s;
+    float p = fmaf(s2, 0.111111111f, 0.142857143f);
+    p = fmaf(s2, p, 0.2f);
+    p = fmaf(s2, p, 0.333333333f);
+    p = p * s2;
+    const float two_s = s + s;
+    const float lm = fmaf(two_s, p, two_s);
+    const float fe = (float)e;
+    return fmaf(fe, 0.693145752f, fmaf(fe, 1.42860677e-06f, lm));
+}
+
+/* exp(x) for x in [-88, 0]: 2^(x log2 e) = 2^n 2^f, 2^f = e^(f ln 2) by a
+ * 10-term Taylor polynomial, 2^n applied to the exponent bits */
+static float s_exp(float x) {
+    const float y = x * 1.44269504f;
+    const float n = floorf(y);
+    const float t = (y - n) * 0.693147181f;
+    float p = fmaf(t, 0.1f, 1.0f);
+    p = fmaf(t * 0.111111111f, p, 1.0f);
+    p = fmaf(t * 0.125f, p, 1.0f);
+    p = fmaf(t * 0.142857143f, p, 1.0f);
+    p = fmaf(t * 0.166666667f, p, 1.0f);
+    p = fmaf(t * 0.2f, p, 1.0f);
+    p = fmaf(t * 0.25f, p, 1.0f);
+    p = fmaf(t * 0.333333333f, p, 1.0f);
+    p = fmaf(t * 0.5f, p, 1.0f);
+    p = fmaf(t, p, 1.0f);
+    const int ni = (int)n;
+    if (ni < -126) return 0.0f;
+    return f_from_bits(bits_from_f(p) + (uint32_t)(ni * (1 << 23)));
+}
+
+/* (1 + y) log1p(y) - y */
+static float s_h(float y) {
+    if (fabsf(y) < 0.125f) {
+        float h = fmaf(y, -1.0f / 72.0f, 1.0f / 56.0f);
+        h = fmaf(y, h, -1.0f / 42.0f);
+        h = fmaf(y, h, 1.0f / 30.0f);
+        h = fmaf(y, h, -1.0f / 20.0f);
+        h = fmaf(y, h, 1.0f / 12.0f);
+        h = fmaf(y, h, -1.0f / 6.0f);
+        h = fmaf(y, h, 0.5f);
+        return h * y * y;
+    }
+    const float u = s_log(1.0f + y);
+    return fmaf(y, u, u - y);
+}
+
+/* log p(k; mu) for k >= 0, mu >= 12 */
+static float s_log_pmf(int k, float mu, float log_mu) {
+    if (k < 10) {
+        float lf = 0.0f;
+        for (int i = 2; i <= k; ++i) lf = lf + s_log((float)i);
+        return fmaf((float)k, log_mu, -mu) - lf;
+    }
+    const float n = (float)(k + 1);
+    const float y = (n - mu) / mu;
+    const float l1p = s_log(1.0f + y);
+    const float rn = 1.0f / n;
+    float v = -(mu * s_h(y));
+    v = fmaf(0.5f, l1p, v);
+    v = v - 0.5f * s_log(6.28318531f * mu);
+    v = v - rn * 0.0833333333f;
+    v = fmaf(rn * rn * rn, 0.00277777778f, v);
+    return v;
+}
+
+/* Poisson variate for mean mu; ctr[1..3] identify the draw, ctr[0] counts
+ * the Philox blocks it consumes. */
+int32_t orc_poisson_one(float mu, const uint32_t key[2], uint32_t c1, uint32_t c2, uint32_t c3) {
+    if (!(mu > 0.0f)) return 0;
+    uint32_t ctr[4] = {0u, c1, c2, c3}, r[4];
+    if (mu < 12.0f) {
+        orc_philox4x32_10(ctr, key, r);
+        const float u = u01(r[0]);
+        float p = s_exp(-mu);
+        float F = p;
+        int32_t k = 0;
+        while (u > F && k < 1000) {
+            k = k + 1;
+            p = (p * mu) / (float)k;
+            F = F + p;
+        }
+        return k;
+    }
+    const float slam = sqrtf(mu);
+    const float log_mu = s_log(mu);
+    const float b = fmaf(2.53f, slam, 0.931f);
+    const float a = fmaf(0.02483f, b, -0.059f);
+    const float inv_alpha = 1.1239f + 1.1328f / (b - 3.4f);
+    const float vr = 0.9277f - 3.6224f / (b - 2.0f);
+    for (uint32_t it = 0; it < 64u; ++it) {
+        ctr[0] = it;
+        orc_philox4x32_10(ctr, key, r);
+        const float U = u01(r[0]) - 0.5f;
+        const float V = u01(r[1]);
+        const float us = 0.5f - fabsf(U);
+        const float kf = floorf(fmaf((a + a) / us + b, U, mu + 0.43f));
+        if (us >= 0.07f && V <= vr) return (int32_t)kf;
+        if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+        const float lhs = s_log((V * inv_alpha) / (a / (us * us) + b));
+        if (lhs <= s_log_pmf((int)kf, mu, log_mu)) return (int32_t)kf;
+    }
+    return (int32_t)floorf(mu + 0.5f);
+}
+
+/* counts[i] for means mu[i]: draw i uses counter words (i lo, i hi, 0xffffffff) */
+void orc_poisson(const float* mu, int64_t n, uint64_t seed, int32_t* counts) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        counts[i] = orc_poisson_one(mu[i], key, (uint32_t)i, (uint32_t)((uint64_t)i >> 32), 0xffffffffu);
+}
+
+/* Rebinned means of the Eq. 1 theory: for each parameter vector s, histogram
+ * k and group j, the sum of N over bins [j rebin, min((j+1) rebin, M_k)).
+ * out: n_samples x sum_k ceil(M_k / rebin), FP64. */
+int orc_rebinned_mean(LAYOUT_ARGS, const double* thetas, int n_samples, int rebin, double* out) {
+    MAKE_LAYOUT;
+    int st = check_layout(&L);
+    if (st) return st;
+    if (rebin < 1 || L.map_width > 64) return ORC_EINVAL;
+    int64_t per = 0;
+    for (int k = 0; k < L.n_hist; ++k) per += (L.n_bins[k] + rebin - 1) / rebin;
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < n_samples; ++s) {
+        const double* th = thetas + (int64_t)s * L.n_params;
+        int64_t o = (int64_t)s * per;
+        for (int k = 0; k < L.n_hist; ++k) {
+            const int64_t M = L.n_bins[k];
+            for (int64_t j0 = 0; j0 < M; j0 += rebin) {
+                orc_acc a = {0.0, 0.0};
+                for (int64_t i = j0; i < j0 + rebin && i < M; ++i)
+                    acc_add(&a, theory_bin(&L, th, k, L.t0 + (double)i * L.dt, NULL));
+                out[o++] = acc_val(&a);
+            }
+        }
+    }
+    return ORC_OK;
+}

@@ -163,6 +163,19 @@ class Run:
             ctypes.c_void_p(status_dev.data_ptr()) if status_dev is not None else None, st),
             "musr_chi2_grad_device")
 
+    # -- synthetic data ------------------------------------------------------
+    def generate(self, thetas_dev, rebin, seed, out_dev, sample_offset=0, log1p_out=False,
+                 mu_dev=None, stream=None):
+        """Poisson histograms of the theory, summed over groups of `rebin` bins,
+        for every row of thetas_dev (CUDA FP64 [n, P]) into out_dev (CUDA FP32)."""
+        st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
+        n = int(thetas_dev.shape[0])
+        check(_lib.load().musr_generate(self.handle, ctypes.c_void_p(thetas_dev.data_ptr()), n, int(rebin),
+                                        int(seed) & 0xffffffffffffffff, int(sample_offset),
+                                        1 if log1p_out else 0, ctypes.c_void_p(out_dev.data_ptr()),
+                                        ctypes.c_void_p(mu_dev.data_ptr()) if mu_dev is not None else None,
+                                        st), "musr_generate")
+
     # -- fit ----------------------------------------------------------------
     def fit(self, theta0, obj=MUSR_CHI2, free=None, method=MUSR_FIT_LM, max_iter=500,
             edm_tol=1e-8, mu0=1e-3, fd_rel_h=0.0):
@@ -271,6 +284,15 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def poisson_sample(mu_dev, seed, counts_dev, stream=None):
+    """counts_dev[i] ~ Poisson(mu_dev[i]) (CUDA FP32 in, CUDA int32 out)."""
+    st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
+    check(_lib.load().musr_poisson_sample(ctypes.c_void_p(mu_dev.data_ptr()), int(mu_dev.numel()),
+                                          int(seed) & 0xffffffffffffffff,
+                                          ctypes.c_void_p(counts_dev.data_ptr()), st),
+          "musr_poisson_sample")
 
 
 def chi2_batch(runs, thetas, n_vec, obj=MUSR_CHI2):

@@ -106,6 +106,9 @@ SIGNATURES = {
     "musr_batch_eval_device": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "musr_fit": (ctypes.c_int, [_run, ctypes.c_int, _dp, _u8p, ctypes.POINTER(musr_fit_opts),
                                 ctypes.POINTER(musr_fit_result)]),
+    "musr_poisson_sample": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]),
+    "musr_generate": (ctypes.c_int, [_run, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                     ctypes.c_uint64, ctypes.c_int32, _vp, _vp, _vp]),
     "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "musr_version": (ctypes.c_char_p, []),
     "musr_last_cuda_error": (ctypes.c_char_p, []),

@@ -327,6 +327,8 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
 
         if (MODE == kModel) {
             if (n0 + g < M) model_dst[n0 + g] = N;
+        } else if (MODE == kSum) {
+            if (n0 + g < M) acc[0] += N;
         } else if (n0 + g < M) {
             const float dv = d[g];
             float term, wg, wh;

@@ -53,7 +53,7 @@ struct Signature {
 };
 
 // Evaluation modes (kernel template parameter).
-enum Mode { kValue = 0, kGrad = 1, kGN = 2, kModel = 3 };
+enum Mode { kValue = 0, kGrad = 1, kGN = 2, kModel = 3, kSum = 4 };
 
 inline int n_acc(int mode, int R) {
     return mode == kValue ? 1 : mode == kGrad ? 1 + R : mode == kGN ? 1 + R + R * (R + 1) / 2 : 0;

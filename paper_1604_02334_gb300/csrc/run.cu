@@ -620,6 +620,7 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
 
 musr_run_s::~musr_run_s() {
     if (fd_batch) musr_batch_destroy(fd_batch);
+    if (d_group_off) cudaFree(d_group_off);
     if (arena) cudaFree(arena);
     if (h_pinned) cudaFreeHost(h_pinned);
     if (cap_stream) cudaStreamDestroy(cap_stream);

@@ -65,6 +65,10 @@ struct musr_run_s {
     // streams
     cudaStream_t stream = nullptr, cap_stream = nullptr;
     bool own_stream = false;
+    // generator: group offsets for the cached rebin factor
+    int64_t* d_group_off = nullptr;
+    int gen_rebin = 0;
+    int64_t gen_per_sample = 0;
     // batched plan over this run alone, used by the central-difference fit
     musr_batch fd_batch = nullptr;
     int fd_batch_vec = 0;

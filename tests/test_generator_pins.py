@@ -1,0 +1,93 @@
+"""Pins of the oracle's synthetic-data generator (CPU).
+
+Philox4x32-10 is pinned by the statistical properties a counter-based
+generator must have (uniform words, full avalanche of counter and key bits,
+no collisions); the Poisson sampler against scipy's Poisson pmf (goodness of
+fit, mean and variance) on both of its branches; the rebinned means against
+the geometric-series closed form.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+import workloads as W
+
+
+def test_philox_words_are_uniform():
+    words = np.array([oracle.philox4x32_10([i, 7, 0, 3], [11, 13]) for i in range(1 << 14)],
+                     dtype=np.uint64).ravel()
+    counts = np.bincount((words >> 24).astype(np.int64), minlength=256)
+    chi2, p = stats.chisquare(counts)
+    assert p > 1e-4
+    bits = np.unpackbits(words.astype(">u4").view(np.uint8))
+    assert abs(bits.mean() - 0.5) < 0.005
+
+
+def test_philox_avalanche_and_no_collisions():
+    rng = np.random.default_rng(1)
+    base_c = [int(x) for x in rng.integers(0, 2**32, 4)]
+    key = [int(x) for x in rng.integers(0, 2**32, 2)]
+    ref = np.array(oracle.philox4x32_10(base_c, key), dtype=np.uint32)
+    flips = []
+    for w in range(4):
+        for b in range(32):
+            c = list(base_c)
+            c[w] ^= 1 << b
+            out = np.array(oracle.philox4x32_10(c, key), dtype=np.uint32)
+            flips.append(int(np.unpackbits((out ^ ref).view(np.uint8)).sum()))
+    for w in range(2):
+        for b in range(32):
+            k = list(key)
+            k[w] ^= 1 << b
+            out = np.array(oracle.philox4x32_10(base_c, k), dtype=np.uint32)
+            flips.append(int(np.unpackbits((out ^ ref).view(np.uint8)).sum()))
+    flips = np.array(flips)
+    assert abs(flips.mean() - 64) < 2.5 and flips.min() > 30
+    seen = {tuple(oracle.philox4x32_10([i, 0, 0, 0], key)) for i in range(20000)}
+    assert len(seen) == 20000
+
+
+@pytest.mark.parametrize("mu", [0.3, 2.5, 11.99, 12.0, 37.5, 600.0, 2.0e4])
+def test_poisson_goodness_of_fit(mu):
+    n = 60000
+    k = oracle.poisson(np.full(n, mu, dtype=np.float32), seed=int(mu * 1000) + 5)
+    # mean and variance (z-tests)
+    assert abs(k.mean() - mu) < 5 * math.sqrt(mu / n)
+    assert abs(k.var() / mu - 1.0) < 5 * math.sqrt(2.0 / n) + 0.01
+    # chi-square against the pmf over the central range, tails pooled
+    lo = int(max(0, math.floor(mu - 5 * math.sqrt(mu) - 2)))
+    hi = int(math.ceil(mu + 5 * math.sqrt(mu) + 2))
+    edges = np.arange(lo, hi + 1)
+    obs = np.array([(k < lo).sum()] + [(k == e).sum() for e in edges] + [(k > hi).sum()], dtype=float)
+    pmf = stats.poisson.pmf(edges, mu)
+    exp = np.r_[stats.poisson.cdf(lo - 1, mu), pmf, stats.poisson.sf(hi, mu)] * n
+    keep = exp >= 5
+    o = np.r_[obs[keep], obs[~keep].sum()]
+    e = np.r_[exp[keep], exp[~keep].sum()]
+    if e[-1] < 5:
+        o, e = o[:-1], e[:-1]
+    chi2 = ((o - e) ** 2 / e).sum()
+    p = stats.chi2.sf(chi2, len(o) - 1)
+    assert p > 1e-5, (mu, chi2, len(o))
+
+
+def test_poisson_edge_means():
+    k = oracle.poisson(np.array([0.0, -1.0, 1e-30, 1e-6], dtype=np.float32), 3)
+    assert k[0] == 0 and k[1] == 0 and k[2] == 0 and k[3] in (0, 1)
+    big = oracle.poisson(np.full(20000, 3.0e6, dtype=np.float32), 4)
+    assert abs(big.mean() - 3.0e6) < 5 * math.sqrt(3.0e6 / 20000)
+
+
+def test_rebinned_mean_geometric_closed_form():
+    """Lifetime-only theory, N0 = 1, bkg = 0: a group of r bins starting at bin j r
+    sums to q^{j r} (1 - q^r) / (1 - q), q = e^{-dt/tau} (the last group is short)."""
+    M, r, dt = 1000, 64, 0.002
+    lay = W.single_hist_layout(M, dt)
+    lay.comp = np.zeros((0, 6), dtype=np.int32)
+    mu = oracle.rebinned_mean(lay, np.array([1.0, 0.0, 0, 0, 0, 0]), r)[0]
+    q = math.exp(-dt / W.TAU_MU_US)
+    ref = [q ** j0 * (1 - q ** min(r, M - j0)) / (1 - q) for j0 in range(0, M, r)]
+    np.testing.assert_allclose(mu, ref, rtol=1e-13)
