@@ -200,6 +200,56 @@ int musr_poisson_sample(const float* mu_dev, int64_t n, uint64_t seed, int32_t* 
 int musr_generate(musr_run run, const double* thetas_dev, int32_t n_samples, int32_t rebin, uint64_t seed,
                   uint64_t sample_offset, int32_t log1p_out, float* out_dev, float* mu_dev, void* stream);
 
+/*
+ * BF16 tensor-core GEMM (the learned start proposer's dense layers; the paper
+ * has no neural component).  C = act(A . B^T + bias): A [m x k] and B [n x k]
+ * BF16 row-major on the device (16-byte aligned), FP32 accumulation, bias [n]
+ * FP32 or NULL, relu != 0 applies max(., 0); results to out_f32 and / or
+ * out_bf16 ([m x ldc] row-major, ldc >= n, ldc % 8 == 0).  m and n must be
+ * multiples of 128 and k of 64 (MUSR_EINVAL otherwise).  err_dev: a device
+ * uint32 the kernel ORs 1 into if a bounded internal wait times out.
+ * Asynchronous on stream.
+ */
+int musr_gemm_bf16(const void* a_dev, const void* b_dev, int32_t m, int32_t n, int32_t k,
+                   const float* bias_dev, int32_t relu, float* out_f32_dev, void* out_bf16_dev,
+                   int32_t ldc, uint32_t* err_dev, void* stream);
+
+/*
+ * Learned start proposer: an MLP n_in -> n_hidden (x n_hidden_layers, ReLU)
+ * -> n_out on the BF16 tensor cores (musr_gemm_bf16), FP32 master weights,
+ * Adam.  Inputs are FP32 [batch x n_in] on the device, multiplied by in_scale
+ * and rounded to BF16; outputs FP32 [batch x n_out].  Requirements: n_in % 128
+ * == 0, n_hidden % 128 == 0, n_out <= 128, batch % 128 == 0 and batch <=
+ * max_batch.  Parameters are exchanged as one FP32 host vector: for every
+ * layer W [out x in] row-major then b [out].  Weights start He-uniform from a
+ * splitmix64 stream of seed.  Forward / backward / train_step are synchronous
+ * with respect to the returned loss and report MUSR_ETIMEOUT if a bounded
+ * wait inside a GEMM timed out.
+ *   musr_mlp_backward: forward, MSE loss mean((y - t)^2) (t FP32 [batch x
+ *   n_out], device) into *loss (may be NULL), gradients kept internally
+ *   (musr_mlp_get_grads); musr_mlp_adam applies one Adam step to them;
+ *   musr_mlp_train_step = backward + Adam(lr, 0.9, 0.999, 1e-8).
+ */
+typedef struct musr_mlp_s* musr_mlp;
+int musr_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out, int32_t max_batch,
+                    float in_scale, uint64_t seed, musr_mlp* out);
+int musr_mlp_destroy(musr_mlp mlp);
+int musr_mlp_n_params(musr_mlp mlp, int64_t* n);
+int musr_mlp_set_params(musr_mlp mlp, const float* host);
+int musr_mlp_get_params(musr_mlp mlp, float* host);
+int musr_mlp_get_grads(musr_mlp mlp, float* host);
+int musr_mlp_forward(musr_mlp mlp, const float* x_dev, int32_t batch, float* y_dev, void* stream);
+/* Activations of the last forward pass (or the forward inside the last
+ * backward) to host FP32: layer 0 = the BF16 scaled input [batch x n_in],
+ * 1..n_hidden_layers = the BF16 hidden outputs [batch x n_hidden],
+ * n_hidden_layers + 1 = the FP32 output [batch x n_out]. */
+int musr_mlp_get_activation(musr_mlp mlp, int32_t layer, int32_t batch, float* host);
+int musr_mlp_backward(musr_mlp mlp, const float* x_dev, const float* t_dev, int32_t batch, float* loss,
+                      void* stream);
+int musr_mlp_adam(musr_mlp mlp, float lr, float beta1, float beta2, float eps, void* stream);
+int musr_mlp_train_step(musr_mlp mlp, const float* x_dev, const float* t_dev, int32_t batch, float lr, float* loss,
+                        void* stream);
+
 /* Fit options and result (the host minimiser that replaces Minuit2's role,
  * Sec. 4.1). */
 enum {

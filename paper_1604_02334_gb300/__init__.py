@@ -295,6 +295,21 @@ def poisson_sample(mu_dev, seed, counts_dev, stream=None):
           "musr_poisson_sample")
 
 
+def gemm_bf16(a, b, bias=None, relu=False, out_f32=None, out_bf16=None, err=None, stream=None):
+    """out = act(a @ b.T + bias) on the tensor cores; a [m, k], b [n, k] CUDA bf16."""
+    import torch
+    m, k = a.shape
+    n = b.shape[0]
+    if err is None:
+        err = torch.zeros(1, dtype=torch.int32, device=a.device)
+    ldc = (out_f32 if out_f32 is not None else out_bf16).shape[1]
+    st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    check(_lib.load().musr_gemm_bf16(p(a), p(b), m, n, k, p(bias), 1 if relu else 0, p(out_f32), p(out_bf16),
+                                     ldc, p(err), st), "musr_gemm_bf16")
+    return err
+
+
 def chi2_batch(runs, thetas, n_vec, obj=MUSR_CHI2):
     """One-shot musr_chi2_batch: plan, evaluate, free."""
     lib = _lib.load()
@@ -306,3 +321,97 @@ def chi2_batch(runs, thetas, n_vec, obj=MUSR_CHI2):
                               nv.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dptr(out)),
           "musr_chi2_batch")
     return out
+
+
+class Mlp:
+    """The learned start proposer's network (musr_mlp_*): BF16 tensor-core
+    layers n_in -> n_hidden (x n_hidden_layers, ReLU) -> n_out, FP32 master
+    weights, Adam.  Inputs, targets and outputs are CUDA FP32 tensors."""
+
+    def __init__(self, n_in, n_hidden, n_hidden_layers, n_out, max_batch, in_scale=1.0, seed=0):
+        self._lib = _lib.load()
+        self.handle = ctypes.c_void_p()
+        check(self._lib.musr_mlp_create(n_in, n_hidden, n_hidden_layers, n_out, max_batch, float(in_scale),
+                                        int(seed), ctypes.byref(self.handle)), "musr_mlp_create")
+        self.n_in, self.n_hidden, self.n_hidden_layers, self.n_out = n_in, n_hidden, n_hidden_layers, n_out
+        n = ctypes.c_int64()
+        check(self._lib.musr_mlp_n_params(self.handle, ctypes.byref(n)), "musr_mlp_n_params")
+        self.n_params = int(n.value)
+
+    def layer_shapes(self):
+        """[(out, in)] per layer, in the order of the flat parameter vector."""
+        dims = [self.n_in] + [self.n_hidden] * self.n_hidden_layers + [self.n_out]
+        return [(dims[i + 1], dims[i]) for i in range(len(dims) - 1)]
+
+    def _flat(self, fn):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        check(fn(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), "musr_mlp params")
+        return out
+
+    def get_params(self):
+        return self._flat(self._lib.musr_mlp_get_params)
+
+    def get_grads(self):
+        return self._flat(self._lib.musr_mlp_get_grads)
+
+    def set_params(self, flat):
+        f = np.ascontiguousarray(flat, dtype=np.float32)
+        assert f.shape == (self.n_params,)
+        check(self._lib.musr_mlp_set_params(self.handle, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "musr_mlp_set_params")
+
+    def _check_x(self, x, width):
+        import torch
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.dim() != 2 or x.shape[1] != width:
+            raise ValueError(f"expected a contiguous CUDA float32 tensor [batch, {width}]")
+
+    def activation(self, layer, batch):
+        """Layer `layer`'s activations of the last forward pass, host FP32."""
+        w = self.n_in if layer == 0 else (self.n_out if layer == self.n_hidden_layers + 1 else self.n_hidden)
+        out = np.zeros((batch, w), dtype=np.float32)
+        check(self._lib.musr_mlp_get_activation(self.handle, int(layer), int(batch),
+                                                out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "musr_mlp_get_activation")
+        return out
+
+    def forward(self, x, out=None):
+        import torch
+        self._check_x(x, self.n_in)
+        b = x.shape[0]
+        if out is None:
+            out = torch.empty((b, self.n_out), dtype=torch.float32, device=x.device)
+        check(self._lib.musr_mlp_forward(self.handle, ctypes.c_void_p(x.data_ptr()), b,
+                                         ctypes.c_void_p(out.data_ptr()), _torch_stream_ptr()), "musr_mlp_forward")
+        return out
+
+    def backward(self, x, t):
+        self._check_x(x, self.n_in)
+        self._check_x(t, self.n_out)
+        loss = ctypes.c_float()
+        check(self._lib.musr_mlp_backward(self.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                          x.shape[0], ctypes.byref(loss), _torch_stream_ptr()), "musr_mlp_backward")
+        return float(loss.value)
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(self._lib.musr_mlp_adam(self.handle, float(lr), float(beta1), float(beta2), float(eps),
+                                      _torch_stream_ptr()), "musr_mlp_adam")
+
+    def train_step(self, x, t, lr):
+        self._check_x(x, self.n_in)
+        self._check_x(t, self.n_out)
+        loss = ctypes.c_float()
+        check(self._lib.musr_mlp_train_step(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                            ctypes.c_void_p(t.data_ptr()), x.shape[0], float(lr),
+                                            ctypes.byref(loss), _torch_stream_ptr()), "musr_mlp_train_step")
+        return float(loss.value)
+
+    def close(self):
+        if self.handle:
+            self._lib.musr_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -109,6 +109,21 @@ SIGNATURES = {
     "musr_poisson_sample": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]),
     "musr_generate": (ctypes.c_int, [_run, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                      ctypes.c_uint64, ctypes.c_int32, _vp, _vp, _vp]),
+    "musr_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
+                                      ctypes.c_int32, _vp, _vp, ctypes.c_int32, _vp, _vp]),
+    "musr_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(_vp)]),
+    "musr_mlp_destroy": (ctypes.c_int, [_vp]),
+    "musr_mlp_n_params": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "musr_mlp_set_params": (ctypes.c_int, [_vp, _fp]),
+    "musr_mlp_get_params": (ctypes.c_int, [_vp, _fp]),
+    "musr_mlp_get_grads": (ctypes.c_int, [_vp, _fp]),
+    "musr_mlp_get_activation": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_int32, _fp]),
+    "musr_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, _vp, _vp]),
+    "musr_mlp_backward": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_float), _vp]),
+    "musr_mlp_adam": (ctypes.c_int, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
+    "musr_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_float), _vp]),
     "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "musr_version": (ctypes.c_char_p, []),
     "musr_last_cuda_error": (ctypes.c_char_p, []),
