@@ -248,6 +248,64 @@ def batched_throughput(dev, rank, reps=5):
             "ms": med, "value": binevals / (med * 1e-3), "unit": "bin-evals/s (chi2, value only)"}
 
 
+def learned_start_ab(dev, rank, train_steps, n_runs=64):
+    """Fits/s and success of the learned-start fit against the plain fit.
+
+    The proposer trains on device-generated histograms (16 x 65536 bins,
+    parameters uniform in the prior box); then n_runs held-out runs (numpy
+    draws of the parameters, device Poisson counts) are fitted (chi2, LM,
+    40 free) three ways: from the truth (the reference minimum), learned start
+    (proposal + fit, plain fit as fallback when chi2/ndf > 1.2), and plain
+    (range centre with a 10-point B1 grid, best of 10).  A fit succeeds when
+    its chi2 is within 1e-6 relative of the truth-start fit's."""
+    import torch
+    from paper_1604_02334_gb300 import MUSR_CHI2, Proposer, Run
+    lay = W.multi_detector_layout(16, 65536, 12.8)
+    lo, hi = W.multi_detector_box(lay)
+    layout = Run(lay)
+    prop = Proposer(layout, lo, hi, seed=W.BASE_SEED + 5 + 100 * rank)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = prop.train(train_steps, 1e-3, 3e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    g = W.rng(W.BASE_SEED + 2005 + rank)
+    thetas = np.stack([W.multi_detector_theta(lay, g) for _ in range(n_runs)])
+    data = torch.empty((n_runs, lay.total_bins), dtype=torch.float32, device=dev)
+    layout.generate(torch.tensor(thetas, device=dev), 1, W.BASE_SEED + 2006 + rank, data)
+    torch.cuda.synchronize()
+    runs = [Run(lay, data[i].contiguous()) for i in range(n_runs)]
+    free = lay.free
+    starts = W.default_starts(lay)
+    ref = [r.fit(thetas[i], MUSR_CHI2, free=free)[1]["value"] for i, r in enumerate(runs)]
+    res = {}
+    for name in ("learned", "plain"):
+        ok, iters, fallback = [], [], 0
+        t0 = time.perf_counter()
+        for i, r in enumerate(runs):
+            if name == "learned":
+                _, info, _ = prop.fit(r, MUSR_CHI2, free=free, chi2ndf_max=1.2, fallback_starts=starts)
+                fallback += int(info["fallback"])
+            else:
+                _, info, _ = r.fit_multistart(starts, MUSR_CHI2, free=free)
+            ok.append(abs(info["value"] - ref[i]) <= 1e-6 * ref[i])
+            iters.append(info["iters"])
+        dt = time.perf_counter() - t0
+        res[name] = {"fits_per_s": n_runs / dt, "success": float(np.mean(ok)), "mean_iters": float(np.mean(iters)),
+                     "ms_per_fit": 1e3 * dt / n_runs}
+        if name == "learned":
+            res[name]["fallbacks"] = fallback
+    for r in runs:
+        r.close()
+    prop.close()
+    layout.close()
+    return {"workload": "16 hist x 65536 bins, 40 free, chi2 LM fits of held-out runs from the prior box",
+            "n_runs": n_runs, "train_steps": train_steps, "train_samples": train_steps * 512,
+            "train_s": t_train, "train_samples_per_s": train_steps * 512 / t_train,
+            "final_loss": float(np.mean(losses[-100:])), **res,
+            "speedup_fits_per_s": res["learned"]["fits_per_s"] / res["plain"]["fits_per_s"]}
+
+
 def run_ours(args):
     import torch
 
@@ -327,6 +385,7 @@ def run_ours(args):
     # sanity: results are finite
     assert torch.isfinite(outs[args.warmup:]).all().item()
     batched = None if args.no_batched else batched_throughput(dev, rank)
+    learned = None if args.learned_steps <= 0 else learned_start_ab(dev, rank, args.learned_steps)
 
     if rank != 0:
         run.close()
@@ -346,11 +405,13 @@ def run_ours(args):
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,  # stage kernel + objective kernel per step
+        "gpu_launches": args.steps,  # one objective kernel launch per step (the flush is a torch fill)
         "wall_s": wall,
     }
     if batched:
         line["batched"] = batched
+    if learned:
+        line["learned_start"] = learned
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lay, data, thetas)
     print(json.dumps(line), flush=True)
@@ -365,6 +426,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--learned-steps", type=int, default=32768,
+                    help="proposer training steps for the learned-start A/B (0: skip it)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

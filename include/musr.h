@@ -284,6 +284,93 @@ typedef struct {
 int musr_fit(musr_run run, int obj, double* theta_inout, const uint8_t* free_mask,
              const musr_fit_opts* opts, musr_fit_result* out);
 
+/* Plain multi-start fit: musr_fit from each of the n_starts rows of starts
+ * (n_starts x n_params, FP64 host) in order; theta_out and out receive the
+ * fit with the smallest finite objective (ties: the earliest).  Returns that
+ * fit's status, or the first error if no fit gave a finite objective.
+ * out->iters and out->n_evals are summed over all starts. */
+int musr_fit_multistart(musr_run run, int obj, const double* starts, int32_t n_starts, const uint8_t* free_mask,
+                        const musr_fit_opts* opts, double* theta_out, musr_fit_result* out);
+
+/*
+ * Learned start proposer (no counterpart in the paper, which starts every fit
+ * from the user's values): an MLP (musr_mlp_*) maps standardised log counts
+ * summed over groups of `rebin` bins (musr_proposer_features) to the parameters
+ * with lo_j < hi_j, each scaled to [-1, 1] over [lo_j, hi_j].  It trains on
+ * histograms that musr_generate draws from the layout run for parameter
+ * vectors uniform in the box [lo, hi] (parameters with lo_j == hi_j held at
+ * lo_j), fresh samples every step, all on the device.
+ *   layout     a run whose layout (histograms, bins, time grid, map,
+ *              components) the proposer serves; its data are not used.  It
+ *              must outlive the proposer.
+ *   lo, hi     FP64 host [n_params]; hi_j >= lo_j; at most 128 with hi > lo.
+ *   opts       NULL or zeros for the defaults: rebin 64, n_hidden 512,
+ *              n_hidden_layers 3, batch 512, in_scale 1 (a factor on the
+ *              standardised features), seed 1.
+ * The features must number <= 2^20 after padding to a multiple of 128.
+ */
+typedef struct musr_proposer_s* musr_proposer;
+typedef struct {
+    int32_t rebin;
+    int32_t n_hidden;
+    int32_t n_hidden_layers;
+    int32_t batch;        /* training batch, multiple of 128 */
+    float in_scale;
+    uint64_t seed;
+} musr_proposer_opts;
+int musr_proposer_create(musr_run layout, const double* lo, const double* hi, const musr_proposer_opts* opts,
+                         musr_proposer* out);
+int musr_proposer_destroy(musr_proposer prop);
+/* The proposer's network (owned by the proposer), e.g. to save or load it. */
+int musr_proposer_mlp(musr_proposer prop, musr_mlp* out);
+/* The training inputs: n parameter vectors (FP64 device [n x n_params]) for
+ * sample indices offset .. offset + n - 1, learned entries lo_j + (hi_j -
+ * lo_j) u with u in (0, 1) of 53 random bits from Philox4x32-10 (counter
+ * (index low, index high, q / 2, 0xfffffffe), key (seed low ^ 0x0A5F00D1,
+ * seed high), q the learned entry's rank; words 2h, 2h + 1 of the block give
+ * entry q = 2 (q / 2) + h as ((w0 >> 5) 2^26 + (w1 >> 6) + 1/2) 2^-53), other
+ * entries lo_j; targets_dev (FP32 [n x n_learned] or NULL) = 2u - 1.
+ * Training step s draws indices s * batch .. (s + 1) * batch - 1 and their
+ * histograms by musr_generate with the same seed and sample_offset s * batch
+ * (counts, turned into features as musr_proposer_features does).
+ * Asynchronous on stream (NULL = the proposer's). */
+int musr_proposer_sample(musr_proposer prop, int32_t n, uint64_t offset, double* thetas_dev, float* targets_dev,
+                         void* stream);
+/* The network's input rows for n_runs runs (the layout's histogram and bin
+ * counts), FP32 device [n_runs x n_features]: with c_kg the data counts
+ * summed over group g of rebin bins of histogram k (musr_generate's order)
+ * and C_k = sum_g c_kg, features f = 0 .. G-1 are
+ * (log(1 + c_kg) - log(1 + C_k) - mu_f) * inv_sigma_f and features G + k are
+ * (log(1 + C_k) - mu_f) * inv_sigma_f, G = sum_k ceil(n_bins[k] / rebin).
+ * mu, inv_sigma: the standardisation (musr_proposer_get_norm).  Synchronous;
+ * stream is unused. */
+int musr_proposer_features(musr_proposer prop, const musr_run* runs, int32_t n_runs, float* out_dev, void* stream);
+/* n_features (G + n_hist), n_learned (entries with hi > lo) and the network's
+ * input width (n_features rounded up to a multiple of 128, zero-padded). */
+int musr_proposer_info(musr_proposer prop, int32_t* n_features, int32_t* n_learned, int32_t* n_inputs);
+/* The feature standardisation, FP32 host [n_features] each: mu_f and
+ * 1 / max(sd_f, 1e-3) of the unstandardised features over 16 generated
+ * batches of sample indices from 2^62 (estimated at the first call that needs
+ * it); set_norm replaces it (e.g. with a saved one). */
+int musr_proposer_get_norm(musr_proposer prop, float* mu, float* inv_sigma);
+int musr_proposer_set_norm(musr_proposer prop, const float* mu, const float* inv_sigma);
+/* n_steps Adam steps on fresh generated batches, learning rate decaying
+ * geometrically from lr_start to lr_end; losses (NULL or n_steps floats)
+ * receive the per-step MSE.  Successive calls continue the sample stream. */
+int musr_proposer_train(musr_proposer prop, int32_t n_steps, float lr_start, float lr_end, float* losses);
+/* Proposals for n_runs runs with the layout's histograms and bin counts
+ * (MUSR_EINVAL otherwise), from each run's data: thetas_out FP64 host
+ * [n_runs x n_params], learned entries clamped to [lo, hi], others lo. */
+int musr_proposer_propose(musr_proposer prop, const musr_run* runs, int32_t n_runs, double* thetas_out);
+/* Learned-start fit: propose, then musr_fit from the proposal.  If that fit
+ * fails or ends with value / ndf > chi2ndf_max, musr_fit_multistart from the
+ * n_fallback rows of fallback_starts follows and the better result is kept;
+ * *used_fallback (may be NULL) is set to 1 then, else 0.  out->iters and
+ * out->n_evals count every fit made. */
+int musr_fit_learned(musr_proposer prop, musr_run run, int obj, const uint8_t* free_mask, const musr_fit_opts* opts,
+                     double chi2ndf_max, const double* fallback_starts, int32_t n_fallback, double* theta_out,
+                     musr_fit_result* out, int32_t* used_fallback);
+
 /* Message for a status code (static string). */
 const char* musr_strerror(int code);
 

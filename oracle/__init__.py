@@ -63,6 +63,9 @@ def _load():
                                         ctypes.POINTER(ctypes.c_int32)]
             lib.orc_poisson.restype = None
             lib.orc_rebinned_mean.argtypes = layout + [dp, ctypes.c_int, ctypes.c_int, dp]
+            lib.orc_sample_thetas.argtypes = [dp, dp, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                              ctypes.c_uint64, dp, ctypes.POINTER(ctypes.c_float)]
+            lib.orc_sample_thetas.restype = None
             for f in (lib.orc_model, lib.orc_objective, lib.orc_gradient, lib.orc_gradient_fd,
                       lib.orc_fit, lib.orc_rebinned_mean):
                 f.restype = ctypes.c_int
@@ -204,3 +207,44 @@ def rebinned_mean(lay, thetas, rebin):
     if st:
         raise OracleError(st)
     return out.reshape(th.shape[0], per)
+
+
+def sample_thetas(lo, hi, n, seed, offset=0):
+    """Uniform training parameter vectors of the learned start proposer and
+    their targets 2u - 1 (entries with hi > lo; others fixed at lo)."""
+    lib = _load()
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    P = lo.shape[0]
+    th = np.zeros((n, P))
+    tg = np.zeros((n, int((hi > lo).sum())), dtype=np.float32)
+    lib.orc_sample_thetas(_dp(lo), _dp(hi), P, int(n), int(seed), int(offset), _dp(th),
+                          tg.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    return th, tg
+
+
+def rebin_sums(lay, data, rebin):
+    """Counts summed over groups of `rebin` bins, per histogram in order, the
+    last group of a histogram possibly short (FP64); list of arrays per histogram."""
+    d = np.asarray(data, dtype=np.float64)
+    out, o = [], 0
+    for m in lay.n_bins:
+        m = int(m)
+        h = d[o:o + m]
+        o += m
+        out.append(np.array([h[g0:g0 + rebin].sum() for g0 in range(0, m, rebin)]))
+    return out
+
+
+def proposer_features(lay, data, rebin, mu=None, inv_sigma=None):
+    """Input features of the learned start proposer (FP64): for every group g
+    of histogram k, log(1 + c_kg) - log(1 + C_k), then log(1 + C_k) for every
+    k, with C_k the histogram's total; standardised as (x - mu) * inv_sigma
+    when those are given."""
+    sums = rebin_sums(lay, data, rebin)
+    tot = np.array([s.sum() for s in sums])
+    u = np.concatenate([np.log1p(s) - np.log1p(t) for s, t in zip(sums, tot)])
+    x = np.concatenate([u, np.log1p(tot)])
+    if mu is not None:
+        x = (x - np.asarray(mu, dtype=np.float64)) * np.asarray(inv_sigma, dtype=np.float64)
+    return x

@@ -804,3 +804,33 @@ int orc_rebinned_mean(LAYOUT_ARGS, const double* thetas, int n_samples, int rebi
     }
     return ORC_OK;
 }
+
+/* Training parameter vectors of the learned start proposer: entries with
+ * hi > lo (ranked q = 0, 1, ... in index order) drawn as lo + (hi - lo) u,
+ * u = ((w_a >> 5) 2^26 + (w_b >> 6) + 1/2) 2^-53 from the Philox4x32-10
+ * block of counter (index low, index high, q / 2, 0xfffffffe) under key
+ * (seed low ^ 0x0A5F00D1, seed high), words (0, 1) for even q and (2, 3) for
+ * odd q; other entries lo.  targets (or NULL) = 2u - 1 as float. */
+void orc_sample_thetas(const double* lo, const double* hi, int P, int64_t n, uint64_t seed, uint64_t offset,
+                       double* thetas, float* targets) {
+    int n_learned = 0;
+    for (int j = 0; j < P; ++j) n_learned += hi[j] > lo[j];
+    for (int64_t s = 0; s < n; ++s) {
+        const uint64_t id = offset + (uint64_t)s;
+        double* th = thetas + s * P;
+        int q = 0;
+        for (int j = 0; j < P; ++j) {
+            th[j] = lo[j];
+            if (!(hi[j] > lo[j])) continue;
+            const uint32_t ctr[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)(q / 2), 0xfffffffeu};
+            const uint32_t key[2] = {(uint32_t)seed ^ 0x0A5F00D1u, (uint32_t)(seed >> 32)};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, key, w);
+            const uint32_t wa = w[2 * (q % 2)], wb = w[2 * (q % 2) + 1];
+            const double u = ((double)(wa >> 5) * 67108864.0 + (double)(wb >> 6) + 0.5) * (1.0 / 9007199254740992.0);
+            th[j] = lo[j] + (hi[j] - lo[j]) * u;
+            if (targets) targets[s * n_learned + q] = (float)(2.0 * u - 1.0);
+            ++q;
+        }
+    }
+}

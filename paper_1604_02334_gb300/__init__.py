@@ -193,6 +193,26 @@ class Run:
                 "evals": r.n_evals, "status": st}
         return th, info, cov
 
+    def fit_multistart(self, starts, obj=MUSR_CHI2, free=None, method=MUSR_FIT_LM, max_iter=500,
+                       edm_tol=1e-8, mu0=1e-3, fd_rel_h=0.0):
+        """musr_fit_multistart: the best of the fits from each row of starts."""
+        st_ = np.ascontiguousarray(np.atleast_2d(starts), dtype=np.float64)
+        assert st_.shape[1] == self.P
+        fm = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
+        nf = self.P if fm is None else int(fm.sum())
+        cov = np.zeros((nf, nf))
+        th = np.zeros(self.P)
+        o = _lib.musr_fit_opts(method, max_iter, edm_tol, mu0, fd_rel_h)
+        r = _lib.musr_fit_result()
+        r.cov = _dptr(cov)
+        st = _lib.load().musr_fit_multistart(self.handle, int(obj), _dptr(st_), st_.shape[0],
+                                             fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                                             if fm is not None else None,
+                                             ctypes.byref(o), _dptr(th), ctypes.byref(r))
+        info = {"value": r.value, "ndf": r.ndf, "edm": r.edm, "mu": r.mu, "iters": r.iters,
+                "evals": r.n_evals, "status": st}
+        return th, info, cov
+
 
 def _make_chi2_function():
     import torch
@@ -408,6 +428,126 @@ class Mlp:
     def close(self):
         if self.handle:
             self._lib.musr_mlp_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Proposer:
+    """Learned start proposer (musr_proposer_*): an MLP trained on device-
+    generated histograms of `layout`'s shape for parameters uniform in
+    [lo, hi]; proposals for runs of that layout; learned-start fits."""
+
+    def __init__(self, layout, lo, hi, rebin=64, n_hidden=512, n_hidden_layers=3, batch=512, in_scale=1.0,
+                 seed=1):
+        self._lib = _lib.load()
+        self.layout = layout  # keeps the layout run alive
+        self.P = layout.P
+        self.lo = np.ascontiguousarray(lo, dtype=np.float64)
+        self.hi = np.ascontiguousarray(hi, dtype=np.float64)
+        assert self.lo.shape == (self.P,) and self.hi.shape == (self.P,)
+        o = _lib.musr_proposer_opts(rebin, n_hidden, n_hidden_layers, batch, in_scale, seed)
+        self.handle = ctypes.c_void_p()
+        check(self._lib.musr_proposer_create(layout.handle, _dptr(self.lo), _dptr(self.hi), ctypes.byref(o),
+                                             ctypes.byref(self.handle)), "musr_proposer_create")
+        self.batch = batch
+        nf, nl, ni = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(self._lib.musr_proposer_info(self.handle, ctypes.byref(nf), ctypes.byref(nl), ctypes.byref(ni)),
+              "musr_proposer_info")
+        self.n_features, self.n_learned, self.n_inputs = int(nf.value), int(nl.value), int(ni.value)
+
+    def norm(self):
+        """(mu, inv_sigma) of the feature standardisation, FP32 host arrays."""
+        mu = np.zeros(self.n_features, dtype=np.float32)
+        isig = np.zeros(self.n_features, dtype=np.float32)
+        check(self._lib.musr_proposer_get_norm(self.handle, mu.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               isig.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "musr_proposer_get_norm")
+        return mu, isig
+
+    def set_norm(self, mu, inv_sigma):
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        isig = np.ascontiguousarray(inv_sigma, dtype=np.float32)
+        check(self._lib.musr_proposer_set_norm(self.handle, mu.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               isig.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "musr_proposer_set_norm")
+
+    def sample(self, n, offset=0, with_targets=True):
+        """Training parameter vectors (and targets) for sample indices offset.., CUDA tensors."""
+        import torch
+        th = torch.empty((n, self.P), dtype=torch.float64, device="cuda")
+        n_learned = int((self.hi > self.lo).sum())
+        tg = torch.empty((n, n_learned), dtype=torch.float32, device="cuda") if with_targets else None
+        check(self._lib.musr_proposer_sample(self.handle, int(n), int(offset), ctypes.c_void_p(th.data_ptr()),
+                                             ctypes.c_void_p(tg.data_ptr()) if tg is not None else None,
+                                             _torch_stream_ptr()), "musr_proposer_sample")
+        return th, tg
+
+    def features(self, runs):
+        """The network's input rows (standardised log counts) for runs, CUDA FP32 [len(runs), n_features]."""
+        import torch
+        runs = list(runs)
+        n_features = self.n_features
+        handles = (ctypes.c_void_p * len(runs))(*[r.handle.value for r in runs])
+        out = torch.empty((len(runs), n_features), dtype=torch.float32, device="cuda")
+        check(self._lib.musr_proposer_features(self.handle, handles, len(runs), ctypes.c_void_p(out.data_ptr()),
+                                               _torch_stream_ptr()), "musr_proposer_features")
+        return out
+
+    def train(self, n_steps, lr_start=1e-3, lr_end=1e-4):
+        losses = np.zeros(max(int(n_steps), 1), dtype=np.float32)
+        check(self._lib.musr_proposer_train(self.handle, int(n_steps), float(lr_start), float(lr_end),
+                                            losses.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "musr_proposer_train")
+        return losses[:int(n_steps)]
+
+    def mlp_params(self):
+        """The network's flat FP32 parameter vector (host copy)."""
+        m = ctypes.c_void_p()
+        check(self._lib.musr_proposer_mlp(self.handle, ctypes.byref(m)), "musr_proposer_mlp")
+        n = ctypes.c_int64()
+        check(self._lib.musr_mlp_n_params(m, ctypes.byref(n)), "musr_mlp_n_params")
+        out = np.zeros(int(n.value), dtype=np.float32)
+        check(self._lib.musr_mlp_get_params(m, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+              "musr_mlp_get_params")
+        return out
+
+    def propose(self, runs):
+        runs = list(runs)
+        handles = (ctypes.c_void_p * len(runs))(*[r.handle.value for r in runs])
+        out = np.zeros((len(runs), self.P))
+        check(self._lib.musr_proposer_propose(self.handle, handles, len(runs), _dptr(out)), "musr_proposer_propose")
+        return out
+
+    def fit(self, run, obj=MUSR_CHI2, free=None, chi2ndf_max=1.2, fallback_starts=None, method=MUSR_FIT_LM,
+            max_iter=500, edm_tol=1e-8, mu0=1e-3, fd_rel_h=0.0):
+        """musr_fit_learned: (theta, info, cov); info["fallback"] tells whether the plain fit ran."""
+        fm = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
+        nf = self.P if fm is None else int(fm.sum())
+        cov = np.zeros((nf, nf))
+        th = np.zeros(self.P)
+        fb = None if fallback_starts is None else np.ascontiguousarray(np.atleast_2d(fallback_starts),
+                                                                       dtype=np.float64)
+        o = _lib.musr_fit_opts(method, max_iter, edm_tol, mu0, fd_rel_h)
+        r = _lib.musr_fit_result()
+        r.cov = _dptr(cov)
+        used = ctypes.c_int32()
+        st = self._lib.musr_fit_learned(self.handle, run.handle, int(obj),
+                                        fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if fm is not None else None,
+                                        ctypes.byref(o), float(chi2ndf_max), _dptr(fb) if fb is not None else None,
+                                        0 if fb is None else fb.shape[0], _dptr(th), ctypes.byref(r),
+                                        ctypes.byref(used))
+        info = {"value": r.value, "ndf": r.ndf, "edm": r.edm, "mu": r.mu, "iters": r.iters,
+                "evals": r.n_evals, "status": st, "fallback": bool(used.value)}
+        return th, info, cov
+
+    def close(self):
+        if self.handle:
+            self._lib.musr_proposer_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

@@ -80,6 +80,17 @@ class musr_fit_result(ctypes.Structure):
     ]
 
 
+class musr_proposer_opts(ctypes.Structure):
+    _fields_ = [
+        ("rebin", ctypes.c_int32),
+        ("n_hidden", ctypes.c_int32),
+        ("n_hidden_layers", ctypes.c_int32),
+        ("batch", ctypes.c_int32),
+        ("in_scale", ctypes.c_float),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -106,6 +117,22 @@ SIGNATURES = {
     "musr_batch_eval_device": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "musr_fit": (ctypes.c_int, [_run, ctypes.c_int, _dp, _u8p, ctypes.POINTER(musr_fit_opts),
                                 ctypes.POINTER(musr_fit_result)]),
+    "musr_fit_multistart": (ctypes.c_int, [_run, ctypes.c_int, _dp, ctypes.c_int32, _u8p,
+                                           ctypes.POINTER(musr_fit_opts), _dp, ctypes.POINTER(musr_fit_result)]),
+    "musr_proposer_create": (ctypes.c_int, [_run, _dp, _dp, ctypes.POINTER(musr_proposer_opts),
+                                            ctypes.POINTER(_vp)]),
+    "musr_proposer_destroy": (ctypes.c_int, [_vp]),
+    "musr_proposer_mlp": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
+    "musr_proposer_sample": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_uint64, _vp, _vp, _vp]),
+    "musr_proposer_features": (ctypes.c_int, [_vp, ctypes.POINTER(_run), ctypes.c_int32, _vp, _vp]),
+    "musr_proposer_info": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p]),
+    "musr_proposer_get_norm": (ctypes.c_int, [_vp, _fp, _fp]),
+    "musr_proposer_set_norm": (ctypes.c_int, [_vp, _fp, _fp]),
+    "musr_proposer_train": (ctypes.c_int, [_vp, ctypes.c_int32, ctypes.c_float, ctypes.c_float, _fp]),
+    "musr_proposer_propose": (ctypes.c_int, [_vp, ctypes.POINTER(_run), ctypes.c_int32, _dp]),
+    "musr_fit_learned": (ctypes.c_int, [_vp, _run, ctypes.c_int, _u8p, ctypes.POINTER(musr_fit_opts),
+                                        ctypes.c_double, _dp, ctypes.c_int32, _dp,
+                                        ctypes.POINTER(musr_fit_result), _i32p]),
     "musr_poisson_sample": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_uint64, _vp, _vp]),
     "musr_generate": (ctypes.c_int, [_run, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                      ctypes.c_uint64, ctypes.c_int32, _vp, _vp, _vp]),

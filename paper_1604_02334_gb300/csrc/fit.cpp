@@ -7,6 +7,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <vector>
 
@@ -315,4 +317,54 @@ extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* fre
     *out = r;
     if (cur != run->device) cudaSetDevice(cur);
     return st;
+}
+
+extern "C" int musr_fit_multistart(musr_run run, int obj, const double* starts, int32_t n_starts,
+                                   const uint8_t* free_mask, const musr_fit_opts* opts, double* theta_out,
+                                   musr_fit_result* out) {
+    if (!run || !starts || n_starts <= 0 || !theta_out || !out) return MUSR_EINVAL;
+    const int P = run->P;
+    int nf = 0;
+    for (int j = 0; j < P; ++j) nf += (!free_mask || free_mask[j]) ? 1 : 0;
+    std::vector<double> th(P), cov(out->cov ? (size_t)nf * nf : 0), best_cov(cov.size());
+    musr_fit_result best;
+    memset(&best, 0, sizeof(best));
+    bool have = false;
+    int first_err = MUSR_OK;
+    int32_t iters = 0, evals = 0;
+    for (int s = 0; s < n_starts; ++s) {
+        std::copy(starts + (size_t)s * P, starts + (size_t)(s + 1) * P, th.begin());
+        musr_fit_result r;
+        memset(&r, 0, sizeof(r));
+        r.cov = cov.empty() ? nullptr : cov.data();
+        const int st = musr_fit(run, obj, th.data(), free_mask, opts, &r);
+        iters += r.iters;
+        evals += r.n_evals;
+        const bool ok = (st == MUSR_OK || st == MUSR_ENOCONV) && std::isfinite(r.value);
+        if (!ok) {
+            if (first_err == MUSR_OK) first_err = st != MUSR_OK ? st : MUSR_ENONFINITE;
+            if (st == MUSR_ECUDA || st == MUSR_ETIMEOUT) return st;
+            continue;
+        }
+        if (!have || r.value < best.value) {
+            have = true;
+            best = r;
+            std::copy(th.begin(), th.end(), theta_out);
+            best_cov.swap(cov);
+            if (!cov.empty() || !best_cov.empty()) cov.resize(best_cov.size());
+        }
+    }
+    if (!have) {
+        out->status = first_err;
+        out->iters = iters;
+        out->n_evals = evals;
+        return first_err;
+    }
+    double* user_cov = out->cov;
+    *out = best;
+    out->cov = user_cov;
+    if (user_cov) std::copy(best_cov.begin(), best_cov.end(), user_cov);
+    out->iters = iters;
+    out->n_evals = evals;
+    return best.status;
 }

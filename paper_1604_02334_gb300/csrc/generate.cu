@@ -182,10 +182,11 @@ struct GenParams {
     const double* thetas;         // [n_samples][P]
     RunConst rc;
     float dt, t0;
-    int K, P, rebin, per_sample, log1p_out;
+    int K, P, rebin, log1p_out;
+    int64_t row_stride;           // floats between consecutive samples in out / mu_out
     uint32_t k0, k1;
     uint64_t sample_offset;
-    float* out;                   // [n_samples][per_sample]
+    float* out;                   // [n_samples][row_stride]
     float* mu_out;                // same layout, or null
 };
 
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_cons
         const float mu = acc[0];
         const int32_t cnt = poisson_one(mu, p.k0, p.k1, (uint32_t)j, (uint32_t)k,
                                         (uint32_t)(p.sample_offset + (uint64_t)s));
-        const int64_t o = s * p.per_sample + p.group_off[k] + j;
+        const int64_t o = s * p.row_stride + p.group_off[k] + j;
         p.out[o] = p.log1p_out ? log1pf((float)cnt) : (float)cnt;
         if (p.mu_out) p.mu_out[o] = mu;
     }
@@ -239,7 +240,91 @@ cudaError_t launch_generate(const Signature& s, int blocks, int threads, cudaStr
     return cudaErrorInvalidValue;
 }
 
+// Parameter vectors drawn uniformly from [lo_j, hi_j] for the learned
+// entries (learned[q] = j), fixed entries at lo_j; targets[s][q] = 2u - 1.
+// u has 53 random bits from two Philox words: counter (sample low, sample
+// high, q / 2, 0xfffffffe) under the key (seed low ^ 0x0A5F00D1, seed high).
+__global__ void sample_thetas_kernel(const double* __restrict__ lo, const double* __restrict__ hi,
+                                     const int32_t* __restrict__ learned, int n_learned, int P, int n,
+                                     uint32_t k0, uint32_t k1, uint64_t offset, double* __restrict__ thetas,
+                                     float* __restrict__ targets) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    double* th = thetas + (size_t)s * P;
+    for (int j = 0; j < P; ++j) th[j] = lo[j];
+    const uint64_t id = offset + (uint64_t)s;
+    for (int q = 0; q < n_learned; q += 2) {
+        uint32_t c[4] = {(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)(q >> 1), 0xfffffffeu};
+        philox4x32_10(c, k0 ^ 0x0A5F00D1u, k1);
+        for (int h = 0; h < 2 && q + h < n_learned; ++h) {
+            const uint32_t wa = c[2 * h], wb = c[2 * h + 1];
+            const double u = __dmul_rn(__dadd_rn(__dadd_rn(__dmul_rn((double)(wa >> 5), 67108864.0), (double)(wb >> 6)),
+                                                 0.5),
+                                       1.1102230246251565e-16);
+            const int j = learned[q + h];
+            th[j] = __dadd_rn(lo[j], __dmul_rn(__dsub_rn(hi[j], lo[j]), u));
+            if (targets) targets[(size_t)s * n_learned + q + h] = (float)__dsub_rn(__dadd_rn(u, u), 1.0);
+        }
+    }
+}
+
+// Rebinned measured histograms: counts summed over groups of `rebin` bins
+// (exact in FP32 below 2^24 per group), in the generator's layout.
+__global__ void rebin_sum_kernel(const float* __restrict__ data, const int64_t* __restrict__ hist_off,
+                                 const int32_t* __restrict__ hist_nbins, const int64_t* __restrict__ group_off,
+                                 int rebin, float* __restrict__ out) {
+    const int k = blockIdx.y;
+    const int M = hist_nbins[k];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g0 = j * rebin;
+    if (g0 >= M) return;
+    const int g1 = min(g0 + rebin, M);
+    const float* d = data + hist_off[k];
+    float sum = 0.f;
+    for (int i = g0; i < g1; ++i) sum += d[i];
+    out[group_off[k] + j] = sum;
+}
+
 }  // namespace
+
+int ensure_groups(musr_run run, int rebin) {
+    if (run->d_group_off && run->gen_rebin == rebin) return MUSR_OK;
+    std::vector<int64_t> off(run->K);
+    int64_t o = 0;
+    for (int k = 0; k < run->K; ++k) {
+        off[k] = o;
+        o += (run->n_bins[k] + rebin - 1) / rebin;
+    }
+    int st = MUSR_OK;
+    if (!run->d_group_off) st = cuda_status(cudaMalloc(&run->d_group_off, sizeof(int64_t) * std::max(run->K, 1)));
+    if (st == MUSR_OK)
+        st = cuda_status(cudaMemcpy(run->d_group_off, off.data(), sizeof(int64_t) * run->K, cudaMemcpyHostToDevice));
+    if (st != MUSR_OK) return st;
+    run->gen_rebin = rebin;
+    run->gen_per_sample = o;
+    return MUSR_OK;
+}
+
+int sample_uniform_thetas(const double* lo_dev, const double* hi_dev, const int32_t* learned_dev, int n_learned,
+                          int P, int n, uint64_t seed, uint64_t offset, double* thetas_dev, float* targets_dev,
+                          cudaStream_t st) {
+    if (n <= 0) return MUSR_OK;
+    sample_thetas_kernel<<<(n + 127) / 128, 128, 0, st>>>(lo_dev, hi_dev, learned_dev, n_learned, P, n, (uint32_t)seed,
+                                                         (uint32_t)(seed >> 32), offset, thetas_dev, targets_dev);
+    return cuda_status(cudaGetLastError());
+}
+
+int rebin_sum_row(musr_run run, int rebin, float* out_dev, cudaStream_t st) {
+    int rc = ensure_groups(run, rebin);
+    if (rc != MUSR_OK || run->K == 0) return rc;
+    int64_t max_groups = 1;
+    for (int k = 0; k < run->K; ++k) max_groups = std::max<int64_t>(max_groups, (run->n_bins[k] + rebin - 1) / rebin);
+    dim3 grid((unsigned)((max_groups + 127) / 128), (unsigned)run->K);
+    rebin_sum_kernel<<<grid, 128, 0, st>>>(run->d_data, run->d_hist_off, run->d_hist_nbins, run->d_group_off, rebin,
+                                          out_dev);
+    return cuda_status(cudaGetLastError());
+}
+
 }  // namespace musr
 
 using namespace musr;
@@ -258,9 +343,9 @@ extern "C" int musr_poisson_sample(const float* mu_dev, int64_t n, uint64_t seed
     return cuda_status(cudaGetLastError());
 }
 
-extern "C" int musr_generate(musr_run run, const double* thetas_dev, int32_t n_samples, int32_t rebin,
-                             uint64_t seed, uint64_t sample_offset, int32_t log1p_out, float* out_dev,
-                             float* mu_dev, void* stream) {
+int musr::generate_rows(musr_run run, const double* thetas_dev, int n_samples, int rebin, uint64_t seed,
+                        uint64_t sample_offset, int log1p_out, float* out_dev, float* mu_dev, int64_t row_stride,
+                        cudaStream_t stream) {
     if (!run || n_samples < 0 || rebin < 1) return MUSR_EINVAL;
     if (n_samples == 0 || run->K == 0) return MUSR_OK;
     if (!thetas_dev || !out_dev) return MUSR_EINVAL;
@@ -268,22 +353,7 @@ extern "C" int musr_generate(musr_run run, const double* thetas_dev, int32_t n_s
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != run->device) cudaSetDevice(run->device);
-    int st = MUSR_OK;
-    if (!run->d_group_off || run->gen_rebin != rebin) {
-        // per-histogram group offsets within one sample, cached for this rebin
-        std::vector<int64_t> off(run->K);
-        int64_t o = 0;
-        for (int k = 0; k < run->K; ++k) {
-            off[k] = o;
-            o += (run->n_bins[k] + rebin - 1) / rebin;
-        }
-        if (!run->d_group_off) st = cuda_status(cudaMalloc(&run->d_group_off, sizeof(int64_t) * run->K));
-        if (st == MUSR_OK)
-            st = cuda_status(cudaMemcpy(run->d_group_off, off.data(), sizeof(int64_t) * run->K,
-                                        cudaMemcpyHostToDevice));
-        run->gen_rebin = rebin;
-        run->gen_per_sample = o;
-    }
+    int st = ensure_groups(run, rebin);
     if (st == MUSR_OK) {
         GenParams p;
         memset(&p, 0, sizeof(p));
@@ -297,7 +367,7 @@ extern "C" int musr_generate(musr_run run, const double* thetas_dev, int32_t n_s
         p.K = run->K;
         p.P = run->P;
         p.rebin = rebin;
-        p.per_sample = (int)run->gen_per_sample;
+        p.row_stride = row_stride > 0 ? row_stride : run->gen_per_sample;
         p.log1p_out = log1p_out;
         p.k0 = (uint32_t)seed;
         p.k1 = (uint32_t)(seed >> 32);
@@ -307,9 +377,17 @@ extern "C" int musr_generate(musr_run run, const double* thetas_dev, int32_t n_s
         int64_t max_groups = 1;
         for (int k = 0; k < run->K; ++k) max_groups = std::max<int64_t>(max_groups, (run->n_bins[k] + rebin - 1) / rebin);
         const int threads = (int)std::min<int64_t>(kMaxThreads, std::max<int64_t>(64, (max_groups + 31) / 32 * 32));
-        cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : run->stream;
-        st = cuda_status(launch_generate(run->sig, n_samples * run->K, threads, s, p));
+        if (row_stride > 0 && row_stride < run->gen_per_sample) st = MUSR_EINVAL;
+        cudaStream_t s = stream ? stream : run->stream;
+        if (st == MUSR_OK) st = cuda_status(launch_generate(run->sig, n_samples * run->K, threads, s, p));
     }
     if (cur != run->device) cudaSetDevice(cur);
     return st;
+}
+
+extern "C" int musr_generate(musr_run run, const double* thetas_dev, int32_t n_samples, int32_t rebin,
+                             uint64_t seed, uint64_t sample_offset, int32_t log1p_out, float* out_dev,
+                             float* mu_dev, void* stream) {
+    return musr::generate_rows(run, thetas_dev, n_samples, rebin, seed, sample_offset, log1p_out, out_dev, mu_dev,
+                               0, static_cast<cudaStream_t>(stream));
 }

@@ -12,6 +12,20 @@
 namespace musr {
 constexpr int kMaxParams = 4096;   // theta length
 constexpr int kMaxGnParams = 1024; // Gauss-Newton output is P x P
+// Generator body: rebinned Poisson samples of n_samples parameter vectors,
+// sample s written at out_dev + s * row_stride (row_stride 0: packed).
+int generate_rows(musr_run run, const double* thetas_dev, int n_samples, int rebin, uint64_t seed,
+                  uint64_t sample_offset, int log1p_out, float* out_dev, float* mu_dev, int64_t row_stride,
+                  cudaStream_t stream);
+// Group offsets of a rebin factor, cached in the run (run->d_group_off).
+int ensure_groups(musr_run run, int rebin);
+// Uniform draws of the learned parameters (see generate.cu) and the matching
+// targets 2u - 1; fixed parameters take lo.
+int sample_uniform_thetas(const double* lo_dev, const double* hi_dev, const int32_t* learned_dev, int n_learned,
+                          int P, int n, uint64_t seed, uint64_t offset, double* thetas_dev, float* targets_dev,
+                          cudaStream_t st);
+// The run's data summed over groups of `rebin` bins, one row.
+int rebin_sum_row(musr_run run, int rebin, float* out_dev, cudaStream_t st);
 }  // namespace musr
 
 struct musr_run_s {

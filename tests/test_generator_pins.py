@@ -91,3 +91,62 @@ def test_rebinned_mean_geometric_closed_form():
     q = math.exp(-dt / W.TAU_MU_US)
     ref = [q ** j0 * (1 - q ** min(r, M - j0)) / (1 - q) for j0 in range(0, M, r)]
     np.testing.assert_allclose(mu, ref, rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# Training parameter vectors of the learned start proposer, and its features
+# ---------------------------------------------------------------------------
+def test_sample_thetas_box_uniform_and_fixed_entries():
+    from scipy import stats
+    lo = np.array([200.0, 1.0, 0.7, 50.0, 0.1])
+    hi = np.array([5000.0, 20.0, 0.7, 500.0, 2.0])
+    th, tg = oracle.sample_thetas(lo, hi, 20000, seed=11)
+    assert np.all(th[:, 2] == 0.7)
+    learned = [0, 1, 3, 4]
+    assert tg.shape == (20000, 4)
+    for q, j in enumerate(learned):
+        u = (th[:, j] - lo[j]) / (hi[j] - lo[j])
+        assert np.all((u > 0) & (u < 1))
+        assert stats.kstest(u, "uniform").pvalue > 1e-3
+        np.testing.assert_allclose(tg[:, q], 2 * u - 1, rtol=0, atol=1e-6)
+    # entries sharing a Philox block (q = 0, 1) and across blocks are uncorrelated
+    c = np.corrcoef(tg.T)
+    assert np.all(np.abs(c - np.eye(4)) < 0.05)
+
+
+def test_sample_thetas_offset_is_a_shift():
+    lo = np.zeros(3)
+    hi = np.array([1.0, 2.0, 3.0])
+    a, ta = oracle.sample_thetas(lo, hi, 10, seed=5, offset=0)
+    b, tb = oracle.sample_thetas(lo, hi, 4, seed=5, offset=6)
+    np.testing.assert_array_equal(a[6:], b)
+    np.testing.assert_array_equal(ta[6:], tb)
+    c, _ = oracle.sample_thetas(lo, hi, 10, seed=6, offset=0)
+    assert not np.any(a == c)
+
+
+def test_sample_thetas_known_word_mapping():
+    # u is built from the documented Philox words, checked against the pinned block function
+    lo = np.array([0.0, 0.0, 0.0])
+    hi = np.array([1.0, 1.0, 1.0])
+    th, _ = oracle.sample_thetas(lo, hi, 1, seed=(3 << 32) | 9, offset=(1 << 32) + 5)
+    w = oracle.philox4x32_10([5, 1, 0, 0xfffffffe], [9 ^ 0x0A5F00D1, 3])
+    w2 = oracle.philox4x32_10([5, 1, 1, 0xfffffffe], [9 ^ 0x0A5F00D1, 3])
+    u = [((w[0] >> 5) * 2.0 ** 26 + (w[1] >> 6) + 0.5) / 2.0 ** 53,
+         ((w[2] >> 5) * 2.0 ** 26 + (w[3] >> 6) + 0.5) / 2.0 ** 53,
+         ((w2[0] >> 5) * 2.0 ** 26 + (w2[1] >> 6) + 0.5) / 2.0 ** 53]
+    np.testing.assert_array_equal(th[0], u)
+
+
+def test_proposer_features_brute_force():
+    from workloads import multi_detector_layout
+    lay = multi_detector_layout(n_hist=2, n_bins=[10, 7], window_us=1.0)
+    data = np.arange(17, dtype=np.float64)
+    sums = [[0 + 1 + 2 + 3, 4 + 5 + 6 + 7, 8 + 9], [10 + 11 + 12 + 13, 14 + 15 + 16]]
+    tot = [sum(sums[0]), sum(sums[1])]
+    assert tot == [45, 91]
+    want = np.array([np.log1p(c) - np.log1p(tot[k]) for k in range(2) for c in sums[k]] + list(np.log1p(tot)))
+    np.testing.assert_array_equal(oracle.proposer_features(lay, data, 4), want)
+    mu = np.arange(7.0)
+    isig = np.full(7, 2.0)
+    np.testing.assert_array_equal(oracle.proposer_features(lay, data, 4, mu, isig), (want - mu) * 2.0)

@@ -207,6 +207,34 @@ def range_centre_theta(layout: RunLayout) -> np.ndarray:
     return theta
 
 
+def multi_detector_box(layout: RunLayout):
+    """(lo, hi) of the uniform prior of multi_detector_theta; phases fixed (lo == hi)."""
+    lo = np.zeros(layout.n_params)
+    hi = np.zeros(layout.n_params)
+    K = layout.n_hist
+    for j, name in enumerate(layout.names):
+        if name.startswith("N0_"):
+            lo[j], hi[j] = N0_RANGE
+        elif name.startswith("bkg"):
+            lo[j], hi[j] = BKG_RANGE
+        elif name.startswith("phi_"):
+            lo[j] = hi[j] = 2.0 * math.pi * int(name.split("_")[1]) / K
+        else:
+            lo[j], hi[j] = SHARED_RANGES[name]
+    return lo, hi
+
+
+def default_starts(layout: RunLayout, n_grid: int = 10) -> np.ndarray:
+    """Plain fit starts: the range centre with B1 at the centres of n_grid
+    equal slices of its range (a multi-start grid over the precession field)."""
+    base = range_centre_theta(layout)
+    j = layout.names.index("B1")
+    b_lo, b_hi = SHARED_RANGES["B1"]
+    starts = np.repeat(base[None, :], n_grid, axis=0)
+    starts[:, j] = b_lo + (np.arange(n_grid) + 0.5) * (b_hi - b_lo) / n_grid
+    return starts
+
+
 def perturb(theta: np.ndarray, free: np.ndarray, rel: float, rng: np.random.Generator) -> np.ndarray:
     """theta * (1 + rel * z), z ~ N(0, 1), free entries only."""
     z = rng.standard_normal(theta.shape[0])
