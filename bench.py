@@ -39,9 +39,10 @@ UNIT = "bin-evals/s"
 WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi2 + gradient"
 
 # FP32-pipe FLOPs per bin of the adjoint (value + gradient) kernel for this
-# signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe), counted from
-# the kernel's per-bin arithmetic (FMA = 2 FLOPs); derivation in the design doc.
-FLOPS_PER_BIN_GRAD = 150
+# signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe): ncu counts
+# 37.07 M FFMA and 51.13 M other FP32 thread instructions in one launch over
+# 1,048,576 bins, i.e. (2 x 37.07 + 51.13) / 1.048576 = 119.5 FLOP / bin.
+FLOPS_PER_BIN_GRAD = 120
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
