@@ -133,13 +133,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest x over all ranks (every rank gets it); NCCL on GPUs, gloo on CPU."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(units_per_rank, seconds_per_rank, world):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds_per_rank, world)
 
 
 # --------------------------------------------------------------------------
@@ -360,7 +367,7 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_total = max_over_ranks(sum(step_ms) / 1e3, world)
-    value = world * lay.total_bins * args.steps / t_total
+    value = job_value(lay.total_bins * args.steps, sum(step_ms) / 1e3, world)
     mean_ms = 1e3 * t_total / args.steps
 
     # end to end through the C ABI with host buffers: per step, upload the

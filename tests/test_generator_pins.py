@@ -16,6 +16,19 @@ import oracle
 import workloads as W
 
 
+def test_philox_known_answer_vectors():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    n = 0
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        w = [int(x, 16) for x in line.split()]
+        assert oracle.philox4x32_10(w[0:4], w[4:6]) == w[6:10]
+        n += 1
+    assert n == 3
+
+
 def test_philox_words_are_uniform():
     words = np.array([oracle.philox4x32_10([i, 7, 0, 3], [11, 13]) for i in range(1 << 14)],
                      dtype=np.uint64).ravel()
