@@ -256,6 +256,109 @@ def batched_throughput(dev, rank, reps=5):
             "ms": med, "value": binevals / (med * 1e-3), "unit": "bin-evals/s (chi2, value only)"}
 
 
+def _device_rate(run, theta, obj, mode, reps=50):
+    """Device-entry evaluations replayed from a captured CUDA graph of `reps`
+    launches (no host dispatch between them; inputs L2-resident):
+    (microseconds per evaluation, bin-evaluations per second)."""
+    import torch
+    P = theta.shape[0]
+    th = torch.tensor(theta, dtype=torch.float64, device="cuda")
+    out = torch.empty(1 + P, dtype=torch.float64, device="cuda")
+    cap = torch.cuda.Stream()
+    cap.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(cap):
+        for _ in range(3):
+            run.chi2_grad_device(th, out, obj, mode, stream=cap.cuda_stream)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap):
+        for _ in range(reps):
+            run.chi2_grad_device(th, out, obj, mode, stream=cap.cuda_stream)
+    graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    del graph
+    return us, run.total_bins / (us * 1e-6)
+
+
+def _fit_rate(run, starts, obj, free, method):
+    from paper_1604_02334_gb300 import MUSR_FIT_LM  # noqa: F401
+    t0 = time.perf_counter()
+    iters, evals, vals = [], [], []
+    for st in starts:
+        _, info, _ = run.fit(st, obj, free=free, method=method)
+        iters.append(info["iters"])
+        evals.append(info["evals"])
+        vals.append(info["value"] / info["ndf"])
+    dt = time.perf_counter() - t0
+    return {"fits_per_s": len(starts) / dt, "ms_per_fit": 1e3 * dt / len(starts),
+            "mean_iters": float(np.mean(iters)), "mean_evals": float(np.mean(evals)),
+            "chi2_ndf": float(np.median(vals))}
+
+
+def other_configs(rank):
+    """The remaining workloads of the measurement plan, each a small extra:
+    single histogram (fits/s, latency), -2lnL on the benchmark workload, the
+    paper's Table 1 shapes, and the 32 x 131072 gradient workload (adjoint vs
+    central-difference fits)."""
+    from paper_1604_02334_gb300 import (MUSR_CHI2, MUSR_FIT_BFGS, MUSR_FIT_BFGS_FD, MUSR_FIT_LM, MUSR_POISSON,
+                                        MUSR_VALUE, MUSR_VALUE_GRAD, Run)
+    res = {}
+    # single histogram, 8192 bins, FP64 data, 6 free: LM fits from 5 % perturbed starts
+    lay, theta, seed = W.config_single()
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+        g = W.rng(seed + 21 + rank)
+        starts = [W.perturb(theta, lay.free, 0.05, g) for _ in range(200)]
+        fit = _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_LM)
+        t0 = time.perf_counter()
+        for i in range(500):
+            run.chi2(starts[i % 200], MUSR_CHI2)
+        host_us = 1e6 * (time.perf_counter() - t0) / 500
+        dev_us, _ = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
+    res["single_8192"] = {"fit_lm": fit, "host_chi2_us": host_us, "device_chi2_us": dev_us}
+    # benchmark workload, Poisson deviance, value + gradient
+    lay, theta, seed = make_workload()
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+        us, rate = _device_rate(run, theta, MUSR_POISSON, MUSR_VALUE_GRAD)
+        us_v, rate_v = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
+    res["multi_16x65536"] = {"poisson_grad_us": us, "poisson_grad_bin_evals_per_s": rate,
+                             "chi2_value_us": us_v, "chi2_value_bin_evals_per_s": rate_v}
+    # the paper's Table 1 shapes: chi2 value per evaluation (its Table 1 times one chi2 per "Iter.")
+    sweep = []
+    for M in W.SWEEP_BINS:
+        lay, theta, seed = W.config_sweep(M)
+        with Run(lay) as m:
+            mean = m.model(theta).astype(np.float64)
+        with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+            us, rate = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
+            us_g, rate_g = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE_GRAD)
+        sweep.append({"bins": f"16x{M}", "chi2_us": us, "chi2_bin_evals_per_s": rate,
+                      "chi2_grad_us": us_g, "chi2_grad_bin_evals_per_s": rate_g})
+    res["table1_shapes"] = sweep
+    # 32 x 131072, 72 free: value + gradient rate; fits from 1 % perturbed starts
+    lay, theta, seed = W.config_gradient()
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+        us, rate = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE_GRAD)
+        g = W.rng(seed + 31 + rank)
+        starts = [W.perturb(theta, lay.free, 0.01, g) for _ in range(5)]
+        fits = {"lm_adjoint_gn": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_LM),
+                "bfgs_adjoint": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS),
+                "bfgs_central_differences": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS_FD)}
+    res["gradient_32x131072"] = {"chi2_grad_us": us, "chi2_grad_bin_evals_per_s": rate, "fits": fits}
+    return res
+
+
 def learned_start_ab(dev, rank, train_steps, n_runs=64):
     """Fits/s and success of the learned-start fit against the plain fit.
 
@@ -394,6 +497,7 @@ def run_ours(args):
     assert torch.isfinite(outs[args.warmup:]).all().item()
     batched = None if args.no_batched else batched_throughput(dev, rank)
     learned = None if args.learned_steps <= 0 else learned_start_ab(dev, rank, args.learned_steps)
+    others = None if args.no_other_configs else other_configs(rank)
 
     if rank != 0:
         run.close()
@@ -420,6 +524,8 @@ def run_ours(args):
         line["batched"] = batched
     if learned:
         line["learned_start"] = learned
+    if others:
+        line["other_configs"] = others
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(lay, data, thetas)
     print(json.dumps(line), flush=True)
@@ -434,6 +540,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--learned-steps", type=int, default=32768,
                     help="proposer training steps for the learned-start A/B (0: skip it)")
     args = ap.parse_args()

@@ -587,7 +587,7 @@ namespace musr {
 // Central-difference gradient over the free parameters from one batched launch
 // per 128 vectors: theta and theta +- h_j e_j, h_j = rel_h max(|theta_j|, 1).
 int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
-                      double rel_h, double* value, double* grad) {
+                      double rel_h, double* value, double* grad, double* hdiag) {
     const int P = run->P;
     const int nv_total = 1 + 2 * (int)fidx.size();
     if (!run->fd_batch) {
@@ -620,6 +620,7 @@ int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vec
         const double fp = vals[1 + 2 * a], fm = vals[2 + 2 * a];
         if (!isfinite(fp) || !isfinite(fm)) return MUSR_EDOMAIN;
         grad[fidx[a]] = (fp - fm) / (2.0 * h[a]);
+        if (hdiag) hdiag[fidx[a]] = (fp - 2.0 * vals[0] + fm) / (h[a] * h[a]);
     }
     return MUSR_OK;
 }

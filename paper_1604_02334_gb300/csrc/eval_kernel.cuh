@@ -22,9 +22,10 @@
 //     point turns, so it is exact at any t (no FP32 phase drift at wt ~ 600);
 //   * the deviance uses N h(r), h(r) = (1+r) ln(1+r) - r, r = (d - N)/N, with
 //     a short series for small |r| so that FP32 keeps full relative accuracy;
-//   * per-histogram constants (the only FP64-heavy arithmetic) are staged once
-//     per call -- on the host for host calls, by a small stage kernel chained
-//     with programmatic dependent launch for device calls -- not per block;
+//   * every block stages its histogram's constants itself, without FP64
+//     instructions: double-float FP32 pairs where precision matters and
+//     integer fixed point for phases, spread over several warps so the
+//     dependency chains overlap (and with the first data loads in flight);
 //   * sums beyond the warp use FP32 double-float pairs (TwoSum, ~44-bit
 //     significand) instead of FP64: warps -> block -> 8-block cluster (read
 //     through distributed shared memory) -> last cluster leader, which forms

@@ -17,8 +17,10 @@
 #include "run_impl.h"
 
 namespace musr {
+// Central-difference gradient (and, if hdiag != NULL, the diagonal second
+// differences) of the objective over the free entries, one batched launch.
 int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
-                      double rel_h, double* value, double* grad);
+                      double rel_h, double* value, double* grad, double* hdiag);
 }
 
 using namespace musr;
@@ -185,19 +187,38 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
     auto value_grad = [&](const double* th, double* f, double* gr) -> int {
         if (fd_h > 0.0) {
             ++ev.evals;
-            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr);
+            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, nullptr);
         }
         return ev(th, kGrad, f, gr, nullptr);
     };
+    // start: value, gradient and the diagonal of the Hessian -- from the
+    // adjoint kernel's Gauss-Newton matrix, or from the second differences of
+    // the same central-difference launch -- which preconditions the initial
+    // inverse-Hessian estimate (the parameters' scales differ by 1e5)
     double f;
-    int st = value_grad(theta, &f, g.data());
+    std::vector<double> hd(P, 0.0);
+    int st;
+    if (fd_h > 0.0) {
+        ++ev.evals;
+        st = batch_fd_gradient(ev.run, ev.obj, theta, fidx, fd_h, &f, g.data(), hd.data());
+    } else if (P <= musr::kMaxGnParams) {
+        std::vector<double> H((size_t)P * P);
+        st = ev(theta, kGN, &f, g.data(), H.data());
+        for (int j = 0; j < P; ++j) hd[j] = H[(size_t)j * P + j];
+    } else {
+        st = value_grad(theta, &f, g.data());
+    }
     if (st != MUSR_OK) return st;
-    // initial inverse Hessian: diagonal scaled by the gradient magnitude
     double gnorm = 0.0;
     for (int a = 0; a < nf; ++a) gnorm += g[fidx[a]] * g[fidx[a]];
     gnorm = sqrt(gnorm);
-    for (int a = 0; a < nf; ++a) Hi[(size_t)a * nf + a] = 1.0 / std::max(gnorm, 1.0);
-    int it = 0, result = MUSR_ENOCONV;
+    std::vector<double> hi0(nf);
+    for (int a = 0; a < nf; ++a) {
+        const double h = hd[fidx[a]];
+        hi0[a] = (h > 0.0 && std::isfinite(h)) ? 1.0 / h : 1.0 / std::max(gnorm, 1.0);
+        Hi[(size_t)a * nf + a] = hi0[a];
+    }
+    int it = 0, result = MUSR_ENOCONV, stall = 0;
     double edm = INFINITY;
     while (it < o.max_iter) {
         ++it;
@@ -213,9 +234,9 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
             result = MUSR_OK;
             break;
         }
-        if (slope >= 0.0) {  // not a descent direction: reset
+        if (slope >= 0.0) {  // not a descent direction: reset to the preconditioner
             for (int a = 0; a < nf; ++a)
-                for (int c = 0; c < nf; ++c) Hi[(size_t)a * nf + c] = a == c ? 1.0 / std::max(gnorm, 1.0) : 0.0;
+                for (int c = 0; c < nf; ++c) Hi[(size_t)a * nf + c] = a == c ? hi0[a] : 0.0;
             continue;
         }
         double step = 1.0, fn = INFINITY;
@@ -270,6 +291,14 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
                                               rho * (Hy[a] * s[c] + s[a] * Hy[c]);
         }
         if (rel >= 0.0 && rel < 1e-15 && it > 1) {
+            result = MUSR_OK;
+            break;
+        }
+        // central differences carry the FP32 value noise into the gradient, so
+        // the EDM test cannot pass; that fit stops once three successive steps
+        // gain less than 1e-8 relative (the objective has stalled at its noise)
+        stall = rel < 1e-8 ? stall + 1 : 0;
+        if (fd_h > 0.0 && stall >= 3) {
             result = MUSR_OK;
             break;
         }

@@ -269,6 +269,15 @@ def config_multi_detector(n_hist=16, n_bins=65536, window_us=12.8, seed_offset=1
     return lay, theta, BASE_SEED + seed_offset
 
 
+# histogram lengths of the paper's Table 1 data sets (16 detectors each)
+SWEEP_BINS = (85320, 106650, 142200, 213300, 426601)
+
+
+def config_sweep(n_bins: int, window_us: float = 10.0):
+    """16 x n_bins bins over a 10 us window (seed BASE_SEED + 4); the paper's data-set shapes."""
+    return config_multi_detector(16, n_bins, window_us, seed_offset=4)
+
+
 def config_gradient(n_hist=32, n_bins=131072, window_us=12.8):
     """32 x 131072 bins, 72 free parameters (seed BASE_SEED + 3)."""
     return config_multi_detector(n_hist, n_bins, window_us, seed_offset=3)
