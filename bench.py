@@ -359,6 +359,47 @@ def other_configs(rank):
     return res
 
 
+def batched_grad_throughput(dev, rank, n_runs=64, reps=5):
+    """chi2 + gradient of 64 runs of the benchmark workload (16 x 65536 bins
+    each, own parameters and counts) in one launch of the batched adjoint
+    kernel: device-resident inputs (268 MB, larger than L2), CUDA events."""
+    import torch
+    from paper_1604_02334_gb300 import MUSR_CHI2, MUSR_VALUE_GRAD, GBatch, Run
+    lay = W.multi_detector_layout(16, 65536, 12.8)
+    g = W.rng(W.BASE_SEED + 3005 + rank)
+    thetas = np.stack([W.multi_detector_theta(lay, g) for _ in range(n_runs)])
+    with Run(lay) as layout:
+        data = torch.empty((n_runs, lay.total_bins), dtype=torch.float32, device=dev)
+        layout.generate(torch.tensor(thetas, device=dev), 1, W.BASE_SEED + 3006 + rank, data)
+        torch.cuda.synchronize()
+    runs = [Run(lay, data[i].contiguous()) for i in range(n_runs)]
+    del data
+    b = GBatch(runs, with_gn=False)
+    th = torch.tensor(np.concatenate([W.perturb(t, lay.free, 0.01, g) for t in thetas]), device=dev)
+    out = torch.empty(int(np.sum(b.out_sizes(MUSR_VALUE_GRAD))), dtype=torch.float64, device=dev)
+    b.eval_device(th, out, MUSR_CHI2, MUSR_VALUE_GRAD)  # tunes on first use
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.eval_device(th, out, MUSR_CHI2, MUSR_VALUE_GRAD)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    med = float(np.median(ms))
+    bins = n_runs * lay.total_bins
+    peak = fp32_peak_tflops()
+    achieved = FLOPS_PER_BIN_GRAD * bins / (med * 1e-3) / 1e12
+    b.close()
+    for r in runs:
+        r.close()
+    return {"workload": f"{n_runs} runs x 16 hist x 65536 bins, chi2 + gradient, one launch", "bin_evals": bins,
+            "ms": med, "value": bins / (med * 1e-3), "unit": "bin-evals/s",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": "gbatch_kernel<1,1,1,kGrad>"}}
+
+
 def learned_start_ab(dev, rank, train_steps, n_runs=64):
     """Fits/s and success of the learned-start fit against the plain fit.
 
@@ -370,7 +411,7 @@ def learned_start_ab(dev, rank, train_steps, n_runs=64):
     (range centre with a 10-point B1 grid, best of 10).  A fit succeeds when
     its chi2 is within 1e-6 relative of the truth-start fit's."""
     import torch
-    from paper_1604_02334_gb300 import MUSR_CHI2, Proposer, Run
+    from paper_1604_02334_gb300 import MUSR_CHI2, GBatch, Proposer, Run, fit_multistart_batch
     lay = W.multi_detector_layout(16, 65536, 12.8)
     lo, hi = W.multi_detector_box(lay)
     layout = Run(lay)
@@ -388,8 +429,23 @@ def learned_start_ab(dev, rank, train_steps, n_runs=64):
     runs = [Run(lay, data[i].contiguous()) for i in range(n_runs)]
     free = lay.free
     starts = W.default_starts(lay)
-    ref = [r.fit(thetas[i], MUSR_CHI2, free=free)[1]["value"] for i, r in enumerate(runs)]
+    gb = GBatch(runs)
+    ref = [x["value"] for x in gb.fit(list(thetas), MUSR_CHI2, free=[free] * n_runs)[1]]
     res = {}
+    # batched arms: every run's learned start fitted in lockstep (fallback batched
+    # too); every (run, start) pair of the plain grid fitted in lockstep
+    t0 = time.perf_counter()
+    _, il = prop.fit_batch(gb, MUSR_CHI2, free=[free] * n_runs, chi2ndf_max=1.2, fallback_starts=[starts] * n_runs)
+    t1 = time.perf_counter()
+    _, ip = fit_multistart_batch(runs, [starts] * n_runs, MUSR_CHI2, free=[free] * n_runs)
+    t2 = time.perf_counter()
+    for name, infos, dt in (("learned_batched", il, t1 - t0), ("plain_batched", ip, t2 - t1)):
+        ok = [abs(x["value"] - r) <= 1e-6 * r for x, r in zip(infos, ref)]
+        res[name] = {"fits_per_s": n_runs / dt, "success": float(np.mean(ok)),
+                     "mean_iters": float(np.mean([x["iters"] for x in infos])), "ms_per_fit": 1e3 * dt / n_runs}
+        if name == "learned_batched":
+            res[name]["fallbacks"] = int(sum(x["fallback"] for x in infos))
+    gb.close()
     for name in ("learned", "plain"):
         ok, iters, fallback = [], [], 0
         t0 = time.perf_counter()
@@ -414,7 +470,8 @@ def learned_start_ab(dev, rank, train_steps, n_runs=64):
             "n_runs": n_runs, "train_steps": train_steps, "train_samples": train_steps * 512,
             "train_s": t_train, "train_samples_per_s": train_steps * 512 / t_train,
             "final_loss": float(np.mean(losses[-100:])), **res,
-            "speedup_fits_per_s": res["learned"]["fits_per_s"] / res["plain"]["fits_per_s"]}
+            "speedup_fits_per_s": res["learned"]["fits_per_s"] / res["plain"]["fits_per_s"],
+            "speedup_fits_per_s_batched": res["learned_batched"]["fits_per_s"] / res["plain_batched"]["fits_per_s"]}
 
 
 def run_ours(args):
@@ -496,6 +553,7 @@ def run_ours(args):
     # sanity: results are finite
     assert torch.isfinite(outs[args.warmup:]).all().item()
     batched = None if args.no_batched else batched_throughput(dev, rank)
+    batched_grad = None if args.no_batched else batched_grad_throughput(dev, rank)
     learned = None if args.learned_steps <= 0 else learned_start_ab(dev, rank, args.learned_steps)
     others = None if args.no_other_configs else other_configs(rank)
 
@@ -522,6 +580,8 @@ def run_ours(args):
     }
     if batched:
         line["batched"] = batched
+    if batched_grad:
+        line["batched_grad"] = batched_grad
     if learned:
         line["learned_start"] = learned
     if others:

@@ -284,6 +284,57 @@ typedef struct {
 int musr_fit(musr_run run, int obj, double* theta_inout, const uint8_t* free_mask,
              const musr_fit_opts* opts, musr_fit_result* out);
 
+/*
+ * Batched adjoint evaluation: value + gradient (and the GN matrix) of many
+ * runs, one parameter vector each, in ONE launch (Eq. 3 / Eq. 4 and their
+ * derivatives as for musr_chi2_grad; the same run may appear several times,
+ * e.g. once per start point).  All runs must use the same component kinds and
+ * device.  with_gn != 0 prepares MUSR_VALUE_GRAD_GN (P <= 1024 per run) as
+ * well as MUSR_VALUE_GRAD.  The handle refers to the runs (they must outlive
+ * it) and owns its own tables, buffers and stream; launch shapes are tuned by
+ * timing a few candidates on the first evaluation of each mode.
+ *   thetas   concatenated parameter vectors, run r at sum_{q<r} P_q (FP64).
+ *   out      concatenated outputs, run r at sum_{q<r} n_q with n_q = 1 + P_q
+ *            (MUSR_VALUE_GRAD) or 1 + P_q + P_q^2 (MUSR_VALUE_GRAD_GN),
+ *            laid out as musr_chi2_grad's value, grad, gn.
+ *   active   NULL or one byte per run: runs with 0 are skipped (outputs and
+ *            flags untouched).
+ *   flags    NULL or one int32 per run: bit 0 deviance domain error (value
+ *            meaningless), bit 1 non-finite value.
+ * musr_gbatch_eval: host buffers, synchronous.  musr_gbatch_eval_device: device
+ * buffers (thetas_dev, out_dev, flags_dev may be NULL), all runs, asynchronous
+ * on stream (NULL = the handle's stream; the first call of a mode tunes and
+ * synchronises).
+ */
+typedef struct musr_gbatch_s* musr_gbatch;
+int musr_gbatch_create(const musr_run* runs, int32_t n_runs, int32_t with_gn, musr_gbatch* out);
+int musr_gbatch_destroy(musr_gbatch batch);
+int musr_gbatch_eval(musr_gbatch batch, int obj, int mode, const double* thetas, const uint8_t* active, double* out,
+                     int32_t* flags);
+int musr_gbatch_eval_device(musr_gbatch batch, int obj, int mode, const double* thetas_dev, double* out_dev,
+                            int32_t* flags_dev, void* stream);
+
+/* Levenberg-Marquardt fits of every run of a batch (created with with_gn) in
+ * lockstep: one batched launch per iteration evaluates the trial points of
+ * all unfinished runs; each run follows exactly musr_fit's LM rules and stops
+ * on its own.  thetas: concatenated start vectors, replaced by the results;
+ * free_masks: NULL (all free) or concatenated per-run masks; opts->method must
+ * be MUSR_FIT_LM (MUSR_ENOTSUP otherwise); results: one per run (cov: caller
+ * buffer n_free x n_free or NULL).  Returns MUSR_OK or the first run's
+ * non-OK status. */
+int musr_fit_batch(musr_gbatch batch, int obj, double* thetas, const uint8_t* free_masks, const musr_fit_opts* opts,
+                   musr_fit_result* results);
+
+/* Multi-start fits of many runs in lockstep: every (run, start) pair is one
+ * entry of an internal batch fitted by musr_fit_batch; per run the fit with
+ * the smallest finite objective is kept.  starts: per run n_starts x P_r,
+ * concatenated over runs; free_masks: NULL or concatenated per-run masks;
+ * thetas_out: concatenated results; results: one per run (iters and n_evals
+ * summed over its starts; cov, if given, is filled with NaN: not computed). */
+int musr_fit_multistart_batch(const musr_run* runs, int32_t n_runs, int obj, const double* starts, int32_t n_starts,
+                              const uint8_t* free_masks, const musr_fit_opts* opts, double* thetas_out,
+                              musr_fit_result* results);
+
 /* Plain multi-start fit: musr_fit from each of the n_starts rows of starts
  * (n_starts x n_params, FP64 host) in order; theta_out and out receive the
  * fit with the smallest finite objective (ties: the earliest).  Returns that
@@ -370,6 +421,16 @@ int musr_proposer_propose(musr_proposer prop, const musr_run* runs, int32_t n_ru
 int musr_fit_learned(musr_proposer prop, musr_run run, int obj, const uint8_t* free_mask, const musr_fit_opts* opts,
                      double chi2ndf_max, const double* fallback_starts, int32_t n_fallback, double* theta_out,
                      musr_fit_result* out, int32_t* used_fallback);
+/* Learned-start fits of every run of a batch (musr_gbatch_create with
+ * with_gn, runs of the proposer's layout): one network pass proposes all
+ * starts, musr_fit_batch fits them in lockstep, and the runs whose fit fails
+ * or ends above chi2ndf_max are refitted by musr_fit_multistart_batch from
+ * their fallback starts (per run n_fallback x P_r, concatenated), keeping the
+ * better result.  thetas_out, results, used_fallback (NULL or one int32):
+ * one per run. */
+int musr_fit_learned_batch(musr_proposer prop, musr_gbatch batch, int obj, const uint8_t* free_masks,
+                           const musr_fit_opts* opts, double chi2ndf_max, const double* fallback_starts,
+                           int32_t n_fallback, double* thetas_out, musr_fit_result* results, int32_t* used_fallback);
 
 /* Message for a status code (static string). */
 const char* musr_strerror(int code);

@@ -330,6 +330,34 @@ def gemm_bf16(a, b, bias=None, relu=False, out_f32=None, out_bf16=None, err=None
     return err
 
 
+def _fit_infos(res):
+    return [{"value": x.value, "ndf": x.ndf, "edm": x.edm, "mu": x.mu, "iters": x.iters, "evals": x.n_evals,
+             "status": x.status} for x in res]
+
+
+def fit_multistart_batch(runs, starts, obj=MUSR_CHI2, free=None, max_iter=500, edm_tol=1e-8, mu0=1e-3):
+    """musr_fit_multistart_batch: starts[r] is an (n_starts, P_r) array per run.
+    Returns (list of theta, list of info dicts)."""
+    runs = list(runs)
+    n_starts = int(np.asarray(starts[0]).shape[0])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(st_, dtype=np.float64).reshape(n_starts, -1).ravel()
+                                                for st_ in starts]))
+    fm = None
+    if free is not None:
+        fm = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.uint8).ravel() for f in free]))
+    out = np.zeros(sum(r.P for r in runs))
+    o = _lib.musr_fit_opts(MUSR_FIT_LM, max_iter, edm_tol, mu0, 0.0)
+    res = (_lib.musr_fit_result * len(runs))()
+    handles = (ctypes.c_void_p * len(runs))(*[r.handle.value for r in runs])
+    st = _lib.load().musr_fit_multistart_batch(handles, len(runs), int(obj), _dptr(flat), n_starts,
+                                               fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                                               if fm is not None else None, ctypes.byref(o), _dptr(out), res)
+    if st not in (0, -7, -5, -4):
+        check(st, "musr_fit_multistart_batch")
+    offs = np.r_[0, np.cumsum([r.P for r in runs])]
+    return [out[offs[i]:offs[i + 1]].copy() for i in range(len(runs))], _fit_infos(res)
+
+
 def chi2_batch(runs, thetas, n_vec, obj=MUSR_CHI2):
     """One-shot musr_chi2_batch: plan, evaluate, free."""
     lib = _lib.load()
@@ -545,10 +573,128 @@ class Proposer:
                 "evals": r.n_evals, "status": st, "fallback": bool(used.value)}
         return th, info, cov
 
+    def fit_batch(self, gbatch, obj=MUSR_CHI2, free=None, chi2ndf_max=1.2, fallback_starts=None, max_iter=500,
+                  edm_tol=1e-8, mu0=1e-3):
+        """musr_fit_learned_batch over the runs of `gbatch` (a GBatch with GN):
+        (list of theta, list of info dicts with "fallback")."""
+        n = len(gbatch.runs)
+        fm = None
+        if free is not None:
+            fm = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.uint8).ravel() for f in free]))
+        fb, n_fb = None, 0
+        if fallback_starts is not None:
+            n_fb = int(np.asarray(fallback_starts[0]).shape[0])
+            fb = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).reshape(n_fb, -1).ravel()
+                                                      for x in fallback_starts]))
+        out = np.zeros(int(gbatch.theta_off[-1]))
+        o = _lib.musr_fit_opts(MUSR_FIT_LM, max_iter, edm_tol, mu0, 0.0)
+        res = (_lib.musr_fit_result * n)()
+        used = np.zeros(n, dtype=np.int32)
+        st = self._lib.musr_fit_learned_batch(self.handle, gbatch.handle, int(obj),
+                                              fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                                              if fm is not None else None, ctypes.byref(o), float(chi2ndf_max),
+                                              _dptr(fb) if fb is not None else None, n_fb, _dptr(out), res,
+                                              used.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if st not in (0, -7, -5, -4):
+            check(st, "musr_fit_learned_batch")
+        infos = _fit_infos(res)
+        for i, u in zip(infos, used):
+            i["fallback"] = bool(u)
+        offs = gbatch.theta_off
+        return [out[offs[i]:offs[i + 1]].copy() for i in range(n)], infos
+
     def close(self):
         if self.handle:
             self._lib.musr_proposer_destroy(self.handle)
             self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GBatch:
+    """Batched adjoint evaluation and lockstep LM fits of many runs
+    (musr_gbatch_*, musr_fit_batch); one parameter vector per entry."""
+
+    def __init__(self, runs, with_gn=True):
+        self._lib = _lib.load()
+        self.runs = list(runs)
+        self.P = [r.P for r in self.runs]
+        self.theta_off = np.r_[0, np.cumsum(self.P)].astype(np.int64)
+        self.with_gn = bool(with_gn)
+        handles = (ctypes.c_void_p * len(self.runs))(*[r.handle.value for r in self.runs])
+        self.handle = ctypes.c_void_p()
+        check(self._lib.musr_gbatch_create(handles, len(self.runs), 1 if with_gn else 0, ctypes.byref(self.handle)),
+              "musr_gbatch_create")
+
+    def out_sizes(self, mode):
+        return [1 + p + (p * p if mode == MUSR_VALUE_GRAD_GN else 0) for p in self.P]
+
+    def _flat(self, thetas):
+        flat = np.concatenate([np.asarray(t, dtype=np.float64).ravel() for t in thetas])
+        assert flat.shape[0] == self.theta_off[-1]
+        return np.ascontiguousarray(flat)
+
+    def eval(self, thetas, obj=MUSR_CHI2, mode=MUSR_VALUE_GRAD, active=None):
+        """[(value, grad, gn or None) or None if inactive], flags."""
+        flat = self._flat(thetas)
+        sizes = self.out_sizes(mode)
+        out = np.full(int(np.sum(sizes)), np.nan)
+        flags = np.zeros(len(self.runs), dtype=np.int32)
+        act = None if active is None else np.ascontiguousarray(active, dtype=np.uint8)
+        check(self._lib.musr_gbatch_eval(self.handle, int(obj), int(mode), _dptr(flat),
+                                         act.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if act is not None else None,
+                                         _dptr(out), flags.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+              "musr_gbatch_eval")
+        res, o = [], 0
+        for r, (p, n) in enumerate(zip(self.P, sizes)):
+            if act is not None and not act[r]:
+                res.append(None)
+            else:
+                v = out[o:o + n]
+                res.append((float(v[0]), v[1:1 + p].copy(),
+                            v[1 + p:].reshape(p, p).copy() if mode == MUSR_VALUE_GRAD_GN else None))
+            o += n
+        return res, flags
+
+    def eval_device(self, thetas_dev, out_dev, obj=MUSR_CHI2, mode=MUSR_VALUE_GRAD, flags_dev=None, stream=None):
+        st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
+        check(self._lib.musr_gbatch_eval_device(self.handle, int(obj), int(mode), ctypes.c_void_p(thetas_dev.data_ptr()),
+                                                ctypes.c_void_p(out_dev.data_ptr()),
+                                                ctypes.c_void_p(flags_dev.data_ptr()) if flags_dev is not None else None,
+                                                st), "musr_gbatch_eval_device")
+
+    def fit(self, thetas, obj=MUSR_CHI2, free=None, max_iter=500, edm_tol=1e-8, mu0=1e-3):
+        """Lockstep LM fits: (list of theta, list of info dicts)."""
+        flat = self._flat(thetas)
+        fm = None
+        if free is not None:
+            fm = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.uint8).ravel() for f in free]))
+        o = _lib.musr_fit_opts(MUSR_FIT_LM, max_iter, edm_tol, mu0, 0.0)
+        res = (_lib.musr_fit_result * len(self.runs))()
+        st = self._lib.musr_fit_batch(self.handle, int(obj), _dptr(flat),
+                                      fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if fm is not None else None,
+                                      ctypes.byref(o), res)
+        if st not in (0, -7, -5, -4):
+            check(st, "musr_fit_batch")
+        ths = [flat[self.theta_off[r]:self.theta_off[r + 1]].copy() for r in range(len(self.runs))]
+        infos = [{"value": x.value, "ndf": x.ndf, "edm": x.edm, "mu": x.mu, "iters": x.iters, "evals": x.n_evals,
+                  "status": x.status} for x in res]
+        return ths, infos
+
+    def close(self):
+        if self.handle:
+            self._lib.musr_gbatch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:

@@ -117,6 +117,19 @@ SIGNATURES = {
     "musr_batch_eval_device": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "musr_fit": (ctypes.c_int, [_run, ctypes.c_int, _dp, _u8p, ctypes.POINTER(musr_fit_opts),
                                 ctypes.POINTER(musr_fit_result)]),
+    "musr_gbatch_create": (ctypes.c_int, [ctypes.POINTER(_run), ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.POINTER(_vp)]),
+    "musr_gbatch_destroy": (ctypes.c_int, [_vp]),
+    "musr_gbatch_eval": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _dp, _u8p, _dp, _i32p]),
+    "musr_gbatch_eval_device": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "musr_fit_batch": (ctypes.c_int, [_vp, ctypes.c_int, _dp, _u8p, ctypes.POINTER(musr_fit_opts),
+                                      ctypes.POINTER(musr_fit_result)]),
+    "musr_fit_multistart_batch": (ctypes.c_int, [ctypes.POINTER(_run), ctypes.c_int32, ctypes.c_int, _dp,
+                                                 ctypes.c_int32, _u8p, ctypes.POINTER(musr_fit_opts), _dp,
+                                                 ctypes.POINTER(musr_fit_result)]),
+    "musr_fit_learned_batch": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _u8p, ctypes.POINTER(musr_fit_opts),
+                                              ctypes.c_double, _dp, ctypes.c_int32, _dp,
+                                              ctypes.POINTER(musr_fit_result), _i32p]),
     "musr_fit_multistart": (ctypes.c_int, [_run, ctypes.c_int, _dp, ctypes.c_int32, _u8p,
                                            ctypes.POINTER(musr_fit_opts), _dp, ctypes.POINTER(musr_fit_result)]),
     "musr_proposer_create": (ctypes.c_int, [_run, _dp, _dp, ctypes.POINTER(musr_proposer_opts),

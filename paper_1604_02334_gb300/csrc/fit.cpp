@@ -17,6 +17,14 @@
 #include "run_impl.h"
 
 namespace musr {
+int gbatch_eval_host(musr_gbatch b, int obj, int mode, const double* thetas, const uint8_t* active, double* out,
+                     int32_t* flags);
+const double* gbatch_host_out(musr_gbatch b);
+int64_t gbatch_out_offset(musr_gbatch b, int mode, int r);
+int64_t gbatch_theta_offset(musr_gbatch b, int r);
+int gbatch_has_gn(musr_gbatch b);
+int gbatch_n_runs(musr_gbatch b);
+musr_run gbatch_run(musr_gbatch b, int r);
 // Central-difference gradient (and, if hdiag != NULL, the diagonal second
 // differences) of the objective over the free entries, one batched launch.
 int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
@@ -93,45 +101,79 @@ double edm_of(const std::vector<double>& g, const std::vector<double>& H, const 
 // FP64 accumulation: below it, value comparisons are decided by rounding.
 constexpr double kValueNoise = 1e-6;
 
-int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
-           musr_fit_result* out) {
-    const int P = ev.P, nf = (int)fidx.size();
-    std::vector<double> g(P), H((size_t)P * P), gt(P), Ht((size_t)P * P), trial(P);
-    std::vector<double> A((size_t)nf * nf), b(nf);
-    double f;
-    int st = ev(theta, kGN, &f, g.data(), H.data());
-    if (st != MUSR_OK) return st;
-    double mu = o.mu0, edm = INFINITY;
+}  // namespace
+
+// One run's Levenberg-Marquardt iteration as a state machine, so that a single
+// fit (musr_fit) and many fits in lockstep (musr_fit_batch) share one
+// definition: next() proposes a trial point (or reports the fit finished),
+// observe() takes the objective, gradient and GN matrix at that point.
+struct LmStepper {
+    int P = 0, nf = 0;
+    std::vector<int> fidx;
+    musr_fit_opts o{};
+    std::vector<double> theta, g, H, gt, Ht, trial, A, b;
+    double f = 0.0, mu = 0.0, edm = INFINITY, pred = 0.0;
     int it = 0, result = MUSR_ENOCONV;
-    edm = edm_of(g, H, fidx, P, A, b);
-    while (it < o.max_iter) {
-        ++it;
-        if (edm < o.edm_tol) {
-            result = MUSR_OK;
-            break;
+    bool done = false;
+
+    void init(int P_, const std::vector<int>& fidx_, const musr_fit_opts& o_, const double* th) {
+        P = P_;
+        fidx = fidx_;
+        nf = (int)fidx.size();
+        o = o_;
+        theta.assign(th, th + P);
+        g.assign(P, 0.0);
+        gt.assign(P, 0.0);
+        trial.assign(P, 0.0);
+        H.assign((size_t)P * P, 0.0);
+        Ht.assign((size_t)P * P, 0.0);
+        A.assign((size_t)nf * nf, 0.0);
+        b.assign(nf, 0.0);
+        mu = o.mu0;
+    }
+    // the evaluation at the start point (g and H filled by the caller)
+    void start(double f0) {
+        f = f0;
+        edm = edm_of(g, H, fidx, P, A, b);
+    }
+    // true: evaluate at `trial` (into gt / Ht) and call observe(); false: finished
+    bool next() {
+        while (!done) {
+            if (it >= o.max_iter) {
+                done = true;
+                break;
+            }
+            ++it;
+            if (edm < o.edm_tol) {
+                result = MUSR_OK;
+                done = true;
+                break;
+            }
+            for (int a = 0; a < nf; ++a) {
+                b[a] = -g[fidx[a]];
+                for (int c = 0; c < nf; ++c) A[(size_t)a * nf + c] = H[(size_t)fidx[a] * P + fidx[c]];
+                A[(size_t)a * nf + a] *= (1.0 + mu);
+            }
+            if (!cholesky_solve(A, b, nf)) {
+                mu *= 10.0;
+                if (mu > 1e20) done = true;
+                continue;
+            }
+            // predicted decrease of the quadratic model
+            pred = 0.0;
+            for (int a = 0; a < nf; ++a) {
+                double hb = 0.0;
+                for (int c = 0; c < nf; ++c) hb += H[(size_t)fidx[a] * P + fidx[c]] * b[c];
+                pred -= g[fidx[a]] * b[a] + 0.5 * b[a] * hb;
+            }
+            memcpy(trial.data(), theta.data(), sizeof(double) * P);
+            for (int a = 0; a < nf; ++a) trial[fidx[a]] += b[a];
+            return true;
         }
-        for (int a = 0; a < nf; ++a) {
-            b[a] = -g[fidx[a]];
-            for (int c = 0; c < nf; ++c) A[(size_t)a * nf + c] = H[(size_t)fidx[a] * P + fidx[c]];
-            A[(size_t)a * nf + a] *= (1.0 + mu);
-        }
-        if (!cholesky_solve(A, b, nf)) {
-            mu *= 10.0;
-            if (mu > 1e20) break;
-            continue;
-        }
-        // predicted decrease of the quadratic model
-        double pred = 0.0;
-        for (int a = 0; a < nf; ++a) {
-            double hb = 0.0;
-            for (int c = 0; c < nf; ++c) hb += H[(size_t)fidx[a] * P + fidx[c]] * b[c];
-            pred -= g[fidx[a]] * b[a] + 0.5 * b[a] * hb;
-        }
-        memcpy(trial.data(), theta, sizeof(double) * P);
-        for (int a = 0; a < nf; ++a) trial[fidx[a]] += b[a];
-        double ft;
-        const int s2 = ev(trial.data(), kGN, &ft, gt.data(), Ht.data());
-        if (s2 != MUSR_OK && s2 != MUSR_EDOMAIN && s2 != MUSR_ENONFINITE) return s2;
+        return false;
+    }
+    // s2: MUSR_OK, MUSR_EDOMAIN or MUSR_ENONFINITE (other errors end the fit upstream)
+    void observe(int s2, double ft) {
         bool accept = false;
         double edm_t = INFINITY;
         if (s2 == MUSR_OK) {
@@ -146,7 +188,7 @@ int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const mus
         }
         if (accept) {
             const double rel = (f - ft) / std::max(fabs(f), 1e-300);
-            memcpy(theta, trial.data(), sizeof(double) * P);
+            theta.swap(trial);
             f = ft;
             g.swap(gt);
             H.swap(Ht);
@@ -154,32 +196,52 @@ int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const mus
             mu = std::max(mu * 0.1, 1e-12);
             if (rel >= 0.0 && rel < 1e-15 && edm < 1e3 * o.edm_tol) {
                 result = MUSR_OK;
-                break;
+                done = true;
             }
         } else {
             mu *= 10.0;
-            if (mu > 1e20) break;
+            if (mu > 1e20) done = true;
         }
     }
-    out->value = f;
-    out->edm = edm;
-    out->mu = mu;
-    out->iters = it;
-    if (out->cov) {
-        for (int c = 0; c < nf; ++c) {
-            for (int a = 0; a < nf; ++a) {
-                for (int e = 0; e < nf; ++e) A[(size_t)a * nf + e] = H[(size_t)fidx[a] * P + fidx[e]];
-                b[a] = a == c ? 2.0 : 0.0;
+    void finish(double* theta_out, musr_fit_result* out) {
+        memcpy(theta_out, theta.data(), sizeof(double) * P);
+        out->value = f;
+        out->edm = edm;
+        out->mu = mu;
+        out->iters = it;
+        if (out->cov) {
+            for (int c = 0; c < nf; ++c) {
+                for (int a = 0; a < nf; ++a) {
+                    for (int e = 0; e < nf; ++e) A[(size_t)a * nf + e] = H[(size_t)fidx[a] * P + fidx[e]];
+                    b[a] = a == c ? 2.0 : 0.0;
+                }
+                const bool ok = cholesky_solve(A, b, nf);
+                for (int a = 0; a < nf; ++a) out->cov[(size_t)a * nf + c] = ok ? b[a] : NAN;
             }
-            const bool ok = cholesky_solve(A, b, nf);
-            for (int a = 0; a < nf; ++a) out->cov[(size_t)a * nf + c] = ok ? b[a] : NAN;
         }
     }
-    return result;
+};
+
+namespace {
+
+int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
+           musr_fit_result* out) {
+    LmStepper lm;
+    lm.init(ev.P, fidx, o, theta);
+    double f;
+    int st = ev(theta, kGN, &f, lm.g.data(), lm.H.data());
+    if (st != MUSR_OK) return st;
+    lm.start(f);
+    while (lm.next()) {
+        double ft;
+        const int s2 = ev(lm.trial.data(), kGN, &ft, lm.gt.data(), lm.Ht.data());
+        if (s2 != MUSR_OK && s2 != MUSR_EDOMAIN && s2 != MUSR_ENONFINITE) return s2;
+        lm.observe(s2, ft);
+    }
+    lm.finish(theta, out);
+    return lm.result;
 }
 
-// BFGS on the inverse Hessian with a backtracking (Armijo) line search.
-// fd_h > 0: gradient by central differences from the batched kernel.
 int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
              double fd_h, musr_fit_result* out) {
     const int P = ev.P, nf = (int)fidx.size();
@@ -396,4 +458,162 @@ extern "C" int musr_fit_multistart(musr_run run, int obj, const double* starts, 
     out->iters = iters;
     out->n_evals = evals;
     return best.status;
+}
+
+extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks,
+                              const musr_fit_opts* opts, musr_fit_result* results) {
+    if (!b || !thetas || !results) return MUSR_EINVAL;
+    if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
+    if (!gbatch_has_gn(b)) return MUSR_EINVAL;
+    musr_fit_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.max_iter <= 0) o.max_iter = 500;
+    if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
+    if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
+    if (o.method != MUSR_FIT_LM) return MUSR_ENOTSUP;
+    const int n = gbatch_n_runs(b);
+    std::vector<LmStepper> lm(n);
+    std::vector<int32_t> flags(n, 0), evals(n, 1);
+    std::vector<uint8_t> active(n, 1);
+    int64_t total_theta = 0;
+    for (int r = 0; r < n; ++r) total_theta += gbatch_run(b, r)->P;
+    for (int64_t i = 0; i < total_theta; ++i)
+        if (!std::isfinite(thetas[i])) return MUSR_ENONFINITE;
+    std::vector<double> work(thetas, thetas + total_theta);
+    for (int r = 0; r < n; ++r) {
+        const musr_run run = gbatch_run(b, r);
+        const int64_t to = gbatch_theta_offset(b, r);
+        std::vector<int> fidx;
+        for (int j = 0; j < run->P; ++j)
+            if (!free_masks || free_masks[to + j]) fidx.push_back(j);
+        lm[r].init(run->P, fidx, o, thetas + to);
+    }
+    // start: value, gradient and GN matrix of every run at its start point
+    int st = gbatch_eval_host(b, obj, kGN, work.data(), nullptr, nullptr, flags.data());
+    if (st != MUSR_OK) return st;
+    std::vector<int> status(n, MUSR_OK);
+    auto take = [&](int r, double* f, double* g, double* H) -> int {
+        const musr_run run = gbatch_run(b, r);
+        const int P = run->P;
+        const double* src = gbatch_host_out(b) + gbatch_out_offset(b, kGN, r);
+        *f = (flags[r] & 1) ? INFINITY : src[0];
+        memcpy(g, src + 1, sizeof(double) * P);
+        memcpy(H, src + 1 + P, sizeof(double) * P * P);
+        if (flags[r] & 1) return MUSR_EDOMAIN;
+        return std::isfinite(*f) ? MUSR_OK : MUSR_ENONFINITE;
+    };
+    for (int r = 0; r < n; ++r) {
+        double f;
+        status[r] = take(r, &f, lm[r].g.data(), lm[r].H.data());
+        if (status[r] == MUSR_OK) lm[r].start(f);
+        else lm[r].done = true;
+    }
+    for (;;) {
+        int n_active = 0;
+        for (int r = 0; r < n; ++r) {
+            active[r] = (status[r] == MUSR_OK && lm[r].next()) ? 1 : 0;
+            if (active[r]) {
+                memcpy(work.data() + gbatch_theta_offset(b, r), lm[r].trial.data(), sizeof(double) * lm[r].P);
+                ++evals[r];
+                ++n_active;
+            }
+        }
+        if (n_active == 0) break;
+        st = gbatch_eval_host(b, obj, kGN, work.data(), active.data(), nullptr, flags.data());
+        if (st != MUSR_OK) return st;
+        for (int r = 0; r < n; ++r) {
+            if (!active[r]) continue;
+            double ft;
+            const int s2 = take(r, &ft, lm[r].gt.data(), lm[r].Ht.data());
+            lm[r].observe(s2, ft);
+        }
+    }
+    int worst = MUSR_OK;
+    for (int r = 0; r < n; ++r) {
+        const musr_run run = gbatch_run(b, r);
+        musr_fit_result& res = results[r];
+        double* cov = res.cov;
+        memset(&res, 0, sizeof(res));
+        res.cov = cov;
+        res.n_free = lm[r].nf;
+        res.ndf = (double)(run->total_bins - (int64_t)lm[r].nf);
+        if (status[r] == MUSR_OK) {
+            lm[r].finish(thetas + gbatch_theta_offset(b, r), &res);
+            res.status = lm[r].result;
+        } else {
+            res.value = INFINITY;
+            res.status = status[r];
+        }
+        res.n_evals = evals[r];
+        if (res.status != MUSR_OK && worst == MUSR_OK) worst = res.status;
+    }
+    return worst;
+}
+
+extern "C" int musr_fit_multistart_batch(const musr_run* runs, int32_t n_runs, int obj, const double* starts,
+                                         int32_t n_starts, const uint8_t* free_masks, const musr_fit_opts* opts,
+                                         double* thetas_out, musr_fit_result* results) {
+    if (!runs || n_runs <= 0 || !starts || n_starts <= 0 || !thetas_out || !results) return MUSR_EINVAL;
+    // entry e = (run r, start s), e = r * n_starts + s
+    std::vector<musr_run> entries;
+    std::vector<int64_t> toff(n_runs + 1, 0);
+    for (int r = 0; r < n_runs; ++r) {
+        if (!runs[r]) return MUSR_EINVAL;
+        toff[r + 1] = toff[r] + runs[r]->P;
+        for (int s = 0; s < n_starts; ++s) entries.push_back(runs[r]);
+    }
+    std::vector<double> th;
+    std::vector<uint8_t> fm;
+    for (int r = 0; r < n_runs; ++r) {
+        const int P = runs[r]->P;
+        const double* st = starts + toff[r] * n_starts;
+        th.insert(th.end(), st, st + (size_t)P * n_starts);
+        for (int s = 0; s < n_starts; ++s) {
+            if (free_masks) fm.insert(fm.end(), free_masks + toff[r], free_masks + toff[r] + P);
+            else fm.insert(fm.end(), (size_t)P, (uint8_t)1);
+        }
+    }
+    musr_gbatch b = nullptr;
+    int st = musr_gbatch_create(entries.data(), (int32_t)entries.size(), 1, &b);
+    if (st != MUSR_OK) return st;
+    std::vector<musr_fit_result> res(entries.size());
+    for (auto& x : res) memset(&x, 0, sizeof(x));
+    st = musr_fit_batch(b, obj, th.data(), fm.data(), opts, res.data());
+    musr_gbatch_destroy(b);
+    if (st != MUSR_OK && st != MUSR_ENOCONV && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
+    int worst = MUSR_OK;
+    int64_t e_off = 0;
+    for (int r = 0; r < n_runs; ++r) {
+        const int P = runs[r]->P;
+        int best = -1;
+        int32_t iters = 0, evals = 0;
+        for (int s = 0; s < n_starts; ++s) {
+            const musr_fit_result& x = res[(size_t)r * n_starts + s];
+            iters += x.iters;
+            evals += x.n_evals;
+            const bool ok = (x.status == MUSR_OK || x.status == MUSR_ENOCONV) && std::isfinite(x.value);
+            if (ok && (best < 0 || x.value < res[(size_t)r * n_starts + best].value)) best = s;
+        }
+        double* cov = results[r].cov;
+        if (best < 0) {
+            memset(&results[r], 0, sizeof(musr_fit_result));
+            results[r].cov = cov;
+            results[r].value = INFINITY;
+            results[r].status = res[(size_t)r * n_starts].status != MUSR_OK ? res[(size_t)r * n_starts].status
+                                                                             : MUSR_ENONFINITE;
+            memcpy(thetas_out + toff[r], starts + toff[r] * n_starts, sizeof(double) * P);
+        } else {
+            results[r] = res[(size_t)r * n_starts + best];
+            results[r].cov = cov;  // the covariance is not kept for batched starts
+            if (cov)
+                for (int i = 0; i < results[r].n_free * results[r].n_free; ++i) cov[i] = NAN;
+            memcpy(thetas_out + toff[r], th.data() + e_off + (size_t)best * P, sizeof(double) * P);
+        }
+        results[r].iters = iters;
+        results[r].n_evals = evals;
+        if (results[r].status != MUSR_OK && worst == MUSR_OK) worst = results[r].status;
+        e_off += (int64_t)P * n_starts;
+    }
+    return worst;
 }

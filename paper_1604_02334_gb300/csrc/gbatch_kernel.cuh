@@ -1,0 +1,226 @@
+// Batched value + gradient (+ Gauss-Newton matrix) for many runs, one
+// parameter vector each, in ONE launch: the evaluation under a lockstep fit of
+// many runs (musr_fit_batch), where a single run's launch would be dominated
+// by its fixed cost (launch, staging, the grid-wide reduction).
+//
+// Work is cut into items (run, histogram, first bin, rows) scheduled onto
+// persistent blocks by a host LPT schedule, as in the value-only batch kernel.
+// Per item the block stages the histogram's constants, evaluates its rows with
+// the objective kernel's per-bin code (adjoint modes), reduces the per-role
+// accumulators (FP32 warp sums, FP64 across warps) into an item partial, and
+// takes a per-run ticket.  The run's last item sums the run's item partials
+// per histogram in a fixed order (shared memory) and maps them to theta
+// through the run's CSR table, so every output is bitwise repeatable.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <queue>
+#include <vector>
+
+#include "eval_kernel.cuh"
+#include "musr.h"
+#include "musr_internal.h"
+#include "run_impl.h"
+
+namespace musr {
+
+struct GRunRef {
+    const float* data;
+    const int64_t* hist_off;
+    const int32_t* hist_nbins;
+    const int32_t* role_theta;
+    const int32_t* csr_ptr;
+    const int32_t* csr_src;
+    RunConst rc;
+    double t0, dt;
+    int32_t P, K, n_out;
+    int64_t theta_off, out_off;
+    int32_t hist_ptr_off;  // into hist_item_ptr: K + 1 offsets into run_items
+};
+
+struct GItem {
+    int32_t run, hist, start, rows;
+};
+
+struct GParams {
+    const GRunRef* runs;
+    const GItem* items;
+    const int32_t* block_ptr;
+    const int32_t* block_items;
+    const int32_t* run_items;      // per run, its items by (histogram, first bin)
+    const int32_t* hist_item_ptr;  // per run, K + 1 offsets into run_items
+    const int32_t* run_nitems;
+    const double* thetas;
+    const uint8_t* active;  // per run, or null (all)
+    int obj;
+    double* partial;  // [n_items][NACC]
+    unsigned* run_count;
+    unsigned* flags;  // per run
+    double* out;
+    int32_t* status;  // per run
+};
+
+template <int NE, int NG, int KT, int MODE>
+__global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_kernel(const __grid_constant__ GParams p) {
+    constexpr int NOSC = NE + NG;
+    constexpr int R = 2 + 4 * NOSC + 2 * KT;
+    constexpr int NACC = MODE == kGrad ? 1 + R : 1 + R + R * (R + 1) / 2;
+    constexpr int NPART = stage_parts<NE, NG, KT>();
+    constexpr int G = kBinsPerThread;
+    extern __shared__ double hsum[];  // the run's per-histogram sums, K x NACC
+    __shared__ HistConst hc;
+    __shared__ float red[kMaxWarps][NACC];
+    __shared__ int s_last;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int stripe = blockDim.x * G;
+
+    for (int it = p.block_ptr[blockIdx.x]; it < p.block_ptr[blockIdx.x + 1]; ++it) {
+        const int item_idx = p.block_items[it];
+        const GItem item = p.items[item_idx];
+        if (p.active && !p.active[item.run]) continue;  // uniform over the block
+        const GRunRef& Rr = p.runs[item.run];
+        const int k = item.hist;
+        const int M = Rr.hist_nbins[k];
+        const float* hdata = Rr.data + Rr.hist_off[k];
+        int n0 = item.start + (int)threadIdx.x * G;
+
+        // first row's loads in flight while the constants are staged
+        float d[G];
+        if (n0 < M) {
+            const float4* src = reinterpret_cast<const float4*>(hdata + n0);
+            const float4 a = __ldg(src), b = __ldg(src + 1);
+            d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
+            d[4] = b.x; d[5] = b.y; d[6] = b.z; d[7] = b.w;
+        } else {
+#pragma unroll
+            for (int g = 0; g < G; ++g) d[g] = 0.f;
+        }
+        __syncthreads();  // the previous item is done with hc / red / hsum
+        {
+            const int32_t* rt = Rr.role_theta + (size_t)k * kMaxRoles * 2;
+            const double* theta = p.thetas + Rr.theta_off;
+            for (int part = warp; part < NPART; part += nwarps)
+                if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, Rr.rc, hc);
+        }
+        __syncthreads();
+
+        float acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
+        bool bad = false;
+        const float dtf = (float)Rr.dt, t0f = (float)Rr.t0;
+        for (int row = 0; row < item.rows; ++row) {
+            const int n1 = n0 + stripe;
+            float dn[G];
+            if (row + 1 < item.rows && n1 < M) {
+                const float4* src = reinterpret_cast<const float4*>(hdata + n1);
+                const float4 a = __ldg(src), b = __ldg(src + 1);
+                dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
+                dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
+            } else {
+#pragma unroll
+                for (int g = 0; g < G; ++g) dn[g] = 0.f;
+            }
+            if (n0 < M) eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr);
+#pragma unroll
+            for (int g = 0; g < G; ++g) d[g] = dn[g];
+            n0 = n1;
+        }
+        warp_sum<NACC>(acc);
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
+        }
+        const int any_bad = __syncthreads_or(bad);
+        if (threadIdx.x == 0 && any_bad) atomicOr(&p.flags[item.run], 1u);
+        for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
+            double s = 0.0;
+            for (int w = 0; w < nwarps; ++w) s += (double)red[w][a];
+            p.partial[(size_t)item_idx * NACC + a] = s;
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned prev = atomicAdd(&p.run_count[item.run], 1u);
+            s_last = prev == (unsigned)p.run_nitems[item.run] - 1u;
+        }
+        __syncthreads();
+        if (!s_last) continue;
+        __threadfence();
+        // the run's last item: per-histogram sums in item order, then theta via the CSR
+        const int32_t* hptr = p.hist_item_ptr + Rr.hist_ptr_off;
+        for (int q = threadIdx.x; q < Rr.K * NACC; q += blockDim.x) {
+            const int kk = q / NACC, a = q % NACC;
+            const int j1 = hptr[kk + 1];
+            double s = 0.0;
+            int j = hptr[kk];
+            for (; j + 4 <= j1; j += 4) {
+                // four partials in flight, added in order
+                double x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = __ldcg(p.partial + (size_t)p.run_items[j + u] * NACC + a);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) s += x[u];
+            }
+            for (; j < j1; ++j) s += __ldcg(p.partial + (size_t)p.run_items[j] * NACC + a);
+            hsum[q] = s;
+        }
+        __syncthreads();
+        double* out = p.out + Rr.out_off;
+        for (int o = threadIdx.x; o < Rr.n_out; o += blockDim.x) {
+            double s = 0.0;
+            const int e = Rr.csr_ptr[o + 1];
+            for (int j = Rr.csr_ptr[o]; j < e; ++j) s += hsum[Rr.csr_src[j]];
+            out[o] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned f = atomicExch(&p.flags[item.run], 0u);
+            if (!isfinite(out[0])) f |= 2u;
+            if (p.status) p.status[item.run] = (int32_t)f;
+            p.run_count[item.run] = 0u;
+        }
+    }
+}
+
+template <int NE, int NG, int KT, int MODE>
+cudaError_t launch_gbatch_sig(int blocks, int threads, size_t smem, cudaStream_t st, const GParams& p) {
+    auto kern = gbatch_kernel<NE, NG, KT, MODE>;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes < smem) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if ((int)smem > optin - (int)fa.sharedSizeBytes) return cudaErrorInvalidValue;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<blocks, threads, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_gbatch_mode(const Signature& s, int blocks, int threads, size_t smem, cudaStream_t st,
+                               const GParams& p) {
+#define MUSR_CASE(NE, NG, KT) \
+    if (s.ne == NE && s.ng == NG && s.kt == KT) return launch_gbatch_sig<NE, NG, KT, MODE>(blocks, threads, smem, st, p);
+    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
+    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
+    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
+    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
+    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
+    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+#undef MUSR_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace musr

@@ -40,6 +40,12 @@ struct musr_proposer_s {
     cudaStream_t stream = nullptr;
 };
 
+namespace musr {
+int gbatch_n_runs(musr_gbatch b);
+musr_run gbatch_run(musr_gbatch b, int r);
+int gbatch_has_gn(musr_gbatch b);
+}  // namespace musr
+
 namespace {
 
 constexpr uint64_t kNormOffset = 1ull << 62;  // sample indices of the standardisation set
@@ -437,6 +443,75 @@ int musr_fit_learned(musr_proposer p, musr_run run, int obj, const uint8_t* free
     out->iters = iters;
     out->n_evals = evals;
     return st;
+}
+
+int musr_fit_learned_batch(musr_proposer p, musr_gbatch batch, int obj, const uint8_t* free_masks,
+                           const musr_fit_opts* opts, double chi2ndf_max, const double* fallback_starts,
+                           int32_t n_fallback, double* thetas_out, musr_fit_result* results, int32_t* used_fallback) {
+    if (!p || !batch || !thetas_out || !results || n_fallback < 0 || (n_fallback > 0 && !fallback_starts))
+        return MUSR_EINVAL;
+    if (!musr::gbatch_has_gn(batch)) return MUSR_EINVAL;
+    const int n = musr::gbatch_n_runs(batch);
+    std::vector<musr_run> runs(n);
+    std::vector<int64_t> toff(n + 1, 0);
+    for (int r = 0; r < n; ++r) {
+        runs[r] = musr::gbatch_run(batch, r);
+        toff[r + 1] = toff[r] + runs[r]->P;
+        if (used_fallback) used_fallback[r] = 0;
+    }
+    int st = musr_proposer_propose(p, runs.data(), n, thetas_out);
+    if (st != MUSR_OK) return st;
+    st = musr_fit_batch(batch, obj, thetas_out, free_masks, opts, results);
+    if (st != MUSR_OK && st != MUSR_ENOCONV && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
+    auto good = [&](const musr_fit_result& x) {
+        return (x.status == MUSR_OK || x.status == MUSR_ENOCONV) && std::isfinite(x.value) && x.ndf > 0 &&
+               x.value / x.ndf <= chi2ndf_max;
+    };
+    std::vector<int> bad;
+    for (int r = 0; r < n; ++r)
+        if (!good(results[r])) bad.push_back(r);
+    if (!bad.empty() && n_fallback > 0) {
+        std::vector<musr_run> fr;
+        std::vector<double> fs, fth;
+        std::vector<uint8_t> fm;
+        for (int r : bad) {
+            fr.push_back(runs[r]);
+            const double* src = fallback_starts + toff[r] * n_fallback;
+            fs.insert(fs.end(), src, src + (size_t)runs[r]->P * n_fallback);
+            if (free_masks) fm.insert(fm.end(), free_masks + toff[r], free_masks + toff[r + 1]);
+            fth.resize(fth.size() + runs[r]->P);
+        }
+        std::vector<musr_fit_result> fres(bad.size());
+        for (auto& x : fres) memset(&x, 0, sizeof(x));
+        const int st2 = musr_fit_multistart_batch(fr.data(), (int32_t)fr.size(), obj, fs.data(), n_fallback,
+                                                  free_masks ? fm.data() : nullptr, opts, fth.data(), fres.data());
+        if (st2 != MUSR_OK && st2 != MUSR_ENOCONV && st2 != MUSR_EDOMAIN && st2 != MUSR_ENONFINITE) return st2;
+        int64_t o = 0;
+        for (size_t i = 0; i < bad.size(); ++i) {
+            const int r = bad[i];
+            if (used_fallback) used_fallback[r] = 1;
+            const musr_fit_result& x = fres[i];
+            const int32_t iters = results[r].iters + x.iters, evals = results[r].n_evals + x.n_evals;
+            const bool first_ok = (results[r].status == MUSR_OK || results[r].status == MUSR_ENOCONV) &&
+                                  std::isfinite(results[r].value);
+            const bool second_ok = (x.status == MUSR_OK || x.status == MUSR_ENOCONV) && std::isfinite(x.value);
+            if (second_ok && (!first_ok || x.value < results[r].value)) {
+                double* cov = results[r].cov;
+                results[r] = x;
+                results[r].cov = cov;
+                if (cov)
+                    for (int e = 0; e < x.n_free * x.n_free; ++e) cov[e] = NAN;
+                memcpy(thetas_out + toff[r], fth.data() + o, sizeof(double) * runs[r]->P);
+            }
+            results[r].iters = iters;
+            results[r].n_evals = evals;
+            o += runs[r]->P;
+        }
+    }
+    int worst = MUSR_OK;
+    for (int r = 0; r < n; ++r)
+        if (results[r].status != MUSR_OK && worst == MUSR_OK) worst = results[r].status;
+    return worst;
 }
 
 }  // extern "C"

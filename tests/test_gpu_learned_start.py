@@ -12,7 +12,7 @@ import pytest
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 pytest.importorskip("paper_1604_02334_gb300")
-from paper_1604_02334_gb300 import MUSR_CHI2, Proposer, Run  # noqa: E402
+from paper_1604_02334_gb300 import MUSR_CHI2, GBatch, Proposer, Run, fit_multistart_batch  # noqa: E402
 import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
@@ -68,6 +68,32 @@ def test_learned_start_beats_plain_fit(trained):
     assert np.mean(ok_l) >= np.mean(ok_p) - 0.07
     assert t_l < 0.2 * t_p
     assert np.mean(it_l) < 0.1 * np.mean(it_p)
+
+
+def test_batched_learned_start_beats_batched_plain_fit(trained):
+    # both arms batched: all runs' learned starts fitted in lockstep, against all
+    # (run, start) pairs of the plain multi-start grid fitted in lockstep
+    lay, lo, hi, layout, prop, losses = trained
+    thetas, data = _held_out(lay, layout, N_RUNS, W.BASE_SEED + 1008)
+    starts = W.default_starts(lay)
+    free = lay.free
+    runs = [Run(lay, data[i].contiguous()) for i in range(N_RUNS)]
+    with GBatch(runs) as b:
+        _, ref = b.fit(list(thetas), MUSR_CHI2, free=[free] * N_RUNS)
+        t0 = time.perf_counter()
+        _, il = prop.fit_batch(b, MUSR_CHI2, free=[free] * N_RUNS, chi2ndf_max=1.2, fallback_starts=[starts] * N_RUNS)
+        t1 = time.perf_counter()
+    _, ip = fit_multistart_batch(runs, [starts] * N_RUNS, MUSR_CHI2, free=[free] * N_RUNS)
+    t2 = time.perf_counter()
+    ok_l = [abs(a["value"] - r["value"]) <= 1e-6 * r["value"] for a, r in zip(il, ref)]
+    ok_p = [abs(a["value"] - r["value"]) <= 1e-6 * r["value"] for a, r in zip(ip, ref)]
+    print(f"batched learned: success {np.mean(ok_l):.2f}, {(t1 - t0) / N_RUNS * 1e3:.2f} ms/fit; "
+          f"batched plain: success {np.mean(ok_p):.2f}, {(t2 - t1) / N_RUNS * 1e3:.2f} ms/fit")
+    assert np.mean(ok_l) >= 0.85
+    assert np.mean(ok_l) >= np.mean(ok_p) - 0.07
+    assert (t1 - t0) < 0.2 * (t2 - t1)
+    for r in runs:
+        r.close()
 
 
 def test_learned_fit_reaches_the_oracle_minimum(trained):
