@@ -38,11 +38,13 @@ METRIC = "chi2+grad bin-evals/s"
 UNIT = "bin-evals/s"
 WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi2 + gradient"
 
-# FP32-pipe FLOPs per bin of the adjoint (value + gradient) kernel for this
-# signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe): ncu counts
-# 37.07 M FFMA and 51.13 M other FP32 thread instructions in one launch over
-# 1,048,576 bins, i.e. (2 x 37.07 + 51.13) / 1.048576 = 119.5 FLOP / bin.
-FLOPS_PER_BIN_GRAD = 120
+# FP32-pipe FLOPs per bin of the adjoint (value + gradient) code for this
+# signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe), counted by
+# ncu on one launch of the batched adjoint kernel over 67,108,864 bins, where
+# per-launch costs are negligible: 76.68 M FFMA and 33.32 M other FP32 warp
+# instructions, i.e. (2 x 76.68 + 33.32) x 32 / 67.108864 = 89.0 FLOP / bin
+# (FMA = 2).  The single-run kernel executes the same per-bin code.
+FLOPS_PER_BIN_GRAD = 89
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0

@@ -14,10 +14,14 @@
 // datapath and a very narrow FP64 one (an FP64 warp instruction occupies the
 // pipe for tens of cycles), so here instead:
 //   * each thread owns 8 consecutive bins, loaded as two 128-bit loads;
-//   * exponential envelopes and the precession rotations are stepped from bin
-//     to bin by exact recurrences (delta form x += x * q), re-seeded every 8
-//     bins from exact per-chunk values, so the SFU does one exp2 / sincos per
-//     chunk instead of per bin; Gaussian envelopes use one SFU exp2 per bin;
+//   * envelopes and precession rotations are stepped from bin to bin by
+//     recurrences re-seeded every 8 bins from exact per-chunk values: each
+//     line is carried as the scaled rotation (env cos, env sin), advanced by a
+//     constant 2 x 2 step (exponential envelope) or by the rotation and the
+//     envelope ratio 1 + gq with gq' = gq Q + (Q - 1) (Gaussian envelope), so
+//     the SFU does one exp2 / sincos per line per chunk, not per bin;
+//   * the adjoint accumulates w x_role with x_role cheap per bin and applies
+//     the per-histogram factor of each role once, after the reduction;
 //   * the precession phase at each chunk start is computed in 64-bit fixed
 //     point turns, so it is exact at any t (no FP32 phase drift at wt ~ 600);
 //   * the deviance uses N h(r), h(r) = (1+r) ln(1+r) - r, r = (d - N)/N, with
@@ -125,12 +129,16 @@ __device__ __forceinline__ unsigned long long fixmul(double x, ulonglong2 c) {
     return (bits >> 63) ? (0ull - r) : r;
 }
 
-// expm1(x) and sin(pi x): short Taylor series for the small per-bin step
-// arguments (|x| < 1/64, truncation below 3e-15 relative), the FP32 library
-// functions otherwise.
+// expm1(x) and sin(pi x): Taylor series for the small per-bin step
+// arguments (expm1: |x| < 1/4, terms to x^9, truncation below 3e-13
+// relative; sin: |x| < 1/32, below 3e-15), the FP32 library functions
+// otherwise.
 __device__ __forceinline__ float step_expm1(float x) {
-    if (fabsf(x) >= 0.015625f) return expm1f(x);
-    float r = fmaf(x, 1.f / 6.f, 1.f);
+    if (fabsf(x) >= 0.25f) return expm1f(x);
+    float r = fmaf(x, 1.f / 9.f, 1.f);
+    r = fmaf(x * 0.125f, r, 1.f);
+    r = fmaf(x * (1.f / 7.f), r, 1.f);
+    r = fmaf(x * (1.f / 6.f), r, 1.f);
     r = fmaf(x * 0.2f, r, 1.f);
     r = fmaf(x * 0.25f, r, 1.f);
     r = fmaf(x * (1.f / 3.f), r, 1.f);
@@ -199,7 +207,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
                 o.a_lo = a.lo;
                 o.b_hi = b.hi;
                 o.b_lo = b.lo;
-                o.q = 0.f;
+                o.q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));  // 2^(-2 b) - 1
                 if (rc.t0_zero) {
                     o.cenv = 1.f;
                 } else {
@@ -239,6 +247,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
         hc.kt_a_lo = a.lo;
         hc.kt_b_hi = b.hi;
         hc.kt_b_lo = b.lo;
+        hc.kt_q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));
         if (rc.t0_zero) {
             hc.kt_cenv = 1.f;
         } else {
@@ -281,69 +290,97 @@ __device__ __forceinline__ void warp_sum(float (&v)[NACC]) {
 // One thread's chunk of kBinsPerThread consecutive bins starting at bin n0 of a
 // histogram with M bins: theory (Eq. 1), objective term (Eq. 3 / Eq. 4) and,
 // by mode, the role partials accumulated into the gradient and GN matrix.
-template <int NE, int NG, int KT, int MODE, int NACC>
-__device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
-                                           const float (&d)[kBinsPerThread], int obj, float dtf,
-                                           float t0f, float (&acc)[NACC], bool& bad,
-                                           float* model_dst) {
+//
+// Each precession line is carried as the scaled rotation (env cos, env sin):
+// an exponential line advances by one constant 2 x 2 step per bin (rotation
+// times the envelope's step), a Gaussian line by the rotation and the
+// envelope ratio (1 + gq), itself stepped by gq' = gq Q + (Q - 1).  Role
+// partials dN/d(role) = f_role x_role with f_role constant per histogram
+// (acc_factor, which also carries the objective's weight factor -2 / 2) and
+// x_role cheap per bin: the accumulators collect sum w' x_role, w' = wg / -2.
+template <int NE, int NG, int KT, int MODE, int NACC, bool FULL>
+__device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int M,
+                                                const float (&d)[kBinsPerThread], int obj, float dtf,
+                                                float t0f, float (&acc)[NACC], bool& bad,
+                                                float* model_dst) {
     constexpr int NOSC = NE + NG;
     constexpr int R = 2 + 4 * NOSC + 2 * KT;
     constexpr int G = kBinsPerThread;
+    constexpr bool NEED_TT = KT || (NG > 0 && MODE >= kGrad);
     const float nf0 = (float)n0;
     const float n0p = hc.n0, n0lo = hc.n0_lo, bkg = hc.bkg;
     float E = hc.cE * ex2_approx(-fmaf(nf0, hc.aE_hi, nf0 * hc.aE_lo));
-    float env[NOSC > 0 ? NOSC : 1], cs[NOSC > 0 ? NOSC : 1], sn[NOSC > 0 ? NOSC : 1];
+    float C[NOSC > 0 ? NOSC : 1], Sn[NOSC > 0 ? NOSC : 1], gq[NOSC > 0 ? NOSC : 1];
+    float stA[NOSC > 0 ? NOSC : 1], stB[NOSC > 0 ? NOSC : 1];
+    const float k1 = fmaf(2.f, nf0, 1.f);  // 2 n0 + 1
+    const float nn0 = nf0 * nf0;
 #pragma unroll
     for (int c = 0; c < NOSC; ++c) {
         const OscConst& o = hc.osc[c];
-        if (c < NE) env[c] = o.cenv * ex2_approx(-fmaf(nf0, o.a_hi, nf0 * o.a_lo));
+        float env;
+        if (c < NE) {
+            env = o.cenv * ex2_approx(-fmaf(nf0, o.a_hi, nf0 * o.a_lo));
+            // one bin's step: (1 + q) (cos d, sin d) = (1 + A, B)
+            stA[c] = fmaf(o.q, o.cm1, o.q + o.cm1);
+            stB[c] = fmaf(o.q, o.sn, o.sn);
+        } else {
+            env = o.cenv * ex2_approx(-fmaf(nn0, o.b_hi, fmaf(nf0, o.a_hi, fmaf(nn0, o.b_lo, nf0 * o.a_lo))));
+            gq[c] = step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
+            stA[c] = o.cm1;
+            stB[c] = o.sn;
+        }
         const unsigned long long ph = o.ph0 + (unsigned long long)n0 * o.step;
         const float x = (float)(int)(ph >> 32) * 2.3283064365386963e-10f;  // turns in [-1/2, 1/2)
-        __sincosf(6.28318530717958647692f * x, &sn[c], &cs[c]);
+        float sc, cc;
+        __sincosf(6.28318530717958647692f * x, &sc, &cc);
+        C[c] = env * cc;
+        Sn[c] = env * sc;
     }
+    // Kubo-Toyabe: G(t) e^{-t/tau} = E / 3 + (1 - x) e23,  x = (Delta t)^2,
+    // e23 = 2/3 exp(-t/tau - x/2), stepped like a Gaussian envelope
+    float e23 = 0.f, gqk = 0.f, kr2 = 0.f;
+    if (KT) {
+        e23 = 0.666666667f * hc.kt_cenv *
+              ex2_approx(-fmaf(nn0, hc.kt_b_hi, fmaf(nf0, hc.kt_a_hi, fmaf(nn0, hc.kt_b_lo, nf0 * hc.kt_a_lo))));
+        gqk = step_expm1(-0.693147180559945309f * fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
+        kr2 = hc.kt_rate * hc.kt_rate;
+    }
+    const float ts = fmaf(nf0, dtf, t0f);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        const float nf = nf0 + (float)g;
-        const float t = fmaf(nf, dtf, t0f);
-        const float nn = nf * nf;
+        const float t = fmaf((float)g, dtf, ts);
+        const float tt = NEED_TT ? t * t : 0.f;
         float S = E;
 #pragma unroll
-        for (int c = 0; c < NOSC; ++c) {
-            const OscConst& o = hc.osc[c];
-            if (c >= NE)
-                env[c] = o.cenv * ex2_approx(-fmaf(nn, o.b_hi, fmaf(nf, o.a_hi, fmaf(nn, o.b_lo, nf * o.a_lo))));
-            S = fmaf(o.amp * env[c], cs[c], S);
-        }
-        float envk = 0.f, xk = 0.f, GE = 0.f;
+        for (int c = 0; c < NOSC; ++c) S = fmaf(hc.osc[c].amp, C[c], S);
+        float xk = 0.f, GE = 0.f;
         if (KT) {
-            envk = hc.kt_cenv *
-                   ex2_approx(-fmaf(nn, hc.kt_b_hi, fmaf(nf, hc.kt_a_hi, fmaf(nn, hc.kt_b_lo, nf * hc.kt_a_lo))));
-            const float dtk = hc.kt_rate * t;
-            xk = dtk * dtk;
-            GE = fmaf(0.666666667f * (1.f - xk), envk, 0.333333333f * E);
+            xk = kr2 * tt;
+            GE = fmaf(E, 0.333333333f, fmaf(-e23, xk, e23));
             S = fmaf(hc.kt_amp, GE, S);
         }
         // N0 carried as an FP32 pair so its rounding does not bias every bin
         const float N = fmaf(n0p, S, fmaf(n0lo, S, bkg));
 
         if (MODE == kModel) {
-            if (n0 + g < M) model_dst[n0 + g] = N;
+            if (FULL || n0 + g < M) model_dst[n0 + g] = N;
         } else if (MODE == kSum) {
-            if (n0 + g < M) acc[0] += N;
-        } else if (n0 + g < M) {
+            if (FULL || n0 + g < M) acc[0] += N;
+        } else if (FULL || n0 + g < M) {
             const float dv = d[g];
-            float term, wg, wh;
+            float wq, wh;  // wq = wg / -2 (gradient weight), wh = GN weight / 2
             if (obj == MUSR_CHI2) {
                 const float w = rcp_approx(fmaxf(dv, 1.f));
                 const float r = dv - N;
-                term = r * r * w;
-                wg = -2.f * r * w;
-                wh = 2.f * w;
+                wq = r * w;
+                acc[0] = fmaf(r, wq, acc[0]);
+                wh = w;
             } else {
+                float term;
                 if (dv > 0.f) {
                     if (!(N > 0.f)) {
                         bad = true;
-                        term = wg = wh = 0.f;
+                        term = wq = wh = 0.f;
                     } else {
                         const float rN = rcp_approx(N);
                         const float rho = (dv - N) * rN;
@@ -363,50 +400,58 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
                             h = fmaf(rho, u, u - rho);
                         }
                         term = 2.f * N * h;
-                        wg = -2.f * rho;
-                        wh = 2.f * rN;
+                        wq = rho;
+                        wh = rN;
                     }
                 } else {
                     if (!(N >= 0.f)) bad = true;
                     term = 2.f * N;
-                    wg = 2.f;
-                    wh = N > 0.f ? 2.f * rcp_approx(N) : 0.f;
+                    wq = -1.f;
+                    wh = N > 0.f ? rcp_approx(N) : 0.f;
                 }
+                acc[0] += term;
             }
-            acc[0] += term;
-            if (MODE >= kGrad) {
-                float pr[R];
-                pr[0] = S;
-                pr[1] = 1.f;
+            if (MODE == kGrad) {
+                const float wt = wq * t;
+                const float wtt = NEED_TT ? wq * tt : 0.f;
+                acc[1] = fmaf(wq, S, acc[1]);
+                acc[2] += wq;
 #pragma unroll
                 for (int c = 0; c < NOSC; ++c) {
-                    const OscConst& o = hc.osc[c];
-                    const float m = n0p * env[c];
-                    const float pa = m * cs[c];
-                    const float q = o.amp * pa;
-                    pr[2 + 4 * c] = pa;
-                    pr[2 + 4 * c + 1] = (c < NE) ? -t * q : -o.rate * t * t * q;
-                    const float ps = -o.amp * m * sn[c];
-                    pr[2 + 4 * c + 2] = ps * t * hc.kfreq;
-                    pr[2 + 4 * c + 3] = ps;
+                    acc[3 + 4 * c] = fmaf(wq, C[c], acc[3 + 4 * c]);
+                    acc[4 + 4 * c] = fmaf(c < NE ? wt : wtt, C[c], acc[4 + 4 * c]);
+                    acc[5 + 4 * c] = fmaf(wt, Sn[c], acc[5 + 4 * c]);
+                    acc[6 + 4 * c] = fmaf(wq, Sn[c], acc[6 + 4 * c]);
                 }
                 if (KT) {
-                    pr[2 + 4 * NOSC] = n0p * GE;
-                    pr[2 + 4 * NOSC + 1] =
-                        n0p * hc.kt_amp * 0.666666667f * hc.kt_rate * t * t * (xk - 3.f) * envk;
+                    acc[3 + 4 * NOSC] = fmaf(wq, GE, acc[3 + 4 * NOSC]);
+                    acc[4 + 4 * NOSC] = fmaf(wtt, (xk - 3.f) * e23, acc[4 + 4 * NOSC]);
+                }
+            } else if (MODE == kGN) {
+                float x[R];
+                x[0] = S;
+                x[1] = 1.f;
+#pragma unroll
+                for (int c = 0; c < NOSC; ++c) {
+                    x[2 + 4 * c] = C[c];
+                    x[3 + 4 * c] = (c < NE ? t : tt) * C[c];
+                    x[4 + 4 * c] = t * Sn[c];
+                    x[5 + 4 * c] = Sn[c];
+                }
+                if (KT) {
+                    x[2 + 4 * NOSC] = GE;
+                    x[3 + 4 * NOSC] = tt * (xk - 3.f) * e23;
                 }
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[1 + r] = fmaf(wg, pr[r], acc[1 + r]);
-                if (MODE == kGN) {
-                    int a = 1 + R;
+                for (int r = 0; r < R; ++r) acc[1 + r] = fmaf(wq, x[r], acc[1 + r]);
+                int a = 1 + R;
 #pragma unroll
-                    for (int r1 = 0; r1 < R; ++r1) {
-                        const float qv = wh * pr[r1];
+                for (int r1 = 0; r1 < R; ++r1) {
+                    const float qv = wh * x[r1];
 #pragma unroll
-                        for (int r2 = r1; r2 < R; ++r2) {
-                            acc[a] = fmaf(qv, pr[r2], acc[a]);
-                            ++a;
-                        }
+                    for (int r2 = r1; r2 < R; ++r2) {
+                        acc[a] = fmaf(qv, x[r2], acc[a]);
+                        ++a;
                     }
                 }
             }
@@ -415,14 +460,69 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M,
         E = fmaf(E, hc.qE, E);
 #pragma unroll
         for (int c = 0; c < NOSC; ++c) {
-            const OscConst& o = hc.osc[c];
-            if (c < NE) env[c] = fmaf(env[c], o.q, env[c]);
-            const float c2 = fmaf(cs[c], o.cm1, fmaf(-sn[c], o.sn, cs[c]));
-            const float s2 = fmaf(sn[c], o.cm1, fmaf(cs[c], o.sn, sn[c]));
-            cs[c] = c2;
-            sn[c] = s2;
+            const float c2 = fmaf(C[c], stA[c], fmaf(-Sn[c], stB[c], C[c]));
+            const float s2 = fmaf(Sn[c], stA[c], fmaf(C[c], stB[c], Sn[c]));
+            if (c < NE) {
+                C[c] = c2;
+                Sn[c] = s2;
+            } else {
+                C[c] = fmaf(c2, gq[c], c2);
+                Sn[c] = fmaf(s2, gq[c], s2);
+                gq[c] = fmaf(gq[c], hc.osc[c].q, gq[c] + hc.osc[c].q);
+            }
+        }
+        if (KT) {
+            e23 = fmaf(e23, gqk, e23);
+            gqk = fmaf(gqk, hc.kt_q, gqk + hc.kt_q);
         }
     }
+}
+
+template <int NE, int NG, int KT, int MODE, int NACC>
+__device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M, const float (&d)[kBinsPerThread],
+                                           int obj, float dtf, float t0f, float (&acc)[NACC], bool& bad,
+                                           float* model_dst) {
+    if (n0 + kBinsPerThread <= M)
+        eval_chunk_body<NE, NG, KT, MODE, NACC, true>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst);
+    else
+        eval_chunk_body<NE, NG, KT, MODE, NACC, false>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst);
+}
+
+// The per-histogram constant of accumulator a (see eval_chunk): 1 for the
+// objective; -2 f_r for the gradient of role r (dN/d role = f_r x_r, the
+// accumulators hold sum (wg / -2) x_r); 2 f_r1 f_r2 for the Gauss-Newton
+// entry of roles (r1, r2) (they hold sum (wh / 2) x_r1 x_r2).
+template <int NE, int NG, int KT>
+__device__ __forceinline__ float role_factor_r(const HistConst& hc, int r) {
+    constexpr int NOSC = NE + NG;
+    if (r < 2) return 1.f;
+    const float n0p = hc.n0;
+    if (r < 2 + 4 * NOSC) {
+        const int c = (r - 2) >> 2, j = (r - 2) & 3;
+        const OscConst& o = hc.osc[c];
+        const float an = -o.amp * n0p;
+        if (j == 0) return n0p;
+        if (j == 1) return c < NE ? an : o.rate * an;
+        if (j == 2) return an * hc.kfreq;
+        return an;
+    }
+    if (r == 2 + 4 * NOSC) return n0p;
+    // x = t^2 (x_KT - 3) e23 with e23 = 2/3 of the envelope
+    return n0p * hc.kt_amp * hc.kt_rate;
+}
+
+template <int NE, int NG, int KT, int MODE>
+__device__ __forceinline__ float acc_factor(const HistConst& hc, int a) {
+    constexpr int R = 2 + 4 * (NE + NG) + 2 * KT;
+    if (a == 0 || MODE < kGrad) return 1.f;
+    if (a <= R) return -2.f * role_factor_r<NE, NG, KT>(hc, a - 1);
+    // Gauss-Newton entry: upper triangle of (r1, r2), row by row
+    int q = a - 1 - R, r1 = 0;
+    while (q >= R - r1) {
+        q -= R - r1;
+        ++r1;
+    }
+    return 2.f * role_factor_r<NE, NG, KT>(hc, r1) * role_factor_r<NE, NG, KT>(hc, r1 + q);
 }
 
 
@@ -535,6 +635,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
             DF v{red[0][a], 0.f};
             for (int w = 1; w < nwarps; ++w) v = df_add(v, DF{red[w][a], 0.f});
+            // the histogram's role factor (all blocks of a cluster share the histogram)
+            if (MODE >= kGrad && a > 0) v = df_mul(v, DF{acc_factor<NE, NG, KT, MODE>(hc, a), 0.f});
             dst[a] = v;
         }
     }

@@ -143,7 +143,8 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
         for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
             double s = 0.0;
             for (int w = 0; w < nwarps; ++w) s += (double)red[w][a];
-            p.partial[(size_t)item_idx * NACC + a] = s;
+            // the histogram's role factor of this accumulator (see eval_chunk)
+            p.partial[(size_t)item_idx * NACC + a] = a > 0 ? s * (double)acc_factor<NE, NG, KT, MODE>(hc, a) : s;
         }
         __threadfence();
         __syncthreads();
