@@ -289,7 +289,8 @@ int musr_fit(musr_run run, int obj, double* theta_inout, const uint8_t* free_mas
  * runs, one parameter vector each, in ONE launch (Eq. 3 / Eq. 4 and their
  * derivatives as for musr_chi2_grad; the same run may appear several times,
  * e.g. once per start point).  All runs must use the same component kinds and
- * device.  with_gn != 0 prepares MUSR_VALUE_GRAD_GN (P <= 1024 per run) as
+ * device and have at least one histogram (MUSR_EINVAL otherwise); histograms
+ * without bins are allowed.  with_gn != 0 prepares MUSR_VALUE_GRAD_GN (P <= 1024 per run) as
  * well as MUSR_VALUE_GRAD.  The handle refers to the runs (they must outlive
  * it) and owns its own tables, buffers and stream; launch shapes are tuned by
  * timing a few candidates on the first evaluation of each mode.

@@ -543,11 +543,21 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     const int tile = blockIdx.x;
-    const int k = p.tile_hist[tile];
-    const int M = p.hist_nbins[k];
+    int k, M, tstart;
+    const float* hdata;
+    if (p.uni_tph > 0) {
+        k = tile / p.uni_tph;
+        M = p.uni_nbins;
+        tstart = min((tile - k * p.uni_tph) * p.uni_tile_bins, (M + 7) & ~7);
+        hdata = p.data + (int64_t)k * p.uni_stride;
+    } else {
+        k = p.tile_hist[tile];
+        M = p.hist_nbins[k];
+        tstart = p.tile_start[tile];
+        hdata = p.data + p.hist_off[k];
+    }
     const int stripe = (int)blockDim.x * G;  // a tile is p.chunks stripes of blockDim x 8 bins
-    int n0 = p.tile_start[tile] + (int)threadIdx.x * G;
-    const float* hdata = p.data + p.hist_off[k];
+    int n0 = tstart + (int)threadIdx.x * G;
 
     // issue the first chunk's loads so their latency overlaps the staging
     float d[G];
@@ -584,7 +594,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
             }
         }
         const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
-        const int32_t* rt = p.role_theta + (size_t)k * kMaxRoles * 2;
+        const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
             if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, p.rc, hc);
     }

@@ -334,7 +334,7 @@ int musr_gbatch_create(const musr_run* runs, int32_t n_runs, int32_t with_gn, mu
     if (!runs || n_runs <= 0 || !out) return MUSR_EINVAL;
     *out = nullptr;
     for (int r = 0; r < n_runs; ++r) {
-        if (!runs[r]) return MUSR_EINVAL;
+        if (!runs[r] || runs[r]->K <= 0) return MUSR_EINVAL;  // a run without histograms has no items
         const Signature& s = runs[r]->sig;
         if (s.ne != runs[0]->sig.ne || s.ng != runs[0]->sig.ng || s.kt != runs[0]->sig.kt ||
             runs[r]->device != runs[0]->device)

@@ -16,6 +16,7 @@ constexpr int kBinsPerThread = 8;                  // consecutive bins per threa
 constexpr int kMaxThreads = 256;                   // block size upper bound
 constexpr int kMaxWarps = kMaxThreads / 32;
 constexpr int kInlineParams = 256;                 // theta passed inside the launch parameters
+constexpr int kInlineRoleHist = 32;                // role-map rows passed inside the launch parameters
 
 // Per-histogram constants of the theory, staged once per evaluation (the
 // paper's kernel keeps the parameter / map values in shared memory for the
@@ -96,10 +97,24 @@ struct EvalParams {
     int32_t* status_out;          // [1] or null
     int theta_inline_n;           // > 0: theta_inline holds theta (host calls)
     double theta_inline[kInlineParams];
+    // Equal-length histograms (the common layout): tile b belongs to histogram
+    // b / uni_tph and starts at min((b mod uni_tph) uni_tile_bins, uni_nbins
+    // rounded up to 8); histogram k starts at float k * uni_stride.  The tile
+    // and histogram tables are then not read, which takes two dependent
+    // memory round trips off the start of every block.  0: use the tables.
+    int uni_tph, uni_tile_bins, uni_nbins;
+    int64_t uni_stride;
+    // role -> theta rows of the first kInlineRoleHist histograms (when K fits),
+    // so staging waits for theta alone
+    int rt_inline;
+    int32_t rt_rows[kInlineRoleHist * kMaxRoles * 2];
     // model output (kModel)
     float* model_out;
     const int64_t* model_off;     // [K] offsets into model_out
 };
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(EvalParams) <= 32000, "EvalParams exceeds the kernel parameter space");
+
 
 // Launch the objective kernel for a signature / mode (eval_*.cu).
 cudaError_t launch_eval(const Signature& sig, int mode, int threads, int n_tiles,

@@ -570,6 +570,19 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
                 (n_out[m] + 1 + n_src[m] + T.n_clusters + 2 * K) <= 1024 &&
                 T.threads > 32 * (2 + 2 * sig.n_osc());  // warps beyond the staging ones exist
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
+    // equal-length histograms: tiles and offsets by arithmetic (see EvalParams)
+    bool uniform = K > 0 && (int64_t)T.n_tiles % K == 0;
+    for (int kk = 1; kk < K && uniform; ++kk) uniform = n_bins[kk] == n_bins[0];
+    if (uniform && n_bins[0] + (int64_t)T.tile_bins < (int64_t)1 << 30) {
+        p.uni_tph = T.n_tiles / K;
+        p.uni_tile_bins = T.tile_bins;
+        p.uni_nbins = (int)n_bins[0];
+        p.uni_stride = round_up(n_bins[0], 8);
+    }
+    if (K <= kInlineRoleHist) {
+        p.rt_inline = 1;
+        memcpy(p.rt_rows, role_theta.data(), sizeof(int32_t) * (size_t)K * kMaxRoles * 2);
+    }
     p.out = out_dev;
     p.status_out = status_dev;
     p.model_off = d_model_off;

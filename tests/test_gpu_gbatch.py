@@ -110,3 +110,41 @@ def test_multistart_batch_matches_sequential_multistart(runs):
         assert rel_err(infos[e]["value"], si["value"]) <= 1e-6
     for r in gruns:
         r.close()
+
+
+def test_gbatch_edge_cases():
+    g = W.rng(77)
+    # a run whose histograms include empty ones and one of 8 bins
+    lay = W.multi_detector_layout(4, [0, 8, 0, 3000], window_us=12.8)
+    theta = W.multi_detector_theta(lay, g)
+    d = W.poisson_counts(oracle.model(lay, theta), 5)
+    # a run where the deviance has no likelihood: N = 0 under counts
+    lay2 = W.multi_detector_layout(2, [500, 700], window_us=12.8)
+    th2 = W.multi_detector_theta(lay2, g)
+    d2 = W.poisson_counts(oracle.model(lay2, th2), 6)
+    bad = th2.copy()
+    bad[0] = 0.0
+    bad[2] = 0.0  # N0 and bkg of histogram 0 -> N = 0 where d > 0
+    r1, r2 = Run(lay, d), Run(lay2, d2)
+    with GBatch([r1, r2, r2]) as b:
+        res, flags = b.eval([theta, bad, th2], MUSR_POISSON, MUSR_VALUE_GRAD_GN)
+        v, gr, H = oracle.gradient(lay, d, theta, oracle.POISSON, with_gn=True)
+        assert grad_rel_err(res[0][1], gr) <= 1e-4
+        assert flags[0] == 0 and flags[2] == 0
+        assert flags[1] & 1
+        v2, g2, _ = oracle.gradient(lay2, d2, th2, oracle.POISSON, with_gn=False)
+        assert grad_rel_err(res[2][1], g2) <= 1e-4
+    r1.close()
+    r2.close()
+
+
+def test_gbatch_rejects_a_run_without_histograms():
+    from paper_1604_02334_gb300 import MusrError
+    from workloads import RunLayout  # noqa: F401
+    import dataclasses
+    lay = W.multi_detector_layout(1, [100], window_us=12.8)
+    empty = dataclasses.replace(lay, n_bins=np.zeros(0, dtype=np.int64), map=np.zeros((0, lay.map_width), np.int32))
+    r = Run(empty)
+    with pytest.raises(MusrError):
+        GBatch([r])
+    r.close()
