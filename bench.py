@@ -41,10 +41,10 @@ WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi
 # FP32-pipe FLOPs per bin of the adjoint (value + gradient) code for this
 # signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe), counted by
 # ncu on one launch of the batched adjoint kernel over 67,108,864 bins, where
-# per-launch costs are negligible: 76.68 M FFMA and 33.32 M other FP32 warp
-# instructions, i.e. (2 x 76.68 + 33.32) x 32 / 67.108864 = 89.0 FLOP / bin
+# per-launch costs are negligible: 73.34 M FFMA and 28.45 M other FP32 warp
+# instructions, i.e. (2 x 73.34 + 28.45) x 32 / 67.108864 = 83.5 FLOP / bin
 # (FMA = 2).  The single-run kernel executes the same per-bin code.
-FLOPS_PER_BIN_GRAD = 89
+FLOPS_PER_BIN_GRAD = 83.5
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0

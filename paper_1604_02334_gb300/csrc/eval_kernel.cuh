@@ -168,9 +168,11 @@ __host__ __device__ constexpr int stage_parts() {
     return 2 + 2 * (NE + NG);
 }
 
+// stripe > 0: bins between a thread's consecutive chunks (for the Gaussian
+// ratio carried from chunk to chunk, see GqCarry); 0 when nothing is carried.
 template <int NE, int NG, int KT>
 __device__ void stage_part(int part, const int32_t* rt, const double* theta, const RunConst& rc,
-                           HistConst& hc) {
+                           HistConst& hc, int stripe = 0) {
     constexpr int NOSC = NE + NG;
     const DF it = df_of(rc.inv_tau), dtL = df_of(rc.dt_log2e), dt = df_of(rc.dt);
     if (part == 0) {
@@ -208,6 +210,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
                 o.b_hi = b.hi;
                 o.b_lo = b.lo;
                 o.q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));  // 2^(-2 b) - 1
+                o.qs = step_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
                 if (rc.t0_zero) {
                     o.cenv = 1.f;
                 } else {
@@ -248,6 +251,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
         hc.kt_b_hi = b.hi;
         hc.kt_b_lo = b.lo;
         hc.kt_q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));
+        hc.kt_qs = step_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
         if (rc.t0_zero) {
             hc.kt_cenv = 1.f;
         } else {
@@ -298,11 +302,21 @@ __device__ __forceinline__ void warp_sum(float (&v)[NACC]) {
 // partials dN/d(role) = f_role x_role with f_role constant per histogram
 // (acc_factor, which also carries the objective's weight factor -2 / 2) and
 // x_role cheap per bin: the accumulators collect sum w' x_role, w' = wg / -2.
+// The Gaussian step ratios at a thread's next chunk (one stripe further):
+// gq(n0 + stripe) = gq(n0) Qs + (Qs - 1), Qs = 2^(-2 b stripe), so only a
+// thread's first chunk evaluates them from scratch.
+template <int NOSC>
+struct GqCarry {
+    float gq[NOSC > 0 ? NOSC : 1];
+    float gqk;
+    bool valid;
+};
+
 template <int NE, int NG, int KT, int MODE, int NACC, bool FULL>
 __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int M,
                                                 const float (&d)[kBinsPerThread], int obj, float dtf,
                                                 float t0f, float (&acc)[NACC], bool& bad,
-                                                float* model_dst) {
+                                                float* model_dst, GqCarry<NE + NG>* carry) {
     constexpr int NOSC = NE + NG;
     constexpr int R = 2 + 4 * NOSC + 2 * KT;
     constexpr int G = kBinsPerThread;
@@ -325,7 +339,12 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
             stB[c] = fmaf(o.q, o.sn, o.sn);
         } else {
             env = o.cenv * ex2_approx(-fmaf(nn0, o.b_hi, fmaf(nf0, o.a_hi, fmaf(nn0, o.b_lo, nf0 * o.a_lo))));
-            gq[c] = step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
+            if (carry && carry->valid) {
+                gq[c] = carry->gq[c];
+            } else {
+                gq[c] = step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
+            }
+            if (carry) carry->gq[c] = fmaf(gq[c], o.qs, gq[c] + o.qs);
             stA[c] = o.cm1;
             stB[c] = o.sn;
         }
@@ -342,9 +361,16 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
     if (KT) {
         e23 = 0.666666667f * hc.kt_cenv *
               ex2_approx(-fmaf(nn0, hc.kt_b_hi, fmaf(nf0, hc.kt_a_hi, fmaf(nn0, hc.kt_b_lo, nf0 * hc.kt_a_lo))));
-        gqk = step_expm1(-0.693147180559945309f * fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
+        if (carry && carry->valid) {
+            gqk = carry->gqk;
+        } else {
+            gqk = step_expm1(-0.693147180559945309f *
+                             fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
+        }
+        if (carry) carry->gqk = fmaf(gqk, hc.kt_qs, gqk + hc.kt_qs);
         kr2 = hc.kt_rate * hc.kt_rate;
     }
+    if (carry) carry->valid = true;
     const float ts = fmaf(nf0, dtf, t0f);
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -478,14 +504,16 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
     }
 }
 
+// carry: NULL, or the thread's GqCarry when its successive calls are one
+// stripe apart (the staged qs constants must be for that stripe)
 template <int NE, int NG, int KT, int MODE, int NACC>
 __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M, const float (&d)[kBinsPerThread],
                                            int obj, float dtf, float t0f, float (&acc)[NACC], bool& bad,
-                                           float* model_dst) {
+                                           float* model_dst, GqCarry<NE + NG>* carry = nullptr) {
     if (n0 + kBinsPerThread <= M)
-        eval_chunk_body<NE, NG, KT, MODE, NACC, true>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst);
+        eval_chunk_body<NE, NG, KT, MODE, NACC, true>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
     else
-        eval_chunk_body<NE, NG, KT, MODE, NACC, false>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst);
+        eval_chunk_body<NE, NG, KT, MODE, NACC, false>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
 }
 
 // The per-histogram constant of accumulator a (see eval_chunk): 1 for the
@@ -596,7 +624,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
         const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
-            if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, p.rc, hc);
+            if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, p.rc, hc, (int)blockDim.x * G);
     }
     __syncthreads();
 
@@ -604,6 +632,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
     bool bad = false;
+    GqCarry<NE + NG> carry;
+    carry.valid = false;
 
     for (int c = 0; c < p.chunks; ++c) {
         // the next chunk's loads are in flight while this one is evaluated
@@ -620,7 +650,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         }
         if (n0 < M)
             eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
-                                               MODE == kModel ? p.model_out + p.model_off[k] : nullptr);
+                                               MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
 #pragma unroll
         for (int g = 0; g < G; ++g) d[g] = dn[g];
         n0 = n1;

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
             const int32_t* rt = Rr.role_theta + (size_t)k * kMaxRoles * 2;
             const double* theta = p.thetas + Rr.theta_off;
             for (int part = warp; part < NPART; part += nwarps)
-                if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, Rr.rc, hc);
+                if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, Rr.rc, hc, stripe);
         }
         __syncthreads();
 
@@ -115,6 +115,8 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
         bool bad = false;
+        GqCarry<NE + NG> carry;
+        carry.valid = false;
         const float dtf = (float)Rr.dt, t0f = (float)Rr.t0;
         for (int row = 0; row < item.rows; ++row) {
             const int n1 = n0 + stripe;
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
                 for (int g = 0; g < G; ++g) dn[g] = 0.f;
             }
-            if (n0 < M) eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr);
+            if (n0 < M) eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr, &carry);
 #pragma unroll
             for (int g = 0; g < G; ++g) d[g] = dn[g];
             n0 = n1;

@@ -25,6 +25,7 @@ struct OscConst {
     // q: per-bin expm1 step of an exponential envelope; for a Gaussian
     // envelope expm1 of the per-bin change of its step ratio, 2^(-2 b) - 1
     float amp, rate, cenv, a_hi, a_lo, b_hi, b_lo, q, cm1, sn;
+    float qs;  // Gaussian envelope: 2^(-2 b stripe) - 1, the change of its step ratio over one stripe
     unsigned long long ph0, step;  // phase at bin 0 and per bin, 64-bit fixed-point turns
 };
 
@@ -32,7 +33,7 @@ struct HistConst {
     float n0, n0_lo, bkg, cE, aE_hi, aE_lo, qE;  // N0 = n0 + n0_lo (FP32 pair)
     float kfreq;  // 2 pi gamma: dN/dB = dN/d(omega) * 2 pi gamma
     OscConst osc[kMaxOsc];
-    float kt_amp, kt_rate, kt_cenv, kt_a_hi, kt_a_lo, kt_b_hi, kt_b_lo, kt_q;
+    float kt_amp, kt_rate, kt_cenv, kt_a_hi, kt_a_lo, kt_b_hi, kt_b_lo, kt_q, kt_qs;
 };
 
 // Theta-independent constants of a run's time grid, prepared on the host in
