@@ -45,6 +45,11 @@ WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi
 # instructions, i.e. (2 x 73.34 + 28.45) x 32 / 67.108864 = 83.5 FLOP / bin
 # (FMA = 2).  The single-run kernel executes the same per-bin code.
 FLOPS_PER_BIN_GRAD = 83.5
+# DRAM bytes (read + write) of one eval_kernel<1,1,1,kGrad> launch of this
+# workload, from the ncu capture summarised in
+# profiles/eval_kernel_grad_16x65536.md (4.28 MB read, 0 written); to be
+# re-measured whenever that kernel changes.
+TRAFFIC_BYTES_GRAD_LAUNCH = 4278784
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -166,20 +171,30 @@ def cpu_sample(lay, data):
 
 
 def cpu_baseline(lay, data, thetas, seconds=12.0):
+    """The FP64 oracle on the host cores, all of them and 8 threads (the
+    paper's CPU baseline used 8 threads), on a bounded sample of the workload."""
     import oracle
     sub, d = cpu_sample(lay, data)
-    n = 0
-    t0 = time.perf_counter()
-    while True:
-        oracle.gradient(sub, d, thetas[n % len(thetas)], oracle.CHI2, with_gn=False)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds and n >= 3:
-            break
-    return {"value": sub.total_bins * n / el, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
+    all_threads = oracle.num_threads()
+
+    def rate(secs):
+        n = 0
+        t0 = time.perf_counter()
+        while True:
+            oracle.gradient(sub, d, thetas[n % len(thetas)], oracle.CHI2, with_gn=False)
+            n += 1
+            el = time.perf_counter() - t0
+            if el >= secs and n >= 3:
+                return sub.total_bins * n / el, n, el
+
+    v, n, el = rate(seconds)
+    oracle.set_num_threads(8)
+    v8, _, _ = rate(seconds / 3)
+    oracle.set_num_threads(all_threads)
+    return {"value": v, "unit": UNIT, "cores": all_threads, "kind": "oracle",
             "sample": f"{sub.n_hist} hist x {SAMPLE_BINS} leading bins of the workload, "
-                      f"{n} chi2+gradient evaluations in {el:.1f} s"}
+                      f"{n} chi2+gradient evaluations in {el:.1f} s",
+            "value_8_threads": v8}
 
 
 # --------------------------------------------------------------------------
@@ -572,7 +587,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "bins": lay.total_bins, "params": P,
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES_GRAD_LAUNCH,
                      "kernel": "eval_kernel<1,1,1,kGrad>",
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
         "clocks": clk,

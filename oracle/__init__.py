@@ -70,6 +70,8 @@ def _load():
                       lib.orc_fit, lib.orc_rebinned_mean):
                 f.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
+            lib.orc_set_num_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_num_threads.restype = None
             _lib = lib
     return _lib
 
@@ -98,6 +100,11 @@ class OracleError(RuntimeError):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's following calls."""
+    _load().orc_set_num_threads(int(n))
 
 
 def model(lay, theta) -> np.ndarray:

@@ -588,6 +588,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Thread count of the following parallel regions (n <= 0: leave unchanged). */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ======================================================================== */
 /* Synthetic-data generator: Philox4x32-10 and a Poisson sampler             */
 /* ======================================================================== */
