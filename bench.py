@@ -373,6 +373,37 @@ def other_configs(rank):
                 "bfgs_adjoint": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS),
                 "bfgs_central_differences": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS_FD)}
     res["gradient_32x131072"] = {"chi2_grad_us": us, "chi2_grad_bin_evals_per_s": rate, "fits": fits}
+    # the benchmark theory as a user expression compiled at run time (FP64 kernel)
+    from paper_1604_02334_gb300 import UserTheory
+    lay, theta, seed = make_workload()
+    t0 = time.perf_counter()
+    th = UserTheory(W.MD_USER_EXPR)
+    compile_s = time.perf_counter() - t0
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+        th.eval(run, theta, MUSR_CHI2)
+        reps = 20
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            th.eval(run, theta, MUSR_CHI2)
+        us = 1e6 * (time.perf_counter() - t0) / reps
+        nvec = 64
+        thetas = np.repeat(theta[None, :], nvec, axis=0)
+        th.eval(run, thetas, MUSR_CHI2)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            th.eval(run, thetas, MUSR_CHI2)
+        us64 = 1e6 * (time.perf_counter() - t0) / 5
+        t0 = time.perf_counter()
+        th.grad(run, theta, MUSR_CHI2, free=lay.free)
+        grad_ms = 1e3 * (time.perf_counter() - t0)
+    th.close()
+    res["user_theory_16x65536"] = {"compile_s": compile_s, "chi2_us_per_call": us,
+                                   "chi2_bin_evals_per_s": lay.total_bins / (us * 1e-6),
+                                   "chi2_64_vectors_us": us64,
+                                   "chi2_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64 * 1e-6),
+                                   "fd_gradient_81_vectors_ms": grad_ms, "arithmetic": "fp64 (host call)"}
     return res
 
 

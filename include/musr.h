@@ -433,6 +433,48 @@ int musr_fit_learned_batch(musr_proposer prop, musr_gbatch batch, int obj, const
                            const musr_fit_opts* opts, double chi2ndf_max, const double* fallback_starts,
                            int32_t n_fallback, double* thetas_out, musr_fit_result* results, int32_t* used_fallback);
 
+/*
+ * User-defined theory functions (Sec. 4.2.1): the asymmetry A_k(t) of Eq. 1 as
+ * a C expression, compiled at run time with NVRTC (loaded from the CUDA
+ * toolkit; MUSR_ENOTSUP if it is missing) into a kernel that evaluates, in
+ * FP64, N_k(t) = p[m[0]] e^{-t/tau} (1 + A_k(t)) + p[m[1]] and the Eq. 3 / Eq. 4
+ * objective for many parameter vectors in one launch.
+ *   expr     an expression (no statements) over: t (us, double); p (the
+ *            parameter vector, double[]); m (the histogram's map row of the run
+ *            descriptor, int[]: m[0] N0, m[1] background, the rest free for the
+ *            expression); f (the function array, double[n_funcs], supplied per
+ *            vector); numeric literals; + - * / ( ) [ ] ,; the CUDA math
+ *            functions (exp, cos, sin, pow, sqrt, log, ...) and the muSR
+ *            functions se(t, lambda) = exp(-lambda t), ge(t, lambda, beta) =
+ *            exp(-(lambda t)^beta), sg(t, sigma) = exp(-(sigma t)^2 / 2),
+ *            stg(t, sigma) = 1/3 + 2/3 (1 - (sigma t)^2) exp(-(sigma t)^2 / 2),
+ *            tf(t, phi, B) = cos(2 pi 0.013554 B t + phi) (B in G, phi in rad).
+ *            Characters outside [A-Za-z0-9_. +-*()/[],] are rejected
+ *            (MUSR_EINVAL); a compile error returns MUSR_EINVAL and no
+ *            handle; musr_utheory_log(NULL) then returns the compiler's log
+ *            (per thread, until the next failure); musr_utheory_log(th) the
+ *            log of a successful compile (warnings).
+ * The run supplies histograms, bins, time grid, data and map rows; its
+ * component table is not used.  Every call below is synchronous.
+ *   musr_utheory_eval: values[v] (host) of obj for the n_vec host vectors
+ *     thetas [n_vec x n_params] and funcs [n_vec x n_funcs] (NULL if
+ *     n_funcs == 0); +inf where the deviance has no likelihood.
+ *   musr_utheory_grad: value and central-difference gradient (free entries,
+ *     step rel_h max(|theta_j|, 1), rel_h <= 0: 1e-6) from one launch.
+ *   musr_utheory_fit: BFGS on those gradients (opts->method ignored; stops when
+ *     the objective stalls at its resolution), results as musr_fit.
+ */
+typedef struct musr_utheory_s* musr_utheory;
+int musr_utheory_create(const char* expr, int32_t n_funcs, musr_utheory* out);
+int musr_utheory_destroy(musr_utheory th);
+const char* musr_utheory_log(musr_utheory th);
+int musr_utheory_eval(musr_utheory th, musr_run run, int obj, const double* thetas, const double* funcs,
+                      int32_t n_vec, double* values);
+int musr_utheory_grad(musr_utheory th, musr_run run, int obj, const double* theta, const double* funcs,
+                      const uint8_t* free_mask, double rel_h, double* value, double* grad);
+int musr_utheory_fit(musr_utheory th, musr_run run, int obj, double* theta_inout, const double* funcs,
+                     const uint8_t* free_mask, const musr_fit_opts* opts, musr_fit_result* out);
+
 /* Message for a status code (static string). */
 const char* musr_strerror(int code);
 

@@ -701,3 +701,76 @@ class GBatch:
             self.close()
         except Exception:
             pass
+
+
+class UserTheory:
+    """A user-defined asymmetry A_k(t) compiled at run time (musr_utheory_*):
+    expr is a C expression over t, p, m and f (see include/musr.h)."""
+
+    def __init__(self, expr, n_funcs=0):
+        self._lib = _lib.load()
+        self.n_funcs = int(n_funcs)
+        self.handle = ctypes.c_void_p()
+        st = self._lib.musr_utheory_create(expr.encode(), self.n_funcs, ctypes.byref(self.handle))
+        if st != 0:
+            log = self._lib.musr_utheory_log(None)
+            raise MusrError(st, "musr_utheory_create" + (": " + log.decode(errors="replace") if log else ""))
+        self.expr = expr
+
+    @property
+    def log(self):
+        return self._lib.musr_utheory_log(self.handle).decode(errors="replace")
+
+    def _funcs(self, funcs, n):
+        if self.n_funcs == 0:
+            return None
+        f = np.ascontiguousarray(np.broadcast_to(np.asarray(funcs, dtype=np.float64), (n, self.n_funcs)))
+        return f
+
+    def eval(self, run, thetas, obj=MUSR_CHI2, funcs=None):
+        th = np.ascontiguousarray(np.atleast_2d(thetas), dtype=np.float64)
+        n = th.shape[0]
+        f = self._funcs(funcs, n)
+        out = np.zeros(n)
+        check(self._lib.musr_utheory_eval(self.handle, run.handle, int(obj), _dptr(th),
+                                          _dptr(f) if f is not None else None, n, _dptr(out)), "musr_utheory_eval")
+        return out
+
+    def grad(self, run, theta, obj=MUSR_CHI2, funcs=None, free=None, rel_h=1e-6):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        f = self._funcs(funcs, 1)
+        fm = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
+        v = ctypes.c_double()
+        g = np.zeros(th.shape[0])
+        check(self._lib.musr_utheory_grad(self.handle, run.handle, int(obj), _dptr(th),
+                                          _dptr(f) if f is not None else None,
+                                          fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if fm is not None else None,
+                                          float(rel_h), ctypes.byref(v), _dptr(g)), "musr_utheory_grad")
+        return float(v.value), g
+
+    def fit(self, run, theta0, obj=MUSR_CHI2, funcs=None, free=None, max_iter=500, fd_rel_h=1e-4):
+        th = np.ascontiguousarray(theta0, dtype=np.float64).copy()
+        f = self._funcs(funcs, 1)
+        fm = None if free is None else np.ascontiguousarray(free, dtype=np.uint8)
+        nf = th.shape[0] if fm is None else int(fm.sum())
+        cov = np.zeros((nf, nf))
+        o = _lib.musr_fit_opts(MUSR_FIT_BFGS_FD, max_iter, 0.0, 0.0, fd_rel_h)
+        r = _lib.musr_fit_result()
+        r.cov = _dptr(cov)
+        st = self._lib.musr_utheory_fit(self.handle, run.handle, int(obj), _dptr(th),
+                                        _dptr(f) if f is not None else None,
+                                        fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if fm is not None else None,
+                                        ctypes.byref(o), ctypes.byref(r))
+        info = {"value": r.value, "ndf": r.ndf, "edm": r.edm, "iters": r.iters, "evals": r.n_evals, "status": st}
+        return th, info, cov
+
+    def close(self):
+        if self.handle:
+            self._lib.musr_utheory_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

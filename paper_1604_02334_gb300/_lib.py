@@ -164,6 +164,13 @@ SIGNATURES = {
     "musr_mlp_adam": (ctypes.c_int, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
     "musr_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float,
                                            ctypes.POINTER(ctypes.c_float), _vp]),
+    "musr_utheory_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(_vp)]),
+    "musr_utheory_destroy": (ctypes.c_int, [_vp]),
+    "musr_utheory_log": (ctypes.c_char_p, [_vp]),
+    "musr_utheory_eval": (ctypes.c_int, [_vp, _run, ctypes.c_int, _dp, _dp, ctypes.c_int32, _dp]),
+    "musr_utheory_grad": (ctypes.c_int, [_vp, _run, ctypes.c_int, _dp, _dp, _u8p, ctypes.c_double, _dp, _dp]),
+    "musr_utheory_fit": (ctypes.c_int, [_vp, _run, ctypes.c_int, _dp, _dp, _u8p, ctypes.POINTER(musr_fit_opts),
+                                        ctypes.POINTER(musr_fit_result)]),
     "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "musr_version": (ctypes.c_char_p, []),
     "musr_last_cuda_error": (ctypes.c_char_p, []),

@@ -50,7 +50,9 @@ def _compile(src, force, verbose):
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     if not force and not _stale(obj, [src] + headers()):
         return obj
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj + ".tmp"]
+    # the host minimiser steps many fits at once on the host cores (OpenMP)
+    extra = ["-Xcompiler", "-fopenmp"] if src.endswith(".cpp") else []
+    cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -70,7 +72,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, force, verbose), srcs))
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "--cudart", "static", "-o", tmp] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "--cudart", "static", "-Xcompiler", "-fopenmp", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

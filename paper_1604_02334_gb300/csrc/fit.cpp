@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 #include "musr.h"
@@ -242,34 +243,23 @@ int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const mus
     return lm.result;
 }
 
-int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
-             double fd_h, musr_fit_result* out) {
-    const int P = ev.P, nf = (int)fidx.size();
+}  // namespace
+
+// BFGS over the free entries for any objective: value_grad(theta, f, g) gives
+// the value and gradient, start(theta, f, g, hd) also the Hessian diagonal hd
+// (zero where unknown), which preconditions the initial inverse-Hessian
+// estimate (the parameters' scales differ by 1e5).  fd: the gradient is a
+// central difference (its value noise rules out the EDM test; see below).
+int fit_bfgs_generic(int P, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o, bool fd,
+                     const std::function<int(const double*, double*, double*)>& value_grad,
+                     const std::function<int(const double*, double*, double*, double*)>& start,
+                     musr_fit_result* out) {
+    const double fd_h = fd ? 1.0 : 0.0;  // only its sign is used below
+    const int nf = (int)fidx.size();
     std::vector<double> g(P), gn_(P), x(P), Hi((size_t)nf * nf, 0.0), d(nf), s(nf), y(nf);
-    auto value_grad = [&](const double* th, double* f, double* gr) -> int {
-        if (fd_h > 0.0) {
-            ++ev.evals;
-            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, nullptr);
-        }
-        return ev(th, kGrad, f, gr, nullptr);
-    };
-    // start: value, gradient and the diagonal of the Hessian -- from the
-    // adjoint kernel's Gauss-Newton matrix, or from the second differences of
-    // the same central-difference launch -- which preconditions the initial
-    // inverse-Hessian estimate (the parameters' scales differ by 1e5)
     double f;
     std::vector<double> hd(P, 0.0);
-    int st;
-    if (fd_h > 0.0) {
-        ++ev.evals;
-        st = batch_fd_gradient(ev.run, ev.obj, theta, fidx, fd_h, &f, g.data(), hd.data());
-    } else if (P <= musr::kMaxGnParams) {
-        std::vector<double> H((size_t)P * P);
-        st = ev(theta, kGN, &f, g.data(), H.data());
-        for (int j = 0; j < P; ++j) hd[j] = H[(size_t)j * P + j];
-    } else {
-        st = value_grad(theta, &f, g.data());
-    }
+    int st = start(theta, &f, g.data(), hd.data());
     if (st != MUSR_OK) return st;
     double gnorm = 0.0;
     for (int a = 0; a < nf; ++a) gnorm += g[fidx[a]] * g[fidx[a]];
@@ -372,6 +362,36 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
     if (out->cov)
         for (size_t e = 0; e < (size_t)nf * nf; ++e) out->cov[e] = 2.0 * Hi[e];
     return result;
+}
+
+namespace {
+
+int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
+             double fd_h, musr_fit_result* out) {
+    const int P = ev.P;
+    auto value_grad = [&](const double* th, double* f, double* gr) -> int {
+        if (fd_h > 0.0) {
+            ++ev.evals;
+            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, nullptr);
+        }
+        return ev(th, kGrad, f, gr, nullptr);
+    };
+    // start: the Hessian diagonal from the adjoint kernel's Gauss-Newton matrix,
+    // or from the second differences of the same central-difference launch
+    auto start = [&](const double* th, double* f, double* gr, double* hd) -> int {
+        if (fd_h > 0.0) {
+            ++ev.evals;
+            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, hd);
+        }
+        if (P <= musr::kMaxGnParams) {
+            std::vector<double> H((size_t)P * P);
+            const int st = ev(th, kGN, f, gr, H.data());
+            for (int j = 0; j < P; ++j) hd[j] = H[(size_t)j * P + j];
+            return st;
+        }
+        return value_grad(th, f, gr);
+    };
+    return fit_bfgs_generic(P, theta, fidx, o, fd_h > 0.0, value_grad, start, out);
 }
 
 }  // namespace
@@ -503,6 +523,8 @@ extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint
         if (flags[r] & 1) return MUSR_EDOMAIN;
         return std::isfinite(*f) ? MUSR_OK : MUSR_ENONFINITE;
     };
+    // every run's LM step is independent: spread them over the host cores
+#pragma omp parallel for schedule(dynamic, 1) if (n >= 8)
     for (int r = 0; r < n; ++r) {
         double f;
         status[r] = take(r, &f, lm[r].g.data(), lm[r].H.data());
@@ -510,18 +532,20 @@ extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint
         else lm[r].done = true;
     }
     for (;;) {
-        int n_active = 0;
+#pragma omp parallel for schedule(dynamic, 1) if (n >= 8)
         for (int r = 0; r < n; ++r) {
             active[r] = (status[r] == MUSR_OK && lm[r].next()) ? 1 : 0;
             if (active[r]) {
                 memcpy(work.data() + gbatch_theta_offset(b, r), lm[r].trial.data(), sizeof(double) * lm[r].P);
                 ++evals[r];
-                ++n_active;
             }
         }
+        int n_active = 0;
+        for (int r = 0; r < n; ++r) n_active += active[r];
         if (n_active == 0) break;
         st = gbatch_eval_host(b, obj, kGN, work.data(), active.data(), nullptr, flags.data());
         if (st != MUSR_OK) return st;
+#pragma omp parallel for schedule(dynamic, 1) if (n_active >= 8)
         for (int r = 0; r < n; ++r) {
             if (!active[r]) continue;
             double ft;

@@ -391,6 +391,7 @@ int musr_run_s::allocate() {
         if (m < 3) max_clusters = std::max(max_clusters, tl[m].n_clusters);
     }
     const size_t o_rt = A.take<int32_t>(role_theta.size() + 1);
+    const size_t o_map = A.take<int32_t>(map.size() + 1);  // raw map rows (user theories)
     size_t o_ptr[3], o_src[3];
     for (int m = 0; m < 3; ++m) {
         o_ptr[m] = A.take<int32_t>(ptr[m].size() + 1);
@@ -420,6 +421,7 @@ int musr_run_s::allocate() {
         tl[m].d_hist_nclusters = reinterpret_cast<int32_t*>(b + o_hn[m]);
     }
     d_role_theta = reinterpret_cast<int32_t*>(b + o_rt);
+    d_map = reinterpret_cast<int32_t*>(b + o_map);
     for (int m = 0; m < 3; ++m) {
         d_csr_ptr[m] = reinterpret_cast<int32_t*>(b + o_ptr[m]);
         d_csr_src[m] = reinterpret_cast<int32_t*>(b + o_src[m]);
@@ -465,6 +467,7 @@ int musr_run_s::allocate() {
         up(T.d_hist_nclusters, T.hist_nclusters.data(), sizeof(int32_t) * K);
     }
     up(d_role_theta, role_theta.data(), sizeof(int32_t) * role_theta.size());
+    up(d_map, map.data(), sizeof(int32_t) * map.size());
     for (int m = 0; m < 3; ++m) {
         up(d_csr_ptr[m], ptr[m].data(), sizeof(int32_t) * ptr[m].size());
         up(d_csr_src[m], src[m].data(), sizeof(int32_t) * src[m].size());

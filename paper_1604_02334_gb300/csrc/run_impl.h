@@ -59,6 +59,7 @@ struct musr_run_s {
     int64_t *d_hist_off = nullptr, *d_model_off = nullptr;
     int32_t* d_hist_nbins = nullptr;
     int32_t* d_role_theta = nullptr;
+    int32_t* d_map = nullptr;  // [K][W] the descriptor's map rows
     int32_t* d_csr_ptr[3] = {nullptr, nullptr, nullptr};
     int32_t* d_csr_src[3] = {nullptr, nullptr, nullptr};
     int n_out[3] = {0, 0, 0};

@@ -138,6 +138,13 @@ MD_COMPONENTS = [
 ]
 
 
+# The multi-detector theory written as a user expression over the map row
+# [N0, bkg, phi, A1, lambda1, B1, A2, sigma2, dB, A_KT, Delta_KT] (MD_COLS).
+MD_USER_EXPR = ("p[m[3]]*se(t,p[m[4]])*tf(t,p[m[2]],p[m[5]])"
+                " + p[m[6]]*sg(t,p[m[7]])*tf(t,p[m[2]],p[m[5]]+p[m[8]])"
+                " + p[m[9]]*stg(t,p[m[10]])")
+
+
 def multi_detector_layout(
     n_hist: int = 16,
     n_bins=65536,
