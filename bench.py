@@ -396,14 +396,20 @@ def other_configs(rank):
             th.eval(run, thetas, MUSR_CHI2)
         us64 = 1e6 * (time.perf_counter() - t0) / 5
         t0 = time.perf_counter()
-        th.grad(run, theta, MUSR_CHI2, free=lay.free)
+        th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=1e-6)
         grad_ms = 1e3 * (time.perf_counter() - t0)
+        th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
+        t0 = time.perf_counter()
+        th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
+        fwd_ms = 1e3 * (time.perf_counter() - t0)
     th.close()
     res["user_theory_16x65536"] = {"compile_s": compile_s, "chi2_us_per_call": us,
                                    "chi2_bin_evals_per_s": lay.total_bins / (us * 1e-6),
                                    "chi2_64_vectors_us": us64,
                                    "chi2_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64 * 1e-6),
-                                   "fd_gradient_81_vectors_ms": grad_ms, "arithmetic": "fp64 (host call)"}
+                                   "fd_gradient_81_vectors_ms": grad_ms,
+                                   "forward_mode_gradient_40_directions_ms": fwd_ms,
+                                   "arithmetic": "fp64 (host call)"}
     return res
 
 

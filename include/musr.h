@@ -459,10 +459,14 @@ int musr_fit_learned_batch(musr_proposer prop, musr_gbatch batch, int obj, const
  *   musr_utheory_eval: values[v] (host) of obj for the n_vec host vectors
  *     thetas [n_vec x n_params] and funcs [n_vec x n_funcs] (NULL if
  *     n_funcs == 0); +inf where the deviance has no likelihood.
- *   musr_utheory_grad: value and central-difference gradient (free entries,
- *     step rel_h max(|theta_j|, 1), rel_h <= 0: 1e-6) from one launch.
- *   musr_utheory_fit: BFGS on those gradients (opts->method ignored; stops when
- *     the objective stalls at its resolution), results as musr_fit.
+ *   musr_utheory_grad: value and gradient over the free entries: rel_h > 0
+ *     central differences with step rel_h max(|theta_j|, 1) (one launch of
+ *     1 + 2 n_free vectors); rel_h <= 0 forward-mode derivatives of the
+ *     expression (dual numbers along each free parameter, one launch over
+ *     histogram tiles x free parameters), exact up to rounding.
+ *   musr_utheory_fit: BFGS on the forward-mode gradients, the start's Hessian
+ *     diagonal from central second differences (opts->method and fd_rel_h
+ *     set only that start's step); results as musr_fit.
  */
 typedef struct musr_utheory_s* musr_utheory;
 int musr_utheory_create(const char* expr, int32_t n_funcs, musr_utheory* out);

@@ -393,7 +393,8 @@ int musr_gbatch_create(const musr_run* runs, int32_t n_runs, int32_t with_gn, mu
         b->h_out = reinterpret_cast<double*>(h + o_out);
         b->h_active = reinterpret_cast<uint8_t*>(h + o_act);
         b->h_status = reinterpret_cast<int32_t*>(h + o_st);
-        st = cuda_status(cudaMemset(b->io, 0, sz));
+        st = cuda_status(cudaMemsetAsync(b->io, 0, sz, b->stream));
+        if (st == MUSR_OK) st = cuda_status(cudaStreamSynchronize(b->stream));
     }
     for (int m = kGrad; m <= top && st == MUSR_OK; ++m) st = b->make_plan(m, GShape{});
     if (cur != b->device) cudaSetDevice(cur);

@@ -598,7 +598,9 @@ int musr_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int
         m->arena = nullptr;
         st = MUSR_ENOMEM;
     }
+    // zeroed and finished before any stream of the network touches the arena
     if (st == MUSR_OK) st = cuda_status(cudaMemset(m->arena, 0, sz));
+    if (st == MUSR_OK) st = cuda_status(cudaDeviceSynchronize());
     if (st == MUSR_OK) st = cuda_status(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
     if (st != MUSR_OK) {
         musr_mlp_destroy(m);

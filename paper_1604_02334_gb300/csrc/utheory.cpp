@@ -31,6 +31,13 @@
 
 using musr::cuda_status;
 
+namespace musr {
+int uth_eval_host(musr_utheory th, musr_run run, int obj, const double* thetas, const double* funcs, int n_vec,
+                  double* values);
+int uth_tangent_host(musr_utheory th, musr_run run, int obj, const double* theta, const double* funcs,
+                     const std::vector<int>& dirs, double* grad_dirs);
+}  // namespace musr
+
 namespace {
 
 // NVRTC entry points, resolved once from the toolkit's shared library
@@ -107,22 +114,83 @@ struct UParams {
     double t0, dt, inv_tau;
     int map_width, P, F, K, tph, n_tiles, obj;
 };
-// predefined functions (Listing 2 of the paper, written from their definitions)
-__device__ __forceinline__ double se(double t, double lambda) { return exp(-lambda * t); }
-__device__ __forceinline__ double ge(double t, double lambda, double beta) {
-    const double x = lambda * t;
-    return x > 0.0 ? exp(-pow(x, beta)) : 1.0;
+// Forward-mode derivatives: a dual number carries a value and its derivative
+// along one parameter; the expression compiled with dual parameters gives
+// dN/dtheta_j exactly (up to rounding).
+struct D {
+    double v, d;
+    __device__ D() : v(0.0), d(0.0) {}
+    __device__ D(double a, double b) : v(a), d(b) {}
+};
+__device__ __forceinline__ double val(double x) { return x; }
+__device__ __forceinline__ double val(D x) { return x.v; }
+__device__ __forceinline__ D operator+(D a, D b) { return D(a.v + b.v, a.d + b.d); }
+__device__ __forceinline__ D operator+(D a, double b) { return D(a.v + b, a.d); }
+__device__ __forceinline__ D operator+(double a, D b) { return D(a + b.v, b.d); }
+__device__ __forceinline__ D operator-(D a, D b) { return D(a.v - b.v, a.d - b.d); }
+__device__ __forceinline__ D operator-(D a, double b) { return D(a.v - b, a.d); }
+__device__ __forceinline__ D operator-(double a, D b) { return D(a - b.v, -b.d); }
+__device__ __forceinline__ D operator-(D a) { return D(-a.v, -a.d); }
+__device__ __forceinline__ D operator+(D a) { return a; }
+__device__ __forceinline__ D operator*(D a, D b) { return D(a.v * b.v, a.d * b.v + a.v * b.d); }
+__device__ __forceinline__ D operator*(D a, double b) { return D(a.v * b, a.d * b); }
+__device__ __forceinline__ D operator*(double a, D b) { return D(a * b.v, a * b.d); }
+__device__ __forceinline__ D operator/(D a, D b) { return D(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+__device__ __forceinline__ D operator/(D a, double b) { return D(a.v / b, a.d / b); }
+__device__ __forceinline__ D operator/(double a, D b) { return D(a / b.v, -a * b.d / (b.v * b.v)); }
+__device__ __forceinline__ D exp(D a) { const double e = exp(a.v); return D(e, e * a.d); }
+__device__ __forceinline__ D log(D a) { return D(log(a.v), a.d / a.v); }
+__device__ __forceinline__ D sqrt(D a) { const double r = sqrt(a.v); return D(r, a.d / (2.0 * r)); }
+__device__ __forceinline__ D cos(D a) { return D(cos(a.v), -sin(a.v) * a.d); }
+__device__ __forceinline__ D sin(D a) { return D(sin(a.v), cos(a.v) * a.d); }
+__device__ __forceinline__ D tan(D a) { const double q = tan(a.v); return D(q, (1.0 + q * q) * a.d); }
+__device__ __forceinline__ D tanh(D a) { const double q = tanh(a.v); return D(q, (1.0 - q * q) * a.d); }
+__device__ __forceinline__ D cosh(D a) { return D(cosh(a.v), sinh(a.v) * a.d); }
+__device__ __forceinline__ D sinh(D a) { return D(sinh(a.v), cosh(a.v) * a.d); }
+__device__ __forceinline__ D atan(D a) { return D(atan(a.v), a.d / (1.0 + a.v * a.v)); }
+__device__ __forceinline__ D fabs(D a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ D pow(D a, double b) {
+    const double q = pow(a.v, b);
+    return D(q, a.v != 0.0 ? b * q / a.v * a.d : (b == 1.0 ? a.d : 0.0));
 }
-__device__ __forceinline__ double sg(double t, double sigma) { const double x = sigma * t; return exp(-0.5 * x * x); }
-__device__ __forceinline__ double stg(double t, double sigma) {
-    const double x2 = sigma * t * sigma * t;
+__device__ __forceinline__ D pow(D a, D b) {
+    const double q = pow(a.v, b.v);
+    return D(q, a.v > 0.0 ? q * (b.d * log(a.v) + b.v * a.d / a.v) : 0.0);
+}
+__device__ __forceinline__ D pow(double a, D b) { const double q = pow(a, b.v); return D(q, q * log(a) * b.d); }
+__device__ __forceinline__ D pow(D a, int b) { return pow(a, (double)b); }
+// predefined functions (Listing 2 of the paper, written from their definitions)
+template <class L> __device__ __forceinline__ auto se(double t, L lambda) { return exp(-(lambda * t)); }
+template <class L, class B> __device__ __forceinline__ auto ge(double t, L lambda, B beta) {
+    const auto x = lambda * t;
+    decltype(exp(-pow(x, beta))) one{};
+    one = one + 1.0;
+    return val(x) > 0.0 ? exp(-pow(x, beta)) : one;
+}
+template <class S> __device__ __forceinline__ auto sg(double t, S sigma) {
+    const auto x = sigma * t;
+    return exp(-0.5 * (x * x));
+}
+template <class S> __device__ __forceinline__ auto stg(double t, S sigma) {
+    const auto x2 = (sigma * t) * (sigma * t);
     return 1.0 / 3.0 + 2.0 / 3.0 * (1.0 - x2) * exp(-0.5 * x2);
 }
 // transverse field precession: cos(2 pi gamma_mu B t + phi), B in G, t in us, phi in rad
-__device__ __forceinline__ double tf(double t, double phi, double field) {
+template <class P, class B> __device__ __forceinline__ auto tf(double t, P phi, B field) {
     return cos(6.283185307179586476925 * 0.013554 * field * t + phi);
 }
-__device__ __forceinline__ double user_asymmetry(double t, const double* p, const int* m, const double* f) {
+// parameter access: plain values, or duals seeded along parameter `dir`
+struct PVal {
+    const double* p;
+    __device__ double operator[](int i) const { return p[i]; }
+};
+struct PTan {
+    const double* p;
+    int dir;
+    __device__ D operator[](int i) const { return D(p[i], i == dir ? 1.0 : 0.0); }
+};
+template <class PA>
+__device__ __forceinline__ auto user_asymmetry(double t, const PA& p, const int* m, const double* f) {
     return (
 )SRC";
     s += expr;
@@ -136,7 +204,7 @@ extern "C" __global__ void __launch_bounds__(256) musr_user_objective(const UPar
     const int k = tile / u.tph;
     const int start = (tile - k * u.tph) * 2048;
     const int M = u.hist_nbins[k];
-    const double* p = u.thetas + (size_t)v * u.P;
+    const PVal p{u.thetas + (size_t)v * u.P};
     const double* f = u.funcs ? u.funcs + (size_t)v * u.F : nullptr;
     const int* m = u.map + (size_t)k * u.map_width;
     const float* d = u.data + u.hist_off[k];
@@ -173,6 +241,39 @@ extern "C" __global__ void __launch_bounds__(256) musr_user_objective(const UPar
         if (bad_s) atomicOr(&u.flags[v], 1u);
     }
 }
+// d obj / d theta_j for the parameters dir_param[blockIdx.y] at one vector:
+// sum over bins of (d obj / d N) (d N / d theta_j), N by forward-mode duals
+extern "C" __global__ void __launch_bounds__(256) musr_user_tangent(const UParams u, const int* dir_param) {
+    __shared__ double red[8];
+    const int tile = blockIdx.x, dir = blockIdx.y;
+    const int k = tile / u.tph;
+    const int start = (tile - k * u.tph) * 2048;
+    const int M = u.hist_nbins[k];
+    const PTan p{u.thetas, dir_param[dir]};
+    const double* f = u.funcs;
+    const int* m = u.map + (size_t)k * u.map_width;
+    const float* d = u.data + u.hist_off[k];
+    const D n0 = p[m[0]], bkg = p[m[1]];
+    double acc = 0.0;
+    const int end = min(M, start + 2048);
+    for (int n = start + (int)threadIdx.x; n < end; n += blockDim.x) {
+        const double t = u.t0 + (double)n * u.dt;
+        const D N = n0 * exp(-t * u.inv_tau) * (1.0 + user_asymmetry(t, p, m, f)) + bkg;
+        const double dv = (double)d[n];
+        double w;
+        if (u.obj == 0) w = -2.0 * (dv - N.v) / fmax(dv, 1.0);
+        else w = dv > 0.0 ? 2.0 * (1.0 - dv / N.v) : 2.0;
+        acc += w * N.d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        u.partial[(size_t)dir * u.n_tiles + tile] = s;
+    }
+}
 // per vector, the tiles' partials in tile order
 extern "C" __global__ void musr_user_sum(const double* partial, int n_tiles, int n_vec, unsigned* flags,
                                          double* values) {
@@ -207,7 +308,7 @@ struct musr_utheory_s {
     int n_funcs = 0;
     int device = 0;
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t k_obj = nullptr, k_sum = nullptr;
+    cudaKernel_t k_obj = nullptr, k_sum = nullptr, k_tan = nullptr;
     // scratch (grown on demand)
     void* scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -263,7 +364,7 @@ int uth_launch(musr_utheory th, musr_run run, int obj, const double* thetas_dev,
 }
 
 int uth_reserve(musr_utheory th, musr_run run, int n_vec, size_t* o_theta, size_t* o_funcs, size_t* o_part,
-                size_t* o_flags, size_t* o_vals, size_t* total) {
+                size_t* o_flags, size_t* o_vals, size_t* total, size_t* o_dirs = nullptr) {
     int64_t max_bins = 1;
     for (int k = 0; k < run->K; ++k) max_bins = std::max<int64_t>(max_bins, run->n_bins[k]);
     const size_t n_tiles = (size_t)std::max(run->K, 1) * ((max_bins + kUTileBins - 1) / kUTileBins);
@@ -278,6 +379,8 @@ int uth_reserve(musr_utheory th, musr_run run, int n_vec, size_t* o_theta, size_
     o += al256(sizeof(unsigned) * (size_t)n_vec);
     *o_vals = o;
     o += al256(sizeof(double) * (size_t)n_vec);
+    if (o_dirs) *o_dirs = o;
+    o += al256(sizeof(int32_t) * (size_t)n_vec);
     *total = o;
     if (o > th->scratch_bytes) {
         if (th->scratch) cudaFree(th->scratch);
@@ -288,7 +391,8 @@ int uth_reserve(musr_utheory th, musr_run run, int n_vec, size_t* o_theta, size_
             return MUSR_ENOMEM;
         }
         th->scratch_bytes = o;
-        if (cudaMemset(th->scratch, 0, o) != cudaSuccess) return MUSR_ECUDA;
+        // zeroed on the handle's (non-blocking) stream, ahead of the launches that read the flags
+        if (cudaMemsetAsync(th->scratch, 0, o, th->stream) != cudaSuccess) return MUSR_ECUDA;
     }
     if (o > th->h_bytes) {
         if (th->h_pinned) cudaFreeHost(th->h_pinned);
@@ -325,6 +429,9 @@ int uth_eval_host(musr_utheory th, musr_run run, int obj, const double* thetas, 
     if (e == cudaSuccess && funcs && th->n_funcs > 0)
         e = cudaMemcpyAsync(d + of, h + of, sizeof(double) * (size_t)n_vec * th->n_funcs, cudaMemcpyHostToDevice,
                             th->stream);
+    // the scratch layout depends on n_vec: this call's flag slots may hold an
+    // earlier call's partial sums
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + ofl, 0, sizeof(unsigned) * (size_t)n_vec, th->stream);
     st = cuda_status(e);
     if (st == MUSR_OK)
         st = uth_launch(th, run, obj, reinterpret_cast<double*>(d + ot),
@@ -335,6 +442,75 @@ int uth_eval_host(musr_utheory th, musr_run run, int obj, const double* thetas, 
         st = cuda_status(cudaMemcpyAsync(h + ov, d + ov, sizeof(double) * n_vec, cudaMemcpyDeviceToHost, th->stream));
     if (st == MUSR_OK) st = cuda_status(cudaStreamSynchronize(th->stream));
     if (st == MUSR_OK) memcpy(values, h + ov, sizeof(double) * n_vec);
+    return st;
+}
+
+// d obj / d theta_j for the n_dirs parameter indices dirs[], by forward-mode
+// duals: one launch over (tile, direction) and the fixed-order tile sums.
+int uth_tangent_host(musr_utheory th, musr_run run, int obj, const double* theta, const double* funcs,
+                     const std::vector<int>& dirs, double* grad_dirs) {
+    const int nd = (int)dirs.size();
+    if (nd == 0) return MUSR_OK;
+    size_t ot, of, op, ofl, ov, od, total;
+    int st = uth_reserve(th, run, std::max(nd, 1), &ot, &of, &op, &ofl, &ov, &total, &od);
+    if (st != MUSR_OK) return st;
+    if (run->K == 0) {
+        for (int i = 0; i < nd; ++i) grad_dirs[i] = 0.0;
+        return MUSR_OK;
+    }
+    char* d = static_cast<char*>(th->scratch);
+    char* h = static_cast<char*>(th->h_pinned);
+    memcpy(h + ot, theta, sizeof(double) * run->P);
+    if (funcs && th->n_funcs > 0) memcpy(h + of, funcs, sizeof(double) * th->n_funcs);
+    memcpy(h + od, dirs.data(), sizeof(int32_t) * nd);
+    cudaError_t e = cudaStreamSynchronize(run->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d + ot, h + ot, sizeof(double) * run->P, cudaMemcpyHostToDevice, th->stream);
+    if (e == cudaSuccess && funcs && th->n_funcs > 0)
+        e = cudaMemcpyAsync(d + of, h + of, sizeof(double) * th->n_funcs, cudaMemcpyHostToDevice, th->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d + od, h + od, sizeof(int32_t) * nd, cudaMemcpyHostToDevice, th->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + ofl, 0, sizeof(unsigned) * nd, th->stream);
+    st = cuda_status(e);
+    if (st != MUSR_OK) return st;
+    int64_t max_bins = 1;
+    for (int k = 0; k < run->K; ++k) max_bins = std::max<int64_t>(max_bins, run->n_bins[k]);
+    UParamsHost u;
+    memset(&u, 0, sizeof(u));
+    u.data = run->d_data;
+    u.hist_off = reinterpret_cast<const long long*>(run->d_hist_off);
+    u.hist_nbins = run->d_hist_nbins;
+    u.map = run->d_map;
+    u.thetas = reinterpret_cast<double*>(d + ot);
+    u.funcs = (funcs && th->n_funcs > 0) ? reinterpret_cast<double*>(d + of) : nullptr;
+    u.partial = reinterpret_cast<double*>(d + op);
+    u.flags = reinterpret_cast<unsigned*>(d + ofl);
+    u.t0 = run->t0;
+    u.dt = run->dt;
+    u.inv_tau = 1.0 / run->tau;
+    u.map_width = run->W;
+    u.P = run->P;
+    u.F = th->n_funcs;
+    u.K = run->K;
+    u.tph = (int)((max_bins + kUTileBins - 1) / kUTileBins);
+    u.n_tiles = u.K * u.tph;
+    u.obj = obj;
+    const int* dirs_dev = reinterpret_cast<const int*>(d + od);
+    void* args[] = {&u, (void*)&dirs_dev};
+    e = cudaLaunchKernel((const void*)th->k_tan, dim3(u.n_tiles, nd), dim3(kUThreads), args, 0, th->stream);
+    if (e == cudaSuccess) {
+        double* part = u.partial;
+        int n_tiles = u.n_tiles, n_vec = nd;
+        unsigned* fl = u.flags;
+        double* vals = reinterpret_cast<double*>(d + ov);
+        void* args2[] = {&part, &n_tiles, &n_vec, &fl, &vals};
+        e = cudaLaunchKernel((const void*)th->k_sum, dim3((nd + 127) / 128), dim3(128), args2, 0, th->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + ov, d + ov, sizeof(double) * nd, cudaMemcpyDeviceToHost, th->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(th->stream);
+    st = cuda_status(e);
+    if (st == MUSR_OK) memcpy(grad_dirs, h + ov, sizeof(double) * nd);
     return st;
 }
 
@@ -373,6 +549,20 @@ int uth_fd(musr_utheory th, musr_run run, int obj, const double* theta, const do
         grad[fidx[a]] = (fp - fm) / (2.0 * h[a]);
         if (hd) hd[fidx[a]] = (fp - 2.0 * vals[0] + fm) / (h[a] * h[a]);
     }
+    return MUSR_OK;
+}
+
+// value and forward-mode gradient over the free entries (two launches)
+int uth_exact(musr_utheory th, musr_run run, int obj, const double* theta, const double* funcs,
+              const std::vector<int>& fidx, double* value, double* grad) {
+    int st = musr::uth_eval_host(th, run, obj, theta, funcs, 1, value);
+    if (st != MUSR_OK) return st;
+    if (!std::isfinite(*value)) return MUSR_EDOMAIN;
+    std::vector<double> gd(fidx.size());
+    st = musr::uth_tangent_host(th, run, obj, theta, funcs, fidx, gd.data());
+    if (st != MUSR_OK) return st;
+    memset(grad, 0, sizeof(double) * run->P);
+    for (size_t a = 0; a < fidx.size(); ++a) grad[fidx[a]] = gd[a];
     return MUSR_OK;
 }
 
@@ -438,6 +628,7 @@ int musr_utheory_create(const char* expr, int32_t n_funcs, musr_utheory* out) {
         st = cuda_status(cudaLibraryLoadData(&th->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0));
     if (st == MUSR_OK) st = cuda_status(cudaLibraryGetKernel(&th->k_obj, th->lib, "musr_user_objective"));
     if (st == MUSR_OK) st = cuda_status(cudaLibraryGetKernel(&th->k_sum, th->lib, "musr_user_sum"));
+    if (st == MUSR_OK) st = cuda_status(cudaLibraryGetKernel(&th->k_tan, th->lib, "musr_user_tangent"));
     if (st == MUSR_OK) st = cuda_status(cudaStreamCreateWithFlags(&th->stream, cudaStreamNonBlocking));
     if (st != MUSR_OK && st != MUSR_EINVAL) {
         delete th;
@@ -480,7 +671,8 @@ int musr_utheory_grad(musr_utheory th, musr_run run, int obj, const double* thet
     std::vector<int> fidx;
     for (int j = 0; j < run->P; ++j)
         if (!free_mask || free_mask[j]) fidx.push_back(j);
-    return uth_fd(th, run, obj, theta, funcs, fidx, rel_h > 0.0 ? rel_h : 1e-6, value, grad, nullptr);
+    if (rel_h > 0.0) return uth_fd(th, run, obj, theta, funcs, fidx, rel_h, value, grad, nullptr);
+    return uth_exact(th, run, obj, theta, funcs, fidx, value, grad);
 }
 
 int musr_utheory_fit(musr_utheory th, musr_run run, int obj, double* theta, const double* funcs,
@@ -500,7 +692,7 @@ int musr_utheory_fit(musr_utheory th, musr_run run, int obj, double* theta, cons
     int evals = 0;
     auto vg = [&](const double* th_, double* f, double* g) {
         ++evals;
-        return uth_fd(th, run, obj, th_, funcs, fidx, o.fd_rel_h, f, g, nullptr);
+        return uth_exact(th, run, obj, th_, funcs, fidx, f, g);
     };
     auto start = [&](const double* th_, double* f, double* g, double* hd) {
         ++evals;
@@ -509,7 +701,7 @@ int musr_utheory_fit(musr_utheory th, musr_run run, int obj, double* theta, cons
     musr_fit_result r = *out;
     r.n_free = (int32_t)fidx.size();
     r.ndf = (double)(run->total_bins - (int64_t)fidx.size());
-    const int st = fit_bfgs_generic(run->P, theta, fidx, o, true, vg, start, &r);
+    const int st = fit_bfgs_generic(run->P, theta, fidx, o, false, vg, start, &r);
     r.n_evals = evals;
     r.status = st;
     *out = r;

@@ -43,16 +43,22 @@ def test_user_objective_matches_oracle_and_builtin(md, obj):
     th.close()
 
 
-def test_user_gradient_matches_oracle_analytic(md):
+@pytest.mark.parametrize("obj", [MUSR_CHI2, MUSR_POISSON])
+def test_user_gradient_matches_oracle_analytic(md, obj):
+    # forward-mode (exact) and central-difference gradients of the user theory
+    # against the C oracle's analytic gradient of the same (built-in) model
     lay, theta, d, g = md
     th = UserTheory(W.MD_USER_EXPR)
     t1 = W.perturb(theta, lay.free, 0.01, g)
     with Run(lay, d) as run:
-        v, gr = th.grad(run, t1, MUSR_CHI2, free=lay.free, rel_h=1e-6)
-    vref, gref, _ = oracle.gradient(lay, d, t1, oracle.CHI2, with_gn=False)
+        v, gr = th.grad(run, t1, obj, free=lay.free, rel_h=0.0)
+        vf, gf = th.grad(run, t1, obj, free=lay.free, rel_h=1e-6)
+    vref, gref, _ = oracle.gradient(lay, d, t1, oracle.CHI2 if obj == MUSR_CHI2 else oracle.POISSON, with_gn=False)
     fr = lay.free.astype(bool)
-    assert rel_err(v, vref) <= 1e-10
-    assert grad_rel_err(gr[fr], gref[fr]) <= 1e-4
+    assert rel_err(v, vref) <= 1e-10 and rel_err(vf, vref) <= 1e-10
+    assert grad_rel_err(gr[fr], gref[fr]) <= 1e-9
+    assert not gr[~fr].any()
+    assert grad_rel_err(gf[fr], gref[fr]) <= 1e-4
     th.close()
 
 
@@ -68,6 +74,17 @@ def test_stretched_exponential_and_function_array():
             v = th.eval(run, theta, MUSR_POISSON, funcs=[beta])[0]
             ref = U.objective(lay, d, theta, expr, 1, funcs=[beta])
             assert rel_err(v, ref) <= 1e-10
+        # forward-mode gradient of the stretched exponential against central
+        # differences of the FP64 oracle (h = 1e-6 relative)
+        _, gr = th.grad(run, theta, MUSR_POISSON, funcs=[0.7], rel_h=0.0)
+    gfd = np.zeros_like(theta)
+    for j in range(theta.shape[0]):
+        h = 1e-6 * max(abs(theta[j]), 1.0)
+        tp, tm = theta.copy(), theta.copy()
+        tp[j] += h
+        tm[j] -= h
+        gfd[j] = (U.objective(lay, d, tp, expr, 1, funcs=[0.7]) - U.objective(lay, d, tm, expr, 1, funcs=[0.7])) / (2 * h)
+    assert grad_rel_err(gr, gfd) <= 1e-6
     th.close()
 
 
@@ -93,4 +110,19 @@ def test_user_fit_reaches_the_builtin_minimum():
         tb, ib, _ = run.fit(start, MUSR_CHI2, free=lay.free)
     assert iu["status"] == 0
     assert rel_err(iu["value"], ib["value"]) <= 1e-6
+    th.close()
+
+
+def test_calls_of_different_vector_counts(md):
+    # alternating batch sizes reuse the scratch with different layouts
+    lay, theta, d, g = md
+    th = UserTheory(W.MD_USER_EXPR)
+    with Run(lay, d) as run:
+        v1 = th.eval(run, theta, MUSR_CHI2)[0]
+        for n in (81, 1, 40, 3, 81, 1):
+            v = th.eval(run, np.repeat(theta[None, :], n, axis=0), MUSR_CHI2)
+            assert np.all(v == v1)
+        _, g0 = th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=1e-6)
+        v2, g1 = th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
+        assert v2 == v1
     th.close()
