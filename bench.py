@@ -488,16 +488,21 @@ def learned_start_ab(dev, rank, train_steps, n_runs=64):
     res = {}
     # batched arms: every run's learned start fitted in lockstep (fallback batched
     # too); every (run, start) pair of the plain grid fitted in lockstep
-    t0 = time.perf_counter()
-    _, il = prop.fit_batch(gb, MUSR_CHI2, free=[free] * n_runs, chi2ndf_max=1.2, fallback_starts=[starts] * n_runs)
-    t1 = time.perf_counter()
-    _, ip = fit_multistart_batch(runs, [starts] * n_runs, MUSR_CHI2, free=[free] * n_runs)
-    t2 = time.perf_counter()
-    for name, infos, dt in (("learned_batched", il, t1 - t0), ("plain_batched", ip, t2 - t1)):
+    from paper_1604_02334_gb300 import MUSR_FIT_BFGS, MUSR_FIT_LM
+    arms = []
+    for tag, method in (("", MUSR_FIT_LM), ("_bfgs", MUSR_FIT_BFGS)):
+        t0 = time.perf_counter()
+        _, il = prop.fit_batch(gb, MUSR_CHI2, free=[free] * n_runs, chi2ndf_max=1.2,
+                               fallback_starts=[starts] * n_runs, method=method)
+        t1 = time.perf_counter()
+        _, ip = fit_multistart_batch(runs, [starts] * n_runs, MUSR_CHI2, free=[free] * n_runs, method=method)
+        t2 = time.perf_counter()
+        arms += [("learned_batched" + tag, il, t1 - t0), ("plain_batched" + tag, ip, t2 - t1)]
+    for name, infos, dt in arms:
         ok = [abs(x["value"] - r) <= 1e-6 * r for x, r in zip(infos, ref)]
         res[name] = {"fits_per_s": n_runs / dt, "success": float(np.mean(ok)),
                      "mean_iters": float(np.mean([x["iters"] for x in infos])), "ms_per_fit": 1e3 * dt / n_runs}
-        if name == "learned_batched":
+        if name.startswith("learned"):
             res[name]["fallbacks"] = int(sum(x["fallback"] for x in infos))
     gb.close()
     for name in ("learned", "plain"):
@@ -525,7 +530,9 @@ def learned_start_ab(dev, rank, train_steps, n_runs=64):
             "train_s": t_train, "train_samples_per_s": train_steps * 512 / t_train,
             "final_loss": float(np.mean(losses[-100:])), **res,
             "speedup_fits_per_s": res["learned"]["fits_per_s"] / res["plain"]["fits_per_s"],
-            "speedup_fits_per_s_batched": res["learned_batched"]["fits_per_s"] / res["plain_batched"]["fits_per_s"]}
+            "speedup_fits_per_s_batched": res["learned_batched"]["fits_per_s"] / res["plain_batched"]["fits_per_s"],
+            "speedup_fits_per_s_batched_bfgs":
+                res["learned_batched_bfgs"]["fits_per_s"] / res["plain_batched_bfgs"]["fits_per_s"]}
 
 
 def run_ours(args):

@@ -319,10 +319,13 @@ int musr_gbatch_eval_device(musr_gbatch batch, int obj, int mode, const double* 
  * lockstep: one batched launch per iteration evaluates the trial points of
  * all unfinished runs; each run follows exactly musr_fit's LM rules and stops
  * on its own.  thetas: concatenated start vectors, replaced by the results;
- * free_masks: NULL (all free) or concatenated per-run masks; opts->method must
- * be MUSR_FIT_LM (MUSR_ENOTSUP otherwise); results: one per run (cov: caller
- * buffer n_free x n_free or NULL).  Returns MUSR_OK or the first run's
- * non-OK status. */
+ * free_masks: NULL (all free) or concatenated per-run masks; opts->method
+ * MUSR_FIT_LM (each run follows musr_fit's LM rules; the batch needs with_gn)
+ * or MUSR_FIT_BFGS (each run follows musr_fit's BFGS rules on the batched
+ * value + gradient, one launch per round of line-search trials, the start's
+ * Hessian diagonal from the GN matrix when the batch has it); others
+ * MUSR_ENOTSUP; results: one per run (cov: caller buffer n_free x n_free or
+ * NULL).  Returns MUSR_OK or the first run's non-OK status. */
 int musr_fit_batch(musr_gbatch batch, int obj, double* thetas, const uint8_t* free_masks, const musr_fit_opts* opts,
                    musr_fit_result* results);
 

@@ -335,7 +335,8 @@ def _fit_infos(res):
              "status": x.status} for x in res]
 
 
-def fit_multistart_batch(runs, starts, obj=MUSR_CHI2, free=None, max_iter=500, edm_tol=1e-8, mu0=1e-3):
+def fit_multistart_batch(runs, starts, obj=MUSR_CHI2, free=None, max_iter=500, edm_tol=1e-8, mu0=1e-3,
+                         method=MUSR_FIT_LM):
     """musr_fit_multistart_batch: starts[r] is an (n_starts, P_r) array per run.
     Returns (list of theta, list of info dicts)."""
     runs = list(runs)
@@ -346,7 +347,7 @@ def fit_multistart_batch(runs, starts, obj=MUSR_CHI2, free=None, max_iter=500, e
     if free is not None:
         fm = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.uint8).ravel() for f in free]))
     out = np.zeros(sum(r.P for r in runs))
-    o = _lib.musr_fit_opts(MUSR_FIT_LM, max_iter, edm_tol, mu0, 0.0)
+    o = _lib.musr_fit_opts(method, max_iter, edm_tol, mu0, 0.0)
     res = (_lib.musr_fit_result * len(runs))()
     handles = (ctypes.c_void_p * len(runs))(*[r.handle.value for r in runs])
     st = _lib.load().musr_fit_multistart_batch(handles, len(runs), int(obj), _dptr(flat), n_starts,
@@ -574,7 +575,7 @@ class Proposer:
         return th, info, cov
 
     def fit_batch(self, gbatch, obj=MUSR_CHI2, free=None, chi2ndf_max=1.2, fallback_starts=None, max_iter=500,
-                  edm_tol=1e-8, mu0=1e-3):
+                  edm_tol=1e-8, mu0=1e-3, method=MUSR_FIT_LM):
         """musr_fit_learned_batch over the runs of `gbatch` (a GBatch with GN):
         (list of theta, list of info dicts with "fallback")."""
         n = len(gbatch.runs)
@@ -587,7 +588,7 @@ class Proposer:
             fb = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64).reshape(n_fb, -1).ravel()
                                                       for x in fallback_starts]))
         out = np.zeros(int(gbatch.theta_off[-1]))
-        o = _lib.musr_fit_opts(MUSR_FIT_LM, max_iter, edm_tol, mu0, 0.0)
+        o = _lib.musr_fit_opts(method, max_iter, edm_tol, mu0, 0.0)
         res = (_lib.musr_fit_result * n)()
         used = np.zeros(n, dtype=np.int32)
         st = self._lib.musr_fit_learned_batch(self.handle, gbatch.handle, int(obj),
@@ -667,13 +668,13 @@ class GBatch:
                                                 ctypes.c_void_p(flags_dev.data_ptr()) if flags_dev is not None else None,
                                                 st), "musr_gbatch_eval_device")
 
-    def fit(self, thetas, obj=MUSR_CHI2, free=None, max_iter=500, edm_tol=1e-8, mu0=1e-3):
-        """Lockstep LM fits: (list of theta, list of info dicts)."""
+    def fit(self, thetas, obj=MUSR_CHI2, free=None, max_iter=500, edm_tol=1e-8, mu0=1e-3, method=MUSR_FIT_LM):
+        """Lockstep fits (LM, or BFGS with method=MUSR_FIT_BFGS): (list of theta, list of info dicts)."""
         flat = self._flat(thetas)
         fm = None
         if free is not None:
             fm = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.uint8).ravel() for f in free]))
-        o = _lib.musr_fit_opts(MUSR_FIT_LM, max_iter, edm_tol, mu0, 0.0)
+        o = _lib.musr_fit_opts(method, max_iter, edm_tol, mu0, 0.0)
         res = (_lib.musr_fit_result * len(self.runs))()
         st = self._lib.musr_fit_batch(self.handle, int(obj), _dptr(flat),
                                       fm.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if fm is not None else None,

@@ -245,123 +245,183 @@ int fit_lm(Evaluator& ev, double* theta, const std::vector<int>& fidx, const mus
 
 }  // namespace
 
-// BFGS over the free entries for any objective: value_grad(theta, f, g) gives
-// the value and gradient, start(theta, f, g, hd) also the Hessian diagonal hd
-// (zero where unknown), which preconditions the initial inverse-Hessian
-// estimate (the parameters' scales differ by 1e5).  fd: the gradient is a
-// central difference (its value noise rules out the EDM test; see below).
-int fit_bfgs_generic(int P, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o, bool fd,
-                     const std::function<int(const double*, double*, double*)>& value_grad,
-                     const std::function<int(const double*, double*, double*, double*)>& start,
-                     musr_fit_result* out) {
-    const double fd_h = fd ? 1.0 : 0.0;  // only its sign is used below
-    const int nf = (int)fidx.size();
-    std::vector<double> g(P), gn_(P), x(P), Hi((size_t)nf * nf, 0.0), d(nf), s(nf), y(nf);
-    double f;
-    std::vector<double> hd(P, 0.0);
-    int st = start(theta, &f, g.data(), hd.data());
-    if (st != MUSR_OK) return st;
-    double gnorm = 0.0;
-    for (int a = 0; a < nf; ++a) gnorm += g[fidx[a]] * g[fidx[a]];
-    gnorm = sqrt(gnorm);
-    std::vector<double> hi0(nf);
-    for (int a = 0; a < nf; ++a) {
-        const double h = hd[fidx[a]];
-        hi0[a] = (h > 0.0 && std::isfinite(h)) ? 1.0 / h : 1.0 / std::max(gnorm, 1.0);
-        Hi[(size_t)a * nf + a] = hi0[a];
+// One run's BFGS iteration as a state machine (like LmStepper), shared by a
+// single fit and many fits in lockstep: next() proposes the point at which the
+// value and gradient are needed next (a line-search trial), observe() takes
+// them.  The inverse-Hessian estimate starts from the diagonal preconditioner
+// 1 / H_jj when the start supplies the Hessian diagonal (the parameters'
+// scales differ by 1e5).  fd: the gradient is a central difference, whose
+// value noise rules out the EDM test (see observe()).
+struct BfgsStepper {
+    int P = 0, nf = 0;
+    std::vector<int> fidx;
+    musr_fit_opts o{};
+    bool fd = false;
+    std::vector<double> theta, g, gt, x, Hi, d, hi0;
+    double f = 0.0, edm = INFINITY, slope = 0.0, step = 1.0;
+    int it = 0, result = MUSR_ENOCONV, stall = 0, ls = 0;
+    bool done = false, in_ls = false;
+
+    void init(int P_, const std::vector<int>& fidx_, const musr_fit_opts& o_, const double* th, bool fd_) {
+        P = P_;
+        fidx = fidx_;
+        nf = (int)fidx.size();
+        o = o_;
+        fd = fd_;
+        theta.assign(th, th + P);
+        g.assign(P, 0.0);
+        gt.assign(P, 0.0);
+        x.assign(P, 0.0);
+        Hi.assign((size_t)nf * nf, 0.0);
+        d.assign(nf, 0.0);
+        hi0.assign(nf, 0.0);
     }
-    int it = 0, result = MUSR_ENOCONV, stall = 0;
-    double edm = INFINITY;
-    while (it < o.max_iter) {
-        ++it;
+    // after the start evaluation (value f0, gradient in g); hd: Hessian diagonal or null
+    void start(double f0, const double* hd) {
+        f = f0;
+        double gnorm = 0.0;
+        for (int a = 0; a < nf; ++a) gnorm += g[fidx[a]] * g[fidx[a]];
+        gnorm = sqrt(gnorm);
         for (int a = 0; a < nf; ++a) {
-            double v = 0.0;
-            for (int c = 0; c < nf; ++c) v -= Hi[(size_t)a * nf + c] * g[fidx[c]];
-            d[a] = v;
+            const double h = hd ? hd[fidx[a]] : 0.0;
+            hi0[a] = (h > 0.0 && std::isfinite(h)) ? 1.0 / h : 1.0 / std::max(gnorm, 1.0);
+            Hi[(size_t)a * nf + a] = hi0[a];
         }
-        double slope = 0.0;
-        for (int a = 0; a < nf; ++a) slope += g[fidx[a]] * d[a];
-        edm = -0.5 * slope;
-        if (edm < o.edm_tol) {
-            result = MUSR_OK;
-            break;
-        }
-        if (slope >= 0.0) {  // not a descent direction: reset to the preconditioner
-            for (int a = 0; a < nf; ++a)
-                for (int c = 0; c < nf; ++c) Hi[(size_t)a * nf + c] = a == c ? hi0[a] : 0.0;
-            continue;
-        }
-        double step = 1.0, fn = INFINITY;
-        bool ok = false;
-        for (int ls = 0; ls < 40; ++ls) {
-            memcpy(x.data(), theta, sizeof(double) * P);
-            for (int a = 0; a < nf; ++a) x[fidx[a]] += step * d[a];
-            st = value_grad(x.data(), &fn, gn_.data());
-            if (st != MUSR_OK && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
-            if (st == MUSR_OK && fn <= f + 1e-4 * step * slope) {
-                ok = true;
+    }
+    void set_trial() {
+        memcpy(x.data(), theta.data(), sizeof(double) * P);
+        for (int a = 0; a < nf; ++a) x[fidx[a]] += step * d[a];
+    }
+    // true: evaluate value and gradient at x (into gt) and call observe()
+    bool next() {
+        while (!done) {
+            if (in_ls) return true;
+            if (it >= o.max_iter) {
+                done = true;
                 break;
             }
-            if (st == MUSR_OK && -step * slope < kValueNoise * fabs(f) &&
-                fn - f < kValueNoise * fabs(f)) {
-                // below the value resolution: accept if the gradient shrinks in the Hi metric
-                double e_new = 0.0;
-                for (int a = 0; a < nf; ++a) {
-                    double v = 0.0;
-                    for (int c = 0; c < nf; ++c) v += Hi[(size_t)a * nf + c] * gn_[fidx[c]];
-                    e_new += 0.5 * gn_[fidx[a]] * v;
-                }
-                if (e_new < edm) {
-                    ok = true;
-                    break;
-                }
+            ++it;
+            for (int a = 0; a < nf; ++a) {
+                double v = 0.0;
+                for (int c = 0; c < nf; ++c) v -= Hi[(size_t)a * nf + c] * g[fidx[c]];
+                d[a] = v;
             }
-            step *= 0.5;
+            slope = 0.0;
+            for (int a = 0; a < nf; ++a) slope += g[fidx[a]] * d[a];
+            edm = -0.5 * slope;
+            if (edm < o.edm_tol) {
+                result = MUSR_OK;
+                done = true;
+                break;
+            }
+            if (slope >= 0.0) {  // not a descent direction: reset to the preconditioner
+                for (int a = 0; a < nf; ++a)
+                    for (int c = 0; c < nf; ++c) Hi[(size_t)a * nf + c] = a == c ? hi0[a] : 0.0;
+                continue;
+            }
+            step = 1.0;
+            ls = 0;
+            set_trial();
+            in_ls = true;
+            return true;
         }
-        if (!ok) break;
+        return false;
+    }
+    // st: MUSR_OK, MUSR_EDOMAIN or MUSR_ENONFINITE (other errors end the fit upstream)
+    void observe(int st, double fn) {
+        bool ok = st == MUSR_OK && fn <= f + 1e-4 * step * slope;
+        if (!ok && st == MUSR_OK && -step * slope < kValueNoise * fabs(f) && fn - f < kValueNoise * fabs(f)) {
+            // below the value resolution: accept if the gradient shrinks in the Hi metric
+            double e_new = 0.0;
+            for (int a = 0; a < nf; ++a) {
+                double v = 0.0;
+                for (int c = 0; c < nf; ++c) v += Hi[(size_t)a * nf + c] * gt[fidx[c]];
+                e_new += 0.5 * gt[fidx[a]] * v;
+            }
+            ok = e_new < edm;
+        }
+        if (!ok) {
+            step *= 0.5;
+            if (++ls >= 40) {  // no acceptable step along d
+                done = true;
+                in_ls = false;
+                return;
+            }
+            set_trial();
+            return;
+        }
+        in_ls = false;
         const double rel = (f - fn) / std::max(fabs(f), 1e-300);
+        std::vector<double> sv(nf), yv(nf);
         double sy = 0.0;
         for (int a = 0; a < nf; ++a) {
-            s[a] = step * d[a];
-            y[a] = gn_[fidx[a]] - g[fidx[a]];
-            sy += s[a] * y[a];
+            sv[a] = step * d[a];
+            yv[a] = gt[fidx[a]] - g[fidx[a]];
+            sy += sv[a] * yv[a];
         }
-        memcpy(theta, x.data(), sizeof(double) * P);
+        theta.swap(x);
         f = fn;
-        g.swap(gn_);
+        g.swap(gt);
         if (sy > 1e-300) {
             // Hi <- (I - rho s y^T) Hi (I - rho y s^T) + rho s s^T
             const double rho = 1.0 / sy;
             std::vector<double> Hy(nf, 0.0);
             for (int a = 0; a < nf; ++a)
-                for (int c = 0; c < nf; ++c) Hy[a] += Hi[(size_t)a * nf + c] * y[c];
+                for (int c = 0; c < nf; ++c) Hy[a] += Hi[(size_t)a * nf + c] * yv[c];
             double yHy = 0.0;
-            for (int a = 0; a < nf; ++a) yHy += y[a] * Hy[a];
+            for (int a = 0; a < nf; ++a) yHy += yv[a] * Hy[a];
             for (int a = 0; a < nf; ++a)
                 for (int c = 0; c < nf; ++c)
-                    Hi[(size_t)a * nf + c] += (1.0 + rho * yHy) * rho * s[a] * s[c] -
-                                              rho * (Hy[a] * s[c] + s[a] * Hy[c]);
+                    Hi[(size_t)a * nf + c] += (1.0 + rho * yHy) * rho * sv[a] * sv[c] -
+                                              rho * (Hy[a] * sv[c] + sv[a] * Hy[c]);
         }
         if (rel >= 0.0 && rel < 1e-15 && it > 1) {
             result = MUSR_OK;
-            break;
+            done = true;
+            return;
         }
         // central differences carry the FP32 value noise into the gradient, so
         // the EDM test cannot pass; that fit stops once three successive steps
         // gain less than 1e-8 relative (the objective has stalled at its noise)
         stall = rel < 1e-8 ? stall + 1 : 0;
-        if (fd_h > 0.0 && stall >= 3) {
+        if (fd && stall >= 3) {
             result = MUSR_OK;
-            break;
+            done = true;
         }
     }
-    out->value = f;
-    out->edm = edm;
-    out->mu = 0.0;
-    out->iters = it;
-    if (out->cov)
-        for (size_t e = 0; e < (size_t)nf * nf; ++e) out->cov[e] = 2.0 * Hi[e];
-    return result;
+    void finish(double* theta_out, musr_fit_result* out) const {
+        memcpy(theta_out, theta.data(), sizeof(double) * P);
+        out->value = f;
+        out->edm = edm;
+        out->mu = 0.0;
+        out->iters = it;
+        if (out->cov)
+            for (size_t e = 0; e < (size_t)nf * nf; ++e) out->cov[e] = 2.0 * Hi[e];
+    }
+};
+
+// BFGS over the free entries for any objective: value_grad(theta, f, g) gives
+// the value and gradient, start(theta, f, g, hd) also the Hessian diagonal hd
+// (zero where unknown).
+int fit_bfgs_generic(int P, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o, bool fd,
+                     const std::function<int(const double*, double*, double*)>& value_grad,
+                     const std::function<int(const double*, double*, double*, double*)>& start,
+                     musr_fit_result* out) {
+    BfgsStepper b;
+    b.init(P, fidx, o, theta, fd);
+    std::vector<double> hd(P, 0.0);
+    double f;
+    int st = start(theta, &f, b.g.data(), hd.data());
+    if (st != MUSR_OK) return st;
+    b.start(f, hd.data());
+    while (b.next()) {
+        double fn;
+        st = value_grad(b.x.data(), &fn, b.gt.data());
+        if (st != MUSR_OK && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
+        b.observe(st, fn);
+    }
+    b.finish(theta, out);
+    return b.result;
 }
 
 namespace {
@@ -480,18 +540,108 @@ extern "C" int musr_fit_multistart(musr_run run, int obj, const double* starts, 
     return best.status;
 }
 
+// BFGS fits of every run of a batch in lockstep: the start evaluation gives
+// the Hessian diagonal (Gauss-Newton mode when the batch has it), then one
+// batched value + gradient launch per round of line-search trials.
+static int fit_batch_bfgs(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks,
+                          const musr_fit_opts& o, musr_fit_result* results) {
+    const int n = gbatch_n_runs(b);
+    std::vector<BfgsStepper> bf(n);
+    std::vector<int32_t> flags(n, 0), evals(n, 1);
+    std::vector<uint8_t> active(n, 1);
+    std::vector<int> status(n, MUSR_OK);
+    int64_t total_theta = 0;
+    for (int r = 0; r < n; ++r) total_theta += gbatch_run(b, r)->P;
+    for (int64_t i = 0; i < total_theta; ++i)
+        if (!std::isfinite(thetas[i])) return MUSR_ENONFINITE;
+    std::vector<double> work(thetas, thetas + total_theta);
+    for (int r = 0; r < n; ++r) {
+        const musr_run run = gbatch_run(b, r);
+        const int64_t to = gbatch_theta_offset(b, r);
+        std::vector<int> fidx;
+        for (int j = 0; j < run->P; ++j)
+            if (!free_masks || free_masks[to + j]) fidx.push_back(j);
+        bf[r].init(run->P, fidx, o, thetas + to, false);
+    }
+    const int start_mode = gbatch_has_gn(b) ? kGN : kGrad;
+    int st = gbatch_eval_host(b, obj, start_mode, work.data(), nullptr, nullptr, flags.data());
+    if (st != MUSR_OK) return st;
+#pragma omp parallel for schedule(dynamic, 1) if (n >= 8)
+    for (int r = 0; r < n; ++r) {
+        const musr_run run = gbatch_run(b, r);
+        const int P = run->P;
+        const double* src = gbatch_host_out(b) + gbatch_out_offset(b, start_mode, r);
+        if ((flags[r] & 1) || !std::isfinite(src[0])) {
+            status[r] = (flags[r] & 1) ? MUSR_EDOMAIN : MUSR_ENONFINITE;
+            bf[r].done = true;
+            continue;
+        }
+        memcpy(bf[r].g.data(), src + 1, sizeof(double) * P);
+        std::vector<double> hd(P, 0.0);
+        if (start_mode == kGN)
+            for (int j = 0; j < P; ++j) hd[j] = src[1 + P + (size_t)j * P + j];
+        bf[r].start(src[0], hd.data());
+    }
+    for (;;) {
+#pragma omp parallel for schedule(dynamic, 1) if (n >= 8)
+        for (int r = 0; r < n; ++r) {
+            active[r] = (status[r] == MUSR_OK && bf[r].next()) ? 1 : 0;
+            if (active[r]) {
+                memcpy(work.data() + gbatch_theta_offset(b, r), bf[r].x.data(), sizeof(double) * bf[r].P);
+                ++evals[r];
+            }
+        }
+        int n_active = 0;
+        for (int r = 0; r < n; ++r) n_active += active[r];
+        if (n_active == 0) break;
+        st = gbatch_eval_host(b, obj, kGrad, work.data(), active.data(), nullptr, flags.data());
+        if (st != MUSR_OK) return st;
+#pragma omp parallel for schedule(dynamic, 1) if (n_active >= 8)
+        for (int r = 0; r < n; ++r) {
+            if (!active[r]) continue;
+            const int P = bf[r].P;
+            const double* src = gbatch_host_out(b) + gbatch_out_offset(b, kGrad, r);
+            const double fn = (flags[r] & 1) ? INFINITY : src[0];
+            memcpy(bf[r].gt.data(), src + 1, sizeof(double) * P);
+            const int s2 = (flags[r] & 1) ? MUSR_EDOMAIN : (std::isfinite(fn) ? MUSR_OK : MUSR_ENONFINITE);
+            bf[r].observe(s2, fn);
+        }
+    }
+    int worst = MUSR_OK;
+    for (int r = 0; r < n; ++r) {
+        const musr_run run = gbatch_run(b, r);
+        musr_fit_result& res = results[r];
+        double* cov = res.cov;
+        memset(&res, 0, sizeof(res));
+        res.cov = cov;
+        res.n_free = bf[r].nf;
+        res.ndf = (double)(run->total_bins - (int64_t)bf[r].nf);
+        if (status[r] == MUSR_OK) {
+            bf[r].finish(thetas + gbatch_theta_offset(b, r), &res);
+            res.status = bf[r].result;
+        } else {
+            res.value = INFINITY;
+            res.status = status[r];
+        }
+        res.n_evals = evals[r];
+        if (res.status != MUSR_OK && worst == MUSR_OK) worst = res.status;
+    }
+    return worst;
+}
+
 extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks,
                               const musr_fit_opts* opts, musr_fit_result* results) {
     if (!b || !thetas || !results) return MUSR_EINVAL;
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
-    if (!gbatch_has_gn(b)) return MUSR_EINVAL;
     musr_fit_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;
     if (o.max_iter <= 0) o.max_iter = 500;
     if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
     if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
+    if (o.method == MUSR_FIT_BFGS) return fit_batch_bfgs(b, obj, thetas, free_masks, o, results);
     if (o.method != MUSR_FIT_LM) return MUSR_ENOTSUP;
+    if (!gbatch_has_gn(b)) return MUSR_EINVAL;
     const int n = gbatch_n_runs(b);
     std::vector<LmStepper> lm(n);
     std::vector<int32_t> flags(n, 0), evals(n, 1);

@@ -18,9 +18,10 @@ constexpr int kMaxWarps = kMaxThreads / 32;
 constexpr int kInlineParams = 256;                 // theta passed inside the launch parameters
 constexpr int kInlineRoleHist = 32;                // role-map rows passed inside the launch parameters
 
-// Per-histogram constants of the theory, staged once per evaluation (the
-// paper's kernel keeps the parameter / map values in shared memory for the
-// same reason, Sec. 4.2.2: every thread reads them many times).
+// Per-histogram constants of the theory, staged into shared memory by every
+// block for its histogram at the start of an evaluation (the paper's kernel
+// keeps the parameter / map values in shared memory for the same reason,
+// Sec. 4.2.2: every thread reads them many times).
 struct OscConst {
     // q: per-bin expm1 step of an exponential envelope; for a Gaussian
     // envelope expm1 of the per-bin change of its step ratio, 2^(-2 b) - 1

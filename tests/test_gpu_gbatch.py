@@ -148,3 +148,24 @@ def test_gbatch_rejects_a_run_without_histograms():
     with pytest.raises(MusrError):
         GBatch([r])
     r.close()
+
+
+def test_fit_batch_bfgs_reaches_the_lm_minimum(runs):
+    from paper_1604_02334_gb300 import MUSR_FIT_BFGS
+    sel = [1, 2]
+    gruns = [Run(runs[i][0], runs[i][1]) for i in sel]
+    starts = [runs[i][2] for i in sel]
+    free = [runs[i][0].free for i in sel]
+    with GBatch(gruns) as b:
+        _, lm = b.fit(starts, MUSR_CHI2, free=free)
+        _, bf = b.fit(starts, MUSR_CHI2, free=free, method=MUSR_FIT_BFGS)
+    with GBatch(gruns, with_gn=False) as b2:
+        _, bf2 = b2.fit(starts, MUSR_CHI2, free=free, method=MUSR_FIT_BFGS)
+    for e in range(len(sel)):
+        _, single, _ = gruns[e].fit(starts[e], MUSR_CHI2, free=free[e], method=MUSR_FIT_BFGS)
+        assert bf[e]["status"] == 0 and bf2[e]["status"] in (0, -7)
+        assert rel_err(bf[e]["value"], lm[e]["value"]) <= 1e-6
+        assert rel_err(bf2[e]["value"], lm[e]["value"]) <= 1e-6
+        assert rel_err(bf[e]["value"], single["value"]) <= 1e-6
+    for r in gruns:
+        r.close()
