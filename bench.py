@@ -403,6 +403,21 @@ def other_configs(rank):
         th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
         fwd_ms = 1e3 * (time.perf_counter() - t0)
     th.close()
+    th32 = UserTheory(W.MD_USER_EXPR, fp32=True)
+    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+        th32.eval(run, thetas, MUSR_CHI2)
+        t0 = time.perf_counter()
+        for _ in range(5):
+            th32.eval(run, thetas, MUSR_CHI2)
+        us64_32 = 1e6 * (time.perf_counter() - t0) / 5
+        th32.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
+        t0 = time.perf_counter()
+        th32.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
+        fwd32_ms = 1e3 * (time.perf_counter() - t0)
+    th32.close()
+    res["user_theory_16x65536_fp32"] = {"chi2_64_vectors_us": us64_32,
+                                        "chi2_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64_32 * 1e-6),
+                                        "forward_mode_gradient_40_directions_ms": fwd32_ms}
     res["user_theory_16x65536"] = {"compile_s": compile_s, "chi2_us_per_call": us,
                                    "chi2_bin_evals_per_s": lay.total_bins / (us * 1e-6),
                                    "chi2_64_vectors_us": us64,

@@ -439,9 +439,18 @@ int musr_fit_learned_batch(musr_proposer prop, musr_gbatch batch, int obj, const
 /*
  * User-defined theory functions (Sec. 4.2.1): the asymmetry A_k(t) of Eq. 1 as
  * a C expression, compiled at run time with NVRTC (loaded from the CUDA
- * toolkit; MUSR_ENOTSUP if it is missing) into a kernel that evaluates, in
- * FP64, N_k(t) = p[m[0]] e^{-t/tau} (1 + A_k(t)) + p[m[1]] and the Eq. 3 / Eq. 4
+ * toolkit; MUSR_ENOTSUP if it is missing) into a kernel that evaluates
+ * N_k(t) = p[m[0]] e^{-t/tau} (1 + A_k(t)) + p[m[1]] and the Eq. 3 / Eq. 4
  * objective for many parameter vectors in one launch.
+ *   dtype    MUSR_F64: everything in FP64 (as the paper's kernels);
+ *            MUSR_F32: the expression, model and objective in FP32 (floating
+ *            literals of the expression are taken as float), per-thread
+ *            partial sums of at most 8 bins, FP64 beyond; tf() keeps its phase
+ *            in FP64 from the exact time, so precession phases should be formed
+ *            with tf (a phase written out in the expression is FP32).
+ *            Relative accuracy of the objective ~1e-6 (FP32) / ~1e-12 (FP64).
+ * An index outside p (n_params), m (map_width) or f (n_funcs) makes the
+ * value +inf (the gradient MUSR_ENONFINITE) instead of reading out of bounds.
  *   expr     an expression (no statements) over: t (us, double); p (the
  *            parameter vector, double[]); m (the histogram's map row of the run
  *            descriptor, int[]: m[0] N0, m[1] background, the rest free for the
@@ -472,7 +481,7 @@ int musr_fit_learned_batch(musr_proposer prop, musr_gbatch batch, int obj, const
  *     set only that start's step); results as musr_fit.
  */
 typedef struct musr_utheory_s* musr_utheory;
-int musr_utheory_create(const char* expr, int32_t n_funcs, musr_utheory* out);
+int musr_utheory_create(const char* expr, int32_t n_funcs, int32_t dtype, musr_utheory* out);
 int musr_utheory_destroy(musr_utheory th);
 const char* musr_utheory_log(musr_utheory th);
 int musr_utheory_eval(musr_utheory th, musr_run run, int obj, const double* thetas, const double* funcs,

@@ -708,11 +708,13 @@ class UserTheory:
     """A user-defined asymmetry A_k(t) compiled at run time (musr_utheory_*):
     expr is a C expression over t, p, m and f (see include/musr.h)."""
 
-    def __init__(self, expr, n_funcs=0):
+    def __init__(self, expr, n_funcs=0, fp32=False):
         self._lib = _lib.load()
         self.n_funcs = int(n_funcs)
+        self.fp32 = bool(fp32)
         self.handle = ctypes.c_void_p()
-        st = self._lib.musr_utheory_create(expr.encode(), self.n_funcs, ctypes.byref(self.handle))
+        st = self._lib.musr_utheory_create(expr.encode(), self.n_funcs, MUSR_F32 if fp32 else MUSR_F64,
+                                           ctypes.byref(self.handle))
         if st != 0:
             log = self._lib.musr_utheory_log(None)
             raise MusrError(st, "musr_utheory_create" + (": " + log.decode(errors="replace") if log else ""))

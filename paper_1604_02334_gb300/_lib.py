@@ -164,7 +164,7 @@ SIGNATURES = {
     "musr_mlp_adam": (ctypes.c_int, [_vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp]),
     "musr_mlp_train_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int32, ctypes.c_float,
                                            ctypes.POINTER(ctypes.c_float), _vp]),
-    "musr_utheory_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, ctypes.POINTER(_vp)]),
+    "musr_utheory_create": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_vp)]),
     "musr_utheory_destroy": (ctypes.c_int, [_vp]),
     "musr_utheory_log": (ctypes.c_char_p, [_vp]),
     "musr_utheory_eval": (ctypes.c_int, [_vp, _run, ctypes.c_int, _dp, _dp, ctypes.c_int32, _dp]),

@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cctype>
 #include <cmath>
 #include <functional>
 #include <mutex>
@@ -99,9 +100,49 @@ bool expression_ok(const char* e) {
     return depth_p == 0 && depth_b == 0;
 }
 
-// the kernel source around the user's expression
-std::string kernel_source(const std::string& expr) {
-    std::string s = R"SRC(
+// Floating literals of an FP32 expression get an f suffix, so that C's usual
+// conversions keep its arithmetic in FP32 (integer literals stay int).
+std::string to_fp32_literals(const std::string& e) {
+    std::string out;
+    size_t i = 0;
+    while (i < e.size()) {
+        const char c = e[i];
+        const bool ident_before = i > 0 && (isalnum((unsigned char)e[i - 1]) || e[i - 1] == '_');
+        if ((isdigit((unsigned char)c) || (c == '.' && i + 1 < e.size() && isdigit((unsigned char)e[i + 1]))) &&
+            !ident_before) {
+            size_t j = i;
+            bool is_float = false;
+            while (j < e.size() && (isdigit((unsigned char)e[j]) || e[j] == '.')) {
+                if (e[j] == '.') is_float = true;
+                ++j;
+            }
+            if (j < e.size() && (e[j] == 'e' || e[j] == 'E')) {
+                size_t k = j + 1;
+                if (k < e.size() && (e[k] == '+' || e[k] == '-')) ++k;
+                if (k < e.size() && isdigit((unsigned char)e[k])) {
+                    is_float = true;
+                    j = k;
+                    while (j < e.size() && isdigit((unsigned char)e[j])) ++j;
+                }
+            }
+            out.append(e, i, j - i);
+            if (is_float && !(j < e.size() && (e[j] == 'f' || e[j] == 'F'))) out.push_back('f');
+            i = j;
+        } else {
+            out.push_back(c);
+            ++i;
+        }
+    }
+    return out;
+}
+
+// the kernel source around the user's expression; fp32: expression, model and
+// objective in FP32 (per-thread partial sums, FP64 across threads), the
+// precession phase of tf() in FP64 from the exact time
+std::string kernel_source(const std::string& expr_in, bool fp32) {
+    const std::string expr = fp32 ? to_fp32_literals(expr_in) : expr_in;
+    std::string s = fp32 ? "typedef float real;\n#define MUSR_FP32 1\n" : "typedef double real;\n#define MUSR_FP32 0\n";
+    s += R"SRC(
 struct UParams {
     const float* data;
     const long long* hist_off;
@@ -118,84 +159,186 @@ struct UParams {
 // along one parameter; the expression compiled with dual parameters gives
 // dN/dtheta_j exactly (up to rounding).
 struct D {
-    double v, d;
-    __device__ D() : v(0.0), d(0.0) {}
-    __device__ D(double a, double b) : v(a), d(b) {}
+    real v, d;
+    __device__ D() : v(0), d(0) {}
+    __device__ D(real a, real b) : v(a), d(b) {}
 };
-__device__ __forceinline__ double val(double x) { return x; }
-__device__ __forceinline__ double val(D x) { return x.v; }
+__device__ __forceinline__ real val(real x) { return x; }
+__device__ __forceinline__ real val(D x) { return x.v; }
 __device__ __forceinline__ D operator+(D a, D b) { return D(a.v + b.v, a.d + b.d); }
-__device__ __forceinline__ D operator+(D a, double b) { return D(a.v + b, a.d); }
-__device__ __forceinline__ D operator+(double a, D b) { return D(a + b.v, b.d); }
+__device__ __forceinline__ D operator+(D a, real b) { return D(a.v + b, a.d); }
+__device__ __forceinline__ D operator+(real a, D b) { return D(a + b.v, b.d); }
 __device__ __forceinline__ D operator-(D a, D b) { return D(a.v - b.v, a.d - b.d); }
-__device__ __forceinline__ D operator-(D a, double b) { return D(a.v - b, a.d); }
-__device__ __forceinline__ D operator-(double a, D b) { return D(a - b.v, -b.d); }
+__device__ __forceinline__ D operator-(D a, real b) { return D(a.v - b, a.d); }
+__device__ __forceinline__ D operator-(real a, D b) { return D(a - b.v, -b.d); }
 __device__ __forceinline__ D operator-(D a) { return D(-a.v, -a.d); }
 __device__ __forceinline__ D operator+(D a) { return a; }
 __device__ __forceinline__ D operator*(D a, D b) { return D(a.v * b.v, a.d * b.v + a.v * b.d); }
-__device__ __forceinline__ D operator*(D a, double b) { return D(a.v * b, a.d * b); }
-__device__ __forceinline__ D operator*(double a, D b) { return D(a * b.v, a * b.d); }
+__device__ __forceinline__ D operator*(D a, real b) { return D(a.v * b, a.d * b); }
+__device__ __forceinline__ D operator*(real a, D b) { return D(a * b.v, a * b.d); }
 __device__ __forceinline__ D operator/(D a, D b) { return D(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
-__device__ __forceinline__ D operator/(D a, double b) { return D(a.v / b, a.d / b); }
-__device__ __forceinline__ D operator/(double a, D b) { return D(a / b.v, -a * b.d / (b.v * b.v)); }
-__device__ __forceinline__ D exp(D a) { const double e = exp(a.v); return D(e, e * a.d); }
+__device__ __forceinline__ D operator/(D a, real b) { return D(a.v / b, a.d / b); }
+__device__ __forceinline__ D operator/(real a, D b) { return D(a / b.v, -a * b.d / (b.v * b.v)); }
+__device__ __forceinline__ D operator+(D a, int b) { return a + (real)b; }
+__device__ __forceinline__ D operator+(int a, D b) { return (real)a + b; }
+__device__ __forceinline__ D operator-(D a, int b) { return a - (real)b; }
+__device__ __forceinline__ D operator-(int a, D b) { return (real)a - b; }
+__device__ __forceinline__ D operator*(D a, int b) { return a * (real)b; }
+__device__ __forceinline__ D operator*(int a, D b) { return (real)a * b; }
+__device__ __forceinline__ D operator/(D a, int b) { return a / (real)b; }
+__device__ __forceinline__ D operator/(int a, D b) { return (real)a / b; }
+__device__ __forceinline__ D exp(D a) { const real e = exp(a.v); return D(e, e * a.d); }
 __device__ __forceinline__ D log(D a) { return D(log(a.v), a.d / a.v); }
-__device__ __forceinline__ D sqrt(D a) { const double r = sqrt(a.v); return D(r, a.d / (2.0 * r)); }
+__device__ __forceinline__ D sqrt(D a) { const real r = sqrt(a.v); return D(r, a.d / (2 * r)); }
 __device__ __forceinline__ D cos(D a) { return D(cos(a.v), -sin(a.v) * a.d); }
 __device__ __forceinline__ D sin(D a) { return D(sin(a.v), cos(a.v) * a.d); }
-__device__ __forceinline__ D tan(D a) { const double q = tan(a.v); return D(q, (1.0 + q * q) * a.d); }
-__device__ __forceinline__ D tanh(D a) { const double q = tanh(a.v); return D(q, (1.0 - q * q) * a.d); }
+__device__ __forceinline__ D tan(D a) { const real q = tan(a.v); return D(q, (1 + q * q) * a.d); }
+__device__ __forceinline__ D tanh(D a) { const real q = tanh(a.v); return D(q, (1 - q * q) * a.d); }
 __device__ __forceinline__ D cosh(D a) { return D(cosh(a.v), sinh(a.v) * a.d); }
 __device__ __forceinline__ D sinh(D a) { return D(sinh(a.v), cosh(a.v) * a.d); }
-__device__ __forceinline__ D atan(D a) { return D(atan(a.v), a.d / (1.0 + a.v * a.v)); }
-__device__ __forceinline__ D fabs(D a) { return a.v < 0.0 ? -a : a; }
-__device__ __forceinline__ D pow(D a, double b) {
-    const double q = pow(a.v, b);
-    return D(q, a.v != 0.0 ? b * q / a.v * a.d : (b == 1.0 ? a.d : 0.0));
+__device__ __forceinline__ D atan(D a) { return D(atan(a.v), a.d / (1 + a.v * a.v)); }
+__device__ __forceinline__ D fabs(D a) { return a.v < 0 ? -a : a; }
+__device__ __forceinline__ D pow(D a, real b) {
+    const real q = pow(a.v, b);
+    return D(q, a.v != 0 ? b * q / a.v * a.d : (b == 1 ? a.d : (real)0));
 }
 __device__ __forceinline__ D pow(D a, D b) {
-    const double q = pow(a.v, b.v);
-    return D(q, a.v > 0.0 ? q * (b.d * log(a.v) + b.v * a.d / a.v) : 0.0);
+    const real q = pow(a.v, b.v);
+    return D(q, a.v > 0 ? q * (b.d * log(a.v) + b.v * a.d / a.v) : (real)0);
 }
-__device__ __forceinline__ D pow(double a, D b) { const double q = pow(a, b.v); return D(q, q * log(a) * b.d); }
-__device__ __forceinline__ D pow(D a, int b) { return pow(a, (double)b); }
+__device__ __forceinline__ D pow(real a, D b) { const real q = pow(a, b.v); return D(q, q * log(a) * b.d); }
+__device__ __forceinline__ D pow(D a, int b) { return pow(a, (real)b); }
+// the time: FP32 or FP64 value for the expression, the exact FP64 value for phases
+struct TT {
+    real f;
+    double x;
+    __device__ operator real() const { return f; }
+};
 // predefined functions (Listing 2 of the paper, written from their definitions)
-template <class L> __device__ __forceinline__ auto se(double t, L lambda) { return exp(-(lambda * t)); }
-template <class L, class B> __device__ __forceinline__ auto ge(double t, L lambda, B beta) {
-    const auto x = lambda * t;
+template <class L> __device__ __forceinline__ auto se(TT t, L lambda) { return exp(-(lambda * (real)t)); }
+template <class L, class B> __device__ __forceinline__ auto ge(TT t, L lambda, B beta) {
+    const auto x = lambda * (real)t;
     decltype(exp(-pow(x, beta))) one{};
-    one = one + 1.0;
-    return val(x) > 0.0 ? exp(-pow(x, beta)) : one;
+    one = one + (real)1;
+    return val(x) > 0 ? exp(-pow(x, beta)) : one;
 }
-template <class S> __device__ __forceinline__ auto sg(double t, S sigma) {
-    const auto x = sigma * t;
-    return exp(-0.5 * (x * x));
+template <class S> __device__ __forceinline__ auto sg(TT t, S sigma) {
+    const auto x = sigma * (real)t;
+    return exp(-(real)0.5 * (x * x));
 }
-template <class S> __device__ __forceinline__ auto stg(double t, S sigma) {
-    const auto x2 = (sigma * t) * (sigma * t);
-    return 1.0 / 3.0 + 2.0 / 3.0 * (1.0 - x2) * exp(-0.5 * x2);
+template <class S> __device__ __forceinline__ auto stg(TT t, S sigma) {
+    const auto x2 = (sigma * (real)t) * (sigma * (real)t);
+    return (real)1 / (real)3 + (real)2 / (real)3 * ((real)1 - x2) * exp(-(real)0.5 * x2);
 }
-// transverse field precession: cos(2 pi gamma_mu B t + phi), B in G, t in us, phi in rad
-template <class P, class B> __device__ __forceinline__ auto tf(double t, P phi, B field) {
-    return cos(6.283185307179586476925 * 0.013554 * field * t + phi);
+// transverse field precession: cos(2 pi gamma_mu B t + phi), B in G, t in us,
+// phi in rad; the phase is formed in FP64 from the exact time and reduced to
+// [-pi, pi] before the (FP32 in the FP32 variant) cosine
+__device__ __forceinline__ double tf_phase(double t, double phi, double field) {
+    const double ph = 6.283185307179586476925 * 0.013554 * field * t + phi;
+    return ph - 6.283185307179586476925 * rint(ph * 0.15915494309189533577);
+}
+__device__ __forceinline__ real tf(TT t, real phi, real field) {
+    return cos((real)tf_phase(t.x, (double)phi, (double)field));
+}
+__device__ __forceinline__ D tf(TT t, D phi, D field) {
+    const real ph = (real)tf_phase(t.x, (double)phi.v, (double)field.v);
+    const real w = (real)(6.283185307179586476925 * 0.013554) * (real)t;
+    return D(cos(ph), -sin(ph) * (phi.d + w * field.d));
+}
+__device__ __forceinline__ D tf(TT t, real phi, D field) { return tf(t, D(phi, 0), field); }
+__device__ __forceinline__ D tf(TT t, D phi, real field) { return tf(t, phi, D(field, 0)); }
+__device__ __forceinline__ real lift(int x) { return (real)x; }
+__device__ __forceinline__ real lift(real x) { return x; }
+__device__ __forceinline__ D lift(D x) { return x; }
+template <class P, class B> __device__ __forceinline__ auto tf(TT t, P phi, B field) {
+    return tf(t, lift(phi), lift(field));
 }
 // parameter access: plain values, or duals seeded along parameter `dir`
+// (an index outside p, m or f marks the bin bad instead of reading out of bounds)
 struct PVal {
     const double* p;
-    __device__ double operator[](int i) const { return p[i]; }
+    int n;
+    bool* bad;
+    __device__ real operator[](int i) const {
+        if ((unsigned)i < (unsigned)n) return (real)p[i];
+        *bad = true;
+        return 0;
+    }
 };
 struct PTan {
     const double* p;
-    int dir;
-    __device__ D operator[](int i) const { return D(p[i], i == dir ? 1.0 : 0.0); }
+    int n, dir;
+    bool* bad;
+    __device__ D operator[](int i) const {
+        if ((unsigned)i < (unsigned)n) return D((real)p[i], i == dir ? (real)1 : (real)0);
+        *bad = true;
+        return D(0, 0);
+    }
+};
+struct MVal {
+    const int* m;
+    int n;
+    bool* bad;
+    __device__ int operator[](int i) const {
+        if ((unsigned)i < (unsigned)n) return m[i];
+        *bad = true;
+        return 0;
+    }
+};
+struct FVal {
+    const double* f;
+    int n;
+    bool* bad;
+    __device__ real operator[](int i) const {
+        if ((unsigned)i < (unsigned)n) return (real)f[i];
+        *bad = true;
+        return 0;
+    }
 };
 template <class PA>
-__device__ __forceinline__ auto user_asymmetry(double t, const PA& p, const int* m, const double* f) {
+__device__ __forceinline__ auto user_asymmetry(TT t, const PA& p, const MVal& m, const FVal& f) {
     return (
 )SRC";
     s += expr;
     s += R"SRC(
     );
+}
+// objective term of one bin and its derivative with respect to N (Eq. 3 / Eq. 4);
+// the deviance as N h(r), h(r) = (1 + r) log1p(r) - r, r = (d - N) / N
+__device__ __forceinline__ real obj_term(int obj, real dv, real N, bool& bad, real& dobj) {
+    if (obj == 0) {
+        const real w = (real)1 / (dv > (real)1 ? dv : (real)1);
+        const real r = dv - N;
+        dobj = (real)-2 * r * w;
+        return r * r * w;
+    }
+    if (dv > 0) {
+        if (!(N > 0)) {
+            bad = true;
+            dobj = 0;
+            return 0;
+        }
+        const real r = (dv - N) / N;
+        real h;
+        if (MUSR_FP32 && fabs(r) < (real)0.125) {
+            h = r * (real)(-1.0 / 72.0) + (real)(1.0 / 56.0);
+            h = h * r - (real)(1.0 / 42.0);
+            h = h * r + (real)(1.0 / 30.0);
+            h = h * r - (real)(1.0 / 20.0);
+            h = h * r + (real)(1.0 / 12.0);
+            h = h * r - (real)(1.0 / 6.0);
+            h = h * r + (real)0.5;
+            h = h * r * r;
+        } else {
+            const real u = log1p(r);
+            h = (1 + r) * u - r;
+        }
+        dobj = (real)2 * ((real)1 - dv / N);
+        return (real)2 * N * h;
+    }
+    if (!(N >= 0)) bad = true;
+    dobj = 2;
+    return (real)2 * N;
 }
 extern "C" __global__ void __launch_bounds__(256) musr_user_objective(const UParams u) {
     __shared__ double red[8];
@@ -204,32 +347,26 @@ extern "C" __global__ void __launch_bounds__(256) musr_user_objective(const UPar
     const int k = tile / u.tph;
     const int start = (tile - k * u.tph) * 2048;
     const int M = u.hist_nbins[k];
-    const PVal p{u.thetas + (size_t)v * u.P};
-    const double* f = u.funcs ? u.funcs + (size_t)v * u.F : nullptr;
-    const int* m = u.map + (size_t)k * u.map_width;
+    bool bad = false;
+    const PVal p{u.thetas + (size_t)v * u.P, u.P, &bad};
+    const FVal f{u.funcs ? u.funcs + (size_t)v * u.F : nullptr, u.funcs ? u.F : 0, &bad};
+    const MVal m{u.map + (size_t)k * u.map_width, u.map_width, &bad};
     const float* d = u.data + u.hist_off[k];
-    const double n0 = p[m[0]], bkg = p[m[1]];
+    const real n0 = p[m[0]], bkg = p[m[1]];
+    const real inv_tau = (real)u.inv_tau;
     if (threadIdx.x == 0) bad_s = 0u;
     __syncthreads();
-    double acc = 0.0;
-    bool bad = false;
+    real part = 0;  // at most 8 bins per thread per tile
     const int end = min(M, start + 2048);
     for (int n = start + (int)threadIdx.x; n < end; n += blockDim.x) {
-        const double t = u.t0 + (double)n * u.dt;
-        const double N = n0 * exp(-t * u.inv_tau) * (1.0 + user_asymmetry(t, p, m, f)) + bkg;
-        const double dv = (double)d[n];
-        if (u.obj == 0) {
-            const double r = dv - N;
-            acc += r * r / fmax(dv, 1.0);
-        } else if (dv > 0.0) {
-            if (!(N > 0.0)) bad = true;
-            else acc += 2.0 * ((N - dv) + dv * log(dv / N));
-        } else {
-            if (!(N >= 0.0)) bad = true;
-            acc += 2.0 * N;
-        }
+        const double tx = u.t0 + (double)n * u.dt;
+        const TT t{(real)tx, tx};
+        const real N = n0 * exp(-(real)t * inv_tau) * ((real)1 + user_asymmetry(t, p, m, f)) + bkg;
+        real dobj;
+        part += obj_term(u.obj, (real)d[n], N, bad, dobj);
         if (!isfinite(N)) bad = true;
     }
+    double acc = (double)part;
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     if (bad) atomicOr(&bad_s, 1u);
@@ -249,22 +386,24 @@ extern "C" __global__ void __launch_bounds__(256) musr_user_tangent(const UParam
     const int k = tile / u.tph;
     const int start = (tile - k * u.tph) * 2048;
     const int M = u.hist_nbins[k];
-    const PTan p{u.thetas, dir_param[dir]};
-    const double* f = u.funcs;
-    const int* m = u.map + (size_t)k * u.map_width;
+    bool bad = false;
+    const PTan p{u.thetas, u.P, dir_param[dir], &bad};
+    const FVal f{u.funcs, u.funcs ? u.F : 0, &bad};
+    const MVal m{u.map + (size_t)k * u.map_width, u.map_width, &bad};
     const float* d = u.data + u.hist_off[k];
     const D n0 = p[m[0]], bkg = p[m[1]];
-    double acc = 0.0;
+    const real inv_tau = (real)u.inv_tau;
+    real part = 0;
     const int end = min(M, start + 2048);
     for (int n = start + (int)threadIdx.x; n < end; n += blockDim.x) {
-        const double t = u.t0 + (double)n * u.dt;
-        const D N = n0 * exp(-t * u.inv_tau) * (1.0 + user_asymmetry(t, p, m, f)) + bkg;
-        const double dv = (double)d[n];
-        double w;
-        if (u.obj == 0) w = -2.0 * (dv - N.v) / fmax(dv, 1.0);
-        else w = dv > 0.0 ? 2.0 * (1.0 - dv / N.v) : 2.0;
-        acc += w * N.d;
+        const double tx = u.t0 + (double)n * u.dt;
+        const TT t{(real)tx, tx};
+        const D N = n0 * exp(-(real)t * inv_tau) * ((real)1 + user_asymmetry(t, p, m, f)) + bkg;
+        real dobj;
+        obj_term(u.obj, (real)d[n], N.v, bad, dobj);
+        part += dobj * N.d;
     }
+    double acc = bad ? __longlong_as_double(0x7ff8000000000000LL) : (double)part;  // NaN marks a bad index
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -306,6 +445,7 @@ struct UParamsHost {  // the generated kernel's parameter block, same layout
 struct musr_utheory_s {
     std::string expr, log;
     int n_funcs = 0;
+    bool fp32 = false;
     int device = 0;
     cudaLibrary_t lib = nullptr;
     cudaKernel_t k_obj = nullptr, k_sum = nullptr, k_tan = nullptr;
@@ -562,7 +702,10 @@ int uth_exact(musr_utheory th, musr_run run, int obj, const double* theta, const
     st = musr::uth_tangent_host(th, run, obj, theta, funcs, fidx, gd.data());
     if (st != MUSR_OK) return st;
     memset(grad, 0, sizeof(double) * run->P);
-    for (size_t a = 0; a < fidx.size(); ++a) grad[fidx[a]] = gd[a];
+    for (size_t a = 0; a < fidx.size(); ++a) {
+        if (!std::isfinite(gd[a])) return MUSR_ENONFINITE;  // an index outside p, m or f
+        grad[fidx[a]] = gd[a];
+    }
     return MUSR_OK;
 }
 
@@ -581,21 +724,22 @@ int musr_utheory_destroy(musr_utheory th) {
 
 const char* musr_utheory_log(musr_utheory th) { return th ? th->log.c_str() : g_last_log.c_str(); }
 
-int musr_utheory_create(const char* expr, int32_t n_funcs, musr_utheory* out) {
+int musr_utheory_create(const char* expr, int32_t n_funcs, int32_t dtype, musr_utheory* out) {
     if (!out) return MUSR_EINVAL;
     *out = nullptr;
-    if (!expression_ok(expr) || n_funcs < 0) return MUSR_EINVAL;
+    if (!expression_ok(expr) || n_funcs < 0 || (dtype != MUSR_F32 && dtype != MUSR_F64)) return MUSR_EINVAL;
     Nvrtc& nv = nvrtc();
     if (!nv.ok) return MUSR_ENOTSUP;
     musr_utheory th = new (std::nothrow) musr_utheory_s();
     if (!th) return MUSR_ENOMEM;
     th->expr = expr;
     th->n_funcs = n_funcs;
+    th->fp32 = dtype == MUSR_F32;
     cudaGetDevice(&th->device);
     int major = 0, minor = 0;
     cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, th->device);
     cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, th->device);
-    const std::string src = kernel_source(th->expr);
+    const std::string src = kernel_source(th->expr, th->fp32);
     nvrtcProgram prog = nullptr;
     if (nv.create(&prog, src.c_str(), "musr_user_theory.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
         delete th;

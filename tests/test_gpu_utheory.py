@@ -1,9 +1,12 @@
-"""User-defined theory functions compiled at run time (NVRTC, FP64 kernel):
-objective parity with the FP64 expression oracle (relative 1e-10: both are
-FP64 with different summation order), agreement with the built-in kernels
-for the same theory, central-difference gradients against the oracle's
-analytic gradient of the equivalent built-in model, a stretched exponential
-and the function array, compile errors, and a fit."""
+"""User-defined theory functions compiled at run time (NVRTC): objective
+parity with the FP64 expression oracle (FP64 variant: relative 1e-10, both
+FP64 with different summation order; FP32 variant: relative 1e-5 — a model
+error of ~5e-7 per bin from FP32 exp / cos and N0 rounding, summed with
+partly coherent signs over ~1e6 bins of ~1e3 counts), agreement with the
+built-in kernels for the same theory, forward-mode and central-difference
+gradients against the oracle's analytic gradient of the equivalent built-in
+model, a stretched exponential and the function array, out-of-range indices,
+compile errors, and a fit."""
 import numpy as np
 import pytest
 
@@ -126,3 +129,31 @@ def test_calls_of_different_vector_counts(md):
         v2, g1 = th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
         assert v2 == v1
     th.close()
+
+
+@pytest.mark.parametrize("obj", [MUSR_CHI2, MUSR_POISSON])
+def test_fp32_variant_matches_oracle(md, obj):
+    lay, theta, d, g = md
+    th = UserTheory(W.MD_USER_EXPR, fp32=True)
+    t1 = W.perturb(theta, lay.free, 0.01, g)
+    with Run(lay, d) as run:
+        v = th.eval(run, t1, obj)[0]
+        vg, gr = th.grad(run, t1, obj, free=lay.free, rel_h=0.0)
+    ref = U.objective(lay, d, t1, W.MD_USER_EXPR, obj)
+    assert rel_err(v, ref) <= 1e-5 and vg == v
+    vref, gref, _ = oracle.gradient(lay, d, t1, oracle.CHI2 if obj == MUSR_CHI2 else oracle.POISSON, with_gn=False)
+    fr = lay.free.astype(bool)
+    assert grad_rel_err(gr[fr], gref[fr]) <= 1e-3
+    th.close()
+
+
+def test_out_of_range_indices_are_flagged(md):
+    lay, theta, d, g = md
+    for expr in ("p[100000] * t", "p[m[40]] * t", "f[3] * t"):
+        th = UserTheory(expr, n_funcs=1)
+        with Run(lay, d) as run:
+            v = th.eval(run, theta, MUSR_CHI2, funcs=[1.0])[0]
+            assert v == np.inf
+            with pytest.raises(MusrError):
+                th.grad(run, theta, MUSR_CHI2, funcs=[1.0], rel_h=0.0)
+        th.close()
