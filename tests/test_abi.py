@@ -62,3 +62,12 @@ def test_create_run_without_gpu_fails_cleanly(lib_path):
     lay, theta, _ = W.config_single()
     with pytest.raises(MusrError):
         Run(lay, None)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the compiled library the binding raises
+    from paper_1604_02334_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libmusr.so"))
+    with pytest.raises(ImportError):
+        _lib.load()
