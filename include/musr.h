@@ -206,13 +206,19 @@ int musr_generate(musr_run run, const double* thetas_dev, int32_t n_samples, int
  * BF16 row-major on the device (16-byte aligned), FP32 accumulation, bias [n]
  * FP32 or NULL, relu != 0 applies max(., 0); results to out_f32 and / or
  * out_bf16 ([m x ldc] row-major, ldc >= n, ldc % 8 == 0).  m and n must be
- * multiples of 128 and k of 64 (MUSR_EINVAL otherwise).  err_dev: a device
- * uint32 the kernel ORs 1 into if a bounded internal wait times out.
+ * multiples of 128 and k of 64 (MUSR_EINVAL otherwise).  ws_dev (FP32, device,
+ * 16-byte aligned, ws_floats elements, may be NULL): scratch for split-K; when
+ * the product has fewer than 76 output tiles of 128 x 128 and k >= 256, K is cut
+ * into up to min(32, 152 / tiles) slices that fit in ws_floats (m * n floats a
+ * slice; 152 * 128 * 128 always suffices), each slice's partial tile is written
+ * there and a second kernel adds the slices in slice order (deterministic), then
+ * bias and ReLU.  NULL or too small: one CTA per output tile.  err_dev: a
+ * device uint32 the kernel ORs 1 into if a bounded internal wait times out.
  * Asynchronous on stream.
  */
 int musr_gemm_bf16(const void* a_dev, const void* b_dev, int32_t m, int32_t n, int32_t k,
                    const float* bias_dev, int32_t relu, float* out_f32_dev, void* out_bf16_dev,
-                   int32_t ldc, uint32_t* err_dev, void* stream);
+                   int32_t ldc, float* ws_dev, int64_t ws_floats, uint32_t* err_dev, void* stream);
 
 /*
  * Learned start proposer: an MLP n_in -> n_hidden (x n_hidden_layers, ReLU)

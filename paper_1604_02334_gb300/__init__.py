@@ -315,8 +315,9 @@ def poisson_sample(mu_dev, seed, counts_dev, stream=None):
           "musr_poisson_sample")
 
 
-def gemm_bf16(a, b, bias=None, relu=False, out_f32=None, out_bf16=None, err=None, stream=None):
-    """out = act(a @ b.T + bias) on the tensor cores; a [m, k], b [n, k] CUDA bf16."""
+def gemm_bf16(a, b, bias=None, relu=False, out_f32=None, out_bf16=None, err=None, stream=None, ws=None):
+    """out = act(a @ b.T + bias) on the tensor cores; a [m, k], b [n, k] CUDA bf16.
+    ws: optional CUDA float32 scratch that enables split-K for products with few output tiles."""
     import torch
     m, k = a.shape
     n = b.shape[0]
@@ -326,7 +327,8 @@ def gemm_bf16(a, b, bias=None, relu=False, out_f32=None, out_bf16=None, err=None
     st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
     p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
     check(_lib.load().musr_gemm_bf16(p(a), p(b), m, n, k, p(bias), 1 if relu else 0, p(out_f32), p(out_bf16),
-                                     ldc, p(err), st), "musr_gemm_bf16")
+                                     ldc, p(ws), ws.numel() if ws is not None else 0, p(err), st),
+          "musr_gemm_bf16")
     return err
 
 

@@ -150,7 +150,7 @@ SIGNATURES = {
     "musr_generate": (ctypes.c_int, [_run, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
                                      ctypes.c_uint64, ctypes.c_int32, _vp, _vp, _vp]),
     "musr_gemm_bf16": (ctypes.c_int, [_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp,
-                                      ctypes.c_int32, _vp, _vp, ctypes.c_int32, _vp, _vp]),
+                                      ctypes.c_int32, _vp, _vp, ctypes.c_int32, _vp, ctypes.c_int64, _vp, _vp]),
     "musr_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, ctypes.POINTER(_vp)]),
     "musr_mlp_destroy": (ctypes.c_int, [_vp]),

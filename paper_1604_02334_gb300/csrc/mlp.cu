@@ -103,6 +103,7 @@ struct GemmArgs {
     __nv_bfloat16* out_bf16;  // [M x ldc] or null
     int ldc;
     unsigned* err;       // device error flag
+    float* partial;      // split-K: [gridDim.z][M][N] raw FP32 tiles (bias / ReLU by the reduce kernel), or null
 };
 
 __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_constant__ CUtensorMap map_a,
@@ -119,7 +120,11 @@ __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_const
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kTileM, n0 = blockIdx.x * kTileN;
-    const int KT = g.K / kTileK;
+    // split-K: this CTA's contiguous range of K tiles (the host keeps every range non-empty)
+    const int KT_all = g.K / kTileK;
+    const int per = (KT_all + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int kt_base = (int)blockIdx.z * per;
+    const int KT = min(per, KT_all - kt_base);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -151,8 +156,8 @@ __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_const
             }
             if (*(volatile int*)&s_abort) break;
             mbar_expect_tx(&full[s], 2 * kTileBytes);
-            tma_load_2d(sA + s * kTileBytes, &map_a, kt * kTileK, m0, &full[s]);
-            tma_load_2d(sB + s * kTileBytes, &map_b, kt * kTileK, n0, &full[s]);
+            tma_load_2d(sA + s * kTileBytes, &map_a, (kt_base + kt) * kTileK, m0, &full[s]);
+            tma_load_2d(sB + s * kTileBytes, &map_b, (kt_base + kt) * kTileK, n0, &full[s]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
@@ -203,6 +208,18 @@ __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_const
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             float v[16];
+            if (g.partial) {
+                // split-K: the raw slice sum, bias and ReLU after the slices are added
+                if (row < g.M) {
+                    float4* dst = reinterpret_cast<float4*>(
+                        g.partial + ((size_t)blockIdx.z * g.M + row) * g.N + n0 + c0);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        dst[i] = make_float4(__uint_as_float(r[4 * i]), __uint_as_float(r[4 * i + 1]),
+                                             __uint_as_float(r[4 * i + 2]), __uint_as_float(r[4 * i + 3]));
+                }
+                continue;
+            }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
                 v[i] = __uint_as_float(r[i]);
@@ -234,6 +251,38 @@ __global__ void __launch_bounds__(128, 1) gemm_tn_bf16_kernel(const __grid_const
     }
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// split-K: out = act(sum over slices in slice order + bias), four columns per thread
+__global__ void splitk_reduce_kernel(const float* __restrict__ part, int splits, int M, int N,
+                                     const float* __restrict__ bias, int relu, float* __restrict__ out_f32,
+                                     __nv_bfloat16* __restrict__ out_bf16, int ldc) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // index of a group of 4 columns
+    const int64_t n4 = (int64_t)M * (N / 4);
+    if (q >= n4) return;
+    const int row = (int)(q / (N / 4)), col = (int)(q % (N / 4)) * 4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int z = 0; z < splits; ++z) {
+        const float4 v = *reinterpret_cast<const float4*>(part + ((size_t)z * M + row) * N + col);
+        acc.x += v.x;
+        acc.y += v.y;
+        acc.z += v.z;
+        acc.w += v.w;
+    }
+    float v[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (bias) v[i] += bias[col + i];
+        if (relu) v[i] = fmaxf(v[i], 0.f);
+    }
+    if (out_f32) *reinterpret_cast<float4*>(out_f32 + (size_t)row * ldc + col) = make_float4(v[0], v[1], v[2], v[3]);
+    if (out_bf16) {
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&h0);
+        u.y = *reinterpret_cast<uint32_t*>(&h1);
+        *reinterpret_cast<uint2*>(out_bf16 + (size_t)row * ldc + col) = u;
+    }
 }
 
 // ---- host: tensor maps through the driver entry point ----
@@ -271,7 +320,7 @@ bool make_map(CUtensorMap* m, const void* ptr, uint64_t rows, uint64_t cols) {
 
 // C = act(A . B^T + bias); see the file header.  err_dev: device unsigned flag.
 int gemm_tn_bf16(const void* A, const void* B, int M, int N, int K, const float* bias, int relu, float* out_f32,
-                 void* out_bf16, int ldc, unsigned* err_dev, cudaStream_t st) {
+                 void* out_bf16, int ldc, unsigned* err_dev, cudaStream_t st, float* ws, size_t ws_floats) {
     if (M <= 0 || N <= 0 || K <= 0 || M % kTileM || N % kTileN || K % kTileK || ldc < N || (ldc % 8)) return MUSR_EINVAL;
     if (((uintptr_t)A & 15) || ((uintptr_t)B & 15)) return MUSR_EINVAL;
     CUtensorMap ma, mb;
@@ -286,24 +335,44 @@ int gemm_tn_bf16(const void* A, const void* B, int M, int N, int K, const float*
     g.out_bf16 = static_cast<__nv_bfloat16*>(out_bf16);
     g.ldc = ldc;
     g.err = err_dev;
+    g.partial = nullptr;
     const size_t smem = 2 * (size_t)kStages * kTileBytes + 1024;
     static std::once_flag once;
     std::call_once(once, [smem] {
         cudaFuncSetAttribute(gemm_tn_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     });
-    dim3 grid(N / kTileN, M / kTileM);
+    // too few output tiles to fill the GPU: split K over CTAs (deterministic slice-order reduction)
+    const int tiles = (N / kTileN) * (M / kTileM), KT = K / kTileK;
+    int splits = 1;
+    if (ws && tiles < 76 && KT >= 4) {
+        splits = std::min(std::min(32, KT), std::max(1, 152 / tiles));
+        while (splits > 1 && (size_t)splits * M * N > ws_floats) --splits;
+        const int per = (KT + splits - 1) / splits;
+        splits = (KT + per - 1) / per;  // every slice non-empty
+    }
+    if (splits > 1) g.partial = ws;
+    dim3 grid(N / kTileN, M / kTileM, splits);
     gemm_tn_bf16_kernel<<<grid, 128, smem, st>>>(ma, mb, g);
-    return cuda_status(cudaGetLastError());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && splits > 1) {
+        const int64_t n4 = (int64_t)M * (N / 4);
+        splitk_reduce_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(ws, splits, M, N, bias, relu, out_f32,
+                                                                          static_cast<__nv_bfloat16*>(out_bf16), ldc);
+        e = cudaGetLastError();
+    }
+    return cuda_status(e);
 }
 
 }  // namespace musr
 
 extern "C" int musr_gemm_bf16(const void* a_dev, const void* b_dev, int32_t m, int32_t n, int32_t k,
                               const float* bias_dev, int32_t relu, float* out_f32_dev, void* out_bf16_dev,
-                              int32_t ldc, uint32_t* err_dev, void* stream) {
-    if (!a_dev || !b_dev || !err_dev || (!out_f32_dev && !out_bf16_dev)) return MUSR_EINVAL;
+                              int32_t ldc, float* ws_dev, int64_t ws_floats, uint32_t* err_dev, void* stream) {
+    if (!a_dev || !b_dev || !err_dev || (!out_f32_dev && !out_bf16_dev) || ws_floats < 0 ||
+        (ws_dev && (reinterpret_cast<uintptr_t>(ws_dev) & 15)))
+        return MUSR_EINVAL;
     return musr::gemm_tn_bf16(a_dev, b_dev, m, n, k, bias_dev, relu, out_f32_dev, out_bf16_dev, ldc, err_dev,
-                              static_cast<cudaStream_t>(stream));
+                              static_cast<cudaStream_t>(stream), ws_dev, ws_dev ? (size_t)ws_floats : 0);
 }
 
 // ===========================================================================
@@ -420,6 +489,7 @@ struct musr_mlp_s {
     float *Y = nullptr, *dY = nullptr, *dH = nullptr, *dZ = nullptr, *loss_part = nullptr;
     __nv_bfloat16 *dYb = nullptr, *dZb = nullptr, *dZT = nullptr;
     unsigned* err = nullptr;
+    float* ws = nullptr;  // split-K partial tiles: at most 152 tiles of 128 x 128 FP32
     int64_t n_params = 0;
     int step = 0;
     cudaStream_t stream = nullptr;
@@ -430,6 +500,9 @@ using namespace musr;
 
 size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
+// split-K only runs with fewer than 76 output tiles and at most 152 / tiles slices
+constexpr size_t kSplitWsFloats = (size_t)152 * 128 * 128;
+
 int mlp_forward(musr_mlp m, const float* x, int B, cudaStream_t st) {
     const int64_t nx = (int64_t)B * m->n_in;
     f32_to_bf16_kernel<<<blocks_for(nx), 256, 0, st>>>(x, m->in_scale, m->X, nx);
@@ -437,7 +510,8 @@ int mlp_forward(musr_mlp m, const float* x, int B, cudaStream_t st) {
     for (int l = 0; l < m->L; ++l) {
         const bool last = l == m->L - 1;
         const int rc = gemm_tn_bf16(in, m->Wb[l], B, m->dout[l], m->din[l], m->b[l], last ? 0 : 1,
-                                    last ? m->Y : nullptr, last ? nullptr : m->H[l], m->dout[l], m->err, st);
+                                    last ? m->Y : nullptr, last ? nullptr : m->H[l], m->dout[l], m->err, st,
+                                    m->ws, kSplitWsFloats);
         if (rc != MUSR_OK) return rc;
         in = last ? nullptr : m->H[l];
     }
@@ -463,12 +537,14 @@ int mlp_backward(musr_mlp m, const float* x, const float* t, int B, float* loss,
         // dW = dZ^T . act  (M = o, N = i, K = B)
         transpose(dzb, m->dZT, B, o, st);
         transpose(act, actT, B, i, st);
-        rc = gemm_tn_bf16(m->dZT, actT, o, i, B, nullptr, 0, m->gW[l], nullptr, i, m->err, st);
+        rc = gemm_tn_bf16(m->dZT, actT, o, i, B, nullptr, 0, m->gW[l], nullptr, i, m->err, st, m->ws,
+                          kSplitWsFloats);
         if (rc != MUSR_OK) return rc;
         colsum_kernel<<<(o + 127) / 128, 128, 0, st>>>(dz, B, o, m->gb[l]);
         if (l > 0) {
             // dH = dZ . W  (M = B, N = i, K = o), then the ReLU of layer l - 1
-            rc = gemm_tn_bf16(dzb, m->WTb[l], B, i, o, nullptr, 0, m->dH, nullptr, i, m->err, st);
+            rc = gemm_tn_bf16(dzb, m->WTb[l], B, i, o, nullptr, 0, m->dH, nullptr, i, m->err, st, m->ws,
+                              kSplitWsFloats);
             if (rc != MUSR_OK) return rc;
             const int64_t n = (int64_t)B * i;
             relu_back_kernel<<<blocks_for(n), 256, 0, st>>>(m->dH, m->H[l - 1], n, m->dZ, m->dZb);
@@ -593,6 +669,7 @@ int musr_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int
     take(2 * B * mx);       // dZT
     take(4 * 1024);         // loss partials
     take(16);               // err
+    take(4 * kSplitWsFloats);  // split-K workspace
     int st = MUSR_OK;
     if (cudaMalloc(&m->arena, sz) != cudaSuccess) {
         m->arena = nullptr;
@@ -636,6 +713,7 @@ int musr_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int
     m->dZT = (__nv_bfloat16*)nxt();
     m->loss_part = (float*)nxt();
     m->err = (unsigned*)nxt();
+    m->ws = (float*)nxt();
     // He-uniform initialisation from a splitmix64 stream (host), zero biases
     m->n_params = 0;
     for (int l = 0; l < m->L; ++l) {
