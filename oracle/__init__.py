@@ -83,7 +83,11 @@ def _dp(a):
 def _layout_args(lay):
     nb = np.ascontiguousarray(lay.n_bins, dtype=np.int64)
     mp = np.ascontiguousarray(lay.map, dtype=np.int32)
-    cp = np.ascontiguousarray(lay.comp, dtype=np.int32)
+    cp = np.asarray(lay.comp, dtype=np.int32)
+    cp = cp.reshape(-1, cp.shape[-1] if cp.ndim == 2 and cp.shape[0] else 7)
+    if cp.shape[1] == 6:  # rows without the stretched line's beta column
+        cp = np.concatenate([cp, np.full((cp.shape[0], 1), -1, dtype=np.int32)], axis=1)
+    cp = np.ascontiguousarray(cp)
     keep = (nb, mp, cp)
     args = [lay.n_hist, nb.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), lay.t0_us, lay.dt_us,
             lay.tau_us, lay.gamma, lay.n_params, lay.map_width,

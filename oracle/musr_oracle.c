@@ -22,6 +22,8 @@
  *                    bin with d = 0 contributes 2N.
  *   Sec. 4.2.1, Listing 2 predefined functions:
  *                    se(t, l)  = exp(-l t)
+ *                    ge(t, l, b) = exp(-(l t)^b); reading: 1 where l t <= 0
+ *                    (the listing's pow of a negative base has no real value)
  *                    sg(t, s)  = exp(-(s t)^2 / 2)
  *                    stg(t, s) = 1/3 + 2/3 (1 - (s t)^2) exp(-(s t)^2 / 2)
  *                    (the listing's integer 1/3 and 2/3 are read as the real
@@ -35,6 +37,7 @@
  *   0  TF_EXP   a * se(t, rate) * cos(2 pi gamma (B + B2) t + phi)
  *   1  TF_GAUSS a * sg(t, rate) * cos(2 pi gamma (B + B2) t + phi)
  *   2  KT_SG    a * stg(t, rate)
+ *   3  TF_GE    a * ge(t, rate, beta) * cos(2 pi gamma (B + B2) t + phi)
  *
  * Every sum over bins uses Neumaier-compensated FP64 summation, so the value
  * returned is the exact sum of the FP64 per-bin terms to within a few ulp.
@@ -69,6 +72,7 @@
 #define ORC_TF_EXP 0
 #define ORC_TF_GAUSS 1
 #define ORC_KT_SG 2
+#define ORC_TF_GE 3
 
 #define ORC_CHI2 0
 #define ORC_POISSON 1
@@ -103,7 +107,7 @@ typedef struct {
     int n_params, map_width;
     const int32_t* map;
     int n_comp;
-    const int32_t* comp; /* n_comp x 6: kind, amp, rate, field, field2, phase */
+    const int32_t* comp; /* n_comp x 7: kind, amp, rate, field, field2, phase, beta */
 } orc_layout;
 
 static int64_t hist_offset(const orc_layout* L, int k) {
@@ -136,9 +140,9 @@ static int check_layout(const orc_layout* L) {
         }
     }
     for (int c = 0; c < L->n_comp; ++c) {
-        const int32_t* d = L->comp + 6 * c;
-        if (d[0] < 0 || d[0] > 2) return ORC_EINVAL;
-        for (int s = 1; s < 6; ++s)
+        const int32_t* d = L->comp + 7 * c;
+        if (d[0] < 0 || d[0] > 3) return ORC_EINVAL;
+        for (int s = 1; s < 7; ++s)
             if (d[s] < -1 || d[s] >= L->map_width) return ORC_EINVAL;
     }
     return ORC_OK;
@@ -148,6 +152,12 @@ static int check_layout(const orc_layout* L) {
 /* Listing 2 predefined functions, written out                               */
 /* ------------------------------------------------------------------------ */
 static double fn_se(double t, double lambda) { return exp(-lambda * t); }
+
+/* l t <= 0 gives 1: the power of a negative base is undefined for real b */
+static double fn_ge(double t, double lambda, double beta) {
+    double x = lambda * t;
+    return x > 0.0 ? exp(-pow(x, beta)) : 1.0;
+}
 
 static double fn_sg(double t, double sigma) {
     double st = sigma * t;
@@ -176,7 +186,7 @@ static double theory_bin(const orc_layout* L, const double* theta, int k, double
         for (int c = 0; c < L->map_width; ++c) dA[c] = 0.0;
     }
     for (int c = 0; c < L->n_comp; ++c) {
-        const int32_t* d = L->comp + 6 * c;
+        const int32_t* d = L->comp + 7 * c;
         int kind = d[0];
         double a = map_value(L, theta, k, d[1]);
         double rate = map_value(L, theta, k, d[2]);
@@ -197,18 +207,27 @@ static double theory_bin(const orc_layout* L, const double* theta, int k, double
         double phi = map_value(L, theta, k, d[5]);
         double arg = 2.0 * ORC_PI * L->gamma * field * t + phi;
         double cs = cos(arg), sn = sin(arg);
-        double env, denv_drate;
+        double env, denv_drate, denv_dbeta = 0.0;
         if (kind == ORC_TF_EXP) {
             env = fn_se(t, rate);
             denv_drate = -t * env;
-        } else {
+        } else if (kind == ORC_TF_GAUSS) {
             env = fn_sg(t, rate);
             denv_drate = -rate * t * t * env;
+        } else {
+            /* d/dl exp(-(l t)^b) = -b t (l t)^(b-1) exp(-(l t)^b);
+               d/db exp(-(l t)^b) = -(l t)^b ln(l t) exp(-(l t)^b); both 0 where l t <= 0 */
+            double beta = map_value(L, theta, k, d[6]);
+            double x = rate * t;
+            env = fn_ge(t, rate, beta);
+            denv_drate = x > 0.0 ? -beta * t * pow(x, beta - 1.0) * env : 0.0;
+            denv_dbeta = x > 0.0 ? -pow(x, beta) * log(x) * env : 0.0;
         }
         asym += a * env * cs;
         if (dA) {
             if (d[1] >= 0) dA[d[1]] += env * cs;
             if (d[2] >= 0) dA[d[2]] += a * denv_drate * cs;
+            if (kind == ORC_TF_GE && d[6] >= 0) dA[d[6]] += a * denv_dbeta * cs;
             double dphase = -a * env * sn;
             if (d[3] >= 0) dA[d[3]] += dphase * 2.0 * ORC_PI * L->gamma * t;
             if (d[4] >= 0) dA[d[4]] += dphase * 2.0 * ORC_PI * L->gamma * t;

@@ -14,8 +14,8 @@ Layout conventions (Sec. 4.1 Eq. 2 and the map array of Sec. 4.2.1):
   * every histogram k has a map row of ``map_width`` entries, each an index
     into theta (or -1 for the constant 0); column 0 is N0, column 1 is Nbkg;
   * every theory component names the map columns it reads:
-    (kind, amp, rate, field, field2, phase), -1 when unused.  The field is
-    theta[field] + theta[field2].
+    (kind, amp, rate, field, field2, phase, beta), -1 when unused.  The field
+    is theta[field] + theta[field2]; beta is the exponent of a stretched line.
 """
 from __future__ import annotations
 
@@ -28,6 +28,7 @@ import numpy as np
 TF_EXP = 0
 TF_GAUSS = 1
 KT_STATIC_GAUSS = 2
+TF_STRETCHED = 3
 
 CHI2 = 0
 POISSON = 1
@@ -48,7 +49,7 @@ class RunLayout:
     gamma: float
     n_params: int
     map: np.ndarray  # int32 [n_hist, map_width]
-    comp: np.ndarray  # int32 [n_comp, 6]
+    comp: np.ndarray  # int32 [n_comp, 7]
     names: List[str]
     free: np.ndarray  # uint8 [n_params]
 
@@ -80,6 +81,12 @@ class RunLayout:
         )
 
 
+def comp_table(comp) -> np.ndarray:
+    """Component rows as int32 [n_comp, 7]; 6-column rows (no beta) get beta = -1."""
+    rows = [[int(x) for x in r] + [-1] * (7 - len(r)) for r in comp]
+    return np.ascontiguousarray(np.asarray(rows, dtype=np.int32).reshape(-1, 7))
+
+
 def _layout(n_bins, dt_us, map_rows, comp, names, free, t0_us=0.0):
     return RunLayout(
         n_bins=np.asarray(n_bins, dtype=np.int64),
@@ -89,7 +96,7 @@ def _layout(n_bins, dt_us, map_rows, comp, names, free, t0_us=0.0):
         gamma=GAMMA_MU_MHZ_PER_G,
         n_params=len(names),
         map=np.ascontiguousarray(np.asarray(map_rows, dtype=np.int32)),
-        comp=np.ascontiguousarray(np.asarray(comp, dtype=np.int32).reshape(-1, 6)),
+        comp=comp_table(comp),
         names=list(names),
         free=np.asarray(free, dtype=np.uint8),
     )
@@ -128,13 +135,24 @@ SHARED_RANGES = {
     "dB": (5.0, 50.0),
     "A_KT": (0.02, 0.08),
     "Delta_KT": (0.1, 1.0),
+    # the stretched-line variant: second line exp(-(lambda2 t)^beta) instead of the Gaussian
+    "lambda2": (0.1, 2.0),
+    "beta": (0.5, 2.0),
 }
+# shared parameters of the stretched-line variant, in map-column order after phi
+ST_SHARED_NAMES = ["A1", "lambda1", "B1", "A2", "lambda2", "dB", "A_KT", "Delta_KT", "beta"]
 N0_RANGE = (200.0, 5000.0)
 BKG_RANGE = (1.0, 20.0)
 MD_COMPONENTS = [
     [TF_EXP, 3, 4, 5, -1, 2],
     [TF_GAUSS, 6, 7, 5, 8, 2],
     [KT_STATIC_GAUSS, 9, 10, -1, -1, -1],
+]
+# map row [N0, bkg, phi, A1, lambda1, B1, A2, lambda2, dB, A_KT, Delta_KT, beta]
+MD_ST_COMPONENTS = [
+    [TF_EXP, 3, 4, 5, -1, 2, -1],
+    [TF_STRETCHED, 6, 7, 5, 8, 2, 11],
+    [KT_STATIC_GAUSS, 9, 10, -1, -1, -1, -1],
 ]
 
 
@@ -151,6 +169,7 @@ def multi_detector_layout(
     window_us: float = 12.8,
     shared_bkg: bool = False,
     t0_us: float = 0.0,
+    stretched: bool = False,
 ) -> RunLayout:
     """K detector histograms sharing the physics parameters.
 
@@ -158,6 +177,9 @@ def multi_detector_layout(
              phi_0..phi_{K-1} (fixed, 2 pi k / K), A1, lambda1, B1, A2, sigma2,
              dB, A_KT, Delta_KT].
     The second line's field is B1 + dB.  Free: N0, bkg and the 8 shared ones.
+    ``stretched``: the second line relaxes as exp(-(lambda2 t)^beta) and the
+    shared block is A1, lambda1, B1, A2, lambda2, dB, A_KT, Delta_KT, beta
+    (9 free).
     ``n_bins`` is an int or a per-histogram sequence; dt = window / max(n_bins).
     """
     if np.isscalar(n_bins):
@@ -171,14 +193,16 @@ def multi_detector_layout(
     names += ["bkg"] if shared_bkg else [f"bkg_{k}" for k in range(n_hist)]
     names += [f"phi_{k}" for k in range(n_hist)]
     base = len(names)
-    names += SHARED_NAMES
+    shared = ST_SHARED_NAMES if stretched else SHARED_NAMES
+    names += shared
     rows = []
     for k in range(n_hist):
         bkg_idx = n_hist if shared_bkg else n_hist + k
         phi_idx = n_hist + n_bkg + k
-        rows.append([k, bkg_idx, phi_idx] + [base + j for j in range(8)])
-    free = [1] * (n_hist + n_bkg) + [0] * n_hist + [1] * 8
-    return _layout(nb, dt, rows, MD_COMPONENTS, names, free, t0_us)
+        rows.append([k, bkg_idx, phi_idx] + [base + j for j in range(len(shared))])
+    free = [1] * (n_hist + n_bkg) + [0] * n_hist + [1] * len(shared)
+    comp = MD_ST_COMPONENTS if stretched else MD_COMPONENTS
+    return _layout(nb, dt, rows, comp, names, free, t0_us)
 
 
 def multi_detector_theta(layout: RunLayout, rng: np.random.Generator) -> np.ndarray:
@@ -278,6 +302,14 @@ def config_multi_detector(n_hist=16, n_bins=65536, window_us=12.8, seed_offset=1
 
 # histogram lengths of the paper's Table 1 data sets (16 detectors each)
 SWEEP_BINS = (85320, 106650, 142200, 213300, 426601)
+
+
+def config_stretched(n_hist=16, n_bins=65536, window_us=12.8):
+    """16 x 65536 bins, the second line a stretched exponential, 41 free parameters
+    (seed BASE_SEED + 6)."""
+    lay = multi_detector_layout(n_hist, n_bins, window_us, stretched=True)
+    theta = multi_detector_theta(lay, rng(BASE_SEED + 6))
+    return lay, theta, BASE_SEED + 6
 
 
 def config_sweep(n_bins: int, window_us: float = 10.0):
