@@ -349,6 +349,15 @@ def other_configs(rank):
         us_v, rate_v = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
     res["multi_16x65536"] = {"poisson_grad_us": us, "poisson_grad_bin_evals_per_s": rate,
                              "chi2_value_us": us_v, "chi2_value_bin_evals_per_s": rate_v}
+    # same shape with the second line a stretched exponential exp(-(lambda t)^beta), 41 free
+    lay, theta, seed = W.config_stretched()
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
+        us, rate = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE_GRAD)
+        us_v, rate_v = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
+    res["stretched_16x65536"] = {"chi2_grad_us": us, "chi2_grad_bin_evals_per_s": rate,
+                                 "chi2_value_us": us_v, "chi2_value_bin_evals_per_s": rate_v}
     # the paper's Table 1 shapes: chi2 value per evaluation (its Table 1 times one chi2 per "Iter.")
     sweep = []
     for M in W.SWEEP_BINS:

@@ -16,6 +16,10 @@
  *   MUSR_TF_EXP          a exp(-lambda t)        cos(2 pi gamma (B + B2) t + phi)
  *   MUSR_TF_GAUSS        a exp(-(sigma t)^2 / 2) cos(2 pi gamma (B + B2) t + phi)
  *   MUSR_KT_STATIC_GAUSS a [1/3 + 2/3 (1 - (D t)^2) exp(-(D t)^2 / 2)]
+ *   MUSR_TF_STRETCHED    a ge(t, lambda, beta)   cos(2 pi gamma (B + B2) t + phi),
+ *                        ge = exp(-(lambda t)^beta) where lambda t > 0, 1 elsewhere
+ *                        (the stretched exponential "ge" of Listing 2; the
+ *                        listing's pow of a negative base is read as 1)
  *
  * Conventions shared by every entry point:
  *   - Every function returns MUSR_OK (0) or a negative status; none aborts.
@@ -29,9 +33,10 @@
  *     one run must not overlap on the GPU (they share the run's scratch).
  *   - Units: t in microseconds, fields in gauss, gamma in MHz/G, phases in
  *     radians, rates in 1/us.
- *   - Limits: map_width <= 32, at most 2 precession components (TF_EXP or
- *     TF_GAUSS) and at most one KT_STATIC_GAUSS per run, at most 2^24 bins per
- *     histogram, at most 4096 parameters.  Other layouts return MUSR_ENOTSUP.
+ *   - Limits: map_width <= 32, at most 2 precession components (TF_EXP,
+ *     TF_GAUSS or TF_STRETCHED, of which at most one TF_STRETCHED) and at most
+ *     one KT_STATIC_GAUSS per run, at most 2^24 bins per histogram, at most
+ *     4096 parameters.  Other layouts return MUSR_ENOTSUP.
  */
 #ifndef MUSR_H
 #define MUSR_H
@@ -59,7 +64,7 @@ enum {
 };
 
 /* theory component kinds */
-enum { MUSR_TF_EXP = 0, MUSR_TF_GAUSS = 1, MUSR_KT_STATIC_GAUSS = 2 };
+enum { MUSR_TF_EXP = 0, MUSR_TF_GAUSS = 1, MUSR_KT_STATIC_GAUSS = 2, MUSR_TF_STRETCHED = 3 };
 /* objectives */
 enum { MUSR_CHI2 = 0, MUSR_POISSON = 1 };
 /* data element types */
@@ -71,13 +76,15 @@ enum { MUSR_VALUE = 0, MUSR_VALUE_GRAD = 1, MUSR_VALUE_GRAD_GN = 2 };
  * One theory component.  Each field is a COLUMN of the histogram's map row
  * (not a theta index); -1 means "not used" (the quantity is 0).
  *   amp    amplitude a
- *   rate   lambda (TF_EXP), sigma (TF_GAUSS) or Delta (KT_STATIC_GAUSS)
+ *   rate   lambda (TF_EXP, TF_STRETCHED), sigma (TF_GAUSS) or Delta
+ *          (KT_STATIC_GAUSS)
  *   field  field B of the precession (TF only)
  *   field2 a second field added to B, e.g. a line splitting dB (TF only)
  *   phase  phase phi in radians (TF only)
+ *   beta   stretching exponent beta (TF_STRETCHED only; ignored otherwise)
  */
 typedef struct {
-    int32_t kind, amp, rate, field, field2, phase;
+    int32_t kind, amp, rate, field, field2, phase, beta;
 } musr_component;
 
 /*

@@ -38,12 +38,24 @@ def _torch_stream_ptr():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _comp_rows(comp) -> np.ndarray:
+    """Component table as C x 7 int32 rows (a 6-column table gets beta = -1)."""
+    c = np.asarray(comp, dtype=np.int32)
+    c = c.reshape(-1, c.shape[-1] if c.ndim == 2 and c.shape[0] else 7)
+    if c.shape[1] == 6:
+        c = np.concatenate([c, np.full((c.shape[0], 1), -1, dtype=np.int32)], axis=1)
+    if c.shape[1] != 7:
+        raise ValueError("component rows need 6 or 7 columns")
+    return np.ascontiguousarray(c)
+
+
 class Run:
     """A run: K histograms on the device plus their layout (Sec. 4.1 Eq. 1-2).
 
     ``layout`` is any object with the attributes n_bins, t0_us, dt_us,
-    tau_us, gamma, n_params, map (K x W int32) and comp (C x 6 int32:
-    kind, amp, rate, field, field2, phase map columns).  ``data`` is a numpy
+    tau_us, gamma, n_params, map (K x W int32) and comp (C x 7 int32:
+    kind, amp, rate, field, field2, phase, beta map columns; C x 6 without
+    beta is accepted).  ``data`` is a numpy
     array (FP32 / FP64) or a CUDA torch tensor of sum(n_bins) counts, or None.
     ``stream``: 'torch' to work on torch's current stream, None for a stream
     of the run's own.
@@ -54,7 +66,7 @@ class Run:
         self.layout = layout
         self._nb = np.ascontiguousarray(layout.n_bins, dtype=np.int64)
         self._map = np.ascontiguousarray(layout.map, dtype=np.int32)
-        comp = np.ascontiguousarray(layout.comp, dtype=np.int32).reshape(-1, 6)
+        comp = _comp_rows(layout.comp)
         self._comp = (_lib.musr_component * max(1, comp.shape[0]))()
         for i, row in enumerate(comp):
             self._comp[i] = _lib.musr_component(*[int(x) for x in row])

@@ -23,7 +23,7 @@ MUSR_ETIMEOUT = -6
 MUSR_ENOCONV = -7
 MUSR_ENOTSUP = -8
 
-MUSR_TF_EXP, MUSR_TF_GAUSS, MUSR_KT_STATIC_GAUSS = 0, 1, 2
+MUSR_TF_EXP, MUSR_TF_GAUSS, MUSR_KT_STATIC_GAUSS, MUSR_TF_STRETCHED = 0, 1, 2, 3
 MUSR_CHI2, MUSR_POISSON = 0, 1
 MUSR_F32, MUSR_F64 = 0, 1
 MUSR_VALUE, MUSR_VALUE_GRAD, MUSR_VALUE_GRAD_GN = 0, 1, 2
@@ -33,7 +33,7 @@ MUSR_TAU_MU_US = 2.197
 
 
 class musr_component(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("kind", "amp", "rate", "field", "field2", "phase")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("kind", "amp", "rate", "field", "field2", "phase", "beta")]
 
 
 class musr_run_desc(ctypes.Structure):

@@ -65,10 +65,9 @@ struct BatchParams {
     double* values;
 };
 
-template <int NE, int NG, int KT>
+template <int NE, int NG, int NS, int KT>
 __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p) {
-    constexpr int NOSC = NE + NG;
-    constexpr int NPART = stage_parts<NE, NG, KT>();
+    constexpr int NPART = stage_parts<NE, NG, NS, KT>();
     constexpr int G = kBinsPerThread;
     extern __shared__ unsigned char smem_raw[];
     HistConst* hcs = reinterpret_cast<HistConst*>(smem_raw);
@@ -93,7 +92,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
             const int32_t* rt = R.role_theta + (size_t)k * kMaxRoles * 2;
             for (int q = threadIdx.x; q < V * NPART; q += blockDim.x) {
                 const int v = q / NPART, part = q % NPART;
-                stage_part<NE, NG, KT>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, R.rc, hcs[v]);
+                stage_part<NE, NG, NS, KT>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, R.rc, hcs[v]);
             }
         }
         for (int v = threadIdx.x; v < V; v += blockDim.x)
@@ -118,7 +117,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
                 float acc[1] = {0.f};
                 bool bad = false;
                 if (active)
-                    eval_chunk<NE, NG, KT, kValue, 1>(hcs[v], n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr);
+                    eval_chunk<NE, NG, NS, KT, kValue, 1>(hcs[v], n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr);
                 if (bad) atomicOr(&p.flags[R.val_off + v], 1u);
                 float s = acc[0];
 #pragma unroll
@@ -165,9 +164,9 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
     }
 }
 
-template <int NE, int NG, int KT>
+template <int NE, int NG, int NS, int KT>
 cudaError_t launch_batch_sig(int blocks, int threads, size_t smem, cudaStream_t st, const BatchParams& p) {
-    auto kern = batch_kernel<NE, NG, KT>;
+    auto kern = batch_kernel<NE, NG, NS, KT>;
     // per-kernel attribute shared by every plan: raise it once to the opt-in maximum
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
@@ -185,14 +184,10 @@ cudaError_t launch_batch_sig(int blocks, int threads, size_t smem, cudaStream_t 
 
 cudaError_t launch_batch(const Signature& s, int blocks, int threads, size_t smem, cudaStream_t st,
                          const BatchParams& p) {
-#define MUSR_CASE(NE, NG, KT) \
-    if (s.ne == NE && s.ng == NG && s.kt == KT) return launch_batch_sig<NE, NG, KT>(blocks, threads, smem, st, p);
-    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
-    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
-    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
-    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
-    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
-    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+#define MUSR_CASE(NE, NG, NS, KT)                             \
+    if (s.ne == NE && s.ng == NG && s.ns == NS && s.kt == KT) \
+        return launch_batch_sig<NE, NG, NS, KT>(blocks, threads, smem, st, p);
+    MUSR_FOR_EACH_SIGNATURE(MUSR_CASE)
 #undef MUSR_CASE
     return cudaErrorInvalidValue;
 }
@@ -437,9 +432,7 @@ int musr_batch_create(const musr_run* runs, int32_t n_runs, const int32_t* max_v
     for (int r = 0; r < n_runs; ++r) {
         if (!runs[r]) return MUSR_EINVAL;
         if (max_vec[r] < 1 || max_vec[r] > kBatchMaxVec) return MUSR_ENOTSUP;
-        if (r && (runs[r]->sig.ne != runs[0]->sig.ne || runs[r]->sig.ng != runs[0]->sig.ng ||
-                  runs[r]->sig.kt != runs[0]->sig.kt))
-            return MUSR_ENOTSUP;
+        if (r && runs[r]->sig != runs[0]->sig) return MUSR_ENOTSUP;
         if (runs[r]->device != runs[0]->device) return MUSR_EINVAL;
     }
     musr_batch_s* B = new (std::nothrow) musr_batch_s();

@@ -58,6 +58,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Sum of the (up to two) theta entries a role reads (at most one FP64 add).
 __device__ __forceinline__ double role_value(const int32_t* rt, const double* theta, int r) {
     const int i0 = rt[2 * r], i1 = rt[2 * r + 1];
@@ -163,17 +169,17 @@ __device__ __forceinline__ float step_sinpi(float x) {
 //   part 1 + 2 NOSC  static Gaussian Kubo-Toyabe term
 // Only FP32 (double-float where precision matters), integer arithmetic and
 // FP32 accurate functions: no chains of FP64 operations.
-template <int NE, int NG, int KT>
+template <int NE, int NG, int NS, int KT>
 __host__ __device__ constexpr int stage_parts() {
-    return 2 + 2 * (NE + NG);
+    return 2 + 2 * (NE + NG + NS);
 }
 
 // stripe > 0: bins between a thread's consecutive chunks (for the Gaussian
 // ratio carried from chunk to chunk, see GqCarry); 0 when nothing is carried.
-template <int NE, int NG, int KT>
+template <int NE, int NG, int NS, int KT>
 __device__ void stage_part(int part, const int32_t* rt, const double* theta, const RunConst& rc,
                            HistConst& hc, int stripe = 0) {
-    constexpr int NOSC = NE + NG;
+    constexpr int NOSC = NE + NG + NS;
     const DF it = df_of(rc.inv_tau), dtL = df_of(rc.dt_log2e), dt = df_of(rc.dt);
     if (part == 0) {
         const DF n0 = df_from(role_value(rt, theta, 0));
@@ -193,7 +199,11 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
             const DF rate = df_from(role_value(rt, theta, r + 1));
             o.amp = __double2float_rn(role_value(rt, theta, r));
             o.rate = rate.hi;
-            if (c < NE) {  // exp(-(1/tau + lambda) t)
+            if (c >= NE + NG) {  // exp(-(lambda t)^beta), evaluated per bin; the rotation alone is stepped
+                o.beta = __double2float_rn(role_value(rt, theta, 2 + 4 * NOSC));
+                o.a_hi = o.a_lo = o.b_hi = o.b_lo = o.q = o.qs = 0.f;
+                o.cenv = 1.f;
+            } else if (c < NE) {  // exp(-(1/tau + lambda) t)
                 const DF rtot = df_add(it, rate);
                 const DF a = df_mul(rtot, dtL);
                 o.a_hi = a.hi;
@@ -239,7 +249,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
             o.sn = step_sinpi(2.f * red);  // sin(step)
         }
     } else if (KT && part == 2 * NOSC + 1) {
-        const int r = 2 + 4 * NOSC;
+        const int r = 2 + 4 * NOSC + NS;
         const DF dl = df_from(role_value(rt, theta, r + 1));
         const DF s2 = df_mul(dl, dl);
         hc.kt_amp = __double2float_rn(role_value(rt, theta, r));
@@ -312,13 +322,16 @@ struct GqCarry {
     bool valid;
 };
 
-template <int NE, int NG, int KT, int MODE, int NACC, bool FULL>
+template <int NE, int NG, int NS, int KT, int MODE, int NACC, bool FULL>
 __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int M,
                                                 const float (&d)[kBinsPerThread], int obj, float dtf,
                                                 float t0f, float (&acc)[NACC], bool& bad,
-                                                float* model_dst, GqCarry<NE + NG>* carry) {
-    constexpr int NOSC = NE + NG;
-    constexpr int R = 2 + 4 * NOSC + 2 * KT;
+                                                float* model_dst, GqCarry<NE + NG + NS>* carry) {
+    constexpr int NOSC = NE + NG + NS;
+    constexpr int R = 2 + 4 * NOSC + NS + 2 * KT;
+    constexpr int CS = NE + NG;    // index of the stretched line (when NS)
+    constexpr int RB = 2 + 4 * NOSC;  // role of its exponent beta
+    constexpr int RK = RB + NS;       // first Kubo-Toyabe role
     constexpr int G = kBinsPerThread;
     constexpr bool NEED_TT = KT || (NG > 0 && MODE >= kGrad);
     const float nf0 = (float)n0;
@@ -332,7 +345,12 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
     for (int c = 0; c < NOSC; ++c) {
         const OscConst& o = hc.osc[c];
         float env;
-        if (c < NE) {
+        if (NS && c >= CS) {
+            // stretched line: the rotation alone is carried, its envelope is evaluated per bin
+            env = 1.f;
+            stA[c] = o.cm1;
+            stB[c] = o.sn;
+        } else if (c < NE) {
             env = o.cenv * ex2_approx(-fmaf(nf0, o.a_hi, nf0 * o.a_lo));
             // one bin's step: (1 + q) (cos d, sin d) = (1 + A, B)
             stA[c] = fmaf(o.q, o.cm1, o.q + o.cm1);
@@ -376,9 +394,29 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
     for (int g = 0; g < G; ++g) {
         const float t = fmaf((float)g, dtf, ts);
         const float tt = NEED_TT ? t * t : 0.f;
+        // this bin's scaled rotation of every line: the carried one, or for the
+        // stretched line the rotation times e^{-t/tau} exp(-(lambda t)^beta)
+        float Cb[NOSC > 0 ? NOSC : 1], Sb[NOSC > 0 ? NOSC : 1];
+        float sp = 0.f, slg = 0.f;  // stretched line: (lambda t)^beta and log2(lambda t), 0 where lambda t <= 0
+#pragma unroll
+        for (int c = 0; c < NOSC; ++c) {
+            if (NS && c >= CS) {
+                const float u = hc.osc[c].rate * t;
+                const bool pos = u > 0.f;
+                const float lg = lg2_approx(u);
+                sp = pos ? ex2_approx(hc.osc[c].beta * lg) : 0.f;
+                slg = pos ? lg : 0.f;
+                const float ev = E * ex2_approx(-1.44269504088896341f * sp);
+                Cb[c] = ev * C[c];
+                Sb[c] = ev * Sn[c];
+            } else {
+                Cb[c] = C[c];
+                Sb[c] = Sn[c];
+            }
+        }
         float S = E;
 #pragma unroll
-        for (int c = 0; c < NOSC; ++c) S = fmaf(hc.osc[c].amp, C[c], S);
+        for (int c = 0; c < NOSC; ++c) S = fmaf(hc.osc[c].amp, Cb[c], S);
         float xk = 0.f, GE = 0.f;
         if (KT) {
             xk = kr2 * tt;
@@ -444,14 +482,20 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
                 acc[2] += wq;
 #pragma unroll
                 for (int c = 0; c < NOSC; ++c) {
-                    acc[3 + 4 * c] = fmaf(wq, C[c], acc[3 + 4 * c]);
-                    acc[4 + 4 * c] = fmaf(c < NE ? wt : wtt, C[c], acc[4 + 4 * c]);
-                    acc[5 + 4 * c] = fmaf(wt, Sn[c], acc[5 + 4 * c]);
-                    acc[6 + 4 * c] = fmaf(wq, Sn[c], acc[6 + 4 * c]);
+                    acc[3 + 4 * c] = fmaf(wq, Cb[c], acc[3 + 4 * c]);
+                    if (NS && c >= CS) {
+                        const float pc = sp * Cb[c];
+                        acc[4 + 4 * c] = fmaf(wq, pc, acc[4 + 4 * c]);
+                        acc[1 + RB] = fmaf(wq, pc * slg, acc[1 + RB]);
+                    } else {
+                        acc[4 + 4 * c] = fmaf(c < NE ? wt : wtt, Cb[c], acc[4 + 4 * c]);
+                    }
+                    acc[5 + 4 * c] = fmaf(wt, Sb[c], acc[5 + 4 * c]);
+                    acc[6 + 4 * c] = fmaf(wq, Sb[c], acc[6 + 4 * c]);
                 }
                 if (KT) {
-                    acc[3 + 4 * NOSC] = fmaf(wq, GE, acc[3 + 4 * NOSC]);
-                    acc[4 + 4 * NOSC] = fmaf(wtt, (xk - 3.f) * e23, acc[4 + 4 * NOSC]);
+                    acc[1 + RK] = fmaf(wq, GE, acc[1 + RK]);
+                    acc[2 + RK] = fmaf(wtt, (xk - 3.f) * e23, acc[2 + RK]);
                 }
             } else if (MODE == kGN) {
                 float x[R];
@@ -459,14 +503,19 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
                 x[1] = 1.f;
 #pragma unroll
                 for (int c = 0; c < NOSC; ++c) {
-                    x[2 + 4 * c] = C[c];
-                    x[3 + 4 * c] = (c < NE ? t : tt) * C[c];
-                    x[4 + 4 * c] = t * Sn[c];
-                    x[5 + 4 * c] = Sn[c];
+                    x[2 + 4 * c] = Cb[c];
+                    if (NS && c >= CS) {
+                        x[3 + 4 * c] = sp * Cb[c];
+                        x[RB] = sp * slg * Cb[c];
+                    } else {
+                        x[3 + 4 * c] = (c < NE ? t : tt) * Cb[c];
+                    }
+                    x[4 + 4 * c] = t * Sb[c];
+                    x[5 + 4 * c] = Sb[c];
                 }
                 if (KT) {
-                    x[2 + 4 * NOSC] = GE;
-                    x[3 + 4 * NOSC] = tt * (xk - 3.f) * e23;
+                    x[RK] = GE;
+                    x[RK + 1] = tt * (xk - 3.f) * e23;
                 }
 #pragma unroll
                 for (int r = 0; r < R; ++r) acc[1 + r] = fmaf(wq, x[r], acc[1 + r]);
@@ -488,7 +537,7 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
         for (int c = 0; c < NOSC; ++c) {
             const float c2 = fmaf(C[c], stA[c], fmaf(-Sn[c], stB[c], C[c]));
             const float s2 = fmaf(Sn[c], stA[c], fmaf(C[c], stB[c], Sn[c]));
-            if (c < NE) {
+            if (c < NE || c >= CS) {
                 C[c] = c2;
                 Sn[c] = s2;
             } else {
@@ -506,23 +555,23 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
 
 // carry: NULL, or the thread's GqCarry when its successive calls are one
 // stripe apart (the staged qs constants must be for that stripe)
-template <int NE, int NG, int KT, int MODE, int NACC>
+template <int NE, int NG, int NS, int KT, int MODE, int NACC>
 __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M, const float (&d)[kBinsPerThread],
                                            int obj, float dtf, float t0f, float (&acc)[NACC], bool& bad,
-                                           float* model_dst, GqCarry<NE + NG>* carry = nullptr) {
+                                           float* model_dst, GqCarry<NE + NG + NS>* carry = nullptr) {
     if (n0 + kBinsPerThread <= M)
-        eval_chunk_body<NE, NG, KT, MODE, NACC, true>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
+        eval_chunk_body<NE, NG, NS, KT, MODE, NACC, true>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
     else
-        eval_chunk_body<NE, NG, KT, MODE, NACC, false>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
+        eval_chunk_body<NE, NG, NS, KT, MODE, NACC, false>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
 }
 
 // The per-histogram constant of accumulator a (see eval_chunk): 1 for the
 // objective; -2 f_r for the gradient of role r (dN/d role = f_r x_r, the
 // accumulators hold sum (wg / -2) x_r); 2 f_r1 f_r2 for the Gauss-Newton
 // entry of roles (r1, r2) (they hold sum (wh / 2) x_r1 x_r2).
-template <int NE, int NG, int KT>
+template <int NE, int NG, int NS, int KT>
 __device__ __forceinline__ float role_factor_r(const HistConst& hc, int r) {
-    constexpr int NOSC = NE + NG;
+    constexpr int NOSC = NE + NG + NS;
     if (r < 2) return 1.f;
     const float n0p = hc.n0;
     if (r < 2 + 4 * NOSC) {
@@ -530,35 +579,45 @@ __device__ __forceinline__ float role_factor_r(const HistConst& hc, int r) {
         const OscConst& o = hc.osc[c];
         const float an = -o.amp * n0p;
         if (j == 0) return n0p;
-        if (j == 1) return c < NE ? an : o.rate * an;
+        if (j == 1) {
+            if (c < NE) return an;
+            if (c < NE + NG) return o.rate * an;
+            // stretched: d(lambda t)^beta / d lambda = beta (lambda t)^beta / lambda (x = (lambda t)^beta x
+            // the line); 0 at lambda = 0, where the envelope is 1 on both sides
+            return o.rate != 0.f ? an * o.beta / o.rate : 0.f;
+        }
         if (j == 2) return an * hc.kfreq;
         return an;
     }
-    if (r == 2 + 4 * NOSC) return n0p;
+    if (NS && r == 2 + 4 * NOSC) {
+        // stretched exponent: d(lambda t)^beta / d beta = ln 2 log2(lambda t) (lambda t)^beta
+        return -hc.osc[NE + NG].amp * n0p * 0.693147180559945309f;
+    }
+    if (r == 2 + 4 * NOSC + NS) return n0p;
     // x = t^2 (x_KT - 3) e23 with e23 = 2/3 of the envelope
     return n0p * hc.kt_amp * hc.kt_rate;
 }
 
-template <int NE, int NG, int KT, int MODE>
+template <int NE, int NG, int NS, int KT, int MODE>
 __device__ __forceinline__ float acc_factor(const HistConst& hc, int a) {
-    constexpr int R = 2 + 4 * (NE + NG) + 2 * KT;
+    constexpr int R = 2 + 4 * (NE + NG + NS) + NS + 2 * KT;
     if (a == 0 || MODE < kGrad) return 1.f;
-    if (a <= R) return -2.f * role_factor_r<NE, NG, KT>(hc, a - 1);
+    if (a <= R) return -2.f * role_factor_r<NE, NG, NS, KT>(hc, a - 1);
     // Gauss-Newton entry: upper triangle of (r1, r2), row by row
     int q = a - 1 - R, r1 = 0;
     while (q >= R - r1) {
         q -= R - r1;
         ++r1;
     }
-    return 2.f * role_factor_r<NE, NG, KT>(hc, r1) * role_factor_r<NE, NG, KT>(hc, r1 + q);
+    return 2.f * role_factor_r<NE, NG, NS, KT>(hc, r1) * role_factor_r<NE, NG, NS, KT>(hc, r1 + q);
 }
 
 
-template <int NE, int NG, int KT, int MODE>
+template <int NE, int NG, int NS, int KT, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant__ EvalParams p) {
     namespace cg = cooperative_groups;
-    constexpr int NOSC = NE + NG;
-    constexpr int R = 2 + 4 * NOSC + 2 * KT;
+    constexpr int NOSC = NE + NG + NS;
+    constexpr int R = 2 + 4 * NOSC + NS + 2 * KT;
     constexpr int NACC = MODE == kValue ? 1 : MODE == kGrad ? 1 + R : MODE == kGN ? 1 + R + R * (R + 1) / 2 : 1;
     constexpr int G = kBinsPerThread;
 
@@ -607,7 +666,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     int32_t* tbl = reinterpret_cast<int32_t*>(reinterpret_cast<DF*>(dyn_smem) + W +
                                               (p.hsum_in_smem ? p.K * NACC : 0));
     {
-        constexpr int NPART = stage_parts<NE, NG, KT>();
+        constexpr int NPART = stage_parts<NE, NG, NS, KT>();
         if (MODE != kModel && p.preload && (int)threadIdx.x >= 32 * NPART) {
             const int n1 = p.n_out + 1, n2 = p.n_src, n3 = p.n_clusters, n4 = p.K;
             const int stride = (int)blockDim.x - 32 * NPART;
@@ -624,7 +683,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
         const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
-            if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, p.rc, hc, (int)blockDim.x * G);
+            if (lane == 0) stage_part<NE, NG, NS, KT>(part, rt, theta, p.rc, hc, (int)blockDim.x * G);
     }
     __syncthreads();
 
@@ -632,7 +691,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
     bool bad = false;
-    GqCarry<NE + NG> carry;
+    GqCarry<NOSC> carry;
     carry.valid = false;
 
     for (int c = 0; c < p.chunks; ++c) {
@@ -649,7 +708,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
             for (int g = 0; g < G; ++g) dn[g] = 0.f;
         }
         if (n0 < M)
-            eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
+            eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
                                                MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
 #pragma unroll
         for (int g = 0; g < G; ++g) d[g] = dn[g];
@@ -676,7 +735,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
             DF v{red[0][a], 0.f};
             for (int w = 1; w < nwarps; ++w) v = df_add(v, DF{red[w][a], 0.f});
             // the histogram's role factor (all blocks of a cluster share the histogram)
-            if (MODE >= kGrad && a > 0) v = df_mul(v, DF{acc_factor<NE, NG, KT, MODE>(hc, a), 0.f});
+            if (MODE >= kGrad && a > 0) v = df_mul(v, DF{acc_factor<NE, NG, NS, KT, MODE>(hc, a), 0.f});
             dst[a] = v;
         }
     }
@@ -756,13 +815,13 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 // Launch the objective kernel in clusters of p.cluster blocks.  n_tiles == 0
 // only sets the kernel's shared-memory attribute (call it outside capture);
 // n_tiles < 0 only reports the kernel's resident blocks per SM.
-template <int NE, int NG, int KT, int MODE>
+template <int NE, int NG, int NS, int KT, int MODE>
 cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const EvalParams& p) {
     const size_t smem = (size_t)p.smem_bytes;
     if (n_tiles < 0) {
         // occupancy query: resident blocks per SM written to p.status_out (host int)
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<NE, NG, KT, MODE>,
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, eval_kernel<NE, NG, NS, KT, MODE>,
                                                                       threads, smem);
         *reinterpret_cast<int*>(p.status_out) = nb;
         return e;
@@ -774,12 +833,12 @@ cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const Eval
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, eval_kernel<NE, NG, KT, MODE>);
+        cudaError_t e = cudaFuncGetAttributes(&fa, eval_kernel<NE, NG, NS, KT, MODE>);
         if (e != cudaSuccess) return e;
         const int avail = optin - (int)fa.sharedSizeBytes;
         if ((int)smem > avail) return cudaErrorInvalidValue;
         if (fa.maxDynamicSharedSizeBytes >= avail) return cudaSuccess;
-        return cudaFuncSetAttribute(eval_kernel<NE, NG, KT, MODE>,
+        return cudaFuncSetAttribute(eval_kernel<NE, NG, NS, KT, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
     }
     cudaLaunchConfig_t cfg = {};
@@ -794,7 +853,7 @@ cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const Eval
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, eval_kernel<NE, NG, KT, MODE>, p);
+    return cudaLaunchKernelEx(&cfg, eval_kernel<NE, NG, NS, KT, MODE>, p);
 }
 
 }  // namespace musr

@@ -336,8 +336,7 @@ int musr_gbatch_create(const musr_run* runs, int32_t n_runs, int32_t with_gn, mu
     for (int r = 0; r < n_runs; ++r) {
         if (!runs[r] || runs[r]->K <= 0) return MUSR_EINVAL;  // a run without histograms has no items
         const Signature& s = runs[r]->sig;
-        if (s.ne != runs[0]->sig.ne || s.ng != runs[0]->sig.ng || s.kt != runs[0]->sig.kt ||
-            runs[r]->device != runs[0]->device)
+        if (s != runs[0]->sig || runs[r]->device != runs[0]->device)
             return MUSR_EINVAL;
         if (with_gn && runs[r]->P > kMaxGnParams) return MUSR_ENOTSUP;
     }

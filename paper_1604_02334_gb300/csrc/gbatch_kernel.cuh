@@ -65,12 +65,12 @@ struct GParams {
     int32_t* status;  // per run
 };
 
-template <int NE, int NG, int KT, int MODE>
+template <int NE, int NG, int NS, int KT, int MODE>
 __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_kernel(const __grid_constant__ GParams p) {
-    constexpr int NOSC = NE + NG;
-    constexpr int R = 2 + 4 * NOSC + 2 * KT;
+    constexpr int NOSC = NE + NG + NS;
+    constexpr int R = 2 + 4 * NOSC + NS + 2 * KT;
     constexpr int NACC = MODE == kGrad ? 1 + R : 1 + R + R * (R + 1) / 2;
-    constexpr int NPART = stage_parts<NE, NG, KT>();
+    constexpr int NPART = stage_parts<NE, NG, NS, KT>();
     constexpr int G = kBinsPerThread;
     extern __shared__ double hsum[];  // the run's per-histogram sums, K x NACC
     __shared__ HistConst hc;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
             const int32_t* rt = Rr.role_theta + (size_t)k * kMaxRoles * 2;
             const double* theta = p.thetas + Rr.theta_off;
             for (int part = warp; part < NPART; part += nwarps)
-                if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, Rr.rc, hc, stripe);
+                if (lane == 0) stage_part<NE, NG, NS, KT>(part, rt, theta, Rr.rc, hc, stripe);
         }
         __syncthreads();
 
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
         bool bad = false;
-        GqCarry<NE + NG> carry;
+        GqCarry<NOSC> carry;
         carry.valid = false;
         const float dtf = (float)Rr.dt, t0f = (float)Rr.t0;
         for (int row = 0; row < item.rows; ++row) {
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
                 for (int g = 0; g < G; ++g) dn[g] = 0.f;
             }
-            if (n0 < M) eval_chunk<NE, NG, KT, MODE, NACC>(hc, n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr, &carry);
+            if (n0 < M) eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr, &carry);
 #pragma unroll
             for (int g = 0; g < G; ++g) d[g] = dn[g];
             n0 = n1;
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
             double s = 0.0;
             for (int w = 0; w < nwarps; ++w) s += (double)red[w][a];
             // the histogram's role factor of this accumulator (see eval_chunk)
-            p.partial[(size_t)item_idx * NACC + a] = a > 0 ? s * (double)acc_factor<NE, NG, KT, MODE>(hc, a) : s;
+            p.partial[(size_t)item_idx * NACC + a] = a > 0 ? s * (double)acc_factor<NE, NG, NS, KT, MODE>(hc, a) : s;
         }
         __threadfence();
         __syncthreads();
@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
     }
 }
 
-template <int NE, int NG, int KT, int MODE>
+template <int NE, int NG, int NS, int KT, int MODE>
 cudaError_t launch_gbatch_sig(int blocks, int threads, size_t smem, cudaStream_t st, const GParams& p) {
-    auto kern = gbatch_kernel<NE, NG, KT, MODE>;
+    auto kern = gbatch_kernel<NE, NG, NS, KT, MODE>;
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
@@ -214,14 +214,10 @@ cudaError_t launch_gbatch_sig(int blocks, int threads, size_t smem, cudaStream_t
 template <int MODE>
 cudaError_t launch_gbatch_mode(const Signature& s, int blocks, int threads, size_t smem, cudaStream_t st,
                                const GParams& p) {
-#define MUSR_CASE(NE, NG, KT) \
-    if (s.ne == NE && s.ng == NG && s.kt == KT) return launch_gbatch_sig<NE, NG, KT, MODE>(blocks, threads, smem, st, p);
-    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
-    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
-    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
-    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
-    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
-    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+#define MUSR_CASE(NE, NG, NS, KT)                             \
+    if (s.ne == NE && s.ng == NG && s.ns == NS && s.kt == KT) \
+        return launch_gbatch_sig<NE, NG, NS, KT, MODE>(blocks, threads, smem, st, p);
+    MUSR_FOR_EACH_SIGNATURE(MUSR_CASE)
 #undef MUSR_CASE
     return cudaErrorInvalidValue;
 }

@@ -192,9 +192,9 @@ struct GenParams {
 
 // One block per (sample, histogram): stage the constants once, then each
 // thread sums the theory over its groups of `rebin` bins and draws a count.
-template <int NE, int NG, int KT>
+template <int NE, int NG, int NS, int KT>
 __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_constant__ GenParams p) {
-    constexpr int NPART = stage_parts<NE, NG, KT>();
+    constexpr int NPART = stage_parts<NE, NG, NS, KT>();
     __shared__ HistConst hc;
     const int k = blockIdx.x % p.K;
     const int64_t s = blockIdx.x / p.K;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_cons
         const double* theta = p.thetas + s * p.P;
         const int32_t* rt = p.role_theta + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
-            if (lane == 0) stage_part<NE, NG, KT>(part, rt, theta, p.rc, hc);
+            if (lane == 0) stage_part<NE, NG, NS, KT>(part, rt, theta, p.rc, hc);
     }
     __syncthreads();
     const int M = p.hist_nbins[k];
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_cons
         float acc[1] = {0.f};
         bool bad = false;
         for (int n0 = g0; n0 < g1; n0 += kBinsPerThread)
-            eval_chunk<NE, NG, KT, kSum, 1>(hc, n0, g1, zero, MUSR_CHI2, p.dt, p.t0, acc, bad, nullptr);
+            eval_chunk<NE, NG, NS, KT, kSum, 1>(hc, n0, g1, zero, MUSR_CHI2, p.dt, p.t0, acc, bad, nullptr);
         const float mu = acc[0];
         const int32_t cnt = poisson_one(mu, p.k0, p.k1, (uint32_t)j, (uint32_t)k,
                                         (uint32_t)(p.sample_offset + (uint64_t)s));
@@ -225,17 +225,12 @@ __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_cons
 }
 
 cudaError_t launch_generate(const Signature& s, int blocks, int threads, cudaStream_t st, const GenParams& p) {
-#define MUSR_CASE(NE, NG, KT)                                               \
-    if (s.ne == NE && s.ng == NG && s.kt == KT) {                           \
-        generate_kernel<NE, NG, KT><<<blocks, threads, 0, st>>>(p);         \
-        return cudaGetLastError();                                          \
+#define MUSR_CASE(NE, NG, NS, KT)                                   \
+    if (s.ne == NE && s.ng == NG && s.ns == NS && s.kt == KT) {     \
+        generate_kernel<NE, NG, NS, KT><<<blocks, threads, 0, st>>>(p); \
+        return cudaGetLastError();                                  \
     }
-    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
-    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
-    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
-    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
-    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
-    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+    MUSR_FOR_EACH_SIGNATURE(MUSR_CASE)
 #undef MUSR_CASE
     return cudaErrorInvalidValue;
 }

@@ -11,7 +11,7 @@
 namespace musr {
 
 constexpr int kMaxOsc = 2;                         // precession lines per run
-constexpr int kMaxRoles = 2 + 4 * kMaxOsc + 2;     // N0, bkg, 4 per line, 2 for KT
+constexpr int kMaxRoles = 2 + 4 * kMaxOsc + 1 + 2; // N0, bkg, 4 per line, stretching exponent, 2 for KT
 constexpr int kBinsPerThread = 8;                  // consecutive bins per thread (2 x float4)
 constexpr int kMaxThreads = 256;                   // block size upper bound
 constexpr int kMaxWarps = kMaxThreads / 32;
@@ -26,7 +26,8 @@ struct OscConst {
     // q: per-bin expm1 step of an exponential envelope; for a Gaussian
     // envelope expm1 of the per-bin change of its step ratio, 2^(-2 b) - 1
     float amp, rate, cenv, a_hi, a_lo, b_hi, b_lo, q, cm1, sn;
-    float qs;  // Gaussian envelope: 2^(-2 b stripe) - 1, the change of its step ratio over one stripe
+    float qs;    // Gaussian envelope: 2^(-2 b stripe) - 1, the change of its step ratio over one stripe
+    float beta;  // stretched envelope: exponent beta (rate holds lambda)
     unsigned long long ph0, step;  // phase at bin 0 and per bin, 64-bit fixed-point turns
 };
 
@@ -50,12 +51,90 @@ struct RunConst {
 
 // Kernel "signature": how many precession lines of each relaxation kind and
 // whether a static Gaussian Kubo-Toyabe term is present.  Exponential lines
-// come first in the kernel's role order, Gaussian lines second.
+// come first in the kernel's role order, Gaussian lines second, the stretched
+// line (at most one) third; roles: N0, bkg, 4 per line (amplitude, rate,
+// field, phase), the stretched line's exponent, then the Kubo-Toyabe pair.
 struct Signature {
-    int ne = 0, ng = 0, kt = 0;
-    int n_osc() const { return ne + ng; }
-    int roles() const { return 2 + 4 * n_osc() + 2 * kt; }
+    int ne = 0, ng = 0, ns = 0, kt = 0;
+    int n_osc() const { return ne + ng + ns; }
+    int roles() const { return 2 + 4 * n_osc() + ns + 2 * kt; }
+    bool operator==(const Signature& o) const { return ne == o.ne && ng == o.ng && ns == o.ns && kt == o.kt; }
+    bool operator!=(const Signature& o) const { return !(*this == o); }
 };
+
+// A run's components in the kernels' role order: the signature, the component
+// index of every line (exponential, Gaussian, stretched) and of the
+// Kubo-Toyabe term (-1 if none).
+struct RoleLayout {
+    Signature sig;
+    int osc[kMaxOsc] = {};
+    int kt = -1;
+};
+
+// Validate the component list against the map width and order it; MUSR_OK,
+// MUSR_EINVAL (bad kind or column) or MUSR_ENOTSUP (too many lines).
+inline int role_layout(const musr_component* comp, int n_comp, int map_width, RoleLayout& L) {
+    int e[kMaxOsc], g[kMaxOsc], st = -1;
+    L = RoleLayout{};
+    for (int c = 0; c < n_comp; ++c) {
+        const musr_component& m = comp[c];
+        const int cols[6] = {m.amp, m.rate, m.field, m.field2, m.phase, m.kind == MUSR_TF_STRETCHED ? m.beta : -1};
+        for (int j = 0; j < 6; ++j)
+            if (cols[j] < -1 || cols[j] >= map_width) return MUSR_EINVAL;
+        if (m.kind == MUSR_TF_EXP || m.kind == MUSR_TF_GAUSS || m.kind == MUSR_TF_STRETCHED) {
+            if (L.sig.n_osc() >= kMaxOsc) return MUSR_ENOTSUP;
+            if (m.kind == MUSR_TF_EXP) e[L.sig.ne++] = c;
+            else if (m.kind == MUSR_TF_GAUSS) g[L.sig.ng++] = c;
+            else if (st >= 0) return MUSR_ENOTSUP;
+            else st = c, L.sig.ns = 1;
+        } else if (m.kind == MUSR_KT_STATIC_GAUSS) {
+            if (L.kt >= 0) return MUSR_ENOTSUP;
+            L.kt = c;
+        } else {
+            return MUSR_EINVAL;
+        }
+    }
+    L.sig.kt = L.kt >= 0;
+    int n = 0;
+    for (int i = 0; i < L.sig.ne; ++i) L.osc[n++] = e[i];
+    for (int i = 0; i < L.sig.ng; ++i) L.osc[n++] = g[i];
+    if (st >= 0) L.osc[n++] = st;
+    return MUSR_OK;
+}
+
+// Role row of one histogram: rt[2 r] and rt[2 r + 1] are the theta indices
+// (or -1) whose sum is role r; map_row is the histogram's map row.
+inline void role_row(const RoleLayout& L, const musr_component* comp, const int32_t* map_row, int32_t* rt) {
+    auto col = [&](int c) { return c < 0 ? -1 : map_row[c]; };
+    for (int i = 0; i < kMaxRoles * 2; ++i) rt[i] = -1;
+    rt[0] = col(0);
+    rt[2] = col(1);
+    const int no = L.sig.n_osc();
+    for (int s = 0; s < no; ++s) {
+        const musr_component& m = comp[L.osc[s]];
+        int32_t* q = rt + 2 * (2 + 4 * s);
+        q[0] = col(m.amp);
+        q[2] = col(m.rate);
+        q[4] = col(m.field);
+        q[5] = col(m.field2);
+        q[6] = col(m.phase);
+        if (m.kind == MUSR_TF_STRETCHED) rt[2 * (2 + 4 * no)] = col(m.beta);
+    }
+    if (L.kt >= 0) {
+        const musr_component& m = comp[L.kt];
+        int32_t* q = rt + 2 * (2 + 4 * no + L.sig.ns);
+        q[0] = col(m.amp);
+        q[2] = col(m.rate);
+    }
+}
+
+// Every signature a kernel is compiled for: X(NE, NG, NS, KT) with at most
+// kMaxOsc lines of which at most one stretched, with and without the
+// Kubo-Toyabe term.
+#define MUSR_FOR_EACH_SIGNATURE(X)                                                    \
+    X(0, 0, 0, 0) X(0, 0, 0, 1) X(1, 0, 0, 0) X(1, 0, 0, 1) X(0, 1, 0, 0) X(0, 1, 0, 1) \
+    X(2, 0, 0, 0) X(2, 0, 0, 1) X(1, 1, 0, 0) X(1, 1, 0, 1) X(0, 2, 0, 0) X(0, 2, 0, 1) \
+    X(0, 0, 1, 0) X(0, 0, 1, 1) X(1, 0, 1, 0) X(1, 0, 1, 1) X(0, 1, 1, 0) X(0, 1, 1, 1)
 
 // Evaluation modes (kernel template parameter).
 enum Mode { kValue = 0, kGrad = 1, kGN = 2, kModel = 3, kSum = 4 };

@@ -60,10 +60,6 @@ std::mutex g_plan_mutex;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-int col_theta(const musr_run_desc* d, int k, int col) {
-    return col < 0 ? -1 : d->map[(int64_t)k * d->map_width + col];
-}
-
 int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
     pl.K = d->n_hist;
     pl.P = d->n_params;
@@ -72,30 +68,11 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
     if (d->n_comp > 0 && !d->comp) return MUSR_EINVAL;
     if (!(d->dt_us > 0.0) || !(d->tau_us > 0.0) || !(d->t0_us >= 0.0) || !(d->gamma_mhz_per_g >= 0.0))
         return MUSR_EINVAL;
-    int exp_c[kMaxOsc], gau_c[kMaxOsc], ne = 0, ng = 0, kt_c = -1;
-    for (int c = 0; c < d->n_comp; ++c) {
-        const musr_component& m = d->comp[c];
-        const int cols[5] = {m.amp, m.rate, m.field, m.field2, m.phase};
-        for (int j = 0; j < 5; ++j)
-            if (cols[j] < -1 || cols[j] >= d->map_width) return MUSR_EINVAL;
-        if (m.kind == MUSR_TF_EXP || m.kind == MUSR_TF_GAUSS) {
-            if (ne + ng >= kMaxOsc) return MUSR_ENOTSUP;
-            if (m.kind == MUSR_TF_EXP) exp_c[ne++] = c;
-            else gau_c[ng++] = c;
-        } else if (m.kind == MUSR_KT_STATIC_GAUSS) {
-            if (kt_c >= 0) return MUSR_ENOTSUP;
-            kt_c = c;
-        } else {
-            return MUSR_EINVAL;
-        }
-    }
-    pl.sig.ne = ne;
-    pl.sig.ng = ng;
-    pl.sig.kt = kt_c >= 0;
+    RoleLayout rl;
+    const int st = role_layout(d->comp, d->n_comp, d->map_width, rl);
+    if (st != MUSR_OK) return st;
+    pl.sig = rl.sig;
     pl.R = pl.sig.roles();
-    int osc[kMaxOsc];
-    for (int i = 0; i < ne; ++i) osc[i] = exp_c[i];
-    for (int i = 0; i < ng; ++i) osc[ne + i] = gau_c[i];
     for (int k = 0; k < pl.K; ++k) {
         if (d->n_bins[k] < 0) return MUSR_EINVAL;
         if (d->n_bins[k] > (int64_t(1) << 24)) return MUSR_ENOTSUP;
@@ -103,25 +80,7 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
             const int i = d->map[(int64_t)k * d->map_width + c];
             if (i < -1 || i >= pl.P) return MUSR_EINVAL;
         }
-        int32_t* rt = pl.role_theta + (size_t)k * kMaxRoles * 2;
-        for (int i = 0; i < kMaxRoles * 2; ++i) rt[i] = -1;
-        rt[0] = col_theta(d, k, 0);
-        rt[2] = col_theta(d, k, 1);
-        for (int s = 0; s < ne + ng; ++s) {
-            const musr_component& m = d->comp[osc[s]];
-            int32_t* q = rt + 2 * (2 + 4 * s);
-            q[0] = col_theta(d, k, m.amp);
-            q[2] = col_theta(d, k, m.rate);
-            q[4] = col_theta(d, k, m.field);
-            q[5] = col_theta(d, k, m.field2);
-            q[6] = col_theta(d, k, m.phase);
-        }
-        if (kt_c >= 0) {
-            const musr_component& m = d->comp[kt_c];
-            int32_t* q = rt + 2 * (2 + 4 * (ne + ng));
-            q[0] = col_theta(d, k, m.amp);
-            q[2] = col_theta(d, k, m.rate);
-        }
+        role_row(rl, d->comp, d->map + (int64_t)k * d->map_width, pl.role_theta + (size_t)k * kMaxRoles * 2);
     }
     // tiling: the largest block that still gives >= 2 blocks per SM, clusters of
     // up to 8 tiles with at most 25 % padding
@@ -203,16 +162,11 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
 
 cudaError_t launch_na(const Signature& s, int mode, int threads, int n_tiles, cudaStream_t st,
                       const EvalParams& p) {
-#define MUSR_CASE(NE, NG, KT)                                                     \
-    if (s.ne == NE && s.ng == NG && s.kt == KT)                                   \
-        return mode == kValue ? launch_one<NE, NG, KT, kValue>(threads, n_tiles, st, p) \
-                              : launch_one<NE, NG, KT, kGrad>(threads, n_tiles, st, p);
-    MUSR_CASE(0, 0, 0) MUSR_CASE(0, 0, 1)
-    MUSR_CASE(1, 0, 0) MUSR_CASE(1, 0, 1)
-    MUSR_CASE(0, 1, 0) MUSR_CASE(0, 1, 1)
-    MUSR_CASE(2, 0, 0) MUSR_CASE(2, 0, 1)
-    MUSR_CASE(1, 1, 0) MUSR_CASE(1, 1, 1)
-    MUSR_CASE(0, 2, 0) MUSR_CASE(0, 2, 1)
+#define MUSR_CASE(NE, NG, NS, KT)                                                          \
+    if (s.ne == NE && s.ng == NG && s.ns == NS && s.kt == KT)                                  \
+        return mode == kValue ? launch_one<NE, NG, NS, KT, kValue>(threads, n_tiles, st, p) \
+                              : launch_one<NE, NG, NS, KT, kGrad>(threads, n_tiles, st, p);
+    MUSR_FOR_EACH_SIGNATURE(MUSR_CASE)
 #undef MUSR_CASE
     return cudaErrorInvalidValue;
 }

@@ -128,12 +128,6 @@ struct DeviceGuard {
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-
-int map_col(const musr_run_s* r, int k, int col) {
-    if (col < 0) return -1;
-    return r->map[(size_t)k * r->W + col];
-}
-
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -167,50 +161,15 @@ int musr_run_s::plan(const musr_run_desc* d) {
             if (i < -1 || i >= P) return MUSR_EINVAL;
         }
     }
-    // signature: exponential lines, Gaussian lines, Kubo-Toyabe
-    std::vector<int> exp_c, gau_c;
-    int kt_c = -1;
-    for (int c = 0; c < (int)comp.size(); ++c) {
-        const musr_component& m = comp[c];
-        const int cols[5] = {m.amp, m.rate, m.field, m.field2, m.phase};
-        for (int j = 0; j < 5; ++j)
-            if (cols[j] < -1 || cols[j] >= W) return MUSR_EINVAL;
-        if (m.kind == MUSR_TF_EXP) exp_c.push_back(c);
-        else if (m.kind == MUSR_TF_GAUSS) gau_c.push_back(c);
-        else if (m.kind == MUSR_KT_STATIC_GAUSS) {
-            if (kt_c >= 0) return MUSR_ENOTSUP;
-            kt_c = c;
-        } else return MUSR_EINVAL;
-    }
-    if (exp_c.size() + gau_c.size() > (size_t)kMaxOsc) return MUSR_ENOTSUP;
-    sig.ne = (int)exp_c.size();
-    sig.ng = (int)gau_c.size();
-    sig.kt = kt_c >= 0;
+    // signature (exponential, Gaussian, stretched lines, Kubo-Toyabe) and the role -> theta table
+    RoleLayout rl;
+    const int st = role_layout(comp.data(), (int)comp.size(), W, rl);
+    if (st != MUSR_OK) return st;
+    sig = rl.sig;
     R = sig.roles();
-    // role -> theta table
     role_theta.assign((size_t)K * kMaxRoles * 2, -1);
-    std::vector<int> osc = exp_c;
-    osc.insert(osc.end(), gau_c.begin(), gau_c.end());
-    for (int k = 0; k < K; ++k) {
-        int32_t* rt = role_theta.data() + (size_t)k * kMaxRoles * 2;
-        rt[0] = map_col(this, k, 0);
-        rt[2] = map_col(this, k, 1);
-        for (int s = 0; s < (int)osc.size(); ++s) {
-            const musr_component& m = comp[osc[s]];
-            int32_t* q = rt + 2 * (2 + 4 * s);
-            q[0] = map_col(this, k, m.amp);
-            q[2] = map_col(this, k, m.rate);
-            q[4] = map_col(this, k, m.field);
-            q[5] = map_col(this, k, m.field2);
-            q[6] = map_col(this, k, m.phase);
-        }
-        if (kt_c >= 0) {
-            const musr_component& m = comp[kt_c];
-            int32_t* q = rt + 2 * (2 + 4 * (int)osc.size());
-            q[0] = map_col(this, k, m.amp);
-            q[2] = map_col(this, k, m.rate);
-        }
-    }
+    for (int k = 0; k < K; ++k)
+        role_row(rl, comp.data(), map.data() + (size_t)k * W, role_theta.data() + (size_t)k * kMaxRoles * 2);
     // data layout: every histogram at a multiple of 8 floats
     hist_off.assign(K, 0);
     model_off.assign(K, 0);

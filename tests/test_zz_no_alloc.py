@@ -47,11 +47,12 @@ def noalloc_desc(lay, data_dev):
     return d, (nb, mp, comp, data_dev)
 
 
+@pytest.mark.parametrize("stretched", [False, True])
 @pytest.mark.parametrize("obj", [MUSR_CHI2, MUSR_POISSON])
-def test_noalloc_matches_device_entry_point_twice(obj):
+def test_noalloc_matches_device_entry_point_twice(obj, stretched):
     lib = _lib.load()
     dev = torch.device("cuda:0")
-    lay, theta, seed = W.config_multi_detector(16, 5000)
+    lay, theta, seed = W.config_stretched(16, 5000) if stretched else W.config_multi_detector(16, 5000)
     d = W.poisson_counts(oracle.model(lay, theta), seed)
     data_dev = torch.tensor(d, dtype=torch.float32, device=dev)
     P = lay.n_params
