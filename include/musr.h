@@ -94,8 +94,9 @@ typedef struct {
  *   tau_us, gamma    muon lifetime and gamma_mu / 2 pi (MUSR_* defaults).
  *   n_params         length P of theta.
  *   map_width, map   K x map_width int32 row-major; map[k][c] is an index
- *                    into theta or -1 (constant 0).  Column 0 is N0 and
- *                    column 1 is Nbkg of histogram k.
+ *                    into theta, -1 (constant 0) or -2 - j for entry j of
+ *                    the function array.  Column 0 is N0 and column 1 is
+ *                    Nbkg of histogram k.
  *   n_comp, comp     the components of A_k(t); the same list for every
  *                    histogram, each histogram reading its own map row.
  *   data_dtype, data counts d, histogram-major, concatenated (sum n_bins
@@ -105,6 +106,21 @@ typedef struct {
  *   data_on_device   nonzero if data is a device pointer (copied D2D).
  *   stream           cudaStream_t the run works on; NULL = the library
  *                    creates one for the run.
+ *   n_funcs, funcs   the function array of Sec. 4.2.1 (n_funcs may be 0 and
+ *                    funcs NULL): funcs[j] is an expression over p[i]
+ *                    (theta entries, 0-based), numeric literals, + - * / ^
+ *                    ( ) and exp log sqrt sin cos tan atan abs pow, whose
+ *                    value a map entry -2 - j stands for.  The library copies
+ *                    and compiles them at create (MUSR_EINVAL on a syntax
+ *                    error or an index outside theta) and evaluates them on
+ *                    the host per call, gradients and Gauss-Newton matrices
+ *                    by the chain rule through their exact derivatives.  Runs
+ *                    with functions serve the host-pointer entry points
+ *                    (musr_chi2, musr_chi2_grad, musr_model, musr_fit,
+ *                    musr_fit_multistart); the device, batched, generator,
+ *                    proposer, user-theory and central-difference paths
+ *                    return MUSR_ENOTSUP for them.  A function value that is
+ *                    not finite gives MUSR_ENONFINITE.
  */
 typedef struct {
     int32_t n_hist;
@@ -118,9 +134,20 @@ typedef struct {
     const void* data;
     int32_t data_on_device;
     void* stream;
+    int32_t n_funcs;
+    const char* const* funcs;
 } musr_run_desc;
 
 typedef struct musr_run_s* musr_run;
+
+/*
+ * One function-array expression (the syntax of musr_run_desc.funcs) at a
+ * host parameter vector theta[n_params]: *value, and grad[n_params] (may be
+ * NULL) its exact derivatives (forward mode; 0 for entries it does not read).
+ * MUSR_EINVAL for a syntax error or an index outside theta, MUSR_ENONFINITE
+ * for a value that is not finite.  Host only; needs no GPU.
+ */
+int musr_function_eval(const char* expr, int32_t n_params, const double* theta, double* value, double* grad);
 
 /* Create a run: validates the layout, uploads the data once (Sec. 4.2) and
  * allocates the run's device scratch.  *out receives the handle. */

@@ -55,7 +55,8 @@ class Run:
     ``layout`` is any object with the attributes n_bins, t0_us, dt_us,
     tau_us, gamma, n_params, map (K x W int32) and comp (C x 7 int32:
     kind, amp, rate, field, field2, phase, beta map columns; C x 6 without
-    beta is accepted).  ``data`` is a numpy
+    beta is accepted), and optionally funcs (a list of function-array
+    expressions over p[i]; map entries -2 - j read function j).  ``data`` is a numpy
     array (FP32 / FP64) or a CUDA torch tensor of sum(n_bins) counts, or None.
     ``stream``: 'torch' to work on torch's current stream, None for a stream
     of the run's own.
@@ -80,6 +81,10 @@ class Run:
         d.map = self._map.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         d.n_comp = int(comp.shape[0])
         d.comp = ctypes.cast(self._comp, ctypes.POINTER(_lib.musr_component))
+        funcs = [str(f).encode() for f in (getattr(layout, "funcs", None) or [])]
+        self._funcs = (ctypes.c_char_p * max(1, len(funcs)))(*funcs)
+        d.n_funcs = len(funcs)
+        d.funcs = ctypes.cast(self._funcs, ctypes.POINTER(ctypes.c_char_p)) if funcs else None
         keep = None
         if data is None:
             d.data = None
@@ -325,6 +330,17 @@ def poisson_sample(mu_dev, seed, counts_dev, stream=None):
                                           int(seed) & 0xffffffffffffffff,
                                           ctypes.c_void_p(counts_dev.data_ptr()), st),
           "musr_poisson_sample")
+
+
+def function_eval(expr, theta):
+    """musr_function_eval: (value, gradient) of one function-array expression at theta (host only)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    v = ctypes.c_double()
+    g = np.zeros(th.shape[0])
+    check(_lib.load().musr_function_eval(str(expr).encode(), th.shape[0], _dptr(th) if th.shape[0] else None,
+                                         ctypes.byref(v), _dptr(g) if th.shape[0] else None),
+          "musr_function_eval")
+    return v.value, g
 
 
 def gemm_bf16(a, b, bias=None, relu=False, out_f32=None, out_bf16=None, err=None, stream=None, ws=None):

@@ -53,6 +53,8 @@ class musr_run_desc(ctypes.Structure):
         ("data", ctypes.c_void_p),
         ("data_on_device", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("n_funcs", ctypes.c_int32),
+        ("funcs", ctypes.POINTER(ctypes.c_char_p)),
     ]
 
 
@@ -173,6 +175,7 @@ SIGNATURES = {
                                         ctypes.POINTER(musr_fit_result)]),
     "musr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "musr_version": (ctypes.c_char_p, []),
+    "musr_function_eval": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int32, _vp, _vp, _vp]),
     "musr_last_cuda_error": (ctypes.c_char_p, []),
     "musr_chi2_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(musr_run_desc), ctypes.c_int, ctypes.c_int,
                                               _vp, _vp, _vp, _vp]),

@@ -431,6 +431,7 @@ int musr_batch_create(const musr_run* runs, int32_t n_runs, const int32_t* max_v
     *out = nullptr;
     for (int r = 0; r < n_runs; ++r) {
         if (!runs[r]) return MUSR_EINVAL;
+        if (runs[r]->F > 0) return MUSR_ENOTSUP;  // function values are formed per host call
         if (max_vec[r] < 1 || max_vec[r] > kBatchMaxVec) return MUSR_ENOTSUP;
         if (r && runs[r]->sig != runs[0]->sig) return MUSR_ENOTSUP;
         if (runs[r]->device != runs[0]->device) return MUSR_EINVAL;

@@ -443,7 +443,7 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
             ++ev.evals;
             return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, hd);
         }
-        if (P <= musr::kMaxGnParams) {
+        if (ev.run->Pk <= musr::kMaxGnParams) {
             std::vector<double> H((size_t)P * P);
             const int st = ev(th, kGN, f, gr, H.data());
             for (int j = 0; j < P; ++j) hd[j] = H[(size_t)j * P + j];
@@ -479,7 +479,7 @@ extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* fre
     r.n_free = (int32_t)fidx.size();
     r.ndf = (double)(run->total_bins - (int64_t)fidx.size());
     int method = o.method;
-    if (method == MUSR_FIT_LM && run->P > musr::kMaxGnParams) method = MUSR_FIT_BFGS;
+    if (method == MUSR_FIT_LM && run->Pk > musr::kMaxGnParams) method = MUSR_FIT_BFGS;
     int st;
     if (method == MUSR_FIT_LM) st = fit_lm(ev, theta, fidx, o, &r);
     else st = fit_bfgs(ev, theta, fidx, o, method == MUSR_FIT_BFGS_FD ? o.fd_rel_h : 0.0, &r);

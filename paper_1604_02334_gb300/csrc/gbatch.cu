@@ -335,6 +335,7 @@ int musr_gbatch_create(const musr_run* runs, int32_t n_runs, int32_t with_gn, mu
     *out = nullptr;
     for (int r = 0; r < n_runs; ++r) {
         if (!runs[r] || runs[r]->K <= 0) return MUSR_EINVAL;  // a run without histograms has no items
+        if (runs[r]->F > 0) return MUSR_ENOTSUP;               // function values are formed per host call
         const Signature& s = runs[r]->sig;
         if (s != runs[0]->sig || runs[r]->device != runs[0]->device)
             return MUSR_EINVAL;

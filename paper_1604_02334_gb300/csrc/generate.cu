@@ -342,6 +342,7 @@ int musr::generate_rows(musr_run run, const double* thetas_dev, int n_samples, i
                         uint64_t sample_offset, int log1p_out, float* out_dev, float* mu_dev, int64_t row_stride,
                         cudaStream_t stream) {
     if (!run || n_samples < 0 || rebin < 1) return MUSR_EINVAL;
+    if (run->F > 0) return MUSR_ENOTSUP;  // function values are formed per host call
     if (n_samples == 0 || run->K == 0) return MUSR_OK;
     if (!thetas_dev || !out_dev) return MUSR_EINVAL;
     if ((int64_t)n_samples * run->K > (int64_t)0x7fffffff) return MUSR_ENOTSUP;

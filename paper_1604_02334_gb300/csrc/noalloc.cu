@@ -64,6 +64,7 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
     pl.K = d->n_hist;
     pl.P = d->n_params;
     if (pl.K < 1 || pl.K > kNaMaxHist || pl.P < 1 || pl.P > kNaMaxParams) return MUSR_ENOTSUP;
+    if (d->n_funcs != 0) return MUSR_ENOTSUP;  // function arrays are evaluated by the host entry points
     if (d->map_width < 2 || d->map_width > 32 || d->n_comp < 0 || !d->n_bins || !d->map) return MUSR_EINVAL;
     if (d->n_comp > 0 && !d->comp) return MUSR_EINVAL;
     if (!(d->dt_us > 0.0) || !(d->tau_us > 0.0) || !(d->t0_us >= 0.0) || !(d->gamma_mhz_per_g >= 0.0))

@@ -189,6 +189,7 @@ int musr_proposer_create(musr_run layout, const double* lo, const double* hi, co
                          musr_proposer* out) {
     if (!layout || !lo || !hi || !out) return MUSR_EINVAL;
     *out = nullptr;
+    if (layout->F > 0) return MUSR_ENOTSUP;  // the generator reads parameters only
     musr_proposer_opts o;
     memset(&o, 0, sizeof(o));
     if (opts) o = *opts;

@@ -151,6 +151,16 @@ int musr_run_s::plan(const musr_run_desc* d) {
     n_bins.assign(d->n_bins, d->n_bins + K);
     map.assign(d->map, d->map + (size_t)K * W);
     comp.assign(d->comp, d->comp + d->n_comp);
+    // function array: compiled once, evaluated per call on the host
+    F = d->n_funcs;
+    if (F < 0 || (F > 0 && !d->funcs)) return MUSR_EINVAL;
+    if (F > kMaxFuncs || P + F > kMaxParams) return MUSR_ENOTSUP;
+    funcs.resize(F);
+    for (int j = 0; j < F; ++j)
+        if (compile_host_expr(d->funcs[j], P, funcs[j]) != MUSR_OK) return MUSR_EINVAL;
+    Pk = P + F;
+    // the kernels' map: entry -2 - j (function j) becomes slot P + j
+    std::vector<int32_t> kmap(map);
     total_bins = 0;
     for (int k = 0; k < K; ++k) {
         if (n_bins[k] < 0) return MUSR_EINVAL;
@@ -158,7 +168,8 @@ int musr_run_s::plan(const musr_run_desc* d) {
         total_bins += n_bins[k];
         for (int c = 0; c < W; ++c) {
             const int i = map[(size_t)k * W + c];
-            if (i < -1 || i >= P) return MUSR_EINVAL;
+            if (i < -1 - F || i >= P) return MUSR_EINVAL;
+            if (i <= -2) kmap[(size_t)k * W + c] = P + (-2 - i);
         }
     }
     // signature (exponential, Gaussian, stretched lines, Kubo-Toyabe) and the role -> theta table
@@ -169,7 +180,7 @@ int musr_run_s::plan(const musr_run_desc* d) {
     R = sig.roles();
     role_theta.assign((size_t)K * kMaxRoles * 2, -1);
     for (int k = 0; k < K; ++k)
-        role_row(rl, comp.data(), map.data() + (size_t)k * W, role_theta.data() + (size_t)k * kMaxRoles * 2);
+        role_row(rl, comp.data(), kmap.data() + (size_t)k * W, role_theta.data() + (size_t)k * kMaxRoles * 2);
     // data layout: every histogram at a multiple of 8 floats
     hist_off.assign(K, 0);
     model_off.assign(K, 0);
@@ -244,7 +255,7 @@ int musr_run_s::tail_smem(int mode, const Tiling& T, int* win, int* hsum_smem, i
 // CSR of output entry -> (histogram, accumulator) sources for one mode.
 void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const {
     const int nacc = n_acc(mode, R);
-    const int64_t n_out = 1 + (mode >= kGrad ? P : 0) + (mode == kGN ? (int64_t)P * P : 0);
+    const int64_t n_out = 1 + (mode >= kGrad ? Pk : 0) + (mode == kGN ? (int64_t)Pk * Pk : 0);
     std::vector<std::pair<int64_t, int32_t>> e;
     for (int k = 0; k < K; ++k) {
         const int32_t* rt = role_theta.data() + (size_t)k * kMaxRoles * 2;
@@ -263,8 +274,8 @@ void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int3
                         for (int j2 = 0; j2 < 2; ++j2) {
                             const int i = rt[2 * r1 + j1], jj = rt[2 * r2 + j2];
                             if (i < 0 || jj < 0) continue;
-                            e.push_back({1 + P + (int64_t)i * P + jj, base + a});
-                            if (r1 != r2) e.push_back({1 + P + (int64_t)jj * P + i, base + a});
+                            e.push_back({1 + Pk + (int64_t)i * Pk + jj, base + a});
+                            if (r1 != r2) e.push_back({1 + Pk + (int64_t)jj * Pk + i, base + a});
                         }
         }
     }
@@ -293,10 +304,10 @@ struct Arena {
 };
 
 int musr_run_s::allocate() {
-    const int nacc_max = n_acc(P <= kMaxGnParams ? kGN : kGrad, R);
+    const int nacc_max = n_acc(Pk <= kMaxGnParams ? kGN : kGrad, R);
     std::vector<int32_t> ptr[3], src[3];
     for (int m = 0; m < 3; ++m) {
-        if (m == kGN && P > kMaxGnParams) continue;
+        if (m == kGN && Pk > kMaxGnParams) continue;
         build_csr(m, ptr[m], src[m]);
         n_out[m] = (int)ptr[m].size() - 1;
         n_src[m] = (int)src[m].size();
@@ -307,7 +318,7 @@ int musr_run_s::allocate() {
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
     for (int m = 0; m < 4; ++m) {
-        if (m == kGN && P > kMaxGnParams) continue;
+        if (m == kGN && Pk > kMaxGnParams) continue;
         int t = 32;
         for (int c = kMaxThreads; c >= 32; c >>= 1) {
             int64_t tiles = 0;
@@ -333,7 +344,7 @@ int musr_run_s::allocate() {
         }
         if (m < 3) smem_bytes[m] = tail_smem(m, tl[m], &win_doubles[m], &hsum_in_smem[m], &csr_in_smem[m]);
     }
-    const int n_out_max = n_out[P <= kMaxGnParams ? kGN : kGrad];
+    const int n_out_max = n_out[Pk <= kMaxGnParams ? kGN : kGrad];
     Arena A;
     const size_t o_data = A.take<float>(data_floats);
     const size_t o_hoff = A.take<int64_t>(K + 1);
@@ -359,10 +370,10 @@ int musr_run_s::allocate() {
     const size_t o_part = A.take<double>((size_t)max_clusters * nacc_max);
     const size_t o_hsum = A.take<double>((size_t)(K + 1) * nacc_max);
     const size_t o_cnt = A.take<unsigned>(4);
-    const size_t o_theta = A.take<double>(P + 1);
+    const size_t o_theta = A.take<double>(Pk + 1);
     const size_t o_out = A.take<double>(n_out_max + 1);
     const size_t o_status = A.take<int32_t>(2);
-    const size_t o_tmp = A.take<double>(P + 1);
+    const size_t o_tmp = A.take<double>(Pk + 1);
     if (cudaMalloc(&arena, A.size) != cudaSuccess) {
         arena = nullptr;
         return MUSR_ENOMEM;
@@ -395,13 +406,13 @@ int musr_run_s::allocate() {
 
     // host staging, mapped so the kernel writes host-call results straight
     // into it (no copy node after the kernel)
-    if (cudaHostAlloc(&h_pinned, sizeof(double) * (size_t)(P + 1 + n_out_max + 1) + 64,
+    if (cudaHostAlloc(&h_pinned, sizeof(double) * (size_t)(Pk + 1 + n_out_max + 1) + 64,
                       cudaHostAllocMapped) != cudaSuccess) {
         h_pinned = nullptr;
         return MUSR_ENOMEM;
     }
     h_theta = static_cast<double*>(h_pinned);
-    h_out = h_theta + P + 1;
+    h_out = h_theta + Pk + 1;
     h_status = reinterpret_cast<int32_t*>(h_out + n_out_max + 1);
     if (cudaHostGetDevicePointer((void**)&hd_out, h_out, 0) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&hd_status, h_status, 0) != cudaSuccess)
@@ -433,7 +444,7 @@ int musr_run_s::allocate() {
     }
     // opt the kernels whose reduction tail needs > 48 KB of shared memory in
     for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
-        if (m == kGN && P > kMaxGnParams) continue;
+        if (m == kGN && Pk > kMaxGnParams) continue;
         EvalParams q = params(MUSR_CHI2, m, d_theta, d_out, d_status);
         e = launch_eval(sig, m, tl[m].threads, 0, stream, q);
     }
@@ -507,7 +518,7 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.gamma = gamma;
     p.rc = rc;
     p.K = K;
-    p.P = P;
+    p.P = Pk;
     p.obj = obj;
     p.partial = d_partial;
     p.hist_sum = d_hist_sum;
@@ -553,43 +564,100 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
 
 int musr_run_s::launch(int obj, int mode, const double* theta_dev, double* out_dev,
                        int32_t* status_dev, cudaStream_t st, float* model_out) {
-    if (mode == kGN && P > kMaxGnParams) return MUSR_ENOTSUP;
+    if (mode == kGN && Pk > kMaxGnParams) return MUSR_ENOTSUP;
     if (K == 0) return MUSR_OK;
     EvalParams p = params(obj, mode, theta_dev, out_dev, status_dev);
     p.model_out = model_out;
     return cuda_status(launch_eval(sig, mode, tl[mode].threads, tl[mode].n_tiles, st, p));
 }
 
-// Host-pointer evaluation through a cached CUDA graph.
+int musr_run_s::extend_theta(const double* theta, double* ext, std::vector<std::vector<double>>* jac) const {
+    memcpy(ext, theta, sizeof(double) * P);
+    if (jac) jac->assign(F, {});
+    for (int j = 0; j < F; ++j) {
+        const HostExpr& f = funcs[j];
+        ext[P + j] = eval_host_expr(f, theta, -1, nullptr);
+        if (!isfinite(ext[P + j])) return MUSR_ENONFINITE;
+        if (!jac) continue;
+        (*jac)[j].resize(f.refs.size());
+        for (size_t r = 0; r < f.refs.size(); ++r) eval_host_expr(f, theta, f.refs[r], &(*jac)[j][r]);
+    }
+    return MUSR_OK;
+}
+
+// Host-pointer evaluation: one launch, theta inline in the launch parameters
+// (through device memory beyond kInlineParams), results written by the kernel
+// into mapped host memory.  With a function array the kernel works on the
+// Pk = P + F slots and the results are folded back onto theta by the chain
+// rule: g = g_p + J^T g_f, H = A^T H' A with A = [I; J].
 int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags) {
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     if (mode < kValue || mode > kGN) return MUSR_EINVAL;
-    if (mode == kGN && P > kMaxGnParams) return MUSR_ENOTSUP;
+    if (mode == kGN && Pk > kMaxGnParams) return MUSR_ENOTSUP;
     for (int j = 0; j < P; ++j)
         if (!isfinite(theta[j])) return MUSR_ENONFINITE;
-    const int nout = n_out[mode];
+    const int nuser = 1 + (mode >= kGrad ? P : 0) + (mode == kGN ? P * P : 0);
     if (K == 0) {
-        memset(out_host, 0, sizeof(double) * nout);
+        memset(out_host, 0, sizeof(double) * nuser);
         *flags = 0;
         return MUSR_OK;
     }
-    // one launch: theta travels inline in the launch parameters (through device
-    // memory beyond kInlineParams), results land in mapped host memory
+    std::vector<double> ext;
+    std::vector<std::vector<double>> jac;
+    const double* th = theta;
+    if (F > 0) {
+        ext.resize(Pk);
+        const int st = extend_theta(theta, ext.data(), mode >= kGrad ? &jac : nullptr);
+        if (st != MUSR_OK) return st;
+        th = ext.data();
+    }
     EvalParams p = params(obj, mode, nullptr, hd_out, hd_status);
     cudaError_t e = cudaSuccess;
-    if (P <= kInlineParams) {
-        p.theta_inline_n = P;
-        memcpy(p.theta_inline, theta, sizeof(double) * P);
+    if (Pk <= kInlineParams) {
+        p.theta_inline_n = Pk;
+        memcpy(p.theta_inline, th, sizeof(double) * Pk);
     } else {
-        memcpy(h_theta, theta, sizeof(double) * P);
-        e = cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * P, cudaMemcpyHostToDevice, stream);
+        memcpy(h_theta, th, sizeof(double) * Pk);
+        e = cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * Pk, cudaMemcpyHostToDevice, stream);
         p.theta = d_theta;
     }
     if (e == cudaSuccess) e = launch_eval(sig, mode, tl[mode].threads, tl[mode].n_tiles, stream, p);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_status(e);
-    memcpy(out_host, h_out, sizeof(double) * nout);
     *flags = *h_status;
+    if (F == 0) {
+        memcpy(out_host, h_out, sizeof(double) * nuser);
+        return MUSR_OK;
+    }
+    out_host[0] = h_out[0];
+    if (mode == kValue) return MUSR_OK;
+    const double* g = h_out + 1;
+    double* go = out_host + 1;
+    memcpy(go, g, sizeof(double) * P);
+    for (int j = 0; j < F; ++j)
+        for (size_t r = 0; r < funcs[j].refs.size(); ++r) go[funcs[j].refs[r]] += jac[j][r] * g[P + j];
+    if (mode != kGN) return MUSR_OK;
+    const double* H = h_out + 1 + Pk;  // Pk x Pk
+    double* Ho = out_host + 1 + P;       // P x P
+    for (int a = 0; a < P; ++a) memcpy(Ho + (size_t)a * P, H + (size_t)a * Pk, sizeof(double) * P);
+    for (int j = 0; j < F; ++j) {
+        const std::vector<int>& rj = funcs[j].refs;
+        for (size_t x = 0; x < rj.size(); ++x) {
+            const int b = rj[x];
+            const double jb = jac[j][x];
+            for (int a = 0; a < P; ++a) {
+                Ho[(size_t)a * P + b] += H[(size_t)a * Pk + P + j] * jb;
+                Ho[(size_t)b * P + a] += jb * H[(size_t)(P + j) * Pk + a];
+            }
+        }
+        for (int l = 0; l < F; ++l) {
+            const double hjl = H[(size_t)(P + j) * Pk + P + l];
+            const std::vector<int>& rl = funcs[l].refs;
+            for (size_t x = 0; x < rj.size(); ++x)
+                for (size_t y = 0; y < rl.size(); ++y)
+                    Ho[(size_t)rj[x] * P + rl[y]] += jac[j][x] * jac[l][y] * hjl;
+        }
+    }
     return MUSR_OK;
 }
 
@@ -677,7 +745,7 @@ int musr_chi2_grad(musr_run run, int obj, const double* theta, double* value, do
     DeviceGuard g(run->device);
     const int mode = gn ? kGN : kGrad;
     std::vector<double> out;
-    out.resize(run->n_out[mode == kGN && run->P > kMaxGnParams ? kGrad : mode] + 1);
+    out.resize(run->n_out[mode == kGN && run->Pk > kMaxGnParams ? kGrad : mode] + 1);
     int32_t flags = 0;
     int st = run->eval_host(obj, mode, theta, out.data(), &flags);
     if (st != MUSR_OK) return st;
@@ -696,6 +764,7 @@ int musr_chi2_grad_device(musr_run run, int obj, int mode, const double* theta_d
     if (!run || !theta_dev || !out_dev) return MUSR_EINVAL;
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     if (mode < MUSR_VALUE || mode > MUSR_VALUE_GRAD_GN) return MUSR_EINVAL;
+    if (run->F > 0) return MUSR_ENOTSUP;  // function values are formed on the host
     DeviceGuard g(run->device);
     cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : run->stream;
     if (run->K == 0) {
@@ -712,7 +781,10 @@ int musr_model(musr_run run, const double* theta, float* out, int32_t out_on_dev
     for (int j = 0; j < run->P; ++j)
         if (!isfinite(theta[j])) return MUSR_ENONFINITE;
     if (run->K == 0 || run->total_bins == 0) return MUSR_OK;
-    cudaError_t e = cudaMemcpyAsync(run->d_theta_tmp, theta, sizeof(double) * run->P,
+    std::vector<double> ext(run->Pk);
+    const int fst = run->extend_theta(theta, ext.data(), nullptr);
+    if (fst != MUSR_OK) return fst;
+    cudaError_t e = cudaMemcpyAsync(run->d_theta_tmp, ext.data(), sizeof(double) * run->Pk,
                                     cudaMemcpyHostToDevice, run->stream);
     float* dst = out;
     float* tmp = nullptr;

@@ -12,6 +12,23 @@
 namespace musr {
 constexpr int kMaxParams = 4096;   // theta length
 constexpr int kMaxGnParams = 1024; // Gauss-Newton output is P x P
+constexpr int kMaxFuncs = 64;      // function array entries per run
+
+// A function-array expression compiled to a postfix program (funcs.cpp).
+struct HostExpr {
+    struct Ins {
+        int op, i;
+        double c;
+    };
+    std::vector<Ins> code;
+    std::vector<int> refs;  // theta indices it reads, ascending
+    int depth = 0;          // evaluation stack depth
+};
+// MUSR_OK or MUSR_EINVAL (syntax, or an index outside theta[0, P)).
+int compile_host_expr(const char* text, int P, HostExpr& out);
+// Value at theta; with dvar >= 0 also the derivative along theta[dvar].
+double eval_host_expr(const HostExpr& e, const double* theta, int dvar, double* deriv);
+
 // Generator body: rebinned Poisson samples of n_samples parameter vectors,
 // sample s written at out_dev + s * row_stride (row_stride 0: packed).
 int generate_rows(musr_run run, const double* thetas_dev, int n_samples, int rebin, uint64_t seed,
@@ -32,6 +49,10 @@ struct musr_run_s {
     int device = 0;
     // layout (host copy)
     int K = 0, P = 0, W = 0;
+    // function array (Sec. 4.2.1): F host expressions whose values the kernels
+    // read as parameter slots P .. P + F - 1 (Pk = P + F slots in all)
+    int F = 0, Pk = 0;
+    std::vector<musr::HostExpr> funcs;
     std::vector<int64_t> n_bins;
     std::vector<int32_t> map;
     std::vector<musr_component> comp;
@@ -98,6 +119,10 @@ struct musr_run_s {
                             int32_t* status_dev) const;
     int launch(int obj, int mode, const double* theta_dev, double* out_dev, int32_t* status_dev,
                cudaStream_t st, float* model_out);
+    // theta (P entries) -> the kernels' Pk slots, and the derivatives of the
+    // function slots (jac[j][r] = d f_j / d theta[funcs[j].refs[r]])
+    int extend_theta(const double* theta, double* ext, std::vector<std::vector<double>>* jac) const;
+    // out_host: value (+ gradient, + Gauss-Newton matrix) over the P parameters
     int eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags);
     ~musr_run_s();
 };

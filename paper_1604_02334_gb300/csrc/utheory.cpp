@@ -792,6 +792,7 @@ int musr_utheory_create(const char* expr, int32_t n_funcs, int32_t dtype, musr_u
 int musr_utheory_eval(musr_utheory th, musr_run run, int obj, const double* thetas, const double* funcs,
                       int32_t n_vec, double* values) {
     if (!run_ok_for(th, run) || n_vec < 0 || (n_vec > 0 && (!thetas || !values))) return MUSR_EINVAL;
+    if (run->F > 0) return MUSR_ENOTSUP;  // the expression takes its function array per call
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     if (th->n_funcs > 0 && n_vec > 0 && !funcs) return MUSR_EINVAL;
     if (n_vec == 0) return MUSR_OK;
@@ -808,6 +809,7 @@ int musr_utheory_eval(musr_utheory th, musr_run run, int obj, const double* thet
 int musr_utheory_grad(musr_utheory th, musr_run run, int obj, const double* theta, const double* funcs,
                       const uint8_t* free_mask, double rel_h, double* value, double* grad) {
     if (!run_ok_for(th, run) || !theta || !value || !grad) return MUSR_EINVAL;
+    if (run->F > 0) return MUSR_ENOTSUP;
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     if (th->n_funcs > 0 && !funcs) return MUSR_EINVAL;
     for (int j = 0; j < run->P; ++j)
@@ -822,6 +824,7 @@ int musr_utheory_grad(musr_utheory th, musr_run run, int obj, const double* thet
 int musr_utheory_fit(musr_utheory th, musr_run run, int obj, double* theta, const double* funcs,
                      const uint8_t* free_mask, const musr_fit_opts* opts, musr_fit_result* out) {
     if (!run_ok_for(th, run) || !theta || !out) return MUSR_EINVAL;
+    if (run->F > 0) return MUSR_ENOTSUP;
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     if (th->n_funcs > 0 && !funcs) return MUSR_EINVAL;
     musr_fit_opts o;

@@ -52,6 +52,8 @@ class RunLayout:
     comp: np.ndarray  # int32 [n_comp, 7]
     names: List[str]
     free: np.ndarray  # uint8 [n_params]
+    # function array (Sec. 4.2.1): expressions over p[i]; a map entry -2 - j reads function j
+    funcs: List[str] = dataclasses.field(default_factory=list)
 
     @property
     def n_hist(self) -> int:
