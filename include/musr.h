@@ -401,7 +401,10 @@ int musr_fit_multistart(musr_run run, int obj, const double* starts, int32_t n_s
  *   lo, hi     FP64 host [n_params]; hi_j >= lo_j; at most 128 with hi > lo.
  *   opts       NULL or zeros for the defaults: rebin 64, n_hidden 512,
  *              n_hidden_layers 3, batch 512, in_scale 1 (a factor on the
- *              standardised features), seed 1.
+ *              standardised features), seed 1, box_margin 0.25 (the
+ *              learned-start fits fall back when a learned parameter ends
+ *              outside [lo - m (hi - lo), hi + m (hi - lo)]; a very large
+ *              value turns the check off).
  * The features must number <= 2^20 after padding to a multiple of 128.
  */
 typedef struct musr_proposer_s* musr_proposer;
@@ -412,6 +415,7 @@ typedef struct {
     int32_t batch;        /* training batch, multiple of 128 */
     float in_scale;
     uint64_t seed;
+    float box_margin;
 } musr_proposer_opts;
 int musr_proposer_create(musr_run layout, const double* lo, const double* hi, const musr_proposer_opts* opts,
                          musr_proposer* out);
@@ -458,17 +462,25 @@ int musr_proposer_train(musr_proposer prop, int32_t n_steps, float lr_start, flo
  * [n_runs x n_params], learned entries clamped to [lo, hi], others lo. */
 int musr_proposer_propose(musr_proposer prop, const musr_run* runs, int32_t n_runs, double* thetas_out);
 /* Learned-start fit: propose, then musr_fit from the proposal.  If that fit
- * fails or ends with value / ndf > chi2ndf_max, musr_fit_multistart from the
- * n_fallback rows of fallback_starts follows and the better result is kept;
- * *used_fallback (may be NULL) is set to 1 then, else 0.  out->iters and
- * out->n_evals count every fit made. */
+ * fails, ends with value / ndf > chi2ndf_max, or ends with a learned
+ * parameter outside the box widened by box_margin (a basin the proposer was
+ * not trained on, e.g. two precession lines that traded places), the
+ * fallback follows in two stages, each keeping the better result:
+ * (1) musr_fit_multistart from the n_fallback rows of fallback_starts shrunk
+ * 8 times about their mean and centred on the proposal (entries the rows do
+ * not scan take the proposal's value, scanned ones are searched finely around
+ * it), at most 100 iterations per start; (2) if that gave no converged fit
+ * within chi2ndf_max and the box, musr_fit_multistart from the rows as given
+ * (the plain fit).  *used_fallback (may be NULL): 0, or the last
+ * stage run (1 or 2).  out->iters and out->n_evals count every fit made. */
 int musr_fit_learned(musr_proposer prop, musr_run run, int obj, const uint8_t* free_mask, const musr_fit_opts* opts,
                      double chi2ndf_max, const double* fallback_starts, int32_t n_fallback, double* theta_out,
                      musr_fit_result* out, int32_t* used_fallback);
 /* Learned-start fits of every run of a batch (musr_gbatch_create with
  * with_gn, runs of the proposer's layout): one network pass proposes all
- * starts, musr_fit_batch fits them in lockstep, and the runs whose fit fails
- * or ends above chi2ndf_max are refitted by musr_fit_multistart_batch from
+ * starts, musr_fit_batch fits them in lockstep, and the runs whose fit fails,
+ * ends above chi2ndf_max or leaves the widened box are refitted by
+ * musr_fit_multistart_batch in the same two stages as musr_fit_learned from
  * their fallback starts (per run n_fallback x P_r, concatenated), keeping the
  * better result.  thetas_out, results, used_fallback (NULL or one int32):
  * one per run. */

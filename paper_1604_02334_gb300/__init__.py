@@ -502,14 +502,14 @@ class Proposer:
     [lo, hi]; proposals for runs of that layout; learned-start fits."""
 
     def __init__(self, layout, lo, hi, rebin=64, n_hidden=512, n_hidden_layers=3, batch=512, in_scale=1.0,
-                 seed=1):
+                 seed=1, box_margin=0.25):
         self._lib = _lib.load()
         self.layout = layout  # keeps the layout run alive
         self.P = layout.P
         self.lo = np.ascontiguousarray(lo, dtype=np.float64)
         self.hi = np.ascontiguousarray(hi, dtype=np.float64)
         assert self.lo.shape == (self.P,) and self.hi.shape == (self.P,)
-        o = _lib.musr_proposer_opts(rebin, n_hidden, n_hidden_layers, batch, in_scale, seed)
+        o = _lib.musr_proposer_opts(rebin, n_hidden, n_hidden_layers, batch, in_scale, seed, box_margin)
         self.handle = ctypes.c_void_p()
         check(self._lib.musr_proposer_create(layout.handle, _dptr(self.lo), _dptr(self.hi), ctypes.byref(o),
                                              ctypes.byref(self.handle)), "musr_proposer_create")
@@ -601,7 +601,7 @@ class Proposer:
                                         0 if fb is None else fb.shape[0], _dptr(th), ctypes.byref(r),
                                         ctypes.byref(used))
         info = {"value": r.value, "ndf": r.ndf, "edm": r.edm, "mu": r.mu, "iters": r.iters,
-                "evals": r.n_evals, "status": st, "fallback": bool(used.value)}
+                "evals": r.n_evals, "status": st, "fallback": bool(used.value), "fallback_stage": int(used.value)}
         return th, info, cov
 
     def fit_batch(self, gbatch, obj=MUSR_CHI2, free=None, chi2ndf_max=1.2, fallback_starts=None, max_iter=500,
@@ -631,6 +631,7 @@ class Proposer:
         infos = _fit_infos(res)
         for i, u in zip(infos, used):
             i["fallback"] = bool(u)
+            i["fallback_stage"] = int(u)
         offs = gbatch.theta_off
         return [out[offs[i]:offs[i + 1]].copy() for i in range(n)], infos
 

@@ -90,6 +90,7 @@ class musr_proposer_opts(ctypes.Structure):
         ("batch", ctypes.c_int32),
         ("in_scale", ctypes.c_float),
         ("seed", ctypes.c_uint64),
+        ("box_margin", ctypes.c_float),
     ]
 
 

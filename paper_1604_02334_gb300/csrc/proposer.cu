@@ -31,6 +31,7 @@ struct musr_proposer_s {
     std::vector<int32_t> learned;
     musr_mlp mlp = nullptr;
     uint64_t seed = 1, drawn = 0;
+    double box_margin = 0.25;  // learned fits ending outside the widened box fall back
     void* arena = nullptr;
     double *d_lo = nullptr, *d_hi = nullptr, *d_thetas = nullptr;
     int32_t* d_learned = nullptr;
@@ -199,6 +200,7 @@ int musr_proposer_create(musr_run layout, const double* lo, const double* hi, co
     if (o.batch <= 0) o.batch = 512;
     if (!(o.in_scale > 0.f)) o.in_scale = 1.f;
     if (o.seed == 0) o.seed = 1;
+    if (!(o.box_margin > 0.f)) o.box_margin = 0.25f;
     if (o.batch % 128 || layout->K <= 0) return MUSR_EINVAL;
     musr_proposer p = new (std::nothrow) musr_proposer_s();
     if (!p) return MUSR_ENOMEM;
@@ -208,6 +210,7 @@ int musr_proposer_create(musr_run layout, const double* lo, const double* hi, co
     p->rebin = o.rebin;
     p->batch = o.batch;
     p->seed = o.seed;
+    p->box_margin = o.box_margin;
     p->lo.assign(lo, lo + p->P);
     p->hi.assign(hi, hi + p->P);
     for (int j = 0; j < p->P; ++j) {
@@ -410,6 +413,48 @@ int musr_proposer_propose(musr_proposer p, const musr_run* runs, int32_t n_runs,
     return st;
 }
 
+namespace {
+// every learned entry of theta inside [lo - m w, hi + m w], w = hi - lo
+bool in_widened_box(const musr_proposer_s* p, const double* theta) {
+    for (int j : p->learned) {
+        const double w = p->hi[j] - p->lo[j], m = p->box_margin * w;
+        if (!(theta[j] >= p->lo[j] - m && theta[j] <= p->hi[j] + m)) return false;
+    }
+    return true;
+}
+
+// The fallback grid (n_starts rows of P) shrunk kInformedShrink times about
+// its centre and moved onto the proposal: row i, entry j = proposal_j +
+// (grid_ij - mean_j) / kInformedShrink.  Entries the grid does not scan
+// (equal in every row) take the proposal's value; scanned ones are searched
+// finely around it.
+constexpr double kInformedShrink = 8.0;
+// iteration cap of those fits: from a start near the minimum LM converges in
+// tens of iterations; starts that wander are cut off
+constexpr int kInformedMaxIter = 100;
+
+musr_fit_opts stage_opts(const musr_fit_opts* opts, int stage) {
+    musr_fit_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (stage == 1) o.max_iter = o.max_iter > 0 ? std::min(o.max_iter, kInformedMaxIter) : kInformedMaxIter;
+    return o;
+}
+std::vector<double> informed_starts(const double* grid, int n_starts, int P, const double* proposal) {
+    std::vector<double> s((size_t)n_starts * P);
+    for (int j = 0; j < P; ++j) {
+        double mean = 0.0;
+        for (int i = 0; i < n_starts; ++i) mean += grid[(size_t)i * P + j];
+        mean /= n_starts;
+        for (int i = 0; i < n_starts; ++i) {
+            const double g = grid[(size_t)i * P + j];
+            s[(size_t)i * P + j] = g == mean ? proposal[j] : proposal[j] + (g - mean) / kInformedShrink;
+        }
+    }
+    return s;
+}
+}  // namespace
+
 int musr_fit_learned(musr_proposer p, musr_run run, int obj, const uint8_t* free_mask, const musr_fit_opts* opts,
                      double chi2ndf_max, const double* fallback_starts, int32_t n_fallback, double* theta_out,
                      musr_fit_result* out, int32_t* used_fallback) {
@@ -418,31 +463,45 @@ int musr_fit_learned(musr_proposer p, musr_run run, int obj, const uint8_t* free
     if (used_fallback) *used_fallback = 0;
     int st = musr_proposer_propose(p, &run, 1, theta_out);
     if (st != MUSR_OK) return st;
+    const std::vector<double> prop0(theta_out, theta_out + p->P);
     st = musr_fit(run, obj, theta_out, free_mask, opts, out);
-    const bool good = (st == MUSR_OK || st == MUSR_ENOCONV) && std::isfinite(out->value) && out->ndf > 0 &&
-                      out->value / out->ndf <= chi2ndf_max;
-    if (good || n_fallback == 0) return st;
+    // after the first fallback stage only a converged fit counts (its starts are cut off early)
+    auto good = [&](int s, bool converged_only = false) {
+        return (s == MUSR_OK || (!converged_only && s == MUSR_ENOCONV)) && std::isfinite(out->value) &&
+               out->ndf > 0 && out->value / out->ndf <= chi2ndf_max && in_widened_box(p, theta_out);
+    };
+    if (good(st) || n_fallback == 0) return st;
     if (st == MUSR_ECUDA || st == MUSR_ETIMEOUT) return st;
-    if (used_fallback) *used_fallback = 1;
-    const int nf = out->n_free;
-    std::vector<double> th(p->P), cov(out->cov ? (size_t)nf * nf : 0);
-    musr_fit_result r;
-    memset(&r, 0, sizeof(r));
-    r.cov = cov.empty() ? nullptr : cov.data();
-    const int st2 = musr_fit_multistart(run, obj, fallback_starts, n_fallback, free_mask, opts, th.data(), &r);
-    const int32_t iters = out->iters + r.iters, evals = out->n_evals + r.n_evals;
-    const bool first_ok = (st == MUSR_OK || st == MUSR_ENOCONV) && std::isfinite(out->value);
-    const bool second_ok = (st2 == MUSR_OK || st2 == MUSR_ENOCONV) && std::isfinite(r.value);
-    if (second_ok && (!first_ok || r.value < out->value)) {
-        double* user_cov = out->cov;
-        *out = r;
-        out->cov = user_cov;
-        if (user_cov) std::copy(cov.begin(), cov.end(), user_cov);
-        std::copy(th.begin(), th.end(), theta_out);
-        st = st2;
+    // stage 1: the fallback grid with every entry it does not scan taken from
+    // the proposal; stage 2 (if still not good): the fallback grid as given
+    for (int stage = 1; stage <= 2; ++stage) {
+        if (used_fallback) *used_fallback = stage;
+        const std::vector<double> starts = stage == 1 ? informed_starts(fallback_starts, n_fallback, p->P, prop0.data())
+                                                      : std::vector<double>(fallback_starts,
+                                                                            fallback_starts + (size_t)n_fallback * p->P);
+        const int nf = out->n_free;
+        std::vector<double> th(p->P), cov(out->cov ? (size_t)nf * nf : 0);
+        musr_fit_result r;
+        memset(&r, 0, sizeof(r));
+        r.cov = cov.empty() ? nullptr : cov.data();
+        const musr_fit_opts so = stage_opts(opts, stage);
+        const int st2 = musr_fit_multistart(run, obj, starts.data(), n_fallback, free_mask, &so, th.data(), &r);
+        if (st2 == MUSR_ECUDA || st2 == MUSR_ETIMEOUT) return st2;
+        const int32_t iters = out->iters + r.iters, evals = out->n_evals + r.n_evals;
+        const bool first_ok = (st == MUSR_OK || st == MUSR_ENOCONV) && std::isfinite(out->value);
+        const bool second_ok = (st2 == MUSR_OK || st2 == MUSR_ENOCONV) && std::isfinite(r.value);
+        if (second_ok && (!first_ok || r.value < out->value)) {
+            double* user_cov = out->cov;
+            *out = r;
+            out->cov = user_cov;
+            if (user_cov) std::copy(cov.begin(), cov.end(), user_cov);
+            std::copy(th.begin(), th.end(), theta_out);
+            st = st2;
+        }
+        out->iters = iters;
+        out->n_evals = evals;
+        if (good(st, stage == 1)) break;
     }
-    out->iters = iters;
-    out->n_evals = evals;
     return st;
 }
 
@@ -462,35 +521,48 @@ int musr_fit_learned_batch(musr_proposer p, musr_gbatch batch, int obj, const ui
     }
     int st = musr_proposer_propose(p, runs.data(), n, thetas_out);
     if (st != MUSR_OK) return st;
+    const std::vector<double> prop0(thetas_out, thetas_out + toff[n]);
     st = musr_fit_batch(batch, obj, thetas_out, free_masks, opts, results);
     if (st != MUSR_OK && st != MUSR_ENOCONV && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
-    auto good = [&](const musr_fit_result& x) {
-        return (x.status == MUSR_OK || x.status == MUSR_ENOCONV) && std::isfinite(x.value) && x.ndf > 0 &&
-               x.value / x.ndf <= chi2ndf_max;
+    // after the first fallback stage only a converged fit counts (its starts are cut off early)
+    auto good = [&](int r, bool converged_only) {
+        const musr_fit_result& x = results[r];
+        return (x.status == MUSR_OK || (!converged_only && x.status == MUSR_ENOCONV)) && std::isfinite(x.value) &&
+               x.ndf > 0 && x.value / x.ndf <= chi2ndf_max && in_widened_box(p, thetas_out + toff[r]);
     };
-    std::vector<int> bad;
-    for (int r = 0; r < n; ++r)
-        if (!good(results[r])) bad.push_back(r);
-    if (!bad.empty() && n_fallback > 0) {
+    // stage 1: the fallback grid with every entry it does not scan taken from
+    // the run's proposal; stage 2, for the runs still not good: the grid as given
+    for (int stage = 1; stage <= 2 && n_fallback > 0; ++stage) {
+        std::vector<int> bad;
+        for (int r = 0; r < n; ++r)
+            if (!good(r, stage == 2)) bad.push_back(r);
+        if (bad.empty()) break;
         std::vector<musr_run> fr;
         std::vector<double> fs, fth;
         std::vector<uint8_t> fm;
         for (int r : bad) {
             fr.push_back(runs[r]);
             const double* src = fallback_starts + toff[r] * n_fallback;
-            fs.insert(fs.end(), src, src + (size_t)runs[r]->P * n_fallback);
+            const int P = runs[r]->P;
+            if (stage == 1) {
+                const std::vector<double> s = informed_starts(src, n_fallback, P, prop0.data() + toff[r]);
+                fs.insert(fs.end(), s.begin(), s.end());
+            } else {
+                fs.insert(fs.end(), src, src + (size_t)P * n_fallback);
+            }
             if (free_masks) fm.insert(fm.end(), free_masks + toff[r], free_masks + toff[r + 1]);
-            fth.resize(fth.size() + runs[r]->P);
+            fth.resize(fth.size() + P);
         }
         std::vector<musr_fit_result> fres(bad.size());
         for (auto& x : fres) memset(&x, 0, sizeof(x));
+        const musr_fit_opts so = stage_opts(opts, stage);
         const int st2 = musr_fit_multistart_batch(fr.data(), (int32_t)fr.size(), obj, fs.data(), n_fallback,
-                                                  free_masks ? fm.data() : nullptr, opts, fth.data(), fres.data());
+                                                  free_masks ? fm.data() : nullptr, &so, fth.data(), fres.data());
         if (st2 != MUSR_OK && st2 != MUSR_ENOCONV && st2 != MUSR_EDOMAIN && st2 != MUSR_ENONFINITE) return st2;
         int64_t o = 0;
         for (size_t i = 0; i < bad.size(); ++i) {
             const int r = bad[i];
-            if (used_fallback) used_fallback[r] = 1;
+            if (used_fallback) used_fallback[r] = stage;
             const musr_fit_result& x = fres[i];
             const int32_t iters = results[r].iters + x.iters, evals = results[r].n_evals + x.n_evals;
             const bool first_ok = (results[r].status == MUSR_OK || results[r].status == MUSR_ENOCONV) &&

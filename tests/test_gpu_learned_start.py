@@ -108,3 +108,27 @@ def test_learned_fit_reaches_the_oracle_minimum(trained):
         with Run(lay, d) as r:
             _, il, _ = prop.fit(r, MUSR_CHI2, free=free, chi2ndf_max=1.2, fallback_starts=W.default_starts(lay))
         assert abs(il["value"] / il["ndf"] - oi["value"] / oi["ndf"]) <= 1e-6 * oi["value"] / oi["ndf"]
+
+
+def test_fallback_stages_keep_the_best(trained):
+    """A run whose field lies outside the prior box widened by a quarter of its
+    width: every fit ends outside it, so both fallback stages run (the grid
+    with the proposal's values for what it does not scan, then the plain
+    grid) and the result is the best of the three fits."""
+    lay, lo, hi, layout, prop, losses = trained
+    theta = W.multi_detector_theta(lay, W.rng(W.BASE_SEED + 1010))
+    theta[lay.names.index("B1")] = 700.0
+    d = W.poisson_counts(oracle.model(lay, theta), W.BASE_SEED + 1011)
+    starts = W.default_starts(lay)
+    free = lay.free
+    with Run(lay, d) as r:
+        _, il, _ = prop.fit(r, MUSR_CHI2, free=free, chi2ndf_max=1.2, fallback_starts=starts)
+        p0 = prop.propose([r])[0]
+        _, only_learned, _ = r.fit(p0, MUSR_CHI2, free=free)
+        _, only_plain, _ = r.fit_multistart(starts, MUSR_CHI2, free=free)
+        with GBatch([r]) as b:
+            _, ib = prop.fit_batch(b, MUSR_CHI2, free=[free], chi2ndf_max=1.2, fallback_starts=[starts])
+    assert il["fallback_stage"] == 2 and ib[0]["fallback_stage"] == 2
+    best = min(only_learned["value"], only_plain["value"])
+    assert il["value"] <= best * (1 + 1e-9)
+    assert ib[0]["value"] <= best * (1 + 1e-6)
