@@ -45,11 +45,17 @@ WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi
 # instructions, i.e. (2 x 73.34 + 28.45) x 32 / 67.108864 = 83.5 FLOP / bin
 # (FMA = 2).  The single-run kernel executes the same per-bin code.
 FLOPS_PER_BIN_GRAD = 83.5
-# DRAM bytes (read + write) of one eval_kernel<1,1,1,kGrad> launch of this
+# DRAM bytes (read + write) of one eval_kernel<1,1,0,1,kGrad> launch of this
 # workload, from the ncu capture summarised in
 # profiles/eval_kernel_grad_16x65536.md (4.28 MB read, 0 written); to be
 # re-measured whenever that kernel changes.
 TRAFFIC_BYTES_GRAD_LAUNCH = 4278784
+# FP32-pipe FLOPs per bin-evaluation of the value-only batched kernel on the
+# 64-run workload (batch_kernel<1,1,0,1>), counted by ncu on one launch of
+# 2,720,958,581 bin-evaluations: 1978.5 M FFMA and 902.0 M other FP32 warp
+# instructions, (2 x 1978.5 + 902.0) x 32 / 2720.96 = 57.1 FLOP per
+# bin-evaluation (profiles/batch_kernel_value_64runs.md).
+FLOPS_PER_BINEVAL_VALUE_BATCH = 57.1
 SMS = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
@@ -268,9 +274,14 @@ def batched_throughput(dev, rank, reps=5):
     b.close()
     for g in gruns:
         g.close()
+    peak = fp32_peak_tflops()
+    achieved = FLOPS_PER_BINEVAL_VALUE_BATCH * binevals / (med * 1e-3) / 1e12
     return {"workload": "64 runs, K~U{1..32} x M~U[2^14,2^17] bins, P+1 vectors each",
             "bins": int(sum(br.layout.total_bins for br in runs)), "bin_evals": int(binevals),
-            "ms": med, "value": binevals / (med * 1e-3), "unit": "bin-evals/s (chi2, value only)"}
+            "ms": med, "value": binevals / (med * 1e-3), "unit": "bin-evals/s (chi2, value only)",
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "kernel": "batch_kernel<1,1,0,1>",
+                         "note": "host-timed (includes the launch), L2 flushed before each"}}
 
 
 def _device_rate(run, theta, obj, mode, reps=50):
@@ -475,7 +486,7 @@ def batched_grad_throughput(dev, rank, n_runs=64, reps=5):
     return {"workload": f"{n_runs} runs x 16 hist x 65536 bins, chi2 + gradient, one launch", "bin_evals": bins,
             "ms": med, "value": bins / (med * 1e-3), "unit": "bin-evals/s",
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "kernel": "gbatch_kernel<1,1,1,kGrad>"}}
+                         "frac": achieved / peak, "kernel": "gbatch_kernel<1,1,0,1,kGrad>"}}
 
 
 def learned_start_ab(dev, rank, train_steps, n_runs=64):
@@ -656,7 +667,7 @@ def run_ours(args):
                    "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": TRAFFIC_BYTES_GRAD_LAUNCH,
-                     "kernel": "eval_kernel<1,1,1,kGrad>",
+                     "kernel": "eval_kernel<1,1,0,1,kGrad>",
                      "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
         "clocks": clk,
         "e2e": e2e,
