@@ -459,7 +459,9 @@ int musr_run_s::upload(int dtype, const void* data, int on_device) {
     if (dtype != MUSR_F32 && dtype != MUSR_F64) return MUSR_EINVAL;
     cudaError_t e = cudaSuccess;
     if (!on_device) {
-        // straight per-histogram copies into the padded layout (padding stays 0)
+        // straight copies into the padded layout (padding stays 0): consecutive
+        // histograms whose device and host offsets differ by the same amount
+        // (every one before them a multiple of 8 bins long) go in one copy
         const float* src = static_cast<const float*>(data);
         std::vector<float> conv;
         if (dtype == MUSR_F64) {
@@ -468,13 +470,27 @@ int musr_run_s::upload(int dtype, const void* data, int on_device) {
             for (int64_t i = 0; i < total_bins; ++i) conv[i] = (float)d64[i];
             src = conv.data();
         }
-        int64_t s = 0;
-        for (int k = 0; k < K && e == cudaSuccess; ++k) {
-            if (n_bins[k])
-                e = cudaMemcpyAsync(d_data + hist_off[k], src + s, sizeof(float) * n_bins[k],
+        int64_t s = 0, run_src = 0, run_dst = 0, run_len = 0;
+        auto flush = [&]() {
+            if (run_len > 0 && e == cudaSuccess)
+                e = cudaMemcpyAsync(d_data + run_dst, src + run_src, sizeof(float) * run_len,
                                     cudaMemcpyHostToDevice, stream);
+            run_len = 0;
+        };
+        for (int k = 0; k < K; ++k) {
+            if (n_bins[k]) {
+                if (run_len > 0 && hist_off[k] == run_dst + run_len && s == run_src + run_len) {
+                    run_len += n_bins[k];
+                } else {
+                    flush();
+                    run_src = s;
+                    run_dst = hist_off[k];
+                    run_len = n_bins[k];
+                }
+            }
             s += n_bins[k];
         }
+        flush();
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         return cuda_status(e);
     }
