@@ -469,9 +469,9 @@ int musr_proposer_propose(musr_proposer prop, const musr_run* runs, int32_t n_ru
  * (1) musr_fit_multistart from the n_fallback rows of fallback_starts shrunk
  * 8 times about their mean and centred on the proposal (entries the rows do
  * not scan take the proposal's value, scanned ones are searched finely around
- * it), at most 100 iterations per start; (2) if that gave no converged fit
- * within chi2ndf_max and the box, musr_fit_multistart from the rows as given
- * (the plain fit).  *used_fallback (may be NULL): 0, or the last
+ * it), at most 100 iterations per start, the first start that converges
+ * within chi2ndf_max and the box ending the stage; (2) if that gave no such
+ * fit, musr_fit_multistart from the rows as given (the plain fit).  *used_fallback (may be NULL): 0, or the last
  * stage run (1 or 2).  out->iters and out->n_evals count every fit made. */
 int musr_fit_learned(musr_proposer prop, musr_run run, int obj, const uint8_t* free_mask, const musr_fit_opts* opts,
                      double chi2ndf_max, const double* fallback_starts, int32_t n_fallback, double* theta_out,

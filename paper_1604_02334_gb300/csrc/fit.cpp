@@ -629,8 +629,15 @@ static int fit_batch_bfgs(musr_gbatch b, int obj, double* thetas, const uint8_t*
     return worst;
 }
 
-extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks,
-                              const musr_fit_opts* opts, musr_fit_result* results) {
+namespace {
+
+// The lockstep fit of every entry of a batch.  group / accept (both null, or
+// both set): when entry r's LM fit converges and accept(r, theta, value)
+// holds, the other entries of group[r] still running stop where they are
+// (status MUSR_ENOCONV).
+int fit_batch_impl(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks, const musr_fit_opts* opts,
+                   musr_fit_result* results, const std::vector<int>* group,
+                   const std::function<bool(int, const double*, double)>* accept) {
     if (!b || !thetas || !results) return MUSR_EINVAL;
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     musr_fit_opts o;
@@ -681,6 +688,7 @@ extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint
         if (status[r] == MUSR_OK) lm[r].start(f);
         else lm[r].done = true;
     }
+    std::vector<uint8_t> seen_done(n, 0);
     for (;;) {
 #pragma omp parallel for schedule(dynamic, 1) if (n >= 8)
         for (int r = 0; r < n; ++r) {
@@ -688,6 +696,20 @@ extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint
             if (active[r]) {
                 memcpy(work.data() + gbatch_theta_offset(b, r), lm[r].trial.data(), sizeof(double) * lm[r].P);
                 ++evals[r];
+            }
+        }
+        if (group && accept) {
+            // a converged entry the caller accepts stops the rest of its group
+            for (int r = 0; r < n; ++r) {
+                if (active[r] || seen_done[r]) continue;
+                seen_done[r] = 1;
+                if (status[r] != MUSR_OK || lm[r].result != MUSR_OK || !(*accept)(r, lm[r].theta.data(), lm[r].f))
+                    continue;
+                for (int q = 0; q < n; ++q)
+                    if (q != r && (*group)[q] == (*group)[r] && !lm[q].done) {
+                        lm[q].done = true;
+                        active[q] = 0;
+                    }
             }
         }
         int n_active = 0;
@@ -725,9 +747,27 @@ extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint
     return worst;
 }
 
+}  // namespace
+
+extern "C" int musr_fit_batch(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks,
+                              const musr_fit_opts* opts, musr_fit_result* results) {
+    return fit_batch_impl(b, obj, thetas, free_masks, opts, results, nullptr, nullptr);
+}
+
 extern "C" int musr_fit_multistart_batch(const musr_run* runs, int32_t n_runs, int obj, const double* starts,
                                          int32_t n_starts, const uint8_t* free_masks, const musr_fit_opts* opts,
                                          double* thetas_out, musr_fit_result* results) {
+    return musr::fit_multistart_batch_accept(runs, n_runs, obj, starts, n_starts, free_masks, opts, nullptr,
+                                             thetas_out, results);
+}
+
+// musr_fit_multistart_batch; with accept (LM only), the first converged start
+// of run r that accept(r, theta, value) takes ends r's other starts and is r's
+// result.
+int musr::fit_multistart_batch_accept(const musr_run* runs, int n_runs, int obj, const double* starts, int n_starts,
+                                      const uint8_t* free_masks, const musr_fit_opts* opts,
+                                      const std::function<bool(int, const double*, double)>* accept,
+                                      double* thetas_out, musr_fit_result* results) {
     if (!runs || n_runs <= 0 || !starts || n_starts <= 0 || !thetas_out || !results) return MUSR_EINVAL;
     // entry e = (run r, start s), e = r * n_starts + s
     std::vector<musr_run> entries;
@@ -753,7 +793,16 @@ extern "C" int musr_fit_multistart_batch(const musr_run* runs, int32_t n_runs, i
     if (st != MUSR_OK) return st;
     std::vector<musr_fit_result> res(entries.size());
     for (auto& x : res) memset(&x, 0, sizeof(x));
-    st = musr_fit_batch(b, obj, th.data(), fm.data(), opts, res.data());
+    std::vector<int> group(entries.size());
+    for (size_t e = 0; e < entries.size(); ++e) group[e] = (int)(e / n_starts);
+    std::vector<uint8_t> taken(entries.size(), 0);
+    std::function<bool(int, const double*, double)> on_converged = [&](int e, const double* theta, double f) {
+        if (!(*accept)(group[e], theta, f)) return false;
+        taken[e] = 1;
+        return true;
+    };
+    st = fit_batch_impl(b, obj, th.data(), fm.data(), opts, res.data(), accept ? &group : nullptr,
+                        accept ? &on_converged : nullptr);
     musr_gbatch_destroy(b);
     if (st != MUSR_OK && st != MUSR_ENOCONV && st != MUSR_EDOMAIN && st != MUSR_ENONFINITE) return st;
     int worst = MUSR_OK;
@@ -769,6 +818,8 @@ extern "C" int musr_fit_multistart_batch(const musr_run* runs, int32_t n_runs, i
             const bool ok = (x.status == MUSR_OK || x.status == MUSR_ENOCONV) && std::isfinite(x.value);
             if (ok && (best < 0 || x.value < res[(size_t)r * n_starts + best].value)) best = s;
         }
+        for (int s = 0; s < n_starts; ++s)
+            if (taken[(size_t)r * n_starts + s]) best = s;  // the accepted start ends the run's search
         double* cov = results[r].cov;
         if (best < 0) {
             memset(&results[r], 0, sizeof(musr_fit_result));

@@ -485,7 +485,37 @@ int musr_fit_learned(musr_proposer p, musr_run run, int obj, const uint8_t* free
         memset(&r, 0, sizeof(r));
         r.cov = cov.empty() ? nullptr : cov.data();
         const musr_fit_opts so = stage_opts(opts, stage);
-        const int st2 = musr_fit_multistart(run, obj, starts.data(), n_fallback, free_mask, &so, th.data(), &r);
+        int st2;
+        if (stage == 1) {
+            // one start after the other; the first converged fit within the threshold and the box ends the stage
+            st2 = MUSR_ENOCONV;
+            r.value = INFINITY;
+            std::vector<double> t(p->P), c(cov.size());
+            for (int i = 0; i < n_fallback; ++i) {
+                std::copy(starts.begin() + (size_t)i * p->P, starts.begin() + (size_t)(i + 1) * p->P, t.begin());
+                musr_fit_result ri;
+                memset(&ri, 0, sizeof(ri));
+                ri.cov = c.empty() ? nullptr : c.data();
+                const int si = musr_fit(run, obj, t.data(), free_mask, &so, &ri);
+                if (si == MUSR_ECUDA || si == MUSR_ETIMEOUT) return si;
+                const int32_t it_sum = r.iters + ri.iters, ev_sum = r.n_evals + ri.n_evals;
+                const bool ok = (si == MUSR_OK || si == MUSR_ENOCONV) && std::isfinite(ri.value);
+                const bool accepted = si == MUSR_OK && ri.ndf > 0 && ri.value / ri.ndf <= chi2ndf_max &&
+                                      in_widened_box(p, t.data());
+                if (ok && (accepted || ri.value < r.value)) {
+                    r = ri;
+                    r.cov = cov.empty() ? nullptr : cov.data();
+                    std::copy(c.begin(), c.end(), cov.begin());
+                    std::copy(t.begin(), t.end(), th.begin());
+                    st2 = si;
+                }
+                r.iters = it_sum;
+                r.n_evals = ev_sum;
+                if (accepted) break;
+            }
+        } else {
+            st2 = musr_fit_multistart(run, obj, starts.data(), n_fallback, free_mask, &so, th.data(), &r);
+        }
         if (st2 == MUSR_ECUDA || st2 == MUSR_ETIMEOUT) return st2;
         const int32_t iters = out->iters + r.iters, evals = out->n_evals + r.n_evals;
         const bool first_ok = (st == MUSR_OK || st == MUSR_ENOCONV) && std::isfinite(out->value);
@@ -556,8 +586,23 @@ int musr_fit_learned_batch(musr_proposer p, musr_gbatch batch, int obj, const ui
         std::vector<musr_fit_result> fres(bad.size());
         for (auto& x : fres) memset(&x, 0, sizeof(x));
         const musr_fit_opts so = stage_opts(opts, stage);
-        const int st2 = musr_fit_multistart_batch(fr.data(), (int32_t)fr.size(), obj, fs.data(), n_fallback,
-                                                  free_masks ? fm.data() : nullptr, &so, fth.data(), fres.data());
+        // stage 1: a run's first converged start within the threshold and the box ends its search
+        std::vector<double> ndf(bad.size());
+        for (size_t i = 0; i < bad.size(); ++i) {
+            const int r = bad[i];
+            int nfree = runs[r]->P;
+            if (free_masks) {
+                nfree = 0;
+                for (int j = 0; j < runs[r]->P; ++j) nfree += free_masks[toff[r] + j] ? 1 : 0;
+            }
+            ndf[i] = (double)(runs[r]->total_bins - nfree);
+        }
+        const std::function<bool(int, const double*, double)> accept = [&](int i, const double* th, double f) {
+            return std::isfinite(f) && ndf[i] > 0 && f / ndf[i] <= chi2ndf_max && in_widened_box(p, th);
+        };
+        const int st2 = musr::fit_multistart_batch_accept(fr.data(), (int)fr.size(), obj, fs.data(), n_fallback,
+                                                          free_masks ? fm.data() : nullptr, &so,
+                                                          stage == 1 ? &accept : nullptr, fth.data(), fres.data());
         if (st2 != MUSR_OK && st2 != MUSR_ENOCONV && st2 != MUSR_EDOMAIN && st2 != MUSR_ENONFINITE) return st2;
         int64_t o = 0;
         for (size_t i = 0; i < bad.size(); ++i) {
