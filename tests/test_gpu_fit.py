@@ -66,3 +66,27 @@ def test_quasi_newton_fits_reach_the_same_minimum(method):
     sig = np.sqrt(np.diag(cov_o))
     assert np.max(np.abs(th_g - th_o) / sig) <= 0.05
     assert rel_err(info_g["value"], info_o["value"]) <= 1e-6
+
+
+def test_fit_pulls_are_unit_normal():
+    """GPU deviance fits of 200 Poisson realisations of the single-histogram run
+    (2048 bins), started at the truth: the pulls (theta_hat - theta_true) /
+    sigma_hat have mean ~0 and spread ~1 (bounds ~4.5 standard errors) and pass
+    a KS test against N(0, 1) for every parameter."""
+    from scipy import stats
+    lay, theta, _ = W.config_single()
+    lay.n_bins = np.array([2048])
+    lay.dt_us = 0.005
+    mean = oracle.model(lay, theta)
+    pulls = []
+    with Run(lay, np.zeros(2048)) as run:
+        for s in range(200):
+            run.set_data(W.poisson_counts(mean, 5000 + s))
+            th, info, cov = run.fit(theta, MUSR_POISSON)
+            assert info["status"] == 0
+            pulls.append((th - theta) / np.sqrt(np.diag(cov)))
+    pulls = np.array(pulls)
+    assert np.all(np.abs(pulls.mean(0)) < 0.32)
+    assert np.all(np.abs(pulls.std(0) - 1.0) < 0.22)
+    for j in range(pulls.shape[1]):
+        assert stats.kstest(pulls[:, j], "norm").pvalue > 1e-3
