@@ -472,8 +472,8 @@ int musr_fit_learned(musr_proposer p, musr_run run, int obj, const uint8_t* free
     };
     if (good(st) || n_fallback == 0) return st;
     if (st == MUSR_ECUDA || st == MUSR_ETIMEOUT) return st;
-    // stage 1: the fallback grid with every entry it does not scan taken from
-    // the proposal; stage 2 (if still not good): the fallback grid as given
+    // stage 1: the fallback grid shrunk onto the proposal (informed_starts);
+    // stage 2 (if still not good): the fallback grid as given
     for (int stage = 1; stage <= 2; ++stage) {
         if (used_fallback) *used_fallback = stage;
         const std::vector<double> starts = stage == 1 ? informed_starts(fallback_starts, n_fallback, p->P, prop0.data())
@@ -560,8 +560,8 @@ int musr_fit_learned_batch(musr_proposer p, musr_gbatch batch, int obj, const ui
         return (x.status == MUSR_OK || (!converged_only && x.status == MUSR_ENOCONV)) && std::isfinite(x.value) &&
                x.ndf > 0 && x.value / x.ndf <= chi2ndf_max && in_widened_box(p, thetas_out + toff[r]);
     };
-    // stage 1: the fallback grid with every entry it does not scan taken from
-    // the run's proposal; stage 2, for the runs still not good: the grid as given
+    // stage 1: the fallback grid shrunk onto the run's proposal (informed_starts);
+    // stage 2, for the runs still not good: the grid as given
     for (int stage = 1; stage <= 2 && n_fallback > 0; ++stage) {
         std::vector<int> bad;
         for (int r = 0; r < n; ++r)
