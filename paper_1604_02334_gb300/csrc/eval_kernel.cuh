@@ -797,18 +797,26 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         cptr = sp;
         csrc = sp + p.n_out + 1;
     }
+    double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
     for (int o = threadIdx.x; o < p.n_out; o += blockDim.x) {
         DF s{0.f, 0.f};
         const int e = cptr[o + 1];
         for (int j = cptr[o]; j < e; ++j) s = df_add(s, hsum[csrc[j]]);
-        p.out[o] = (double)s.hi + (double)s.lo;  // exact: |lo| <= ulp(hi) / 2
+        const double v = (double)s.hi + (double)s.lo;  // exact: |lo| <= ulp(hi) / 2
+        p.out[o] = v;
+        if (o == 0) out0 = v;
     }
+    // results in mapped host memory: visible to the host before the status that announces them
+    if (p.status_sys_fence) __threadfence_system();
     __syncthreads();
     if (threadIdx.x == 0) {
         *p.global_count = 0u;
         unsigned f = atomicExch(p.flags, 0u);
-        if (!isfinite(p.out[0])) f |= 2u;
-        if (p.status_out) *p.status_out = (int32_t)f;
+        if (!isfinite(out0)) f |= 2u;
+        if (p.status_out) {
+            if (p.status_sys_fence) __threadfence_system();
+            *reinterpret_cast<volatile int32_t*>(p.status_out) = (int32_t)f;
+        }
     }
 }
 

@@ -176,6 +176,7 @@ struct EvalParams {
     int smem_bytes;               // dynamic shared memory of the objective kernel
     double* out;                  // [n_out]
     int32_t* status_out;          // [1] or null
+    int status_sys_fence;         // 1: out / status_out are mapped host memory the host polls
     int theta_inline_n;           // > 0: theta_inline holds theta (host calls)
     double theta_inline[kInlineParams];
     // Equal-length histograms (the common layout): tile b belongs to histogram

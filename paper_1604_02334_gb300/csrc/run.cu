@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <new>
 #include <utility>
 #include <vector>
@@ -127,6 +128,11 @@ struct DeviceGuard {
 };
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// host calls: the status word's value while the kernel runs, and how long the
+// host polls it before it blocks in a stream synchronisation instead
+constexpr int32_t kStatusPending = INT32_MIN;
+constexpr int kStatusSpinUs = 2000;
 
 }  // namespace
 
@@ -637,10 +643,24 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
         e = cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * Pk, cudaMemcpyHostToDevice, stream);
         p.theta = d_theta;
     }
+    // the kernel's last block writes the status word after the results: poll it
+    // (a short bounded spin, then a blocking stream synchronisation)
+    p.status_sys_fence = 1;
+    __atomic_store_n(h_status, kStatusPending, __ATOMIC_RELAXED);
     if (e == cudaSuccess) e = launch_eval(sig, mode, tl[mode].threads, tl[mode].n_tiles, stream, p);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    bool seen = false;
+    if (e == cudaSuccess) {
+        const auto t0 = std::chrono::steady_clock::now();
+        for (int spin = 0; !seen; ++spin) {
+            seen = __atomic_load_n(h_status, __ATOMIC_ACQUIRE) != kStatusPending;
+            if (!seen && (spin & 255) == 255 &&
+                std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(kStatusSpinUs))
+                break;
+        }
+        if (!seen) e = cudaStreamSynchronize(stream);
+    }
     if (e != cudaSuccess) return cuda_status(e);
-    *flags = *h_status;
+    *flags = __atomic_load_n(h_status, __ATOMIC_ACQUIRE);
     if (F == 0) {
         memcpy(out_host, h_out, sizeof(double) * nuser);
         return MUSR_OK;
