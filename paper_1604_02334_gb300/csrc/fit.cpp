@@ -543,8 +543,10 @@ extern "C" int musr_fit_multistart(musr_run run, int obj, const double* starts, 
 // BFGS fits of every run of a batch in lockstep: the start evaluation gives
 // the Hessian diagonal (Gauss-Newton mode when the batch has it), then one
 // batched value + gradient launch per round of line-search trials.
+// group / accept: as for the lockstep LM (fit_batch_impl)
 static int fit_batch_bfgs(musr_gbatch b, int obj, double* thetas, const uint8_t* free_masks,
-                          const musr_fit_opts& o, musr_fit_result* results) {
+                          const musr_fit_opts& o, musr_fit_result* results, const std::vector<int>* group = nullptr,
+                          const std::function<bool(int, const double*, double)>* accept = nullptr) {
     const int n = gbatch_n_runs(b);
     std::vector<BfgsStepper> bf(n);
     std::vector<int32_t> flags(n, 0), evals(n, 1);
@@ -582,6 +584,7 @@ static int fit_batch_bfgs(musr_gbatch b, int obj, double* thetas, const uint8_t*
             for (int j = 0; j < P; ++j) hd[j] = src[1 + P + (size_t)j * P + j];
         bf[r].start(src[0], hd.data());
     }
+    std::vector<uint8_t> seen_done(n, 0);
     for (;;) {
 #pragma omp parallel for schedule(dynamic, 1) if (n >= 8)
         for (int r = 0; r < n; ++r) {
@@ -589,6 +592,19 @@ static int fit_batch_bfgs(musr_gbatch b, int obj, double* thetas, const uint8_t*
             if (active[r]) {
                 memcpy(work.data() + gbatch_theta_offset(b, r), bf[r].x.data(), sizeof(double) * bf[r].P);
                 ++evals[r];
+            }
+        }
+        if (group && accept) {
+            for (int r = 0; r < n; ++r) {
+                if (active[r] || seen_done[r]) continue;
+                seen_done[r] = 1;
+                if (status[r] != MUSR_OK || bf[r].result != MUSR_OK || !(*accept)(r, bf[r].theta.data(), bf[r].f))
+                    continue;
+                for (int q = 0; q < n; ++q)
+                    if (q != r && (*group)[q] == (*group)[r] && !bf[q].done) {
+                        bf[q].done = true;
+                        active[q] = 0;
+                    }
             }
         }
         int n_active = 0;
@@ -646,7 +662,7 @@ int fit_batch_impl(musr_gbatch b, int obj, double* thetas, const uint8_t* free_m
     if (o.max_iter <= 0) o.max_iter = 500;
     if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
     if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
-    if (o.method == MUSR_FIT_BFGS) return fit_batch_bfgs(b, obj, thetas, free_masks, o, results);
+    if (o.method == MUSR_FIT_BFGS) return fit_batch_bfgs(b, obj, thetas, free_masks, o, results, group, accept);
     if (o.method != MUSR_FIT_LM) return MUSR_ENOTSUP;
     if (!gbatch_has_gn(b)) return MUSR_EINVAL;
     const int n = gbatch_n_runs(b);
@@ -761,7 +777,7 @@ extern "C" int musr_fit_multistart_batch(const musr_run* runs, int32_t n_runs, i
                                              thetas_out, results);
 }
 
-// musr_fit_multistart_batch; with accept (LM only), the first converged start
+// musr_fit_multistart_batch; with accept, the first converged start
 // of run r that accept(r, theta, value) takes ends r's other starts and is r's
 // result.
 int musr::fit_multistart_batch_accept(const musr_run* runs, int n_runs, int obj, const double* starts, int n_starts,

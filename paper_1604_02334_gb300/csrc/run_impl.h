@@ -44,7 +44,7 @@ int sample_uniform_thetas(const double* lo_dev, const double* hi_dev, const int3
                           cudaStream_t st);
 // The run's data summed over groups of `rebin` bins, one row.
 int rebin_sum_row(musr_run run, int rebin, float* out_dev, cudaStream_t st);
-// musr_fit_multistart_batch; with accept non-null (LM), the first start of run
+// musr_fit_multistart_batch; with accept non-null, the first start of run
 // r that converges with accept(r, theta, value) true stops r's other starts
 // and is r's result (fit.cpp).
 int fit_multistart_batch_accept(const musr_run* runs, int n_runs, int obj, const double* starts, int n_starts,
