@@ -133,6 +133,7 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // host polls it before it blocks in a stream synchronisation instead
 constexpr int32_t kStatusPending = INT32_MIN;
 constexpr int kStatusSpinUs = 2000;
+constexpr int kMinThreadsGn = 128;
 
 }  // namespace
 
@@ -325,8 +326,12 @@ int musr_run_s::allocate() {
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
     for (int m = 0; m < 4; ++m) {
         if (m == kGN && Pk > kMaxGnParams) continue;
-        int t = 32;
-        for (int c = kMaxThreads; c >= 32; c >>= 1) {
+        // the Gauss-Newton mode reduces 1 + R + R(R+1)/2 accumulators per block and
+        // maps ~P^2 outputs in its tail: blocks of fewer than kMinThreadsGn threads
+        // spend more on that than they save in parallelism
+        const int t_min = m == kGN ? kMinThreadsGn : 32;
+        int t = t_min;
+        for (int c = kMaxThreads; c >= t_min; c >>= 1) {
             int64_t tiles = 0;
             for (int k = 0; k < K; ++k)
                 tiles += std::max<int64_t>(1, (n_bins[k] + c * kBinsPerThread - 1) / (c * kBinsPerThread));
