@@ -81,11 +81,12 @@ def test_full_size_multi_detector(obj, oobj):
     d = poisson_data(lay, theta, seed)
     th = W.perturb(theta, lay.free, 0.01, W.rng(seed + 1))
     with Run(lay, d.astype(np.float32)) as run:
-        v, g, _ = run.chi2_grad(th, obj)
+        v, g, H = run.chi2_grad(th, obj, gn=True)
         vt = run.chi2(theta, obj)
-    rv, rg, _ = oracle.gradient(lay, d, th, oobj, with_gn=False)
+    rv, rg, rH = oracle.gradient(lay, d, th, oobj, with_gn=True)
     assert rel_err(v, rv) <= 1e-6
     assert grad_rel_err(g, rg) <= 1e-4
+    assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
     assert rel_err(vt, oracle.objective(lay, d, theta, oobj)) <= 1e-6
 
 
