@@ -441,6 +441,7 @@ int musr_run_s::allocate() {
     up(d_hist_nbins, nb32.data(), sizeof(int32_t) * K);
     for (int m = 0; m < 4; ++m) {
         const Tiling& T = tl[m];
+        if (T.n_tiles == 0) continue;  // a mode without a tiling (Gauss-Newton beyond kMaxGnParams)
         up(T.d_tile_hist, T.tile_hist.data(), sizeof(int32_t) * T.n_tiles);
         up(T.d_tile_start, T.tile_start.data(), sizeof(int32_t) * T.n_tiles);
         up(T.d_cluster_hist, T.cluster_hist.data(), sizeof(int32_t) * T.n_clusters);

@@ -10,7 +10,9 @@ configurations the benchmark times:
     every vector of the three smallest runs and the base vector of the three
     largest -- against the oracle, which computes them one by one;
   * the batched adjoint over 64 runs of 16 x 65536: sampled runs' values and
-    gradients against the oracle.
+    gradients against the oracle;
+  * the limits: one histogram of 2^24 bins, and 1024 histograms with 3080
+    parameters (beyond the Gauss-Newton limit of 1024).
 Tolerances as elsewhere: objective relative 1e-6, gradient 1e-4 norm-wise.
 """
 import numpy as np
@@ -100,3 +102,35 @@ def test_batched_adjoint_64x16x65536_sampled():
         assert grad_rel_err(res[i][1], gr) <= 1e-4
     for r in runs:
         r.close()
+
+
+def test_maximum_histogram_length():
+    """One histogram at the per-histogram limit of 2^24 bins (t up to 21 us with
+    1.25 ns bins): value and gradient against the oracle."""
+    lay = W.single_hist_layout(1 << 24, 0.00125)
+    theta = W.single_hist_truth()
+    d = W.poisson_counts(oracle.model(lay, theta), 31)
+    th = W.perturb(theta, lay.free, 0.01, W.rng(32))
+    with Run(lay, d.astype(np.float32)) as run:
+        for obj, oobj in OBJS:
+            v, g, _ = run.chi2_grad(th, obj)
+            rv, rg, _ = oracle.gradient(lay, d, th, oobj, with_gn=False)
+            assert rel_err(v, rv) <= 1e-6
+            assert grad_rel_err(g, rg) <= 1e-4
+
+
+def test_many_histograms_many_parameters():
+    """1024 histograms of 777 bins with per-histogram N0, background and phase:
+    3080 parameters (theta through device memory, role rows from the device
+    table), beyond the Gauss-Newton limit (1024): value and gradient only."""
+    lay = W.multi_detector_layout(1024, 777, 12.8)
+    theta = W.multi_detector_theta(lay, W.rng(33))
+    d = W.poisson_counts(oracle.model(lay, theta), 34)
+    th = W.perturb(theta, lay.free, 0.01, W.rng(35))
+    assert lay.n_params > 1024
+    with Run(lay, d.astype(np.float32)) as run:
+        for obj, oobj in OBJS:
+            v, g, _ = run.chi2_grad(th, obj)
+            rv, rg, _ = oracle.gradient(lay, d, th, oobj, with_gn=False)
+            assert rel_err(v, rv) <= 1e-6
+            assert grad_rel_err(g, rg) <= 1e-4
