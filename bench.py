@@ -47,9 +47,9 @@ WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi
 FLOPS_PER_BIN_GRAD = 83.5
 # DRAM bytes (read + write) of one eval_kernel<1,1,0,1,kGrad> launch of this
 # workload, from the ncu capture summarised in
-# profiles/eval_kernel_grad_16x65536.md (4,278,528 B read, 0 written); to be
+# profiles/eval_kernel_grad_16x65536.md (4,278,784 B read, 0 written); to be
 # re-measured whenever that kernel changes.
-TRAFFIC_BYTES_GRAD_LAUNCH = 4278528
+TRAFFIC_BYTES_GRAD_LAUNCH = 4278784
 # FP32-pipe FLOPs per bin-evaluation of the value-only batched kernel on the
 # 64-run workload (batch_kernel<1,1,0,1>), counted by ncu on one launch of
 # 2,720,958,581 bin-evaluations: 1978.5 M FFMA and 902.0 M other FP32 warp
