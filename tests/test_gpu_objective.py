@@ -227,3 +227,39 @@ def test_set_data_from_device_fp64(md_small):
         run.set_data(torch.tensor(d, dtype=torch.float64, device="cuda:0"))
         b = run.chi2(th, MUSR_CHI2)
     assert a == b
+
+
+def test_concurrent_runs_on_host_threads():
+    """Runs are independent: four host threads, each with its own run, evaluate
+    concurrently (ctypes releases the GIL) and get, bit for bit, what the same
+    calls give one after the other."""
+    import threading
+    cases = []
+    for i in range(4):
+        lay, theta, seed = W.config_multi_detector(8, 3000 + 1000 * i)
+        d = poisson_data(lay, theta, seed + i)
+        cases.append((lay, d, [W.perturb(theta, lay.free, 0.01, W.rng(seed + 10 * i + j)) for j in range(20)]))
+    runs = [Run(lay, d) for lay, d, _ in cases]
+    expected = [[run.chi2_grad(th, MUSR_CHI2, gn=(j % 2 == 1)) for j, th in enumerate(ths)]
+                for run, (_, _, ths) in zip(runs, cases)]
+    got = [None] * 4
+    errors = []
+
+    def work(i):
+        try:
+            got[i] = [runs[i].chi2_grad(th, MUSR_CHI2, gn=(j % 2 == 1)) for j, th in enumerate(cases[i][2])]
+        except Exception as e:  # noqa: BLE001 -- reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for e_run, g_run in zip(expected, got):
+        for (v0, g0, h0), (v1, g1, h1) in zip(e_run, g_run):
+            assert v0 == v1 and np.array_equal(g0, g1)
+            assert (h0 is None and h1 is None) or np.array_equal(h0, h1)
+    for r in runs:
+        r.close()
