@@ -1,18 +1,23 @@
 #!/usr/bin/env python
 """Benchmark: chi2 + gradient bin-evaluations per second on one GB300.
 
-Workload: 16 detector histograms x 65536 bins of 0.1953125 ns (12.8 us),
-theory = exponentially damped line + Gaussian-damped line (B1 + dB) + static
-Gaussian Kubo-Toyabe, 56 parameters (40 free), Poisson counts.  One step is
-one evaluation of chi2 and its gradient over every bin (objective kernel in
-adjoint mode), for a fresh parameter vector; L2 is flushed (256 MB write)
-between steps, outside the timed events.
+Workload (the gradient configuration): 32 detector histograms x 131072 bins
+of 0.09765625 ns (12.8 us), theory = exponentially damped line +
+Gaussian-damped line (B1 + dB) + static Gaussian Kubo-Toyabe, 104 parameters
+(72 free), Poisson counts.  One step is one evaluation of chi2 and its
+gradient over every bin (objective kernel in adjoint mode) for a fresh
+parameter vector.  The steps cycle through 16 independent runs of the
+workload (268 MB of counts, larger than L2) so every step reads its counts
+from HBM; they are launched back to back between two CUDA events.  The same
+evaluation timed one launch at a time with L2 flushed before each is reported
+beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 (torchrun): every rank runs an independent replica (the path has no
 exchange step); value = all ranks' bin-evaluations / max-over-ranks time.
-Prints one JSON line on rank 0.
+Prints one JSON line on rank 0 (details of the extra measurements go to
+stderr as one JSON line before it).
 """
 from __future__ import annotations
 
@@ -36,33 +41,82 @@ import workloads as W  # noqa: E402
 
 METRIC = "chi2+grad bin-evals/s"
 UNIT = "bin-evals/s"
-WORKLOAD = "16 hist x 65536 bins, 2 lines + static GKT, 56 params (40 free), chi2 + gradient"
+WORKLOAD = "32 hist x 131072 bins, 2 lines + static GKT, 104 params (72 free), chi2 + gradient"
 
-# FP32-pipe FLOPs per bin of the adjoint (value + gradient) code for this
-# signature (1 exponential line, 1 Gaussian line, Kubo-Toyabe), counted by
-# ncu on one launch of the batched adjoint kernel over 67,108,864 bins, where
-# per-launch costs are negligible: 73.34 M FFMA and 28.45 M other FP32 warp
-# instructions, i.e. (2 x 73.34 + 28.45) x 32 / 67.108864 = 83.5 FLOP / bin
-# (FMA = 2).  The single-run kernel executes the same per-bin code.
-FLOPS_PER_BIN_GRAD = 83.5
+# Algorithmic work per bin of chi2 + gradient for this theory (the scope
+# table's count, independent of how the kernel schedules it): the model needs
+# 4 exponentials (lifetime, two line envelopes, Kubo-Toyabe), 2 cosines and,
+# for the chi2 weight, 1 reciprocal on the SFU, and ~25 FMA; the adjoint adds
+# ~10 partials x ~3 FMA; the counts are read once (4 B, FP32).
+ALG_FP32_FLOP_PER_BIN = 2 * (25 + 30)
+ALG_SFU_PER_BIN = {"ex2": 4, "cos": 2, "rcp": 1}
+ALG_BYTES_PER_BIN = 4
+# FP32 FLOPs per bin the kernel executes for the same work (ncu instruction
+# counts of the batched adjoint kernel over 67,108,864 bins, where per-launch
+# costs vanish; FMA = 2); reported beside the algorithmic count
+EXEC_FP32_FLOP_PER_BIN = 83.5
 # DRAM bytes (read + write) of one eval_kernel<1,1,0,1,kGrad> launch of this
-# workload, from the ncu capture summarised in
-# profiles/eval_kernel_grad_16x65536.md (4,278,784 B read, 0 written); to be
-# re-measured whenever that kernel changes.
-TRAFFIC_BYTES_GRAD_LAUNCH = 4278784
-# FP32-pipe FLOPs per bin-evaluation of the value-only batched kernel on the
-# 64-run workload (batch_kernel<1,1,0,1>), counted by ncu on one launch of
-# 2,720,958,581 bin-evaluations: 1978.5 M FFMA and 902.0 M other FP32 warp
-# instructions, (2 x 1978.5 + 902.0) x 32 / 2720.96 = 57.1 FLOP per
-# bin-evaluation (profiles/batch_kernel_value_64runs.md).
+# workload from an ncu capture of the current kernel (None until captured)
+TRAFFIC_BYTES_GRAD_LAUNCH = None
+# FP32-pipe FLOPs per bin-evaluation the value-only batched kernel executes on
+# the 64-run workload (batch_kernel<1,1,0,1>, ncu instruction counts over
+# 2,720,958,581 bin-evaluations)
 FLOPS_PER_BINEVAL_VALUE_BATCH = 57.1
-SMS = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+# algorithmic work per bin-evaluation of the value-only objective: the model's
+# SFU operations and FMAs, no partials
+ALG_FP32_FLOP_PER_BINEVAL_VALUE = 2 * 25
+HBM_FALLBACK_GBS = 6800.0
 
 
-def fp32_peak_tflops(mhz=SM_MAX_MHZ):
-    return SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+def measured_peaks():
+    """Denominators of the roofline: the device's measured pipe rates (library
+    probe) and the measured HBM copy bandwidth of the GB300s."""
+    from paper_1604_02334_gb300 import pipe_rates
+    r = pipe_rates()
+    hbm, src = HBM_FALLBACK_GBS, "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm, src = float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        pass
+    fp32 = 2.0 * max(r["ffma"], r["ffma2"])
+    return {"rates": r, "fp32_flops": fp32, "hbm_bytes": hbm * 1e9, "hbm_src": src}
+
+
+def roofline(bins, seconds, peaks, flop_per_bin, sfu_per_bin, bytes_per_bin, traffic=None, kernel=""):
+    """Fractions of the FP32, SFU and HBM rooflines for `bins` bins in
+    `seconds` (one launch), by algorithmic counts; the binding one is reported."""
+    r = peaks["rates"]
+    sfu_s_per_bin = sum(n / r[op] for op, n in sfu_per_bin.items())
+    n_sfu = sum(sfu_per_bin.values())
+    fr = {"fp32": flop_per_bin * bins / seconds / peaks["fp32_flops"],
+          "sfu": sfu_s_per_bin * bins / seconds,
+          "hbm": bytes_per_bin * bins / seconds / peaks["hbm_bytes"]}
+    pipe = max(fr, key=fr.get)
+    if pipe == "fp32":
+        a, p, u = flop_per_bin * bins / seconds / 1e12, peaks["fp32_flops"] / 1e12, "TFLOP/s"
+    elif pipe == "sfu":
+        a, p, u = n_sfu * bins / seconds / 1e12, n_sfu / sfu_s_per_bin / 1e12, "T SFU-op/s"
+    else:
+        a, p, u = bytes_per_bin * bins / seconds / 1e9, peaks["hbm_bytes"] / 1e9, "GB/s"
+    return {"bound": "hbm" if pipe == "hbm" else "alu", "pipe": pipe, "achieved": _r(a), "peak": _r(p),
+            "unit": u, "frac": _r(a / p), "traffic": traffic, "fracs": {k: _r(v) for k, v in fr.items()},
+            "kernel": kernel}
+
+
+def _r(x, n=4):
+    """Round to n significant digits (keeps the JSON line short)."""
+    if x is None or not isinstance(x, float) or x == 0.0 or not math.isfinite(x):
+        return x
+    return float(f"{x:.{n}g}")
+
+
+def _short(obj):
+    if isinstance(obj, dict):
+        return {k: _short(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return [_short(v) for v in obj]
+    return _r(obj) if isinstance(obj, float) else obj
 
 
 # --------------------------------------------------------------------------
@@ -165,7 +219,8 @@ def job_value(units_per_rank, seconds_per_rank, world):
 # --------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, on a bounded sample
 # --------------------------------------------------------------------------
-SAMPLE_BINS = 8192  # leading bins of each of the 16 histograms
+SAMPLE_BINS = 8192  # leading bins of each histogram
+N_RUNS = 16          # independent runs cycled by the timed steps
 
 
 def cpu_sample(lay, data):
@@ -212,7 +267,7 @@ def cpu_baseline(lay, data, thetas, seconds=12.0):
 
 # --------------------------------------------------------------------------
 def make_workload():
-    lay, theta, seed = W.config_multi_detector()
+    lay, theta, seed = W.config_gradient()
     return lay, theta, seed
 
 
@@ -247,7 +302,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_throughput(dev, rank, reps=5):
+def batched_throughput(dev, rank, peaks, reps=5):
     """Value-only bin-evaluations per second of the batched persistent kernel on
     64 uneven runs x (P+1) Jacobian vectors, device-resident (L2 flushed)."""
     import torch
@@ -281,14 +336,13 @@ def batched_throughput(dev, rank, reps=5):
     b.close()
     for g in gruns:
         g.close()
-    peak = fp32_peak_tflops()
-    achieved = FLOPS_PER_BINEVAL_VALUE_BATCH * binevals / (med * 1e-3) / 1e12
+    rl = roofline(binevals, med * 1e-3, peaks, ALG_FP32_FLOP_PER_BINEVAL_VALUE, {"ex2": 4, "cos": 2, "rcp": 1},
+                  0.0, kernel="batch_kernel<1,1,0,1>")
+    rl["exec_fp32_frac"] = _r(FLOPS_PER_BINEVAL_VALUE_BATCH * binevals / (med * 1e-3) / peaks["fp32_flops"])
     return {"workload": "64 runs, K~U{1..32} x M~U[2^14,2^17] bins, P+1 vectors each",
             "bins": int(sum(br.layout.total_bins for br in runs)), "bin_evals": int(binevals),
             "ms": med, "value": binevals / (med * 1e-3), "unit": "bin-evals/s (chi2, value only)",
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "kernel": "batch_kernel<1,1,0,1>",
-                         "note": "host-timed (includes the launch), L2 flushed before each"}}
+            "roofline": rl, "note": "host-timed (includes the launch), L2 flushed before each"}
 
 
 def _device_rate(run, theta, obj, mode, reps=50):
@@ -336,14 +390,87 @@ def _fit_rate(run, starts, obj, free, method):
             "chi2_ndf": float(np.median(vals))}
 
 
-def other_configs(rank):
+def _flushed_us(run, thetas_t, out, obj, mode, flush, stream, steps=20):
+    """Median microseconds of one device-entry evaluation, L2 flushed before
+    each, CUDA events on the launching stream around the launch alone."""
+    import torch
+    ms = []
+    n = thetas_t.shape[0]
+    for j in range(steps + 3):
+        flush.fill_(j & 255)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.chi2_grad_device(thetas_t[j % n], out, obj, mode, stream=stream.cuda_stream)
+        e1.record(stream)
+        if j >= 3:
+            ms.append((e0, e1))
+    torch.cuda.synchronize()
+    return 1e3 * float(np.median([x.elapsed_time(y) for x, y in ms]))
+
+
+def _b2b_us(run, thetas_t, out, obj, mode, stream, steps=50):
+    """Microseconds per device-entry evaluation launched back to back (no
+    flush; the inputs stay in L2), CUDA events around all of them."""
+    import torch
+    n = thetas_t.shape[0]
+    for j in range(5):
+        run.chi2_grad_device(thetas_t[j % n], out, obj, mode, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(steps):
+        run.chi2_grad_device(thetas_t[j % n], out, obj, mode, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / steps
+
+
+def other_configs(rank, peaks, flush, stream):
     """The remaining workloads of the measurement plan, each a small extra:
-    single histogram (fits/s, latency), -2lnL on the benchmark workload, the
-    paper's Table 1 shapes, and the 32 x 131072 gradient workload (adjoint vs
-    central-difference fits)."""
+    the 16 x 65536 workload (chi2 + gradient, Gauss-Newton, value, deviance;
+    L2 flushed), the Gauss-Newton mode on the headline shape, the single
+    histogram (fits/s, latency), the stretched-line variant, the paper's
+    Table 1 shapes, fits on the headline shape (adjoint LM / BFGS, central
+    differences) and the user-theory kernels."""
+    import torch
     from paper_1604_02334_gb300 import (MUSR_CHI2, MUSR_FIT_BFGS, MUSR_FIT_BFGS_FD, MUSR_FIT_LM, MUSR_POISSON,
-                                        MUSR_VALUE, MUSR_VALUE_GRAD, Run)
+                                        MUSR_VALUE, MUSR_VALUE_GRAD, MUSR_VALUE_GRAD_GN, Run)
     res = {}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    # 16 x 65536, 40 free: every mode, L2 flushed, events around the launch
+    lay, theta, seed = W.config_multi_detector()
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    g = W.rng(seed + 11 + rank)
+    ths = torch.tensor(np.stack([W.perturb(theta, lay.free, 0.01, g) for _ in range(8)]), device=dev)
+    P = lay.n_params
+    out = torch.empty(1 + P + P * P, dtype=torch.float64, device=dev)
+    with Run(lay, torch.tensor(W.poisson_counts(mean, seed + rank), dtype=torch.float32, device=dev)) as run:
+        t_grad = _flushed_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD, flush, stream)
+        t_gn = _flushed_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD_GN, flush, stream)
+        t_val = _flushed_us(run, ths, out, MUSR_CHI2, MUSR_VALUE, flush, stream)
+        t_dev = _flushed_us(run, ths, out, MUSR_POISSON, MUSR_VALUE_GRAD, flush, stream)
+        t_b2b = _b2b_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD, stream)
+        t_b2b_gn = _b2b_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD_GN, stream)
+    rl = roofline(lay.total_bins, t_grad * 1e-6, peaks, ALG_FP32_FLOP_PER_BIN, ALG_SFU_PER_BIN, ALG_BYTES_PER_BIN)
+    res["cfg_16x65536"] = {"chi2_grad_us": t_grad, "bin_evals_per_s": lay.total_bins / (t_grad * 1e-6),
+                           "frac": rl["frac"], "pipe": rl["pipe"], "gn_us": t_gn, "value_us": t_val,
+                           "deviance_grad_us": t_dev, "chi2_grad_us_b2b_l2": t_b2b, "gn_us_b2b_l2": t_b2b_gn}
+    # Gauss-Newton mode on the headline shape (what every LM iteration evaluates)
+    lay, theta, seed = W.config_gradient()
+    with Run(lay) as m:
+        mean = m.model(theta).astype(np.float64)
+    g = W.rng(seed + 31 + rank)
+    P = lay.n_params
+    ths = torch.tensor(np.stack([W.perturb(theta, lay.free, 0.01, g) for _ in range(8)]), device=dev)
+    out = torch.empty(1 + P + P * P, dtype=torch.float64, device=dev)
+    data = W.poisson_counts(mean, seed + rank)
+    with Run(lay, torch.tensor(data, dtype=torch.float32, device=dev)) as run:
+        res["cfg_32x131072_gn_us"] = _flushed_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD_GN, flush, stream)
+        starts = [W.perturb(theta, lay.free, 0.01, g) for _ in range(5)]
+        res["cfg_32x131072_fits"] = {
+            "lm_adjoint_gn": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_LM),
+            "bfgs_adjoint": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS),
+            "bfgs_central_differences": _fit_rate(run, starts[:2], MUSR_CHI2, lay.free, MUSR_FIT_BFGS_FD)}
     # single histogram, 8192 bins, FP64 data, 6 free: LM fits from 5 % perturbed starts
     lay, theta, seed = W.config_single()
     with Run(lay) as m:
@@ -358,24 +485,14 @@ def other_configs(rank):
         host_us = 1e6 * (time.perf_counter() - t0) / 500
         dev_us, _ = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
     res["single_8192"] = {"fit_lm": fit, "host_chi2_us": host_us, "device_chi2_us": dev_us}
-    # benchmark workload, Poisson deviance, value + gradient
-    lay, theta, seed = make_workload()
-    with Run(lay) as m:
-        mean = m.model(theta).astype(np.float64)
-    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
-        us, rate = _device_rate(run, theta, MUSR_POISSON, MUSR_VALUE_GRAD)
-        us_v, rate_v = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
-    res["multi_16x65536"] = {"poisson_grad_us": us, "poisson_grad_bin_evals_per_s": rate,
-                             "chi2_value_us": us_v, "chi2_value_bin_evals_per_s": rate_v}
-    # same shape with the second line a stretched exponential exp(-(lambda t)^beta), 41 free
+    # same shape as 16 x 65536 with the second line a stretched exponential, 41 free
     lay, theta, seed = W.config_stretched()
     with Run(lay) as m:
         mean = m.model(theta).astype(np.float64)
     with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
         us, rate = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE_GRAD)
         us_v, rate_v = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
-    res["stretched_16x65536"] = {"chi2_grad_us": us, "chi2_grad_bin_evals_per_s": rate,
-                                 "chi2_value_us": us_v, "chi2_value_bin_evals_per_s": rate_v}
+    res["stretched_16x65536"] = {"chi2_grad_us": us, "chi2_value_us": us_v}
     # the paper's Table 1 shapes: chi2 value per evaluation (its Table 1 times one chi2 per "Iter.")
     sweep = []
     for M in W.SWEEP_BINS:
@@ -385,46 +502,24 @@ def other_configs(rank):
         with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
             us, rate = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE)
             us_g, rate_g = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE_GRAD)
-        sweep.append({"bins": f"16x{M}", "chi2_us": us, "chi2_bin_evals_per_s": rate,
-                      "chi2_grad_us": us_g, "chi2_grad_bin_evals_per_s": rate_g})
-    res["table1_shapes"] = sweep
-    # 32 x 131072, 72 free: value + gradient rate; fits from 1 % perturbed starts
-    lay, theta, seed = W.config_gradient()
-    with Run(lay) as m:
-        mean = m.model(theta).astype(np.float64)
-    with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
-        us, rate = _device_rate(run, theta, MUSR_CHI2, MUSR_VALUE_GRAD)
-        g = W.rng(seed + 31 + rank)
-        starts = [W.perturb(theta, lay.free, 0.01, g) for _ in range(5)]
-        fits = {"lm_adjoint_gn": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_LM),
-                "bfgs_adjoint": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS),
-                "bfgs_central_differences": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_BFGS_FD)}
-    res["gradient_32x131072"] = {"chi2_grad_us": us, "chi2_grad_bin_evals_per_s": rate, "fits": fits}
-    # the benchmark theory as a user expression compiled at run time (FP64 kernel)
+        sweep.append({"bins": f"16x{M}", "chi2_us": us, "chi2_grad_us": us_g})
+    res["table1_shapes_graph_replay"] = sweep
+    # the 16 x 65536 theory as a user expression compiled at run time (FP64 and FP32 kernels)
     from paper_1604_02334_gb300 import UserTheory
-    lay, theta, seed = make_workload()
+    lay, theta, seed = W.config_multi_detector()
     t0 = time.perf_counter()
     th = UserTheory(W.MD_USER_EXPR)
     compile_s = time.perf_counter() - t0
     with Run(lay) as m:
         mean = m.model(theta).astype(np.float64)
+    nvec = 64
+    thetas = np.repeat(theta[None, :], nvec, axis=0)
     with Run(lay, W.poisson_counts(mean, seed + rank)) as run:
-        th.eval(run, theta, MUSR_CHI2)
-        reps = 20
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            th.eval(run, theta, MUSR_CHI2)
-        us = 1e6 * (time.perf_counter() - t0) / reps
-        nvec = 64
-        thetas = np.repeat(theta[None, :], nvec, axis=0)
         th.eval(run, thetas, MUSR_CHI2)
         t0 = time.perf_counter()
         for _ in range(5):
             th.eval(run, thetas, MUSR_CHI2)
         us64 = 1e6 * (time.perf_counter() - t0) / 5
-        t0 = time.perf_counter()
-        th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=1e-6)
-        grad_ms = 1e3 * (time.perf_counter() - t0)
         th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
         t0 = time.perf_counter()
         th.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
@@ -442,20 +537,16 @@ def other_configs(rank):
         th32.grad(run, theta, MUSR_CHI2, free=lay.free, rel_h=0.0)
         fwd32_ms = 1e3 * (time.perf_counter() - t0)
     th32.close()
-    res["user_theory_16x65536_fp32"] = {"chi2_64_vectors_us": us64_32,
-                                        "chi2_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64_32 * 1e-6),
-                                        "forward_mode_gradient_40_directions_ms": fwd32_ms}
-    res["user_theory_16x65536"] = {"compile_s": compile_s, "chi2_us_per_call": us,
-                                   "chi2_bin_evals_per_s": lay.total_bins / (us * 1e-6),
-                                   "chi2_64_vectors_us": us64,
-                                   "chi2_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64 * 1e-6),
-                                   "fd_gradient_81_vectors_ms": grad_ms,
-                                   "forward_mode_gradient_40_directions_ms": fwd_ms,
-                                   "arithmetic": "fp64 (host call)"}
+    res["user_theory_16x65536"] = {
+        "compile_s": compile_s,
+        "fp64_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64 * 1e-6),
+        "fp64_forward_mode_gradient_ms": fwd_ms,
+        "fp32_bin_evals_per_s_64_vectors": 64 * lay.total_bins / (us64_32 * 1e-6),
+        "fp32_forward_mode_gradient_ms": fwd32_ms}
     return res
 
 
-def batched_grad_throughput(dev, rank, n_runs=64, reps=5):
+def batched_grad_throughput(dev, rank, peaks, n_runs=64, reps=5):
     """chi2 + gradient of 64 runs of the benchmark workload (16 x 65536 bins
     each, own parameters and counts) in one launch of the batched adjoint
     kernel: device-resident inputs (268 MB, larger than L2), CUDA events."""
@@ -485,15 +576,14 @@ def batched_grad_throughput(dev, rank, n_runs=64, reps=5):
         ms.append(e0.elapsed_time(e1))
     med = float(np.median(ms))
     bins = n_runs * lay.total_bins
-    peak = fp32_peak_tflops()
-    achieved = FLOPS_PER_BIN_GRAD * bins / (med * 1e-3) / 1e12
     b.close()
     for r in runs:
         r.close()
+    rl = roofline(bins, med * 1e-3, peaks, ALG_FP32_FLOP_PER_BIN, ALG_SFU_PER_BIN, ALG_BYTES_PER_BIN,
+                  kernel="gbatch_kernel<1,1,0,1,kGrad>")
+    rl["exec_fp32_frac"] = _r(EXEC_FP32_FLOP_PER_BIN * bins / (med * 1e-3) / peaks["fp32_flops"])
     return {"workload": f"{n_runs} runs x 16 hist x 65536 bins, chi2 + gradient, one launch", "bin_evals": bins,
-            "ms": med, "value": bins / (med * 1e-3), "unit": "bin-evals/s",
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "kernel": "gbatch_kernel<1,1,0,1,kGrad>"}}
+            "ms": med, "value": bins / (med * 1e-3), "unit": "bin-evals/s", "roofline": rl}
 
 
 def learned_start_ab(dev, rank, train_steps, n_runs=64):
@@ -577,6 +667,23 @@ def learned_start_ab(dev, rank, train_steps, n_runs=64):
                 res["learned_batched_bfgs"]["fits_per_s"] / res["plain_batched_bfgs"]["fits_per_s"]}
 
 
+def learned_summary(ls):
+    """The learned-start A/B in a few keys: fits/s of both arms, success, fallbacks."""
+    if not ls:
+        return None
+    out = {"speedup_batched_lm": ls["speedup_fits_per_s_batched"],
+           "speedup_batched_bfgs": ls["speedup_fits_per_s_batched_bfgs"],
+           "speedup_sequential": ls["speedup_fits_per_s"]}
+    for k in ("learned_batched", "plain_batched", "learned_batched_bfgs", "plain_batched_bfgs", "learned", "plain"):
+        x = ls[k]
+        out[k] = {"fits_per_s": x["fits_per_s"], "success": x["success"], "iters": x["mean_iters"]}
+        if "fallbacks" in x:
+            out[k]["fallbacks"] = x["fallbacks"]
+    out["n_runs"] = ls["n_runs"]
+    out["train_samples"] = ls["train_samples"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -584,54 +691,62 @@ def run_ours(args):
     from paper_1604_02334_gb300 import MUSR_CHI2, MUSR_VALUE_GRAD, Run
 
     dev = torch.device("cuda", torch.cuda.current_device())
+    peaks = measured_peaks()
     lay, theta, seed = make_workload()
     P = lay.n_params
-    # synthetic Poisson counts: mean from the library's model kernel, noise from numpy PCG64
+    # N_RUNS independent runs of the workload (own Poisson counts each), cycled
+    # step by step: together larger than L2, so each step reads its counts
+    # from HBM without a flush between launches
     with Run(lay) as mrun:
         mean = mrun.model(theta).astype(np.float64)
-    data = W.poisson_counts(mean, seed + rank)
-    data_t = torch.tensor(data, dtype=torch.float32, device=dev)
-    run = Run(lay, data_t)
+    datas = [W.poisson_counts(mean, seed + rank + 1000 * r) for r in range(N_RUNS)]
+    data = datas[0]
+    runs = [Run(lay, torch.tensor(d, dtype=torch.float32, device=dev)) for d in datas]
+    run = runs[0]
     g = W.rng(seed + 11 + rank)
     n_vec = args.steps + args.warmup
     thetas = np.stack([W.perturb(theta, lay.free, 0.01, g) for _ in range(n_vec)])
     thetas_t = torch.tensor(thetas, dtype=torch.float64, device=dev)
     outs = torch.empty((n_vec, 1 + P), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    # one explicit (non-default) stream carries the flush, the events and the kernel
+    # one explicit (non-default) stream carries the events and the kernels
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
 
     def step(i):
-        run.chi2_grad_device(thetas_t[i], outs[i], MUSR_CHI2, MUSR_VALUE_GRAD, stream=sptr)
+        runs[i % N_RUNS].chi2_grad_device(thetas_t[i], outs[i], MUSR_CHI2, MUSR_VALUE_GRAD, stream=sptr)
 
     for i in range(args.warmup):
-        flush.fill_(i & 255)
         step(i)
     torch.cuda.synchronize()
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
-    time.sleep(0.3)
+    # untimed soak (the same steps) so the clock samples see the GPU under load
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < 0.4:
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     wall0 = time.perf_counter()
+    e_start.record(stream)
     for j in range(args.steps):
-        flush.fill_((j + 1) & 255)
-        starts[j].record(stream)
         step(args.warmup + j)
-        ends[j].record(stream)
+    e_end.record(stream)
     torch.cuda.synchronize()
     barrier(world)
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    t_total = max_over_ranks(sum(step_ms) / 1e3, world)
-    value = job_value(lay.total_bins * args.steps, sum(step_ms) / 1e3, world)
+    t_timed = e_start.elapsed_time(e_end) / 1e3
+    t_total = max_over_ranks(t_timed, world)
+    value = job_value(lay.total_bins * args.steps, t_timed, world)
     mean_ms = 1e3 * t_total / args.steps
+    # the same evaluation one launch at a time, L2 flushed before each, events around the launch alone
+    flushed_us = _flushed_us(run, thetas_t, outs[0], MUSR_CHI2, MUSR_VALUE_GRAD, flush, stream)
 
     # end to end through the C ABI with host buffers: per step, upload the
     # histograms from pinned memory, evaluate chi2 + gradient, read them back
@@ -655,42 +770,67 @@ def run_ours(args):
 
     # sanity: results are finite
     assert torch.isfinite(outs[args.warmup:]).all().item()
-    batched = None if args.no_batched else batched_throughput(dev, rank)
-    batched_grad = None if args.no_batched else batched_grad_throughput(dev, rank)
+    for r in runs[1:]:
+        r.close()
+    others = None if args.no_other_configs else other_configs(rank, peaks, flush, stream)
+    # the batched legs record their events on the current (explicit) stream and
+    # launch on it: a NULL stream would send the library's work to its own
+    batched = None if args.no_batched else batched_throughput(dev, rank, peaks)
+    batched_grad = None if args.no_batched else batched_grad_throughput(dev, rank, peaks)
     learned = None if args.learned_steps <= 0 else learned_start_ab(dev, rank, args.learned_steps)
-    others = None if args.no_other_configs else other_configs(rank)
 
     if rank != 0:
         run.close()
         return
-    peak = fp32_peak_tflops()
-    achieved = FLOPS_PER_BIN_GRAD * lay.total_bins / (mean_ms * 1e-3) / 1e12
+    rl = roofline(lay.total_bins, mean_ms * 1e-3, peaks, ALG_FP32_FLOP_PER_BIN, ALG_SFU_PER_BIN,
+                  ALG_BYTES_PER_BIN, traffic=TRAFFIC_BYTES_GRAD_LAUNCH, kernel="eval_kernel<1,1,0,1,kGrad>")
+    rl["exec_fp32_frac"] = _r(EXEC_FP32_FLOP_PER_BIN * lay.total_bins / (mean_ms * 1e-3) / peaks["fp32_flops"])
+    rl["peak_src"] = ("measured: musr_pipe_rates probe (FP32 FMA, SFU ex2/cos/rcp); HBM from the pool's "
+                      f"copy bandwidth ({peaks['hbm_src']})")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 eval / f64 accumulate",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 eval (packed pairs), f64 block partials, exact fixed-point final sum, f64 out",
         "data": "synthetic (Poisson counts of the model, numpy PCG64)",
         "config": {"workload": WORKLOAD, "bins": lay.total_bins, "params": P,
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES_GRAD_LAUNCH,
-                     "kernel": "eval_kernel<1,1,0,1,kGrad>",
-                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 x 2070 MHz"},
+                   "l2": f"inputs larger than L2: {N_RUNS} independent runs of the workload "
+                         f"({N_RUNS * lay.total_bins * 4 / 1e6:.0f} MB of counts) cycled step by step, "
+                         "launches back to back",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": rl,
         "clocks": clk,
-        "e2e": e2e,
-        "gpu_launches": args.steps,  # one objective kernel launch per step (the flush is a torch fill)
-        "wall_s": wall,
+        "e2e": _short(e2e),
+        "gpu_launches": args.steps,  # one objective kernel launch per step
+        "flushed_step_us": _r(flushed_us),
+        "pipe_rates_per_s": _short(peaks["rates"]),
     }
-    if batched:
-        line["batched"] = batched
-    if batched_grad:
-        line["batched_grad"] = batched_grad
-    if learned:
-        line["learned_start"] = learned
+    details = {"wall_s": wall}
     if others:
-        line["other_configs"] = others
+        details["other_configs"] = others
+        c2 = others["cfg_16x65536"]
+        line["cfg_16x65536"] = _short(
+            {"chi2_grad_us_flushed": c2["chi2_grad_us"], "chi2_grad_us_b2b_l2": c2["chi2_grad_us_b2b_l2"],
+             "gn_us_flushed": c2["gn_us"], "gn_us_b2b_l2": c2["gn_us_b2b_l2"], "value_us_flushed": c2["value_us"],
+             "deviance_grad_us_flushed": c2["deviance_grad_us"]})
+        line["cfg_32x131072_gn_us"] = _r(others["cfg_32x131072_gn_us"])
+        f4 = others["cfg_32x131072_fits"]
+        line["cfg_32x131072_fits_per_s"] = _short({k: v["fits_per_s"] for k, v in f4.items()})
+    if batched:
+        details["batched"] = batched
+        line["batched_value"] = _short({"bin_evals_per_s": batched["value"], "frac": batched["roofline"]["frac"],
+                                        "pipe": batched["roofline"]["pipe"]})
+    if batched_grad:
+        details["batched_grad"] = batched_grad
+        line["batched_grad"] = _short({"bin_evals_per_s": batched_grad["value"],
+                                       "frac": batched_grad["roofline"]["frac"],
+                                       "pipe": batched_grad["roofline"]["pipe"]})
+    if learned:
+        details["learned_start"] = learned
+        line["learned_start"] = _short(learned_summary(learned))
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(lay, data, thetas)
+        line["cpu_baseline"] = _short(cpu_baseline(lay, data, thetas))
+    print(json.dumps(_short(details)), file=sys.stderr, flush=True)
     print(json.dumps(line), flush=True)
     run.close()
 

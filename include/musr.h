@@ -302,8 +302,13 @@ typedef struct {
     int32_t max_iter; /* <= 0: 500 */
     double edm_tol;   /* <= 0: 1e-8; stop when 1/2 g^T H^-1 g < edm_tol */
     double mu0;       /* <= 0: 1e-3; initial LM damping */
-    double fd_rel_h;  /* <= 0: 1e-4; relative step of MUSR_FIT_BFGS_FD (the FP32
-                         evaluation noise makes smaller steps noise-dominated) */
+    double fd_rel_h;  /* MUSR_FIT_BFGS_FD steps: > 0 second-order central
+                         differences with a fixed relative step
+                         fd_rel_h * max(|theta_j|, 1); <= 0 (default)
+                         fourth-order central differences with a step of each
+                         parameter's standard error, from two passes of second
+                         differences at the start (the FP32 value noise
+                         enters the gradient divided by the step) */
 } musr_fit_opts;
 
 typedef struct {
@@ -557,7 +562,11 @@ const char* musr_version(void);
  * point evaluates the objective (mode MUSR_VALUE) or the objective and its
  * gradient (MUSR_VALUE_GRAD) without allocating anything: all scratch lives
  * in one static device array of MUSR_NOALLOC_SCRATCH_BYTES inside the
- * library, held on every GPU that loads the library until the process ends.
+ * library.  The CUDA driver reserves that array on a device when it loads
+ * the code of this entry point there, which with lazy module loading (the
+ * default) happens during the first call on that device; from then on the
+ * device holds it until the process ends.  Callers that start while another
+ * framework may take the device memory therefore make one call at start-up.
  *   desc        layout as for musr_create_run; data must be FP32 on the device
  *               (data_on_device != 0, data_dtype == MUSR_F32); desc->stream
  *               is ignored.
@@ -571,8 +580,10 @@ const char* musr_version(void);
  * Every call shares the one array and rewrites it, so calls whose work
  * overlaps on the GPU (different streams or host threads) race and must be
  * serialised by the caller.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.
+ * array's device address (cudaGetSymbolAddress).  Each call uploads its
+ * small tables from a host buffer the next call rewrites (pageable
+ * cudaMemcpyAsync, which may block the host briefly); a call made while
+ * `stream` is being captured into a graph returns MUSR_ENOTSUP.
  */
 #define MUSR_NOALLOC_SCRATCH_BYTES (32u << 20)
 #define MUSR_NOALLOC_MAX_HIST 64
@@ -583,6 +594,33 @@ int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mode, const d
 /* Name of the CUDA error behind the most recent MUSR_ECUDA / MUSR_ENOMEM
  * returned on the calling host thread ("none" if there was none). */
 const char* musr_last_cuda_error(void);
+
+/*
+ * Measured pipe throughputs of the current device.  (No counterpart in the
+ * paper: the objective kernels are bound by the FP32 and SFU pipes, Sec. 4.2.2
+ * states none, and this call measures both so that fractions of peak are
+ * fractions of what the GPU does.)  Each rate comes from a probe kernel that
+ * keeps 16 independent chains of one operation per thread over four waves of
+ * fully occupied SMs, best of five launches timed with CUDA events.
+ *   rates    FP64 [n_rates >= MUSR_RATE_COUNT], thread-level operations per
+ *            second, indexed by the MUSR_RATE_* constants: FP32 FMA (scalar),
+ *            FP32 FMA issued as packed pairs (each pair counts two), and the
+ *            SFU approximations ex2, sin, cos, rcp, lg2 (one PTX instruction
+ *            each).
+ * Allocates 4 bytes of device memory and a stream for the duration of the
+ * call; returns MUSR_EINVAL for a short array, MUSR_ECUDA on a CUDA error.
+ */
+enum {
+    MUSR_RATE_FFMA = 0,
+    MUSR_RATE_FFMA2 = 1,
+    MUSR_RATE_EX2 = 2,
+    MUSR_RATE_SIN = 3,
+    MUSR_RATE_COS = 4,
+    MUSR_RATE_RCP = 5,
+    MUSR_RATE_LG2 = 6,
+    MUSR_RATE_COUNT = 7
+};
+int musr_pipe_rates(double* rates, int32_t n_rates);
 
 #ifdef __cplusplus
 }

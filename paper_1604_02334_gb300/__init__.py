@@ -332,6 +332,15 @@ def poisson_sample(mu_dev, seed, counts_dev, stream=None):
           "musr_poisson_sample")
 
 
+def pipe_rates():
+    """musr_pipe_rates: measured thread-level operations per second of the
+    current device's FP32 FMA (scalar and packed pairs) and SFU ex2, sin, cos,
+    rcp, lg2, as a dict keyed by those names."""
+    out = np.zeros(_lib.MUSR_RATE_COUNT)
+    check(_lib.load().musr_pipe_rates(_dptr(out), out.shape[0]), "musr_pipe_rates")
+    return dict(zip(_lib.MUSR_RATE_NAMES, (float(x) for x in out)))
+
+
 def function_eval(expr, theta):
     """musr_function_eval: (value, gradient) of one function-array expression at theta (host only)."""
     th = np.ascontiguousarray(theta, dtype=np.float64)

@@ -28,6 +28,11 @@ MUSR_CHI2, MUSR_POISSON = 0, 1
 MUSR_F32, MUSR_F64 = 0, 1
 MUSR_VALUE, MUSR_VALUE_GRAD, MUSR_VALUE_GRAD_GN = 0, 1, 2
 MUSR_FIT_LM, MUSR_FIT_BFGS, MUSR_FIT_BFGS_FD = 0, 1, 2
+MUSR_NOALLOC_SCRATCH_BYTES = 32 << 20
+MUSR_NOALLOC_MAX_HIST = 64
+MUSR_NOALLOC_MAX_PARAMS = 256
+MUSR_RATE_NAMES = ("ffma", "ffma2", "ex2", "sin", "cos", "rcp", "lg2")
+MUSR_RATE_COUNT = len(MUSR_RATE_NAMES)
 MUSR_GAMMA_MU_MHZ_PER_G = 0.013554
 MUSR_TAU_MU_US = 2.197
 
@@ -180,6 +185,7 @@ SIGNATURES = {
     "musr_last_cuda_error": (ctypes.c_char_p, []),
     "musr_chi2_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(musr_run_desc), ctypes.c_int, ctypes.c_int,
                                               _vp, _vp, _vp, _vp]),
+    "musr_pipe_rates": (ctypes.c_int, [_dp, ctypes.c_int32]),
 }
 
 _lib = None

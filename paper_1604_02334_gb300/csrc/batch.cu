@@ -36,6 +36,7 @@ struct BatchRunRef {
     const int64_t* hist_off;
     const int32_t* hist_nbins;
     const int32_t* role_theta;
+    const float* etab;      // lifetime factor at every chunk start
     RunConst rc;
     double t0, dt;
     int32_t P, V;           // parameters, vectors evaluated this launch
@@ -104,7 +105,9 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
             const int n0 = item.start + row * stripe + (int)threadIdx.x * G;
             const bool active = n0 < M;
             float d[G];
+            float E0 = 0.f;
             if (active) {
+                E0 = __ldg(R.etab + (n0 >> 3));
                 const float4* src = reinterpret_cast<const float4*>(hdata + n0);
                 const float4 a = __ldg(src), b = __ldg(src + 1);
                 d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
@@ -117,7 +120,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
                 float acc[1] = {0.f};
                 bool bad = false;
                 if (active)
-                    eval_chunk<NE, NG, NS, KT, kValue, 1>(hcs[v], n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr);
+                    eval_chunk<NE, NG, NS, KT, kValue, 1>(hcs[v], n0, M, d, E0, p.obj, dtf, t0f, acc, bad, nullptr);
                 if (bad) atomicOr(&p.flags[R.val_off + v], 1u);
                 float s = acc[0];
 #pragma unroll
@@ -313,6 +316,7 @@ int musr_batch_s::plan(const BatchShape& sh) {
         R.hist_nbins = run->d_hist_nbins;
         R.role_theta = run->d_role_theta;
         R.rc = run->rc;
+        R.etab = run->d_etab;
         R.t0 = run->t0;
         R.dt = run->dt;
         R.P = run->P;
@@ -581,9 +585,12 @@ namespace musr {
 // Central-difference gradient over the free parameters from one batched launch
 // per 128 vectors: theta and theta +- h_j e_j, h_j = rel_h max(|theta_j|, 1).
 int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
-                      double rel_h, double* value, double* grad, double* hdiag) {
+                      const double* h_abs, int order, double* value, double* grad, double* hdiag) {
     const int P = run->P;
-    const int nv_total = 1 + 2 * (int)fidx.size();
+    const int nf = (int)fidx.size();
+    // vector 0 is theta; then per free parameter +h, -h (and +2h, -2h for order 4)
+    const int per = order == 4 ? 4 : 2;
+    const int nv_total = 1 + per * nf;
     if (!run->fd_batch) {
         int32_t mv = std::min(nv_total, kBatchMaxVec);
         musr_run r = run;
@@ -594,14 +601,10 @@ int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vec
     musr_batch B = run->fd_batch;
     const int cap = run->fd_batch_vec;
     std::vector<double> vecs((size_t)nv_total * P), vals(nv_total);
-    std::vector<double> h(fidx.size());
     for (int v = 0; v < nv_total; ++v) memcpy(vecs.data() + (size_t)v * P, theta, sizeof(double) * P);
-    for (size_t a = 0; a < fidx.size(); ++a) {
-        const int j = fidx[a];
-        h[a] = rel_h * fmax(fabs(theta[j]), 1.0);
-        vecs[(size_t)(1 + 2 * a) * P + j] += h[a];
-        vecs[(size_t)(2 + 2 * a) * P + j] -= h[a];
-    }
+    static const double kOffsets[4] = {1.0, -1.0, 2.0, -2.0};
+    for (int a = 0; a < nf; ++a)
+        for (int u = 0; u < per; ++u) vecs[(size_t)(1 + per * a + u) * P + fidx[a]] += kOffsets[u] * h_abs[a];
     for (int v0 = 0; v0 < nv_total; v0 += cap) {
         const int32_t nv = std::min(cap, nv_total - v0);
         int st = musr_batch_eval(B, obj, vecs.data() + (size_t)v0 * P, &nv, vals.data() + v0);
@@ -610,11 +613,19 @@ int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vec
     *value = vals[0];
     if (!isfinite(vals[0])) return MUSR_EDOMAIN;
     memset(grad, 0, sizeof(double) * P);
-    for (size_t a = 0; a < fidx.size(); ++a) {
-        const double fp = vals[1 + 2 * a], fm = vals[2 + 2 * a];
-        if (!isfinite(fp) || !isfinite(fm)) return MUSR_EDOMAIN;
-        grad[fidx[a]] = (fp - fm) / (2.0 * h[a]);
-        if (hdiag) hdiag[fidx[a]] = (fp - 2.0 * vals[0] + fm) / (h[a] * h[a]);
+    for (int a = 0; a < nf; ++a) {
+        const double* f = vals.data() + 1 + per * a;  // f(+h), f(-h) [, f(+2h), f(-2h)]
+        for (int u = 0; u < per; ++u)
+            if (!isfinite(f[u])) return MUSR_EDOMAIN;
+        const double h = h_abs[a];
+        if (order == 4) {
+            // fourth-order central differences: truncation error O(h^4)
+            grad[fidx[a]] = (8.0 * (f[0] - f[1]) - (f[2] - f[3])) / (12.0 * h);
+            if (hdiag) hdiag[fidx[a]] = (16.0 * (f[0] + f[1]) - (f[2] + f[3]) - 30.0 * vals[0]) / (12.0 * h * h);
+        } else {
+            grad[fidx[a]] = (f[0] - f[1]) / (2.0 * h);
+            if (hdiag) hdiag[fidx[a]] = (f[0] - 2.0 * vals[0] + f[1]) / (h * h);
+        }
     }
     return MUSR_OK;
 }

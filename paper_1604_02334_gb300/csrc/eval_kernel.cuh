@@ -26,18 +26,23 @@
 //     point turns, so it is exact at any t (no FP32 phase drift at wt ~ 600);
 //   * the deviance uses N h(r), h(r) = (1+r) ln(1+r) - r, r = (d - N)/N, with
 //     a short series for small |r| so that FP32 keeps full relative accuracy;
-//   * every block stages its histogram's constants itself, without FP64
+//   * every block stages its histogram's constants itself, with few FP64
 //     instructions: double-float FP32 pairs where precision matters and
 //     integer fixed point for phases, spread over several warps so the
 //     dependency chains overlap (and with the first data loads in flight);
-//   * sums beyond the warp use FP32 double-float pairs (TwoSum, ~44-bit
-//     significand) instead of FP64: warps -> block -> 8-block cluster (read
-//     through distributed shared memory) -> last cluster leader, which forms
-//     the per-histogram sums and the theta-space outputs, converting each
-//     output to FP64 once.
+//   * the lifetime factor exp(-t/tau), which multiplies every bin, is seeded
+//     per chunk from a per-run table rounded once from FP64, so no coherent
+//     bias enters N (the gradient sums cancel ~100-fold and would amplify it);
+//   * the value and gradient modes evaluate the even and odd bins of a chunk
+//     as the two lanes of packed FP32 instructions (FFMA2 and kin);
+//   * reduction: FP32 warp shuffles, FP64 across the block's warps (with the
+//     histogram's role factors applied), then each block adds its FP64
+//     partials as 126-bit fixed-point integers into per-histogram
+//     accumulators; integer sums do not depend on the order in which blocks
+//     finish, so the last block's FP64 conversion and the map to theta give
+//     bitwise repeatable results without cluster barriers or partial arrays.
 #pragma once
 
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -186,10 +191,8 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
         hc.n0 = n0.hi;
         hc.n0_lo = n0.lo;
         hc.bkg = __double2float_rn(role_value(rt, theta, 1));
-        hc.aE_hi = rc.aE_hi;
-        hc.aE_lo = rc.aE_lo;
         hc.qE = rc.qE;
-        hc.cE = rc.cE;
+        hc.qE2 = rc.qE * (2.f + rc.qE);
         hc.kfreq = rc.kfreq;
     } else if (part <= 2 * NOSC) {
         const int c = (part - 1) >> 1;
@@ -201,7 +204,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
             o.rate = rate.hi;
             if (c >= NE + NG) {  // exp(-(lambda t)^beta), evaluated per bin; the rotation alone is stepped
                 o.beta = __double2float_rn(role_value(rt, theta, 2 + 4 * NOSC));
-                o.a_hi = o.a_lo = o.b_hi = o.b_lo = o.q = o.qs = 0.f;
+                o.a_hi = o.a_lo = o.b_hi = o.b_lo = o.q = o.qs = o.q2 = o.qs2 = 0.f;
                 o.cenv = 1.f;
             } else if (c < NE) {  // exp(-(1/tau + lambda) t)
                 const DF rtot = df_add(it, rate);
@@ -210,6 +213,8 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
                 o.a_lo = a.lo;
                 o.b_hi = o.b_lo = 0.f;
                 o.q = step_expm1(-df_mul(rtot, dt).hi);
+                o.q2 = o.q * (2.f + o.q);
+                o.qs = o.qs2 = 0.f;
                 o.cenv = rc.t0_zero ? 1.f : expf(-df_mul(rtot, df_of(rc.t0)).hi);
             } else {  // exp(-t/tau - sigma^2 t^2 / 2), t = t0 + n dt
                 const DF s2 = df_mul(rate, rate);
@@ -221,6 +226,8 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
                 o.b_lo = b.lo;
                 o.q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));  // 2^(-2 b) - 1
                 o.qs = step_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
+                o.q2 = step_expm1(-5.54517744447956247532f * (b.hi + b.lo));  // 2^(-8 b) - 1
+                o.qs2 = step_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
                 if (rc.t0_zero) {
                     o.cenv = 1.f;
                 } else {
@@ -247,6 +254,8 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
             const float sh = step_sinpi(red);
             o.cm1 = -2.f * sh * sh;        // cos(step) - 1
             o.sn = step_sinpi(2.f * red);  // sin(step)
+            o.cm1_2 = -2.f * o.sn * o.sn;  // cos(2 step) - 1
+            o.sn_2 = step_sinpi(4.f * red);
         }
     } else if (KT && part == 2 * NOSC + 1) {
         const int r = 2 + 4 * NOSC + NS;
@@ -262,6 +271,8 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
         hc.kt_b_lo = b.lo;
         hc.kt_q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));
         hc.kt_qs = step_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
+        hc.kt_q2 = step_expm1(-5.54517744447956247532f * (b.hi + b.lo));
+        hc.kt_qs2 = step_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
         if (rc.t0_zero) {
             hc.kt_cenv = 1.f;
         } else {
@@ -322,9 +333,18 @@ struct GqCarry {
     bool valid;
 };
 
+// The lifetime factor at any bin n0 from the run's table of chunk starts,
+// stepped by the per-bin recurrence over the n0 mod 8 bins past the start.
+__device__ __forceinline__ float lifetime_from_table(const float* etab, int n0, float qE) {
+    float E = __ldg(etab + (n0 >> 3));
+    for (int r = n0 & 7; r > 0; --r) E = fmaf(E, qE, E);
+    return E;
+}
+
+// E0: the lifetime factor exp(-t/tau) at bin n0 (from the run's lifetime table)
 template <int NE, int NG, int NS, int KT, int MODE, int NACC, bool FULL>
 __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int M,
-                                                const float (&d)[kBinsPerThread], int obj, float dtf,
+                                                const float (&d)[kBinsPerThread], float E0, int obj, float dtf,
                                                 float t0f, float (&acc)[NACC], bool& bad,
                                                 float* model_dst, GqCarry<NE + NG + NS>* carry) {
     constexpr int NOSC = NE + NG + NS;
@@ -336,7 +356,7 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
     constexpr bool NEED_TT = KT || (NG > 0 && MODE >= kGrad);
     const float nf0 = (float)n0;
     const float n0p = hc.n0, n0lo = hc.n0_lo, bkg = hc.bkg;
-    float E = hc.cE * ex2_approx(-fmaf(nf0, hc.aE_hi, nf0 * hc.aE_lo));
+    float E = E0;
     float C[NOSC > 0 ? NOSC : 1], Sn[NOSC > 0 ? NOSC : 1], gq[NOSC > 0 ? NOSC : 1];
     float stA[NOSC > 0 ? NOSC : 1], stB[NOSC > 0 ? NOSC : 1];
     const float k1 = fmaf(2.f, nf0, 1.f);  // 2 n0 + 1
@@ -557,12 +577,276 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
 // stripe apart (the staged qs constants must be for that stripe)
 template <int NE, int NG, int NS, int KT, int MODE, int NACC>
 __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M, const float (&d)[kBinsPerThread],
-                                           int obj, float dtf, float t0f, float (&acc)[NACC], bool& bad,
+                                           float E0, int obj, float dtf, float t0f, float (&acc)[NACC], bool& bad,
                                            float* model_dst, GqCarry<NE + NG + NS>* carry = nullptr) {
     if (n0 + kBinsPerThread <= M)
-        eval_chunk_body<NE, NG, NS, KT, MODE, NACC, true>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
+        eval_chunk_body<NE, NG, NS, KT, MODE, NACC, true>(hc, n0, M, d, E0, obj, dtf, t0f, acc, bad, model_dst,
+                                                          carry);
     else
-        eval_chunk_body<NE, NG, NS, KT, MODE, NACC, false>(hc, n0, M, d, obj, dtf, t0f, acc, bad, model_dst, carry);
+        eval_chunk_body<NE, NG, NS, KT, MODE, NACC, false>(hc, n0, M, d, E0, obj, dtf, t0f, acc, bad, model_dst,
+                                                           carry);
+}
+
+// ---- packed FP32 pairs: two bins per instruction (FFMA2 / FMUL2 / FADD2) ----
+//
+// The value and adjoint modes step the even and odd bins of a thread's 8-bin
+// chunk as the two lanes of float2 operands: lane x holds bins n0, n0+2, n0+4,
+// n0+6 and lane y bins n0+1, n0+3, n0+5, n0+7, so the counts come out of the
+// two 128-bit loads already paired.  Every recurrence advances a lane by two
+// bins (the 2-bin constants staged with the 1-bin ones); lane y is seeded
+// from lane x by one 1-bin step.  The arithmetic per bin is that of
+// eval_chunk_body, in half the instructions.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// The Gaussian 2-bin step ratios (minus 1) of both lanes at a thread's next
+// chunk, one stripe further: G2(n + stripe) = G2(n) Qs2 + (Qs2 - 1).
+template <int NOSC>
+struct G2Carry {
+    float2 g2[NOSC > 0 ? NOSC : 1];
+    float2 g2k;
+    bool valid;
+};
+
+// 2-bin ratio minus 1 of a Gaussian envelope exp2(-(a n + b n^2)) at bin n:
+// 2^(-(2 a + 4 b (n + 1))) - 1.
+__device__ __forceinline__ float gauss_ratio2(float a_hi, float a_lo, float b_hi, float b_lo, int n) {
+    const float k4 = 4.f * (float)(n + 1);
+    return step_expm1(-0.693147180559945309f * fmaf(k4, b_hi, fmaf(k4, b_lo, 2.f * (a_hi + a_lo))));
+}
+
+// One chunk of 8 bins starting at n0 (a multiple of 8) in packed lanes:
+// MODE kValue or kGrad.  d holds the chunk's counts, E0 the lifetime factor at
+// n0; acc are the per-lane accumulators (lane sums are added after the
+// chunks).  FULL: all 8 bins lie below M.
+template <int NE, int NG, int NS, int KT, int MODE, int NACC, bool FULL>
+__device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int M,
+                                               const float (&d)[kBinsPerThread], float E0, int obj, float dtf,
+                                               float t0f, float2 (&acc)[NACC], bool& bad,
+                                               G2Carry<NE + NG + NS>* carry) {
+    static_assert(MODE == kValue || MODE == kGrad, "packed lanes serve the value and gradient modes");
+    constexpr int NOSC = NE + NG + NS;
+    constexpr int CS = NE + NG;       // index of the stretched line (when NS)
+    constexpr int RB = 2 + 4 * NOSC;  // role of its exponent beta
+    constexpr int RK = RB + NS;       // first Kubo-Toyabe role
+    constexpr bool NEED_TT = KT || (NG > 0 && MODE >= kGrad);
+    const float nf0 = (float)n0;
+    const float2 n0p = bc2(hc.n0), n0lo = bc2(hc.n0_lo), bkg = bc2(hc.bkg);
+    // lifetime factor: lane y one bin further
+    float2 E = make_float2(E0, fmaf(E0, hc.qE, E0));
+    const float2 qE2 = bc2(hc.qE2);
+    float2 C[NOSC > 0 ? NOSC : 1], Sn[NOSC > 0 ? NOSC : 1], g2[NOSC > 0 ? NOSC : 1];
+    float2 stA[NOSC > 0 ? NOSC : 1], stB[NOSC > 0 ? NOSC : 1], nstB[NOSC > 0 ? NOSC : 1];
+    const float k1 = fmaf(2.f, nf0, 1.f);  // 2 n0 + 1
+    const float nn0 = nf0 * nf0;
+#pragma unroll
+    for (int c = 0; c < NOSC; ++c) {
+        const OscConst& o = hc.osc[c];
+        // lane x: exact seed at n0 (fixed-point phase, SFU sincos and exp2)
+        const unsigned long long ph = o.ph0 + (unsigned long long)n0 * o.step;
+        const float x = (float)(int)(ph >> 32) * 2.3283064365386963e-10f;  // turns in [-1/2, 1/2)
+        float sc, cc;
+        __sincosf(6.28318530717958647692f * x, &sc, &cc);
+        // lane y: one 1-bin rotation further
+        const float cy = fmaf(cc, o.cm1, fmaf(-sc, o.sn, cc));
+        const float sy = fmaf(sc, o.cm1, fmaf(cc, o.sn, sc));
+        float env, envy;
+        if (NS && c >= CS) {
+            env = envy = 1.f;  // the stretched envelope is evaluated per bin
+            stA[c] = bc2(o.cm1_2);
+            stB[c] = bc2(o.sn_2);
+        } else if (c < NE) {
+            env = o.cenv * ex2_approx(-fmaf(nf0, o.a_hi, nf0 * o.a_lo));
+            envy = fmaf(env, o.q, env);
+            // two bins' step: (1 + q2) (cos 2d, sin 2d) = (1 + A, B)
+            stA[c] = bc2(fmaf(o.q2, o.cm1_2, o.q2 + o.cm1_2));
+            stB[c] = bc2(fmaf(o.q2, o.sn_2, o.sn_2));
+        } else {
+            env = o.cenv * ex2_approx(-fmaf(nn0, o.b_hi, fmaf(nf0, o.a_hi, fmaf(nn0, o.b_lo, nf0 * o.a_lo))));
+            // 1-bin ratio at n0 (lane y's seed), then both lanes' 2-bin ratios
+            const float gq1 = step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
+            envy = fmaf(env, gq1, env);
+            if (carry && carry->valid) {
+                g2[c] = carry->g2[c];
+            } else {
+                g2[c] = make_float2(gauss_ratio2(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0),
+                                    gauss_ratio2(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0 + 1));
+            }
+            if (carry) carry->g2[c] = fma2(g2[c], bc2(o.qs2), add2(g2[c], bc2(o.qs2)));
+            stA[c] = bc2(o.cm1_2);
+            stB[c] = bc2(o.sn_2);
+        }
+        nstB[c] = make_float2(-stB[c].x, -stB[c].y);
+        C[c] = make_float2(env * cc, envy * cy);
+        Sn[c] = make_float2(env * sc, envy * sy);
+    }
+    // Kubo-Toyabe: G(t) e^{-t/tau} = E / 3 + (1 - x) e23,  x = (Delta t)^2,
+    // e23 = 2/3 exp(-t/tau - x/2), stepped like a Gaussian envelope
+    float2 e23 = bc2(0.f), g2k = bc2(0.f), nkr2 = bc2(0.f), kr2 = bc2(0.f);
+    if (KT) {
+        const float ex = 0.666666667f * hc.kt_cenv *
+                         ex2_approx(-fmaf(nn0, hc.kt_b_hi, fmaf(nf0, hc.kt_a_hi, fmaf(nn0, hc.kt_b_lo, nf0 * hc.kt_a_lo))));
+        const float gq1 =
+            step_expm1(-0.693147180559945309f * fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
+        e23 = make_float2(ex, fmaf(ex, gq1, ex));
+        if (carry && carry->valid) {
+            g2k = carry->g2k;
+        } else {
+            g2k = make_float2(gauss_ratio2(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0),
+                              gauss_ratio2(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0 + 1));
+        }
+        if (carry) carry->g2k = fma2(g2k, bc2(hc.kt_qs2), add2(g2k, bc2(hc.kt_qs2)));
+        const float r2 = hc.kt_rate * hc.kt_rate;
+        kr2 = bc2(r2);
+        nkr2 = bc2(-r2);
+    }
+    if (carry) carry->valid = true;
+    const float tsx = fmaf(nf0, dtf, t0f);
+    const float2 ts = make_float2(tsx, tsx + dtf);
+    const float2 dt2 = bc2(2.f * dtf);
+    const float2 m1 = bc2(-1.f), one = bc2(1.f), third = bc2(0.333333333f), m3 = bc2(-3.f);
+#pragma unroll
+    for (int j = 0; j < kBinsPerThread / 2; ++j) {
+        const float2 t = fma2(bc2((float)j), dt2, ts);
+        const float2 tt = NEED_TT ? mul2(t, t) : bc2(0.f);
+        float2 Cb[NOSC > 0 ? NOSC : 1], Sb[NOSC > 0 ? NOSC : 1];
+        float2 sp = bc2(0.f), slg = bc2(0.f);  // stretched line: (lambda t)^beta and log2(lambda t) per lane
+#pragma unroll
+        for (int c = 0; c < NOSC; ++c) {
+            if (NS && c >= CS) {
+                const float2 u = mul2(bc2(hc.osc[c].rate), t);
+                const float lx = lg2_approx(u.x), ly = lg2_approx(u.y);
+                sp = make_float2(u.x > 0.f ? ex2_approx(hc.osc[c].beta * lx) : 0.f,
+                                 u.y > 0.f ? ex2_approx(hc.osc[c].beta * ly) : 0.f);
+                slg = make_float2(u.x > 0.f ? lx : 0.f, u.y > 0.f ? ly : 0.f);
+                const float2 ev = mul2(E, make_float2(ex2_approx(-1.44269504088896341f * sp.x),
+                                                      ex2_approx(-1.44269504088896341f * sp.y)));
+                Cb[c] = mul2(ev, C[c]);
+                Sb[c] = mul2(ev, Sn[c]);
+            } else {
+                Cb[c] = C[c];
+                Sb[c] = Sn[c];
+            }
+        }
+        float2 S = E;
+#pragma unroll
+        for (int c = 0; c < NOSC; ++c) S = fma2(bc2(hc.osc[c].amp), Cb[c], S);
+        float2 GE = bc2(0.f), xm3 = bc2(0.f);
+        if (KT) {
+            const float2 omx = fma2(nkr2, tt, one);  // 1 - (Delta t)^2
+            GE = fma2(e23, omx, mul2(E, third));
+            if (MODE == kGrad) xm3 = fma2(kr2, tt, m3);  // (Delta t)^2 - 3
+            S = fma2(bc2(hc.kt_amp), GE, S);
+        }
+        // N0 carried as an FP32 pair so its rounding does not bias every bin
+        const float2 N = fma2(n0p, S, fma2(n0lo, S, bkg));
+        const float2 dv = make_float2(d[2 * j], d[2 * j + 1]);
+        const bool vx = FULL || n0 + 2 * j < M, vy = FULL || n0 + 2 * j + 1 < M;
+        float2 wq;
+        if (obj == MUSR_CHI2) {
+            float2 w = make_float2(rcp_approx(fmaxf(dv.x, 1.f)), rcp_approx(fmaxf(dv.y, 1.f)));
+            if (!FULL) w = make_float2(vx ? w.x : 0.f, vy ? w.y : 0.f);
+            const float2 r = fma2(N, m1, dv);
+            wq = mul2(r, w);
+            acc[0] = fma2(r, wq, acc[0]);
+        } else {
+            float term[2], wl[2];
+            const float dl[2] = {dv.x, dv.y}, Nl[2] = {N.x, N.y};
+            const bool vl[2] = {vx, vy};
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                term[h] = wl[h] = 0.f;
+                if (!vl[h]) continue;
+                if (dl[h] > 0.f) {
+                    if (!(Nl[h] > 0.f)) {
+                        bad = true;
+                    } else {
+                        const float rN = rcp_approx(Nl[h]);
+                        const float rho = (dl[h] - Nl[h]) * rN;
+                        float hh;
+                        if (fabsf(rho) < 0.125f) {
+                            // sum_{j>=2} (-1)^j rho^j / (j (j-1)), truncated after j = 9
+                            hh = fmaf(rho, -1.f / 72.f, 1.f / 56.f);
+                            hh = fmaf(rho, hh, -1.f / 42.f);
+                            hh = fmaf(rho, hh, 1.f / 30.f);
+                            hh = fmaf(rho, hh, -1.f / 20.f);
+                            hh = fmaf(rho, hh, 1.f / 12.f);
+                            hh = fmaf(rho, hh, -1.f / 6.f);
+                            hh = fmaf(rho, hh, 0.5f);
+                            hh = hh * rho * rho;
+                        } else {
+                            const float u = log1pf(rho);
+                            hh = fmaf(rho, u, u - rho);
+                        }
+                        term[h] = 2.f * Nl[h] * hh;
+                        wl[h] = rho;
+                    }
+                } else {
+                    if (!(Nl[h] >= 0.f)) bad = true;
+                    term[h] = 2.f * Nl[h];
+                    wl[h] = -1.f;
+                }
+            }
+            acc[0] = add2(acc[0], make_float2(term[0], term[1]));
+            wq = make_float2(wl[0], wl[1]);
+        }
+        if (MODE == kGrad) {
+            const float2 wt = mul2(wq, t);
+            const float2 wtt = NEED_TT ? mul2(wq, tt) : bc2(0.f);
+            acc[1] = fma2(wq, S, acc[1]);
+            acc[2] = add2(acc[2], wq);
+#pragma unroll
+            for (int c = 0; c < NOSC; ++c) {
+                acc[3 + 4 * c] = fma2(wq, Cb[c], acc[3 + 4 * c]);
+                if (NS && c >= CS) {
+                    const float2 pc = mul2(sp, Cb[c]);
+                    acc[4 + 4 * c] = fma2(wq, pc, acc[4 + 4 * c]);
+                    acc[1 + RB] = fma2(wq, mul2(pc, slg), acc[1 + RB]);
+                } else {
+                    acc[4 + 4 * c] = fma2(c < NE ? wt : wtt, Cb[c], acc[4 + 4 * c]);
+                }
+                acc[5 + 4 * c] = fma2(wt, Sb[c], acc[5 + 4 * c]);
+                acc[6 + 4 * c] = fma2(wq, Sb[c], acc[6 + 4 * c]);
+            }
+            if (KT) {
+                acc[1 + RK] = fma2(wq, GE, acc[1 + RK]);
+                acc[2 + RK] = fma2(mul2(wtt, xm3), e23, acc[2 + RK]);
+            }
+        }
+        // step every lane by two bins
+        E = fma2(E, qE2, E);
+#pragma unroll
+        for (int c = 0; c < NOSC; ++c) {
+            const float2 c2 = fma2(C[c], stA[c], fma2(Sn[c], nstB[c], C[c]));
+            const float2 s2 = fma2(Sn[c], stA[c], fma2(C[c], stB[c], Sn[c]));
+            if (c < NE || c >= CS) {
+                C[c] = c2;
+                Sn[c] = s2;
+            } else {
+                C[c] = fma2(c2, g2[c], c2);
+                Sn[c] = fma2(s2, g2[c], s2);
+                const float2 q2 = bc2(hc.osc[c].q2);
+                g2[c] = fma2(g2[c], q2, add2(g2[c], q2));
+            }
+        }
+        if (KT) {
+            e23 = fma2(e23, g2k, e23);
+            const float2 q2 = bc2(hc.kt_q2);
+            g2k = fma2(g2k, q2, add2(g2k, q2));
+        }
+    }
+}
+
+template <int NE, int NG, int NS, int KT, int MODE, int NACC>
+__device__ __forceinline__ void eval_pair(const HistConst& hc, int n0, int M, const float (&d)[kBinsPerThread],
+                                          float E0, int obj, float dtf, float t0f, float2 (&acc)[NACC], bool& bad,
+                                          G2Carry<NE + NG + NS>* carry) {
+    if (n0 + kBinsPerThread <= M)
+        eval_pair_body<NE, NG, NS, KT, MODE, NACC, true>(hc, n0, M, d, E0, obj, dtf, t0f, acc, bad, carry);
+    else
+        eval_pair_body<NE, NG, NS, KT, MODE, NACC, false>(hc, n0, M, d, E0, obj, dtf, t0f, acc, bad, carry);
 }
 
 // The per-histogram constant of accumulator a (see eval_chunk): 1 for the
@@ -613,9 +897,57 @@ __device__ __forceinline__ float acc_factor(const HistConst& hc, int a) {
 }
 
 
+// ---- deterministic fixed-point accumulation ----
+// Each warp's role-factored FP32 totals become the integers X = v 2^48 (exact
+// for |v| >= 2^-24, truncated below; |v| < 2^72); a block sums its warps' X
+// in shared memory and adds the block total, split into three 42-bit limbs,
+// with 64-bit atomic adds whose results are unused (no round trip).  Integer
+// addition is associative, so the per-histogram totals are bitwise the same
+// whatever order the blocks finish in; with at most 2^22 additions per
+// accumulator no limb overflows.  Sums of totals (the map to theta) are formed on the
+// integers too, and each output is converted to FP64 once: no FP64 addition
+// chains (FP64 has a long latency on this GPU).
+constexpr int kFixFracBits = 48;
+constexpr int kFixLimbBits = 42;
+
+// X = v 2^48 as an integer (truncated below 2^-48); false when v is not
+// finite or |v| >= 2^72 (X = 0 then).  A block sums at most 8 such values, so
+// its total stays below 2^123.
+__device__ __forceinline__ bool fix_of(float v, __int128& X) {
+    const unsigned bits = __float_as_uint(v);
+    const int e = (int)((bits >> 23) & 0xffu);
+    X = 0;
+    if (e == 0xff || e >= 127 + 72) return false;
+    if (e == 0) return true;  // zero or below 2^-126: nothing at the 2^-48 resolution
+    const long long m = (long long)((bits & 0x7fffffu) | 0x800000u);
+    const int sh = e - 150 + kFixFracBits;  // |v| 2^48 = m 2^sh
+    X = sh >= 0 ? ((__int128)m << sh) : (__int128)(m >> min(-sh, 63));
+    if (bits >> 31) X = -X;
+    return true;
+}
+
+// Add X to three 42-bit limbs (atomics whose results are unused).
+__device__ __forceinline__ void fix_add(unsigned long long* limbs, __int128 X) {
+    const unsigned long long mask = (1ull << kFixLimbBits) - 1ull;
+    atomicAdd(limbs + 0, (unsigned long long)X & mask);
+    atomicAdd(limbs + 1, (unsigned long long)(X >> kFixLimbBits) & mask);
+    atomicAdd(limbs + 2, (unsigned long long)(long long)(X >> (2 * kFixLimbBits)));
+}
+
+// The integer total of three accumulated limbs.
+__device__ __forceinline__ __int128 fix_total(unsigned long long l0, unsigned long long l1, unsigned long long l2) {
+    return (__int128)l0 + ((__int128)l1 << kFixLimbBits) + ((__int128)(long long)l2 << (2 * kFixLimbBits));
+}
+
+// X / 2^48 in FP64 (the one rounding of a sum).
+__device__ __forceinline__ double fix_to_double(__int128 X) {
+    const long long hi = (long long)(X >> 64);
+    const unsigned long long lo = (unsigned long long)X;
+    return fma((double)hi, 65536.0, (double)lo * 3.5527136788005009e-15);  // hi 2^16 + lo 2^-48
+}
+
 template <int NE, int NG, int NS, int KT, int MODE>
 __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant__ EvalParams p) {
-    namespace cg = cooperative_groups;
     constexpr int NOSC = NE + NG + NS;
     constexpr int R = 2 + 4 * NOSC + NS + 2 * KT;
     constexpr int NACC = MODE == kValue ? 1 : MODE == kGrad ? 1 + R : MODE == kGN ? 1 + R + R * (R + 1) / 2 : 1;
@@ -623,7 +955,6 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 
     __shared__ HistConst hc;
     __shared__ float red[kMaxWarps][NACC];
-    __shared__ DF cpart[8][NACC];  // the cluster leader's copy receives every block's sums
     __shared__ int s_last;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
@@ -646,8 +977,11 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     const int stripe = (int)blockDim.x * G;  // a tile is p.chunks stripes of blockDim x 8 bins
     int n0 = tstart + (int)threadIdx.x * G;
 
-    // issue the first chunk's loads so their latency overlaps the staging
+    // issue the first chunk's loads (counts and the lifetime factor at its
+    // start) so their latency overlaps the staging
     float d[G];
+    float E0 = 0.f;
+    if (n0 < M) E0 = __ldg(p.etab + (n0 >> 3));
     if (MODE != kModel && n0 < M) {
         const float4* src = reinterpret_cast<const float4*>(hdata + n0);
         float4 a = __ldg(src), b = __ldg(src + 1);
@@ -660,25 +994,17 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 
     // stage histogram k's constants: one part per warp, so the parts' latency
     // chains overlap (theta is inline in the launch parameters for host calls);
-    // warps not staging preload the tail's small tables (only the last block
-    // will read them, but no block knows yet whether it is last)
-    const int W = p.win_doubles;  // window of cluster partials, a multiple of NACC
-    int32_t* tbl = reinterpret_cast<int32_t*>(reinterpret_cast<DF*>(dyn_smem) + W +
-                                              (p.hsum_in_smem ? p.K * NACC : 0));
+    // warps not staging preload the tail's CSR (only the last block will read
+    // it, but no block knows yet whether it is last)
+    __int128* hsum = p.hsum_in_smem ? reinterpret_cast<__int128*>(dyn_smem) : p.hist_sum;
+    int32_t* tbl = reinterpret_cast<int32_t*>(dyn_smem + (p.hsum_in_smem ? sizeof(__int128) * p.K * NACC : 0));
     {
         constexpr int NPART = stage_parts<NE, NG, NS, KT>();
         if (MODE != kModel && p.preload && (int)threadIdx.x >= 32 * NPART) {
-            const int n1 = p.n_out + 1, n2 = p.n_src, n3 = p.n_clusters, n4 = p.K;
+            const int n1 = p.n_out + 1, n2 = p.n_src;
             const int stride = (int)blockDim.x - 32 * NPART;
-            for (int i = (int)threadIdx.x - 32 * NPART; i < n1 + n2 + n3 + 2 * n4; i += stride) {
-                int32_t v;
-                if (i < n1) v = p.csr_ptr[i];
-                else if (i < n1 + n2) v = p.csr_src[i - n1];
-                else if (i < n1 + n2 + n3) v = p.cluster_hist[i - n1 - n2];
-                else if (i < n1 + n2 + n3 + n4) v = p.hist_first_cluster[i - n1 - n2 - n3];
-                else v = p.hist_nclusters[i - n1 - n2 - n3 - n4];
-                tbl[i] = v;
-            }
+            for (int i = (int)threadIdx.x - 32 * NPART; i < n1 + n2; i += stride)
+                tbl[i] = i < n1 ? p.csr_ptr[i] : p.csr_src[i - n1];
         }
         const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
         const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
@@ -691,118 +1017,135 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
     bool bad = false;
-    GqCarry<NOSC> carry;
-    carry.valid = false;
 
-    for (int c = 0; c < p.chunks; ++c) {
-        // the next chunk's loads are in flight while this one is evaluated
-        const int n1 = n0 + stripe;
-        float dn[G];
-        if (MODE != kModel && c + 1 < p.chunks && n1 < M) {
-            const float4* src = reinterpret_cast<const float4*>(hdata + n1);
-            float4 a = __ldg(src), b = __ldg(src + 1);
-            dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
-            dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
-        } else {
+    if constexpr (MODE == kValue || MODE == kGrad) {
+        // packed lanes (even / odd bins), lane sums added after the chunks
+        float2 acc2[NACC];
 #pragma unroll
-            for (int g = 0; g < G; ++g) dn[g] = 0.f;
+        for (int a = 0; a < NACC; ++a) acc2[a] = make_float2(0.f, 0.f);
+        G2Carry<NOSC> carry;
+        carry.valid = false;
+        for (int c = 0; c < p.chunks; ++c) {
+            // the next chunk's loads are in flight while this one is evaluated
+            const int n1 = n0 + stripe;
+            float dn[G];
+            float En = 0.f;
+            if (c + 1 < p.chunks && n1 < M) {
+                const float4* src = reinterpret_cast<const float4*>(hdata + n1);
+                float4 a = __ldg(src), b = __ldg(src + 1);
+                dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
+                dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
+                En = __ldg(p.etab + (n1 >> 3));
+            } else {
+#pragma unroll
+                for (int g = 0; g < G; ++g) dn[g] = 0.f;
+            }
+            if (n0 < M)
+                eval_pair<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc2, bad,
+                                                      &carry);
+#pragma unroll
+            for (int g = 0; g < G; ++g) d[g] = dn[g];
+            E0 = En;
+            n0 = n1;
         }
-        if (n0 < M)
-            eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, p.obj, (float)p.dt, (float)p.t0, acc, bad,
-                                               MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
 #pragma unroll
-        for (int g = 0; g < G; ++g) d[g] = dn[g];
-        n0 = n1;
+        for (int a = 0; a < NACC; ++a) acc[a] = acc2[a].x + acc2[a].y;
+    } else {
+        GqCarry<NOSC> carry;
+        carry.valid = false;
+        for (int c = 0; c < p.chunks; ++c) {
+            // the next chunk's loads are in flight while this one is evaluated
+            const int n1 = n0 + stripe;
+            float dn[G];
+            float En = 0.f;
+            if (c + 1 < p.chunks && n1 < M) {
+                En = __ldg(p.etab + (n1 >> 3));
+                if (MODE != kModel) {
+                    const float4* src = reinterpret_cast<const float4*>(hdata + n1);
+                    float4 a = __ldg(src), b = __ldg(src + 1);
+                    dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
+                    dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
+                }
+            }
+            if (MODE == kModel || !(c + 1 < p.chunks && n1 < M)) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) dn[g] = 0.f;
+            }
+            if (n0 < M)
+                eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc, bad,
+                                                       MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
+#pragma unroll
+            for (int g = 0; g < G; ++g) d[g] = dn[g];
+            E0 = En;
+            n0 = n1;
+        }
     }
     if (MODE == kModel) return;
 
-    // ---- block: FP32 warp sums, double-float across warps ----
+    // ---- block: FP32 warp sums scaled by the histogram's role factors, as
+    // fixed-point integers summed over the warps, one fixed-point add per
+    // accumulator into the histogram's totals ----
     warp_sum<NACC>(acc);
     if (lane == 0) {
 #pragma unroll
         for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
     }
     const int any_bad = __syncthreads_or(bad);
-    if (threadIdx.x == 0 && any_bad) atomicOr(p.flags, 1u);
-
-    // ---- cluster: every block pushes its sums into the leader's shared memory
-    // (distributed shared memory stores), one cluster barrier, the leader adds ----
-    cg::cluster_group cl = cg::this_cluster();
-    const unsigned rank = cl.block_rank(), csize = cl.num_blocks();
     {
-        DF* dst = &cl.map_shared_rank(&cpart[0][0], 0)[rank * NACC];
+        unsigned flag = (threadIdx.x == 0 && any_bad) ? 1u : 0u;
         for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
-            DF v{red[0][a], 0.f};
-            for (int w = 1; w < nwarps; ++w) v = df_add(v, DF{red[w][a], 0.f});
-            // the histogram's role factor (all blocks of a cluster share the histogram)
-            if (MODE >= kGrad && a > 0) v = df_mul(v, DF{acc_factor<NE, NG, NS, KT, MODE>(hc, a), 0.f});
-            dst[a] = v;
+            const float f = (MODE >= kGrad && a > 0) ? acc_factor<NE, NG, NS, KT, MODE>(hc, a) : 1.f;
+            __int128 X = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                __int128 x;
+                if (!fix_of(red[w][a] * f, x)) flag |= 2u;
+                X += x;
+            }
+            fix_add(p.facc + ((size_t)k * NACC + a) * 3, X);
         }
-    }
-    cl.sync();
-    if (rank != 0) return;
-    DF* partial = reinterpret_cast<DF*>(p.partial);
-    {
-        const int cidx = blockIdx.x / (int)csize;
-        for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
-            DF v = cpart[0][a];
-            for (unsigned r = 1; r < csize; ++r) v = df_add(v, cpart[r][a]);
-            partial[(size_t)cidx * NACC + a] = v;
-        }
+        if (flag) atomicOr(p.flags, flag);
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned prev = atomicAdd(p.global_count, 1u);
-        s_last = (prev == (unsigned)p.n_clusters - 1u);
+        s_last = (prev == gridDim.x - 1u);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
 
-    // ---- last cluster leader: histogram sums (fixed order), then theta via the map ----
-    DF* win = reinterpret_cast<DF*>(dyn_smem);
-    const int32_t* t_cptr = p.preload ? tbl : p.csr_ptr;
-    const int32_t* t_csrc = p.preload ? tbl + p.n_out + 1 : p.csr_src;
-    const int32_t* t_chist = p.preload ? tbl + p.n_out + 1 + p.n_src : p.cluster_hist;
-    const int32_t* t_hfirst = p.preload ? t_chist + p.n_clusters : p.hist_first_cluster;
-    const int32_t* t_hncl = p.preload ? t_hfirst + p.K : p.hist_nclusters;
-    DF* hsum = p.hsum_in_smem ? win + W : reinterpret_cast<DF*>(p.hist_sum);
-    for (int i = threadIdx.x; i < p.K * NACC; i += blockDim.x) hsum[i] = DF{0.f, 0.f};
-    const int total = p.n_clusters * NACC;
-    for (int i0 = 0; i0 < total; i0 += W) {
-        const int n = min(W, total - i0);
-        __syncthreads();
-        copy_to_smem(reinterpret_cast<float2*>(win), reinterpret_cast<const float2*>(partial + i0), n);
-        __syncthreads();
-        const int c0 = i0 / NACC, c1 = c0 + n / NACC;
-        const int k0 = t_chist[c0], k1 = t_chist[c1 - 1];
-        for (int q = threadIdx.x; q < (k1 - k0 + 1) * NACC; q += blockDim.x) {
-            const int kk = k0 + q / NACC, a = q % NACC;
-            const int first = t_hfirst[kk];
-            const int lo = max(first, c0), hi = min(first + t_hncl[kk], c1);
-            DF s = hsum[kk * NACC + a];
-            for (int c = lo; c < hi; ++c) s = df_add(s, win[(c - c0) * NACC + a]);
-            hsum[kk * NACC + a] = s;
-        }
+    // ---- last block: per-histogram integer totals (their limbs zeroed for the
+    // next launch), then theta via the CSR map, summed as integers; every load
+    // of the tail is issued before any result is needed ----
+    const unsigned fl = *reinterpret_cast<volatile unsigned*>(p.flags);
+    const int32_t* cptr = p.preload ? tbl : p.csr_ptr;
+    const int32_t* csrc = p.preload ? tbl + p.n_out + 1 : p.csr_src;
+    if (!p.preload && p.csr_in_smem) {
+        copy_to_smem(tbl, p.csr_ptr, p.n_out + 1);
+        copy_to_smem(tbl + p.n_out + 1, p.csr_src, p.n_src);
+        cptr = tbl;
+        csrc = tbl + p.n_out + 1;
+    }
+#pragma unroll 2
+    for (int i = threadIdx.x; i < p.K * NACC; i += blockDim.x) {
+        unsigned long long* l = p.facc + (size_t)i * 3;
+        const unsigned long long l0 = __ldcg(l), l1 = __ldcg(l + 1), l2 = __ldcg(l + 2);
+        hsum[i] = fix_total(l0, l1, l2);
+        l[0] = 0ull;
+        l[1] = 0ull;
+        l[2] = 0ull;
     }
     __syncthreads();
-    const int32_t* cptr = t_cptr;
-    const int32_t* csrc = t_csrc;
-    if (!p.preload && p.csr_in_smem) {
-        int32_t* sp = reinterpret_cast<int32_t*>(win + W + (p.hsum_in_smem ? p.K * NACC : 0));
-        copy_to_smem(sp, p.csr_ptr, p.n_out + 1);
-        copy_to_smem(sp + p.n_out + 1, p.csr_src, p.n_src);
-        __syncthreads();
-        cptr = sp;
-        csrc = sp + p.n_out + 1;
-    }
+    const bool overflow = (fl & 2u) != 0u;
     double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
     for (int o = threadIdx.x; o < p.n_out; o += blockDim.x) {
-        DF s{0.f, 0.f};
+        __int128 X = 0;
         const int e = cptr[o + 1];
-        for (int j = cptr[o]; j < e; ++j) s = df_add(s, hsum[csrc[j]]);
-        const double v = (double)s.hi + (double)s.lo;  // exact: |lo| <= ulp(hi) / 2
+#pragma unroll 4
+        for (int j = cptr[o]; j < e; ++j) X += hsum[csrc[j]];
+        // NaN when a warp total was not representable (not finite, or >= 2^72)
+        const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll) : fix_to_double(X);
         p.out[o] = v;
         if (o == 0) out0 = v;
     }
@@ -811,7 +1154,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     __syncthreads();
     if (threadIdx.x == 0) {
         *p.global_count = 0u;
-        unsigned f = atomicExch(p.flags, 0u);
+        *p.flags = 0u;  // every block's flags arrived before its ticket
+        unsigned f = fl & 1u;
         if (!isfinite(out0)) f |= 2u;
         if (p.status_out) {
             if (p.status_sys_fence) __threadfence_system();
@@ -820,9 +1164,9 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     }
 }
 
-// Launch the objective kernel in clusters of p.cluster blocks.  n_tiles == 0
-// only sets the kernel's shared-memory attribute (call it outside capture);
-// n_tiles < 0 only reports the kernel's resident blocks per SM.
+// Launch the objective kernel.  n_tiles == 0 only sets the kernel's
+// shared-memory attribute (call it outside capture); n_tiles < 0 only reports
+// the kernel's resident blocks per SM.
 template <int NE, int NG, int NS, int KT, int MODE>
 cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const EvalParams& p) {
     const size_t smem = (size_t)p.smem_bytes;
@@ -849,19 +1193,8 @@ cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const Eval
         return cudaFuncSetAttribute(eval_kernel<NE, NG, NS, KT, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(n_tiles);
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = p.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, eval_kernel<NE, NG, NS, KT, MODE>, p);
+    eval_kernel<NE, NG, NS, KT, MODE><<<n_tiles, threads, smem, stream>>>(p);
+    return cudaGetLastError();
 }
 
 }  // namespace musr

@@ -28,8 +28,11 @@ int gbatch_n_runs(musr_gbatch b);
 musr_run gbatch_run(musr_gbatch b, int r);
 // Central-difference gradient (and, if hdiag != NULL, the diagonal second
 // differences) of the objective over the free entries, one batched launch.
+// Central differences of the objective along every free parameter fidx[a]
+// with absolute steps h_abs[a] (order 2: +-h; order 4: +-h, +-2h), in one
+// batched launch (batch.cu); hdiag (or NULL) receives the second differences.
 int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
-                      double rel_h, double* value, double* grad, double* hdiag);
+                      const double* h_abs, int order, double* value, double* grad, double* hdiag);
 }
 
 using namespace musr;
@@ -101,6 +104,26 @@ double edm_of(const std::vector<double>& g, const std::vector<double>& H, const 
 // Relative resolution of objective values computed with FP32 evaluation and
 // FP64 accumulation: below it, value comparisons are decided by rounding.
 constexpr double kValueNoise = 1e-6;
+
+// The adjoint gradient of an FP32 evaluation resolves the EDM only down to a
+// floor that grows with the number of bins (~2e-8 at 4e6 bins).  When a step
+// below the value resolution no longer lowers the EDM and the EDM is within
+// this factor of the tolerance (distance to the minimum ~3e-4 of the
+// parameter errors for the default 1e-8), the fit has converged as far as
+// the arithmetic allows.
+constexpr double kEdmResolution = 10.0;
+
+// Central-difference fits with automatic steps: fourth-order differences
+// with a step of kFdStepSigma standard errors along each free parameter (from
+// second differences at the start).  The FP32 value noise enters the gradient
+// divided by the step, so the step must be of the parameter's own scale, and
+// at that scale second-order differences would carry a truncation error of
+// ~1e-3 of the errors on correlated, curved directions; fourth-order ones
+// do not.  They stop after kFdStallSteps successive accepted steps that each
+// move every free parameter by less than kFdStallSigma of its standard error.
+constexpr double kFdStepSigma = 1.0;
+constexpr double kFdStallSigma = 1e-4;
+constexpr int kFdStallSteps = 3;
 
 }  // namespace
 
@@ -175,7 +198,7 @@ struct LmStepper {
     }
     // s2: MUSR_OK, MUSR_EDOMAIN or MUSR_ENONFINITE (other errors end the fit upstream)
     void observe(int s2, double ft) {
-        bool accept = false;
+        bool accept = false, at_resolution = false;
         double edm_t = INFINITY;
         if (s2 == MUSR_OK) {
             const double noise = kValueNoise * fabs(f);
@@ -185,7 +208,13 @@ struct LmStepper {
                 // the change is below the value resolution: let the gradient decide
                 edm_t = edm_of(gt, Ht, fidx, P, A, b);
                 accept = edm_t < edm;
+                at_resolution = !accept && edm < kEdmResolution * o.edm_tol;
             }
+        }
+        if (at_resolution) {
+            result = MUSR_OK;
+            done = true;
+            return;
         }
         if (accept) {
             const double rel = (f - ft) / std::max(fabs(f), 1e-300);
@@ -257,7 +286,7 @@ struct BfgsStepper {
     std::vector<int> fidx;
     musr_fit_opts o{};
     bool fd = false;
-    std::vector<double> theta, g, gt, x, Hi, d, hi0;
+    std::vector<double> theta, g, gt, x, Hi, d, hi0, inv_sig;
     double f = 0.0, edm = INFINITY, slope = 0.0, step = 1.0;
     int it = 0, result = MUSR_ENOCONV, stall = 0, ls = 0;
     bool done = false, in_ls = false;
@@ -275,6 +304,7 @@ struct BfgsStepper {
         Hi.assign((size_t)nf * nf, 0.0);
         d.assign(nf, 0.0);
         hi0.assign(nf, 0.0);
+        inv_sig.assign(nf, 0.0);
     }
     // after the start evaluation (value f0, gradient in g); hd: Hessian diagonal or null
     void start(double f0, const double* hd) {
@@ -286,6 +316,7 @@ struct BfgsStepper {
             const double h = hd ? hd[fidx[a]] : 0.0;
             hi0[a] = (h > 0.0 && std::isfinite(h)) ? 1.0 / h : 1.0 / std::max(gnorm, 1.0);
             Hi[(size_t)a * nf + a] = hi0[a];
+            inv_sig[a] = 1.0 / sqrt(2.0 * hi0[a]);  // standard error sqrt(2 / H_jj)
         }
     }
     void set_trial() {
@@ -343,6 +374,9 @@ struct BfgsStepper {
         if (!ok) {
             step *= 0.5;
             if (++ls >= 40) {  // no acceptable step along d
+                // a central-difference fit whose last steps were already below
+                // its stall size has reached the resolution of its gradient
+                if (fd && stall > 0) result = MUSR_OK;
                 done = true;
                 in_ls = false;
                 return;
@@ -381,12 +415,17 @@ struct BfgsStepper {
             return;
         }
         // central differences carry the FP32 value noise into the gradient, so
-        // the EDM test cannot pass; that fit stops once three successive steps
-        // gain less than 1e-8 relative (the objective has stalled at its noise)
-        stall = rel < 1e-8 ? stall + 1 : 0;
-        if (fd && stall >= 3) {
-            result = MUSR_OK;
-            done = true;
+        // the EDM test cannot pass; that fit stops once kFdStallSteps
+        // successive steps each moved every parameter by less than
+        // kFdStallSigma of its standard error
+        if (fd) {
+            double smax = 0.0;
+            for (int a = 0; a < nf; ++a) smax = std::max(smax, fabs(sv[a]) * inv_sig[a]);
+            stall = smax < kFdStallSigma ? stall + 1 : 0;
+            if (stall >= kFdStallSteps) {
+                result = MUSR_OK;
+                done = true;
+            }
         }
     }
     void finish(double* theta_out, musr_fit_result* out) const {
@@ -426,22 +465,40 @@ int fit_bfgs_generic(int P, double* theta, const std::vector<int>& fidx, const m
 
 namespace {
 
-int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o,
-             double fd_h, musr_fit_result* out) {
+// fd: 0 adjoint gradient; 1 second-order central differences with relative
+// steps rel_h; 2 fourth-order central differences with steps of kFdStepSigma
+// standard errors, found by two passes of second differences at the start
+// (the first with relative steps rel_h, the second with steps from the
+// first's curvature)
+int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const musr_fit_opts& o, int fd,
+             double rel_h, musr_fit_result* out) {
     const int P = ev.P;
+    const int nf = (int)fidx.size();
+    std::vector<double> h(nf);
+    for (int a = 0; a < nf; ++a) h[a] = rel_h * fmax(fabs(theta[fidx[a]]), 1.0);
     auto value_grad = [&](const double* th, double* f, double* gr) -> int {
-        if (fd_h > 0.0) {
+        if (fd) {
             ++ev.evals;
-            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, nullptr);
+            return batch_fd_gradient(ev.run, ev.obj, th, fidx, h.data(), fd == 2 ? 4 : 2, f, gr, nullptr);
         }
         return ev(th, kGrad, f, gr, nullptr);
     };
     // start: the Hessian diagonal from the adjoint kernel's Gauss-Newton matrix,
     // or from the second differences of the same central-difference launch
     auto start = [&](const double* th, double* f, double* gr, double* hd) -> int {
-        if (fd_h > 0.0) {
+        if (fd) {
             ++ev.evals;
-            return batch_fd_gradient(ev.run, ev.obj, th, fidx, fd_h, f, gr, hd);
+            int st = batch_fd_gradient(ev.run, ev.obj, th, fidx, h.data(), 2, f, gr, hd);
+            for (int pass = 0; fd == 2 && pass < 2 && st == MUSR_OK; ++pass) {
+                for (int a = 0; a < nf; ++a) {
+                    const double c = hd[fidx[a]];
+                    if (c > 0.0 && std::isfinite(c)) h[a] = kFdStepSigma * sqrt(2.0 / c);
+                }
+                if (pass == 1) break;  // the second pass's curvature sets the steps
+                ++ev.evals;
+                st = batch_fd_gradient(ev.run, ev.obj, th, fidx, h.data(), 4, f, gr, hd);
+            }
+            return st;
         }
         if (ev.run->Pk <= musr::kMaxGnParams) {
             std::vector<double> H((size_t)P * P);
@@ -451,7 +508,7 @@ int fit_bfgs(Evaluator& ev, double* theta, const std::vector<int>& fidx, const m
         }
         return value_grad(th, f, gr);
     };
-    return fit_bfgs_generic(P, theta, fidx, o, fd_h > 0.0, value_grad, start, out);
+    return fit_bfgs_generic(P, theta, fidx, o, fd != 0, value_grad, start, out);
 }
 
 }  // namespace
@@ -466,6 +523,7 @@ extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* fre
     if (o.max_iter <= 0) o.max_iter = 500;
     if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
     if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
+    const int fd_mode = o.fd_rel_h > 0.0 ? 1 : 2;  // fixed relative steps, or steps of the standard errors
     if (!(o.fd_rel_h > 0.0)) o.fd_rel_h = 1e-4;
     if (o.method < MUSR_FIT_LM || o.method > MUSR_FIT_BFGS_FD) return MUSR_EINVAL;
     int cur = 0;
@@ -482,7 +540,7 @@ extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* fre
     if (method == MUSR_FIT_LM && run->Pk > musr::kMaxGnParams) method = MUSR_FIT_BFGS;
     int st;
     if (method == MUSR_FIT_LM) st = fit_lm(ev, theta, fidx, o, &r);
-    else st = fit_bfgs(ev, theta, fidx, o, method == MUSR_FIT_BFGS_FD ? o.fd_rel_h : 0.0, &r);
+    else st = fit_bfgs(ev, theta, fidx, o, method == MUSR_FIT_BFGS_FD ? fd_mode : 0, o.fd_rel_h, &r);
     r.n_evals = ev.evals;
     r.status = st;
     *out = r;

@@ -126,6 +126,7 @@ int musr_gbatch_s::make_plan(int mode, const GShape& sh) {
         Rr.csr_ptr = run->d_csr_ptr[mode];
         Rr.csr_src = run->d_csr_src[mode];
         Rr.rc = run->rc;
+        Rr.etab = run->d_etab;
         Rr.t0 = run->t0;
         Rr.dt = run->dt;
         Rr.P = run->P;

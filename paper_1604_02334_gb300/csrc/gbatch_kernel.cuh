@@ -36,6 +36,7 @@ struct GRunRef {
     const int32_t* role_theta;
     const int32_t* csr_ptr;
     const int32_t* csr_src;
+    const float* etab;  // lifetime factor at every chunk start
     RunConst rc;
     double t0, dt;
     int32_t P, K, n_out;
@@ -93,7 +94,9 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 
         // first row's loads in flight while the constants are staged
         float d[G];
+        float E0 = 0.f;
         if (n0 < M) {
+            E0 = __ldg(Rr.etab + (n0 >> 3));
             const float4* src = reinterpret_cast<const float4*>(hdata + n0);
             const float4 a = __ldg(src), b = __ldg(src + 1);
             d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
@@ -115,25 +118,31 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
         bool bad = false;
-        GqCarry<NOSC> carry;
-        carry.valid = false;
         const float dtf = (float)Rr.dt, t0f = (float)Rr.t0;
-        for (int row = 0; row < item.rows; ++row) {
-            const int n1 = n0 + stripe;
-            float dn[G];
-            if (row + 1 < item.rows && n1 < M) {
-                const float4* src = reinterpret_cast<const float4*>(hdata + n1);
-                const float4 a = __ldg(src), b = __ldg(src + 1);
-                dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
-                dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
-            } else {
+        {
+            GqCarry<NOSC> carry;
+            carry.valid = false;
+            for (int row = 0; row < item.rows; ++row) {
+                const int n1 = n0 + stripe;
+                float dn[G];
+                float En = 0.f;
+                if (row + 1 < item.rows && n1 < M) {
+                    const float4* src = reinterpret_cast<const float4*>(hdata + n1);
+                    const float4 a = __ldg(src), b = __ldg(src + 1);
+                    dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
+                    dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
+                    En = __ldg(Rr.etab + (n1 >> 3));
+                } else {
 #pragma unroll
-                for (int g = 0; g < G; ++g) dn[g] = 0.f;
+                    for (int g = 0; g < G; ++g) dn[g] = 0.f;
+                }
+                if (n0 < M)
+                    eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, dtf, t0f, acc, bad, nullptr, &carry);
+#pragma unroll
+                for (int g = 0; g < G; ++g) d[g] = dn[g];
+                E0 = En;
+                n0 = n1;
             }
-            if (n0 < M) eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, p.obj, dtf, t0f, acc, bad, nullptr, &carry);
-#pragma unroll
-            for (int g = 0; g < G; ++g) d[g] = dn[g];
-            n0 = n1;
         }
         warp_sum<NACC>(acc);
         if (lane == 0) {

@@ -188,6 +188,7 @@ struct GenParams {
     uint64_t sample_offset;
     float* out;                   // [n_samples][row_stride]
     float* mu_out;                // same layout, or null
+    const float* etab;            // the run's lifetime factor at every chunk start
 };
 
 // One block per (sample, histogram): stage the constants once, then each
@@ -214,7 +215,8 @@ __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_cons
         float acc[1] = {0.f};
         bool bad = false;
         for (int n0 = g0; n0 < g1; n0 += kBinsPerThread)
-            eval_chunk<NE, NG, NS, KT, kSum, 1>(hc, n0, g1, zero, MUSR_CHI2, p.dt, p.t0, acc, bad, nullptr);
+            eval_chunk<NE, NG, NS, KT, kSum, 1>(hc, n0, g1, zero, lifetime_from_table(p.etab, n0, hc.qE), MUSR_CHI2,
+                                                p.dt, p.t0, acc, bad, nullptr);
         const float mu = acc[0];
         const int32_t cnt = poisson_one(mu, p.k0, p.k1, (uint32_t)j, (uint32_t)k,
                                         (uint32_t)(p.sample_offset + (uint64_t)s));
@@ -358,6 +360,7 @@ int musr::generate_rows(musr_run run, const double* thetas_dev, int n_samples, i
         p.group_off = run->d_group_off;
         p.thetas = thetas_dev;
         p.rc = run->rc;
+        p.etab = run->d_etab;
         p.dt = (float)run->dt;
         p.t0 = (float)run->t0;
         p.K = run->K;

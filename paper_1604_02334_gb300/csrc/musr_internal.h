@@ -28,21 +28,28 @@ struct OscConst {
     float amp, rate, cenv, a_hi, a_lo, b_hi, b_lo, q, cm1, sn;
     float qs;    // Gaussian envelope: 2^(-2 b stripe) - 1, the change of its step ratio over one stripe
     float beta;  // stretched envelope: exponent beta (rate holds lambda)
+    // two-bin steps (the packed kernels step even and odd bins as two lanes):
+    // q2 = expm1 of the exponential envelope over 2 bins, or for a Gaussian
+    // envelope the change of its 2-bin ratio, 2^(-8 b) - 1; cm1_2 / sn_2 the
+    // rotation over 2 bins; qs2 = 2^(-4 b stripe) - 1
+    float q2, cm1_2, sn_2, qs2;
     unsigned long long ph0, step;  // phase at bin 0 and per bin, 64-bit fixed-point turns
 };
 
 struct HistConst {
-    float n0, n0_lo, bkg, cE, aE_hi, aE_lo, qE;  // N0 = n0 + n0_lo (FP32 pair)
+    float n0, n0_lo, bkg, qE;  // N0 = n0 + n0_lo (FP32 pair); qE = expm1(-dt / tau), the lifetime step
+    float qE2;    // expm1(-2 dt / tau)
     float kfreq;  // 2 pi gamma: dN/dB = dN/d(omega) * 2 pi gamma
     OscConst osc[kMaxOsc];
     float kt_amp, kt_rate, kt_cenv, kt_a_hi, kt_a_lo, kt_b_hi, kt_b_lo, kt_q, kt_qs;
+    float kt_q2, kt_qs2;  // the Kubo-Toyabe envelope's 2-bin ratio constants (as OscConst q2, qs2)
 };
 
 // Theta-independent constants of a run's time grid, prepared on the host in
 // FP64 / exact integer arithmetic (float2 = double-float hi, lo).
 struct RunConst {
     float2 inv_tau, dt, dt_log2e, t0, t0_dt_log2e, half_dt2_log2e;
-    float aE_hi, aE_lo, qE, cE, kfreq;  // lifetime recurrence, 2 pi gamma
+    float qE, kfreq;  // lifetime step expm1(-dt / tau), 2 pi gamma
     int t0_zero;
     ulonglong2 turns_per_bin;  // gamma * dt as unsigned 64.64 fixed point (turns per gauss)
     ulonglong2 turns_at_t0;    // gamma * t0
@@ -157,22 +164,17 @@ struct EvalParams {
     double t0, dt, inv_tau, gamma;
     int K, P, obj;
     // reduction scratch
-    double* partial;              // [n_clusters][nacc] double-float pairs
-    double* hist_sum;             // [K][nacc] pairs (when they do not fit in shared memory)
+    unsigned long long* facc;     // [K][nacc][3] fixed-point limbs of the per-histogram sums (self-resetting)
+    __int128* hist_sum;           // [K][nacc] integer totals (when they do not fit in shared memory)
     unsigned* global_count;       // [1]   (self-resetting)
     unsigned* flags;              // [1]   (self-resetting)
-    const int32_t* cluster_hist;        // [n_clusters]
-    const int32_t* hist_first_cluster;  // [K]
-    const int32_t* hist_nclusters;      // [K]
-    int n_clusters, cluster;      // clusters of `cluster` consecutive tiles of one histogram
     int chunks;                   // stripes of blockDim x 8 bins per tile
     const int32_t* csr_ptr;       // [n_out + 1]
     const int32_t* csr_src;       // sources: k * nacc + acc
     int n_out;
     int n_src;                    // csr_src length
-    int win_doubles;              // shared-memory window for cluster partials
     int hsum_in_smem, csr_in_smem;
-    int preload;                  // 1: every block preloads the tail's tables (CSR, cluster tables)
+    int preload;                  // 1: every block preloads the tail's CSR
     int smem_bytes;               // dynamic shared memory of the objective kernel
     double* out;                  // [n_out]
     int32_t* status_out;          // [1] or null
@@ -193,6 +195,8 @@ struct EvalParams {
     // model output (kModel)
     float* model_out;
     const int64_t* model_off;     // [K] offsets into model_out
+    // lifetime factor exp(-t/tau) at every 8-bin chunk start (see lifetime_table_len)
+    const float* etab;
 };
 // kernel parameters are limited to 32764 bytes
 static_assert(sizeof(EvalParams) <= 32000, "EvalParams exceeds the kernel parameter space");
@@ -208,5 +212,14 @@ int cuda_status(cudaError_t e);
 
 // Theta-independent constants of a time grid (host, FP64 / integer).
 RunConst make_run_const(double t0, double dt, double tau, double gamma);
+
+// The lifetime factor exp(-(t0 + 8 j dt) / tau) at every chunk start j of a
+// time grid, evaluated in FP64 and rounded once to FP32.  The kernels seed
+// their per-bin lifetime recurrence from it: the factor multiplies every bin
+// of the model, so a seed computed in FP32 (an SFU exp2 of a rounded
+// argument) would bias N coherently over many bins, and the objective's
+// gradient sums, which cancel ~100-fold, would inherit that bias amplified.
+inline int64_t lifetime_table_len(int64_t max_bins) { return max_bins / kBinsPerThread + 2; }
+cudaError_t fill_lifetime_table(float* tab, int64_t n, double t0, double dt, double tau, cudaStream_t st);
 
 }  // namespace musr

@@ -6,8 +6,8 @@
 // allocation after start-up, or plug-ins whose host application hands them
 // only pre-allocated device buffers.  For them this entry point keeps every
 // piece of scratch the evaluation needs (tiling tables, the parameter map,
-// the staged per-histogram constants, the reduction partials and a padded
-// copy of the histograms) in one file-scope device array of a fixed size,
+// the lifetime-factor table, the reduction accumulators and a padded copy of
+// the histograms) in one file-scope device array of a fixed size,
 // MUSR_NOALLOC_SCRATCH_BYTES.  The array belongs to this library's module:
 // every GPU that loads it holds the array until the process exits.  The
 // entry point itself calls no cudaMalloc, cudaFree or other allocating
@@ -15,7 +15,15 @@
 //
 // Host code cannot use the array's name as a device address, so the first
 // call on each device looks the address up with cudaGetSymbolAddress (that
-// device current) and keeps it; later calls reuse it.
+// device current) and keeps it; later calls reuse it.  With CUDA's lazy
+// module loading (the default) that first call is also when the driver loads
+// this file's module on the device and reserves the array's memory, so
+// callers make it at start-up, before another framework takes the memory.
+//
+// Each call uploads its tables from a static host plan with cudaMemcpyAsync
+// (pageable source), which the next call rewrites: calls made while the
+// stream is being captured into a graph are refused (MUSR_ENOTSUP), since a
+// captured copy would read that buffer again at every replay.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -43,13 +51,12 @@ std::atomic<unsigned char*> g_scratch_addr[kMaxDevices];
 // Host-side plan of one call, built in a static buffer under a mutex (no
 // heap use); the device work itself is asynchronous.
 struct NaPlan {
-    int K, P, R, threads, tile_bins, cluster, n_tiles, n_clusters, n_out, n_src;
+    int K, P, R, threads, tile_bins, n_tiles, n_out, n_src;
     Signature sig;
     int64_t hist_off[kNaMaxHist];
     int32_t hist_nbins[kNaMaxHist];
-    int32_t hist_first_cluster[kNaMaxHist], hist_nclusters[kNaMaxHist];
     int32_t role_theta[kNaMaxHist * kMaxRoles * 2];
-    int32_t tile_hist[kNaMaxTiles], tile_start[kNaMaxTiles], cluster_hist[kNaMaxTiles];
+    int32_t tile_hist[kNaMaxTiles], tile_start[kNaMaxTiles];
     int32_t csr_ptr[kNaMaxParams + 2];
     int32_t csr_src[kNaMaxHist * (1 + 2 * kMaxRoles)];
     int32_t csr_cnt[kNaMaxParams + 2];
@@ -83,8 +90,7 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
         }
         role_row(rl, d->comp, d->map + (int64_t)k * d->map_width, pl.role_theta + (size_t)k * kMaxRoles * 2);
     }
-    // tiling: the largest block that still gives >= 2 blocks per SM, clusters of
-    // up to 8 tiles with at most 25 % padding
+    // tiling: the largest block that still gives >= 2 blocks per SM
     pl.threads = 32;
     for (int t = kMaxThreads; t >= 32; t >>= 1) {
         int64_t tiles = 0;
@@ -96,39 +102,20 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
         }
     }
     pl.tile_bins = pl.threads * kBinsPerThread;
-    int64_t raw = 0;
-    for (int k = 0; k < pl.K; ++k) raw += std::max<int64_t>(1, (d->n_bins[k] + pl.tile_bins - 1) / pl.tile_bins);
-    pl.cluster = 1;
-    for (int c = 8; c >= 2; c >>= 1) {
-        int64_t padded = 0;
-        for (int k = 0; k < pl.K; ++k) {
-            const int64_t nt = std::max<int64_t>(1, (d->n_bins[k] + pl.tile_bins - 1) / pl.tile_bins);
-            padded += (nt + c - 1) / c * c;
-        }
-        if (padded * 4 <= raw * 5) {
-            pl.cluster = c;
-            break;
-        }
-    }
     int64_t off = 0;
     pl.n_tiles = 0;
-    pl.n_clusters = 0;
     for (int k = 0; k < pl.K; ++k) {
         const int64_t M = d->n_bins[k];
         pl.hist_off[k] = off;
         pl.hist_nbins[k] = (int32_t)M;
         off += round_up(M, 8);
         const int64_t nt = std::max<int64_t>(1, (M + pl.tile_bins - 1) / pl.tile_bins);
-        const int64_t ncl = (nt + pl.cluster - 1) / pl.cluster;
-        if (pl.n_tiles + ncl * pl.cluster > kNaMaxTiles) return MUSR_ENOTSUP;
-        pl.hist_first_cluster[k] = pl.n_clusters;
-        pl.hist_nclusters[k] = (int32_t)ncl;
-        for (int64_t j = 0; j < ncl * pl.cluster; ++j) {
+        if (pl.n_tiles + nt > kNaMaxTiles) return MUSR_ENOTSUP;
+        for (int64_t j = 0; j < nt; ++j) {
             pl.tile_hist[pl.n_tiles] = k;
             pl.tile_start[pl.n_tiles] = (int32_t)std::min<int64_t>(j * pl.tile_bins, round_up(M, 8));
             ++pl.n_tiles;
         }
-        for (int64_t c = 0; c < ncl; ++c) pl.cluster_hist[pl.n_clusters++] = k;
     }
     pl.data_floats = off + 8;
     // CSR of output -> (histogram, accumulator) in (k, role, entry) order, by
@@ -186,6 +173,12 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     if (!desc->data || !desc->data_on_device || desc->data_dtype != MUSR_F32) return MUSR_ENOTSUP;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MUSR_ECUDA;
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t e = cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &cs);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (cs != cudaStreamCaptureStatusNone) return MUSR_ENOTSUP;
+    }
     // one-time set-up on this device: the device address of the scratch array
     unsigned char* base = g_scratch_addr[dev].load();
     if (!base) {
@@ -215,19 +208,22 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     const size_t o_nb = take(sizeof(int32_t) * pl.K);
     const size_t o_th = take(sizeof(int32_t) * pl.n_tiles);
     const size_t o_ts = take(sizeof(int32_t) * pl.n_tiles);
-    const size_t o_ch = take(sizeof(int32_t) * pl.n_clusters);
-    const size_t o_hf = take(sizeof(int32_t) * pl.K);
-    const size_t o_hn = take(sizeof(int32_t) * pl.K);
     const size_t o_rt = take(sizeof(int32_t) * pl.K * kMaxRoles * 2);
     const size_t o_cp = take(sizeof(int32_t) * (pl.n_out + 1));
     const size_t o_cs = take(sizeof(int32_t) * (pl.n_src + 1));
-    const size_t o_part = take(sizeof(double) * (size_t)pl.n_clusters * nacc);
-    const size_t o_hsum = take(sizeof(double) * (size_t)pl.K * nacc);
+    const size_t o_facc = take(sizeof(unsigned long long) * (size_t)pl.K * nacc * 3);
+    const size_t o_hsum = take(sizeof(__int128) * (size_t)pl.K * nacc);
     const size_t o_data = take(sizeof(float) * (size_t)pl.data_floats);
+    int64_t max_m = 0;
+    for (int k = 0; k < pl.K; ++k) max_m = std::max<int64_t>(max_m, pl.hist_nbins[k]);
+    const int64_t etab_len = lifetime_table_len(max_m);
+    const size_t o_etab = take(sizeof(float) * (size_t)etab_len);
     if (off > kScratchBytes) return MUSR_ENOTSUP;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(base + o_cnt, 0, 4 * sizeof(unsigned), s);  // tickets start at 0
+    // the fixed-point accumulators start at 0 (the kernel's last block also leaves them at 0)
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_facc, 0, sizeof(unsigned long long) * (size_t)pl.K * nacc * 3, s);
     auto up = [&](size_t o, const void* src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(base + o, src, bytes, cudaMemcpyHostToDevice, s);
     };
@@ -235,9 +231,6 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     up(o_nb, pl.hist_nbins, sizeof(int32_t) * pl.K);
     up(o_th, pl.tile_hist, sizeof(int32_t) * pl.n_tiles);
     up(o_ts, pl.tile_start, sizeof(int32_t) * pl.n_tiles);
-    up(o_ch, pl.cluster_hist, sizeof(int32_t) * pl.n_clusters);
-    up(o_hf, pl.hist_first_cluster, sizeof(int32_t) * pl.K);
-    up(o_hn, pl.hist_nclusters, sizeof(int32_t) * pl.K);
     up(o_rt, pl.role_theta, sizeof(int32_t) * pl.K * kMaxRoles * 2);
     up(o_cp, pl.csr_ptr, sizeof(int32_t) * (pl.n_out + 1));
     up(o_cs, pl.csr_src, sizeof(int32_t) * pl.n_src);
@@ -250,6 +243,9 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
         if (M) e = cudaMemcpyAsync(data + pl.hist_off[k], src + so, sizeof(float) * M, cudaMemcpyDeviceToDevice, s);
         so += M;
     }
+    // the lifetime factor at every chunk start of the time grid
+    float* etab = reinterpret_cast<float*>(base + o_etab);
+    if (e == cudaSuccess) e = fill_lifetime_table(etab, etab_len, desc->t0_us, desc->dt_us, desc->tau_us, s);
     if (e != cudaSuccess) return cuda_status(e);
 
     EvalParams p;
@@ -269,28 +265,22 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.K = pl.K;
     p.P = pl.P;
     p.obj = obj;
-    p.partial = reinterpret_cast<double*>(base + o_part);
-    p.hist_sum = reinterpret_cast<double*>(base + o_hsum);
+    p.facc = reinterpret_cast<unsigned long long*>(base + o_facc);
+    p.hist_sum = reinterpret_cast<__int128*>(base + o_hsum);
     p.global_count = reinterpret_cast<unsigned*>(base + o_cnt);
     p.flags = reinterpret_cast<unsigned*>(base + o_cnt) + 1;
-    p.cluster_hist = reinterpret_cast<const int32_t*>(base + o_ch);
-    p.hist_first_cluster = reinterpret_cast<const int32_t*>(base + o_hf);
-    p.hist_nclusters = reinterpret_cast<const int32_t*>(base + o_hn);
-    p.n_clusters = pl.n_clusters;
-    p.cluster = pl.cluster;
     p.chunks = 1;
     p.preload = 0;
     p.csr_ptr = reinterpret_cast<const int32_t*>(base + o_cp);
     p.csr_src = reinterpret_cast<const int32_t*>(base + o_cs);
     p.n_out = pl.n_out;
     p.n_src = pl.n_src;
-    p.win_doubles = std::max(nacc, std::min(pl.n_clusters * nacc, 4096 / nacc * nacc));
-    p.hsum_in_smem = 1;  // K <= 64 and nacc <= 13: at most 6.5 KB
+    p.hsum_in_smem = 1;  // K <= 64 and nacc <= 13: at most 13 KB
     p.csr_in_smem = 1;   // at most ~7 KB
-    p.smem_bytes = (int)(8 * ((size_t)p.win_doubles + (size_t)pl.K * nacc) +
-                         4 * ((size_t)pl.n_out + 1 + pl.n_src));
+    p.smem_bytes = (int)(16 * (size_t)pl.K * nacc + 4 * ((size_t)pl.n_out + 1 + pl.n_src));
     p.out = out_dev;
     p.status_out = status_dev;
+    p.etab = etab;
     // allow the tail's shared memory, then stage the constants and evaluate
     e = launch_na(pl.sig, mode, pl.threads, 0, s, p);
     if (e == cudaSuccess) e = launch_na(pl.sig, mode, pl.threads, pl.n_tiles, s, p);

@@ -72,11 +72,7 @@ RunConst make_run_const(double t0, double dt, double tau, double gamma) {
     rc.t0 = df_split(t0);
     rc.t0_dt_log2e = df_split(t0 * dt * LOG2E);
     rc.half_dt2_log2e = df_split(0.5 * dt * dt * LOG2E);
-    const float2 aE = df_split(dt / tau * LOG2E);
-    rc.aE_hi = aE.x;
-    rc.aE_lo = aE.y;
     rc.qE = (float)expm1(-dt / tau);
-    rc.cE = (float)exp(-t0 / tau);
     rc.kfreq = (float)(2.0 * 3.14159265358979323846 * gamma);
     rc.t0_zero = t0 == 0.0;
     int neg = 0;
@@ -94,6 +90,19 @@ int cuda_status(cudaError_t e) {
     g_last_cuda_error = cudaGetErrorName(e);
     if (e == cudaErrorMemoryAllocation) return MUSR_ENOMEM;
     return MUSR_ECUDA;
+}
+
+__global__ void lifetime_table_kernel(float* tab, int64_t n, double t0, double dt8, double inv_tau) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        tab[j] = (float)exp(-(t0 + (double)j * dt8) * inv_tau);
+}
+
+cudaError_t fill_lifetime_table(float* tab, int64_t n, double t0, double dt, double tau, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 1024);
+    lifetime_table_kernel<<<blocks, threads, 0, st>>>(tab, n, t0, dt * kBinsPerThread, 1.0 / tau);
+    return cudaGetLastError();
 }
 
 // Copy concatenated counts (FP32 or FP64, device) into the padded FP32 layout.
@@ -134,6 +143,10 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 constexpr int32_t kStatusPending = INT32_MIN;
 constexpr int kStatusSpinUs = 2000;
 constexpr int kMinThreadsGn = 128;
+// the tiling planner's cost of one wave of blocks, in bins of one SM's work:
+// a block's staging and reduction take ~2 us, which an SM spends on ~7000
+// bins of the gradient mode
+constexpr int64_t kWaveCostBins = 7000;
 
 }  // namespace
 
@@ -202,61 +215,32 @@ int musr_run_s::plan(const musr_run_desc* d) {
     return MUSR_OK;
 }
 
-// Tiles of `chunks` stripes of t x 8 bins; cluster size the largest of 8, 4,
-// 2, 1 whose padding (every histogram's tiles rounded up to whole clusters)
-// adds at most 25 % empty tiles.
+// Tiles of `chunks` stripes of t x 8 bins, each within one histogram.
 void musr_run_s::build_tiles(Tiling& T, int t, int chunks) const {
     T.threads = t;
     T.chunks = chunks;
     T.tile_bins = t * kBinsPerThread * chunks;
-    std::vector<int64_t> nt(K);
-    int64_t raw = 0;
-    for (int k = 0; k < K; ++k) {
-        nt[k] = std::max<int64_t>(1, (n_bins[k] + T.tile_bins - 1) / T.tile_bins);
-        raw += nt[k];
-    }
-    T.cluster = 1;
-    for (int c = 8; c >= 2; c >>= 1) {
-        int64_t padded = 0;
-        for (int k = 0; k < K; ++k) padded += (nt[k] + c - 1) / c * c;
-        if (padded * 4 <= raw * 5) {
-            T.cluster = c;
-            break;
-        }
-    }
     T.tile_hist.clear();
     T.tile_start.clear();
-    T.cluster_hist.clear();
-    T.hist_first_cluster.assign(K, 0);
-    T.hist_nclusters.assign(K, 0);
     for (int k = 0; k < K; ++k) {
-        const int64_t ncl = (nt[k] + T.cluster - 1) / T.cluster;
-        T.hist_first_cluster[k] = (int32_t)T.cluster_hist.size();
-        T.hist_nclusters[k] = (int32_t)ncl;
-        for (int64_t j = 0; j < ncl * T.cluster; ++j) {
+        const int64_t nt = std::max<int64_t>(1, (n_bins[k] + T.tile_bins - 1) / T.tile_bins);
+        for (int64_t j = 0; j < nt; ++j) {
             T.tile_hist.push_back(k);
             T.tile_start.push_back((int32_t)std::min<int64_t>(j * T.tile_bins, round_up(n_bins[k], 8)));
         }
-        for (int64_t c = 0; c < ncl; ++c) T.cluster_hist.push_back(k);
     }
     T.n_tiles = (int)T.tile_hist.size();
-    T.n_clusters = (int)T.cluster_hist.size();
 }
 
-// Dynamic shared memory of the objective kernel's tail for a mode / tiling: a
-// window of cluster partials, the histogram sums and the CSR when they fit.
-int musr_run_s::tail_smem(int mode, const Tiling& T, int* win, int* hsum_smem, int* csr_smem) const {
+// Dynamic shared memory of the objective kernel's tail for a mode: the
+// per-histogram totals and the CSR, each when it fits.
+int musr_run_s::tail_smem(int mode, int* hsum_smem, int* csr_smem) const {
     const int nacc = n_acc(mode, R);
-    const int w = std::max(nacc, std::min(T.n_clusters * nacc, 4096 / nacc * nacc));
-    const int hs = (size_t)K * nacc * 8 <= 64 * 1024;
+    const int hs = (size_t)K * nacc * 16 <= 64 * 1024;
     const int cs = ((size_t)n_out[mode] + 1 + n_src[mode]) * 4 <= 64 * 1024;
-    if (win) *win = w;
     if (hsum_smem) *hsum_smem = hs;
     if (csr_smem) *csr_smem = cs;
-    // the CSR region doubles as the preloaded-table region (CSR + cluster tables)
-    const size_t tables = (size_t)n_out[mode] + 1 + n_src[mode] + T.n_clusters + 2 * (size_t)K;
-    const size_t csr_ints = cs ? std::max(tables, (size_t)n_out[mode] + 1 + n_src[mode]) : 0;
-    return (int)(8 * ((size_t)w + (hs ? (size_t)K * nacc : 0)) + 4 * csr_ints);
+    return (int)(16 * (hs ? (size_t)K * nacc : 0) + 4 * (cs ? (size_t)n_out[mode] + 1 + n_src[mode] : 0));
 }
 
 // CSR of output entry -> (histogram, accumulator) sources for one mode.
@@ -319,9 +303,10 @@ int musr_run_s::allocate() {
         n_out[m] = (int)ptr[m].size() - 1;
         n_src[m] = (int)src[m].size();
     }
-    // per-mode tiling: the largest block giving >= 2 blocks per SM at one
-    // stripe per tile, then enough stripes per tile that the whole grid is one
-    // wave of resident blocks (resident count from the kernel's occupancy)
+    // per-mode tiling: among block sizes and stripes per tile, the one whose
+    // busiest SM holds the fewest bins, the blocks of a wave being spread
+    // evenly over the SMs (resident count from the kernel's occupancy), plus a
+    // cost per wave for the blocks' fixed work (staging, reduction)
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
     for (int m = 0; m < 4; ++m) {
@@ -329,31 +314,36 @@ int musr_run_s::allocate() {
         // the Gauss-Newton mode reduces 1 + R + R(R+1)/2 accumulators per block and
         // maps ~P^2 outputs in its tail: blocks of fewer than kMinThreadsGn threads
         // spend more on that than they save in parallelism
-        const int t_min = m == kGN ? kMinThreadsGn : 32;
-        int t = t_min;
-        for (int c = kMaxThreads; c >= t_min; c >>= 1) {
-            int64_t tiles = 0;
-            for (int k = 0; k < K; ++k)
-                tiles += std::max<int64_t>(1, (n_bins[k] + c * kBinsPerThread - 1) / (c * kBinsPerThread));
-            if (tiles >= 2 * dev_sms) {
-                t = c;
-                break;
+        int t_min = m == kGN ? kMinThreadsGn : 32;
+        // runs that fill the GPU keep a warp per staging part, so the parts'
+        // latency chains run side by side
+        if (total_bins >= (int64_t)2 * dev_sms * kMaxThreads * kBinsPerThread)
+            while (t_min < kMaxThreads && t_min < 32 * (2 + 2 * sig.n_osc())) t_min <<= 1;
+        int best_t = kMaxThreads, best_c = 1;
+        int64_t best_cost = INT64_MAX;
+        for (int t = kMaxThreads; t >= t_min; t >>= 1) {
+            int per_sm = 0;
+            EvalParams q;
+            memset(&q, 0, sizeof(q));
+            q.smem_bytes = m == kModel ? 0 : tail_smem(m, nullptr, nullptr);
+            q.status_out = reinterpret_cast<int32_t*>(&per_sm);
+            if (launch_eval(sig, m, t, -1, stream, q) != cudaSuccess || per_sm < 1) per_sm = 1;
+            const int64_t slots = (int64_t)per_sm * dev_sms;
+            for (int c = 1; c <= 8; ++c) {
+                const int64_t tile_bins = (int64_t)t * kBinsPerThread * c;
+                int64_t n = 0;
+                for (int k = 0; k < K; ++k) n += std::max<int64_t>(1, (n_bins[k] + tile_bins - 1) / tile_bins);
+                const int64_t waves = (n + slots - 1) / slots;
+                const int64_t cost = (n + dev_sms - 1) / dev_sms * tile_bins + kWaveCostBins * waves;
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_t = t;
+                    best_c = c;
+                }
             }
         }
-        build_tiles(tl[m], t, 1);
-        int per_sm = 0;
-        EvalParams q;
-        memset(&q, 0, sizeof(q));
-        q.smem_bytes = m == kModel ? 0 : tail_smem(m, tl[m], nullptr, nullptr, nullptr);
-        q.status_out = reinterpret_cast<int32_t*>(&per_sm);
-        if (launch_eval(sig, m, t, -1, stream, q) != cudaSuccess || per_sm < 1) per_sm = 1;
-        const int64_t resident = (int64_t)per_sm * dev_sms * 9 / 10;
-        int chunks = 1;
-        while (chunks < 8 && tl[m].n_tiles > resident) {
-            ++chunks;
-            build_tiles(tl[m], t, chunks);
-        }
-        if (m < 3) smem_bytes[m] = tail_smem(m, tl[m], &win_doubles[m], &hsum_in_smem[m], &csr_in_smem[m]);
+        build_tiles(tl[m], best_t, best_c);
+        if (m < 3) smem_bytes[m] = tail_smem(m, &hsum_in_smem[m], &csr_in_smem[m]);
     }
     const int n_out_max = n_out[Pk <= kMaxGnParams ? kGN : kGrad];
     Arena A;
@@ -361,25 +351,24 @@ int musr_run_s::allocate() {
     const size_t o_hoff = A.take<int64_t>(K + 1);
     const size_t o_moff = A.take<int64_t>(K + 1);
     const size_t o_nb = A.take<int32_t>(K + 1);
-    size_t o_th[4], o_ts[4], o_ch[4], o_hf[4], o_hn[4];
-    int max_clusters = 1;
+    size_t o_th[4], o_ts[4];
     for (int m = 0; m < 4; ++m) {
         o_th[m] = A.take<int32_t>(tl[m].n_tiles + 1);
         o_ts[m] = A.take<int32_t>(tl[m].n_tiles + 1);
-        o_ch[m] = A.take<int32_t>(tl[m].n_clusters + 1);
-        o_hf[m] = A.take<int32_t>(K + 1);
-        o_hn[m] = A.take<int32_t>(K + 1);
-        if (m < 3) max_clusters = std::max(max_clusters, tl[m].n_clusters);
     }
     const size_t o_rt = A.take<int32_t>(role_theta.size() + 1);
     const size_t o_map = A.take<int32_t>(map.size() + 1);  // raw map rows (user theories)
+    int64_t max_m = 0;
+    for (int k = 0; k < K; ++k) max_m = std::max(max_m, n_bins[k]);
+    etab_len = lifetime_table_len(max_m);
+    const size_t o_etab = A.take<float>((size_t)etab_len);
     size_t o_ptr[3], o_src[3];
     for (int m = 0; m < 3; ++m) {
         o_ptr[m] = A.take<int32_t>(ptr[m].size() + 1);
         o_src[m] = A.take<int32_t>(src[m].size() + 1);
     }
-    const size_t o_part = A.take<double>((size_t)max_clusters * nacc_max);
-    const size_t o_hsum = A.take<double>((size_t)(K + 1) * nacc_max);
+    const size_t o_facc = A.take<unsigned long long>((size_t)(K + 1) * nacc_max * 3);
+    const size_t o_hsum = A.take<__int128>((size_t)(K + 1) * nacc_max);
     const size_t o_cnt = A.take<unsigned>(4);
     const size_t o_theta = A.take<double>(Pk + 1);
     const size_t o_out = A.take<double>(n_out_max + 1);
@@ -397,18 +386,16 @@ int musr_run_s::allocate() {
     for (int m = 0; m < 4; ++m) {
         tl[m].d_tile_hist = reinterpret_cast<int32_t*>(b + o_th[m]);
         tl[m].d_tile_start = reinterpret_cast<int32_t*>(b + o_ts[m]);
-        tl[m].d_cluster_hist = reinterpret_cast<int32_t*>(b + o_ch[m]);
-        tl[m].d_hist_first_cluster = reinterpret_cast<int32_t*>(b + o_hf[m]);
-        tl[m].d_hist_nclusters = reinterpret_cast<int32_t*>(b + o_hn[m]);
     }
     d_role_theta = reinterpret_cast<int32_t*>(b + o_rt);
     d_map = reinterpret_cast<int32_t*>(b + o_map);
+    d_etab = reinterpret_cast<float*>(b + o_etab);
     for (int m = 0; m < 3; ++m) {
         d_csr_ptr[m] = reinterpret_cast<int32_t*>(b + o_ptr[m]);
         d_csr_src[m] = reinterpret_cast<int32_t*>(b + o_src[m]);
     }
-    d_partial = reinterpret_cast<double*>(b + o_part);
-    d_hist_sum = reinterpret_cast<double*>(b + o_hsum);
+    d_facc = reinterpret_cast<unsigned long long*>(b + o_facc);
+    d_hist_sum = reinterpret_cast<__int128*>(b + o_hsum);
     d_counters = reinterpret_cast<unsigned*>(b + o_cnt);
     d_theta = reinterpret_cast<double*>(b + o_theta);
     d_out = reinterpret_cast<double*>(b + o_out);
@@ -444,12 +431,10 @@ int musr_run_s::allocate() {
         if (T.n_tiles == 0) continue;  // a mode without a tiling (Gauss-Newton beyond kMaxGnParams)
         up(T.d_tile_hist, T.tile_hist.data(), sizeof(int32_t) * T.n_tiles);
         up(T.d_tile_start, T.tile_start.data(), sizeof(int32_t) * T.n_tiles);
-        up(T.d_cluster_hist, T.cluster_hist.data(), sizeof(int32_t) * T.n_clusters);
-        up(T.d_hist_first_cluster, T.hist_first_cluster.data(), sizeof(int32_t) * K);
-        up(T.d_hist_nclusters, T.hist_nclusters.data(), sizeof(int32_t) * K);
     }
     up(d_role_theta, role_theta.data(), sizeof(int32_t) * role_theta.size());
     up(d_map, map.data(), sizeof(int32_t) * map.size());
+    if (e == cudaSuccess) e = fill_lifetime_table(d_etab, etab_len, t0, dt, tau, stream);
     for (int m = 0; m < 3; ++m) {
         up(d_csr_ptr[m], ptr[m].data(), sizeof(int32_t) * ptr[m].size());
         up(d_csr_src[m], src[m].data(), sizeof(int32_t) * src[m].size());
@@ -461,6 +446,8 @@ int musr_run_s::allocate() {
         e = launch_eval(sig, m, tl[m].threads, 0, stream, q);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, sizeof(unsigned) * 4, stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_facc, 0, sizeof(unsigned long long) * (size_t)(K + 1) * nacc_max * 3, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_data, 0, sizeof(float) * data_floats, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     return cuda_status(e);
@@ -506,7 +493,7 @@ int musr_run_s::upload(int dtype, const void* data, int on_device) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
         return cuda_status(e);
     }
-    // device source: pack with a kernel (offsets staged through d_partial scratch)
+    // device source: pack with a kernel (source offsets in a small temporary buffer)
     std::vector<int64_t> src_off(K);
     int64_t s = 0;
     for (int k = 0; k < K; ++k) {
@@ -548,27 +535,20 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.K = K;
     p.P = Pk;
     p.obj = obj;
-    p.partial = d_partial;
+    p.facc = d_facc;
     p.hist_sum = d_hist_sum;
     p.global_count = d_counters;
     p.flags = d_counters + 1;
-    p.cluster_hist = T.d_cluster_hist;
-    p.hist_first_cluster = T.d_hist_first_cluster;
-    p.hist_nclusters = T.d_hist_nclusters;
-    p.n_clusters = T.n_clusters;
-    p.cluster = mode == kModel ? 1 : T.cluster;
     p.chunks = T.chunks;
     const int m = mode == kModel ? kValue : mode;
     p.csr_ptr = d_csr_ptr[m];
     p.csr_src = d_csr_src[m];
     p.n_out = n_out[m];
     p.n_src = n_src[m];
-    p.win_doubles = win_doubles[m];
     p.hsum_in_smem = hsum_in_smem[m];
     p.csr_in_smem = csr_in_smem[m];
-    // small tables are preloaded by every block (overlapping its staging)
-    p.preload = mode != kModel && csr_in_smem[m] &&
-                (n_out[m] + 1 + n_src[m] + T.n_clusters + 2 * K) <= 1024 &&
+    // a small CSR is preloaded by every block (overlapping its staging)
+    p.preload = mode != kModel && csr_in_smem[m] && (n_out[m] + 1 + n_src[m]) <= 1024 &&
                 T.threads > 32 * (2 + 2 * sig.n_osc());  // warps beyond the staging ones exist
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
     // equal-length histograms: tiles and offsets by arithmetic (see EvalParams)
@@ -587,6 +567,7 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.out = out_dev;
     p.status_out = status_dev;
     p.model_off = d_model_off;
+    p.etab = d_etab;
     return p;
 }
 

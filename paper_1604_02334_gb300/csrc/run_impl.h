@@ -71,13 +71,12 @@ struct musr_run_s {
     int R = 0;
     std::vector<int32_t> role_theta;  // [K][kMaxRoles][2]
     // tiling, per mode (value, grad, GN, model): tiles of `chunks` stripes of
-    // threads x 8 bins, grouped in clusters of `cluster` tiles of one histogram,
-    // sized so a launch is one wave of resident blocks
+    // threads x 8 bins of one histogram, sized so a launch is one wave of
+    // resident blocks
     struct Tiling {
-        int threads = 256, chunks = 1, tile_bins = 2048, cluster = 1, n_tiles = 0, n_clusters = 0;
-        std::vector<int32_t> tile_hist, tile_start, cluster_hist, hist_first_cluster, hist_nclusters;
-        int32_t *d_tile_hist = nullptr, *d_tile_start = nullptr, *d_cluster_hist = nullptr;
-        int32_t *d_hist_first_cluster = nullptr, *d_hist_nclusters = nullptr;
+        int threads = 256, chunks = 1, tile_bins = 2048, n_tiles = 0;
+        std::vector<int32_t> tile_hist, tile_start;
+        int32_t *d_tile_hist = nullptr, *d_tile_start = nullptr;
     };
     Tiling tl[4];
     std::vector<int64_t> hist_off, model_off;
@@ -89,14 +88,17 @@ struct musr_run_s {
     int32_t* d_hist_nbins = nullptr;
     int32_t* d_role_theta = nullptr;
     int32_t* d_map = nullptr;  // [K][W] the descriptor's map rows
+    float* d_etab = nullptr;   // lifetime factor at every chunk start (lifetime_table_len)
+    int64_t etab_len = 0;
     int32_t* d_csr_ptr[3] = {nullptr, nullptr, nullptr};
     int32_t* d_csr_src[3] = {nullptr, nullptr, nullptr};
     int n_out[3] = {0, 0, 0};
     int n_src[3] = {0, 0, 0};
     // dynamic shared memory of the reduction tail per mode
-    int win_doubles[3] = {0, 0, 0}, hsum_in_smem[3] = {0, 0, 0}, csr_in_smem[3] = {0, 0, 0};
+    int hsum_in_smem[3] = {0, 0, 0}, csr_in_smem[3] = {0, 0, 0};
     int smem_bytes[3] = {0, 0, 0};
-    double *d_partial = nullptr, *d_hist_sum = nullptr;
+    unsigned long long* d_facc = nullptr;  // fixed-point limbs, K x nacc x 3
+    __int128* d_hist_sum = nullptr;
     unsigned* d_counters = nullptr;  // [0] global ticket, [1] flags
     double *d_theta = nullptr, *d_out = nullptr, *d_theta_tmp = nullptr;
     int32_t* d_status = nullptr;
@@ -119,7 +121,7 @@ struct musr_run_s {
 
     int plan(const musr_run_desc* d);
     void build_tiles(Tiling& t, int threads, int chunks) const;
-    int tail_smem(int mode, const Tiling& t, int* win, int* hsum_smem, int* csr_smem) const;
+    int tail_smem(int mode, int* hsum_smem, int* csr_smem) const;
     void build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const;
     int allocate();
     int upload(int dtype, const void* data, int on_device);

@@ -9,8 +9,16 @@ def rel_err(a, b):
 
 
 def grad_rel_err(g, ref):
-    """||g - ref|| / ||ref|| (the gradient tolerance is stated norm-wise)."""
-    return float(np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-300))
+    """Gradient error against the oracle's, as the larger of the norm-wise
+    relative error ||g - ref|| / ||ref|| and the per-component error
+    max_j |g_j - ref_j| / ||ref||_inf, so that `<= 1e-4` states both
+    tolerances: 1e-4 norm-wise, and no component off by more than 1e-4 of the
+    largest one (a wrong small component cannot hide under the norm)."""
+    g = np.asarray(g, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    norm = np.linalg.norm(g - ref) / max(np.linalg.norm(ref), 1e-300)
+    comp = np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-300) if ref.size else 0.0
+    return float(max(norm, comp))
 
 
 def split_by_hist(lay, x):

@@ -55,17 +55,17 @@ def test_multi_detector_fit_lm():
 
 @pytest.mark.parametrize("method", [MUSR_FIT_BFGS, MUSR_FIT_BFGS_FD])
 def test_quasi_newton_fits_reach_the_same_minimum(method):
-    """BFGS on the adjoint gradient and on central differences: same chi2 minimum."""
+    """BFGS on the adjoint gradient and on central differences: the oracle's
+    minimum, every parameter within 1e-3 sigma."""
     lay, theta, seed = W.config_single()
     d = W.poisson_counts(oracle.model(lay, theta), seed)
     start = W.perturb(theta, lay.free, 0.02, W.rng(seed))
     th_o, info_o, cov_o = oracle.fit(lay, d, start, oracle.CHI2)
+    assert info_o["status"] == 0
     with Run(lay, d) as run:
-        th_g, info_g, _ = run.fit(start, MUSR_CHI2, method=method, max_iter=2000, edm_tol=1e-6)
+        th_g, info_g, _ = run.fit(start, MUSR_CHI2, method=method, max_iter=2000)
     assert info_g["status"] == 0, info_g
-    sig = np.sqrt(np.diag(cov_o))
-    assert np.max(np.abs(th_g - th_o) / sig) <= 0.05
-    assert rel_err(info_g["value"], info_o["value"]) <= 1e-6
+    check_fit_parity(th_g, info_g, th_o, info_o, cov_o, lay.free.astype(bool))
 
 
 def test_fit_pulls_are_unit_normal():

@@ -1,8 +1,9 @@
 """GPU parity at the full sizes of the measured configurations, in the launch
 configurations the benchmark times:
 
-  * 32 x 131072 bins, 72 free parameters (the gradient workload): value and
-    gradient against the FP64 oracle for both objectives;
+  * 32 x 131072 bins, 72 free parameters (the gradient workload): value,
+    gradient and Gauss-Newton matrix against the FP64 oracle for both
+    objectives;
   * the paper's Table 1 histogram lengths (16 x 85320 ... 16 x 426601): chi2
     against the oracle;
   * the batched workload (64 uneven runs x (P+1) vectors, 2.7e9
@@ -13,7 +14,8 @@ configurations the benchmark times:
     gradients against the oracle;
   * the limits: one histogram of 2^24 bins, and 1024 histograms with 3080
     parameters (beyond the Gauss-Newton limit of 1024).
-Tolerances as elsewhere: objective relative 1e-6, gradient 1e-4 norm-wise.
+Tolerances as elsewhere: objective relative 1e-6, gradient 1e-4 norm-wise and
+per component (of the largest), GN matrix 1e-4 Frobenius.
 """
 import numpy as np
 import pytest
@@ -33,14 +35,20 @@ OBJS = [(MUSR_CHI2, oracle.CHI2), (MUSR_POISSON, oracle.POISSON)]
 
 @pytest.mark.parametrize("obj,oobj", OBJS)
 def test_gradient_workload_32x131072(obj, oobj):
+    """Value, gradient (norm-wise and per component) and Gauss-Newton matrix
+    (Frobenius relative 1e-4) of the 32 x 131072 workload against the oracle."""
     lay, theta, seed = W.config_gradient()
     d = W.poisson_counts(oracle.model(lay, theta), seed)
     th = W.perturb(theta, lay.free, 0.01, W.rng(seed + 1))
     with Run(lay, d.astype(np.float32)) as run:
         v, g, _ = run.chi2_grad(th, obj)
-    rv, rg, _ = oracle.gradient(lay, d, th, oobj, with_gn=False)
+        vh, gh, H = run.chi2_grad(th, obj, gn=True)
+    rv, rg, rH = oracle.gradient(lay, d, th, oobj, with_gn=True)
     assert rel_err(v, rv) <= 1e-6
     assert grad_rel_err(g, rg) <= 1e-4
+    assert rel_err(vh, rv) <= 1e-6
+    assert grad_rel_err(gh, rg) <= 1e-4
+    assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
 
 
 @pytest.mark.parametrize("M", [W.SWEEP_BINS[0], W.SWEEP_BINS[-1]])
