@@ -56,8 +56,9 @@ ALG_BYTES_PER_BIN = 4
 # costs vanish; FMA = 2); reported beside the algorithmic count
 EXEC_FP32_FLOP_PER_BIN = 83.5
 # DRAM bytes (read + write) of one eval_kernel<1,1,0,1,kGrad> launch of this
-# workload from an ncu capture of the current kernel (None until captured)
-TRAFFIC_BYTES_GRAD_LAUNCH = None
+# workload from an ncu capture of the current kernel (16,939,008 B read, 0
+# written; algorithmic 16,777,216 B)
+TRAFFIC_BYTES_GRAD_LAUNCH = 16939008
 # FP32-pipe FLOPs per bin-evaluation the value-only batched kernel executes on
 # the 64-run workload (batch_kernel<1,1,0,1>, ncu instruction counts over
 # 2,720,958,581 bin-evaluations)
@@ -791,7 +792,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 eval (packed pairs), f64 block partials, exact fixed-point final sum, f64 out",
+        "dtype": "f32 eval (packed pairs), f32 warp sums, exact 126-bit fixed-point block and final sums, f64 out",
         "data": "synthetic (Poisson counts of the model, numpy PCG64)",
         "config": {"workload": WORKLOAD, "bins": lay.total_bins, "params": P,
                    "l2": f"inputs larger than L2: {N_RUNS} independent runs of the workload "
@@ -835,6 +836,61 @@ def run_ours(args):
     run.close()
 
 
+def run_sharded(args):
+    """Strong scaling: the headline run split by histogram over the ranks
+    (one GPU each); one step = chi2 + gradient of the whole run, every rank
+    evaluating its shard through the library's host call and the shards'
+    1 + P sums combined by an all-gather added in rank order."""
+    import torch
+    import torch.distributed as dist
+    world, rank, local = dist_setup(args.gpus)
+    if not dist.is_initialized():  # one rank: a process group of its own
+        import tempfile
+        pg_file = os.path.join(tempfile.mkdtemp(), "pg")
+        dist.init_process_group("gloo", init_method=f"file://{pg_file}", rank=0, world_size=1)
+    from paper_1604_02334_gb300 import MUSR_CHI2, MUSR_VALUE_GRAD
+    from paper_1604_02334_gb300.shard import ShardedRun
+    lay, theta, seed = make_workload()
+    from paper_1604_02334_gb300 import Run
+    with Run(lay) as mrun:
+        mean = mrun.model(theta).astype(np.float64)
+    data = W.poisson_counts(mean, seed)  # the same run on every rank
+    sr = ShardedRun(lay, data)
+    g = W.rng(seed + 11)
+    thetas = [W.perturb(theta, lay.free, 0.01, g) for _ in range(args.steps + args.warmup)]
+    for i in range(args.warmup):
+        sr.chi2_grad(thetas[i], MUSR_CHI2, MUSR_VALUE_GRAD)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    barrier(world)
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        sr.chi2_grad(thetas[args.warmup + j], MUSR_CHI2, MUSR_VALUE_GRAD)
+    barrier(world)
+    el = max_over_ranks(time.perf_counter() - t0, world)
+    clk = clocks.stop()
+    sr.close()
+    if rank != 0:
+        return
+    value = lay.total_bins * args.steps / el
+    P = lay.n_params
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32 eval, exact fixed-point sums per shard, f64 combine in rank order",
+        "data": "synthetic (Poisson counts of the model, numpy PCG64)",
+        "config": {"workload": WORKLOAD, "bins": lay.total_bins, "params": P,
+                   "l2": "host calls, one whole-run evaluation per step (counts resident per shard)",
+                   "parallelism": f"histogram shards x{world}, all-gather of 1 + P sums"},
+        "clocks": clk,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": world * P * 8,
+                "d2h_bytes_per_step": world * (1 + P) * 8},
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -846,11 +902,15 @@ def main():
     ap.add_argument("--no-other-configs", action="store_true")
     ap.add_argument("--learned-steps", type=int, default=32768,
                     help="proposer training steps for the learned-start A/B (0: skip it)")
+    ap.add_argument("--shard", action="store_true",
+                    help="strong scaling: split the run by histogram over the ranks instead of replicas")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_sharded(args)
     else:
         run_ours(args)
 

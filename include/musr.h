@@ -330,6 +330,30 @@ int musr_fit(musr_run run, int obj, double* theta_inout, const uint8_t* free_mas
              const musr_fit_opts* opts, musr_fit_result* out);
 
 /*
+ * Fit with a caller-supplied evaluation (histogram-sharded runs).  Every
+ * objective sum of Sec. 4.1 (Eq. 3, Eq. 4) and its derivatives are sums over
+ * histograms, so a run split by histogram over several GPUs (the multi-GPU
+ * extension the paper's Sec. 6 names as future work) evaluates its shard on
+ * each GPU and adds the shards' sums; this entry point drives the same
+ * Levenberg-Marquardt (opts->method MUSR_FIT_LM) or BFGS (MUSR_FIT_BFGS)
+ * steps as musr_fit, each evaluation a call of `eval`.  Called with the same
+ * arguments on every rank, and with evaluations that return the same combined
+ * sums on every rank, every rank takes the same steps and returns the same
+ * theta.  Host only: the call itself makes no CUDA call.
+ *   eval(user, mode, theta, value, grad, gn): at theta[n_params], *value,
+ *            and for mode MUSR_VALUE_GRAD grad[n_params], for
+ *            MUSR_VALUE_GRAD_GN also gn[n_params^2] (row-major); returns
+ *            MUSR_OK, MUSR_EDOMAIN (the deviance has no likelihood there: a
+ *            rejected step), or any other status, which ends the fit with it.
+ *   n_bins_total  bins of the whole run (for ndf).
+ *   theta_inout, free_mask, opts, out   as for musr_fit (MUSR_FIT_BFGS_FD
+ *            returns MUSR_ENOTSUP).
+ */
+typedef int (*musr_eval_fn)(void* user, int mode, const double* theta, double* value, double* grad, double* gn);
+int musr_fit_eval(int32_t n_params, int64_t n_bins_total, musr_eval_fn eval, void* user, double* theta_inout,
+                  const uint8_t* free_mask, const musr_fit_opts* opts, musr_fit_result* out);
+
+/*
  * Batched adjoint evaluation: value + gradient (and the GN matrix) of many
  * runs, one parameter vector each, in ONE launch (Eq. 3 / Eq. 4 and their
  * derivatives as for musr_chi2_grad; the same run may appear several times,

@@ -186,7 +186,12 @@ SIGNATURES = {
     "musr_chi2_grad_noalloc": (ctypes.c_int, [ctypes.POINTER(musr_run_desc), ctypes.c_int, ctypes.c_int,
                                               _vp, _vp, _vp, _vp]),
     "musr_pipe_rates": (ctypes.c_int, [_dp, ctypes.c_int32]),
+    "musr_fit_eval": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _dp, _u8p,
+                                     ctypes.POINTER(musr_fit_opts), ctypes.POINTER(musr_fit_result)]),
 }
+
+# int eval(void* user, int mode, const double* theta, double* value, double* grad, double* gn)
+musr_eval_fn = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, _dp, _dp, _dp, _dp)
 
 _lib = None
 

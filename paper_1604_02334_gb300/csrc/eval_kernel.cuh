@@ -250,6 +250,7 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
             if (ip >= 0) ph0 += fixmul(theta[ip], rc.inv_two_pi);
             o.ph0 = ph0;
             o.step = step;
+            o.step_s = step * (unsigned long long)stripe;  // mod 2^64: whole turns drop out
             const float red = (float)(long long)step * 5.42101086242752217e-20f;  // turns in [-1/2, 1/2)
             const float sh = step_sinpi(red);
             o.cm1 = -2.f * sh * sh;        // cos(step) - 1
@@ -330,6 +331,7 @@ template <int NOSC>
 struct GqCarry {
     float gq[NOSC > 0 ? NOSC : 1];
     float gqk;
+    unsigned long long ph[NOSC > 0 ? NOSC : 1];  // fixed-point phase at the next chunk (exact 64-bit sums)
     bool valid;
 };
 
@@ -386,7 +388,9 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
             stA[c] = o.cm1;
             stB[c] = o.sn;
         }
-        const unsigned long long ph = o.ph0 + (unsigned long long)n0 * o.step;
+        const unsigned long long ph =
+            (carry && carry->valid) ? carry->ph[c] : o.ph0 + (unsigned long long)n0 * o.step;
+        if (carry) carry->ph[c] = ph + o.step_s;
         const float x = (float)(int)(ph >> 32) * 2.3283064365386963e-10f;  // turns in [-1/2, 1/2)
         float sc, cc;
         __sincosf(6.28318530717958647692f * x, &sc, &cc);
@@ -601,12 +605,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
-// The Gaussian 2-bin step ratios (minus 1) of both lanes at a thread's next
-// chunk, one stripe further: G2(n + stripe) = G2(n) Qs2 + (Qs2 - 1).
+// What a thread carries from one chunk to its next, one stripe further, so
+// the next chunk's seeds need no multiplication or series: the fixed-point
+// phase of every line (advanced by an exact 64-bit addition), the Gaussian
+// envelopes' 1-bin ratio at the chunk start (gq(n + stripe) = gq(n) Qs +
+// (Qs - 1)) and both lanes' 2-bin ratios (G2(n + stripe) = G2(n) Qs2 +
+// (Qs2 - 1)), likewise for the Kubo-Toyabe envelope.
 template <int NOSC>
 struct G2Carry {
     float2 g2[NOSC > 0 ? NOSC : 1];
     float2 g2k;
+    float gq1[NOSC > 0 ? NOSC : 1];
+    float gqk1;
+    unsigned long long ph[NOSC > 0 ? NOSC : 1];
     bool valid;
 };
 
@@ -641,11 +652,13 @@ __device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int 
     float2 stA[NOSC > 0 ? NOSC : 1], stB[NOSC > 0 ? NOSC : 1], nstB[NOSC > 0 ? NOSC : 1];
     const float k1 = fmaf(2.f, nf0, 1.f);  // 2 n0 + 1
     const float nn0 = nf0 * nf0;
+    const bool carried = carry && carry->valid;
 #pragma unroll
     for (int c = 0; c < NOSC; ++c) {
         const OscConst& o = hc.osc[c];
         // lane x: exact seed at n0 (fixed-point phase, SFU sincos and exp2)
-        const unsigned long long ph = o.ph0 + (unsigned long long)n0 * o.step;
+        const unsigned long long ph = carried ? carry->ph[c] : o.ph0 + (unsigned long long)n0 * o.step;
+        if (carry) carry->ph[c] = ph + o.step_s;
         const float x = (float)(int)(ph >> 32) * 2.3283064365386963e-10f;  // turns in [-1/2, 1/2)
         float sc, cc;
         __sincosf(6.28318530717958647692f * x, &sc, &cc);
@@ -666,9 +679,12 @@ __device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int 
         } else {
             env = o.cenv * ex2_approx(-fmaf(nn0, o.b_hi, fmaf(nf0, o.a_hi, fmaf(nn0, o.b_lo, nf0 * o.a_lo))));
             // 1-bin ratio at n0 (lane y's seed), then both lanes' 2-bin ratios
-            const float gq1 = step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
+            const float gq1 =
+                carried ? carry->gq1[c]
+                        : step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
+            if (carry) carry->gq1[c] = fmaf(gq1, o.qs, gq1 + o.qs);
             envy = fmaf(env, gq1, env);
-            if (carry && carry->valid) {
+            if (carried) {
                 g2[c] = carry->g2[c];
             } else {
                 g2[c] = make_float2(gauss_ratio2(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0),
@@ -689,9 +705,12 @@ __device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int 
         const float ex = 0.666666667f * hc.kt_cenv *
                          ex2_approx(-fmaf(nn0, hc.kt_b_hi, fmaf(nf0, hc.kt_a_hi, fmaf(nn0, hc.kt_b_lo, nf0 * hc.kt_a_lo))));
         const float gq1 =
-            step_expm1(-0.693147180559945309f * fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
+            carried ? carry->gqk1
+                    : step_expm1(-0.693147180559945309f *
+                                 fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
+        if (carry) carry->gqk1 = fmaf(gq1, hc.kt_qs, gq1 + hc.kt_qs);
         e23 = make_float2(ex, fmaf(ex, gq1, ex));
-        if (carry && carry->valid) {
+        if (carried) {
             g2k = carry->g2k;
         } else {
             g2k = make_float2(gauss_ratio2(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0),
@@ -955,34 +974,44 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 
     __shared__ HistConst hc;
     __shared__ float red[kMaxWarps][NACC];
+    __shared__ __align__(16) __int128 xred[kMaxWarps][NACC];
     __shared__ int s_last;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
+    // programmatic dependent launch: this grid may be scheduled while the
+    // previous one in the stream finishes; nothing it wrote is read before
+    // the previous grid has completed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int tile = blockIdx.x;
-    int k, M, tstart;
+    int k, M, tstart, tend;
     const float* hdata;
     if (p.uni_tph > 0) {
         k = tile / p.uni_tph;
         M = p.uni_nbins;
-        tstart = min((tile - k * p.uni_tph) * p.uni_tile_bins, (M + 7) & ~7);
+        const int64_t j = tile - k * p.uni_tph;
+        tstart = (int)(j * p.uni_chunks / p.uni_tph) * G;
+        tend = (int)((j + 1) * p.uni_chunks / p.uni_tph) * G;
         hdata = p.data + (int64_t)k * p.uni_stride;
     } else {
         k = p.tile_hist[tile];
         M = p.hist_nbins[k];
         tstart = p.tile_start[tile];
+        tend = p.tile_end[tile];
         hdata = p.data + p.hist_off[k];
     }
-    const int stripe = (int)blockDim.x * G;  // a tile is p.chunks stripes of blockDim x 8 bins
+    // a tile is a range of 8-bin chunks; thread t takes chunks t, t + blockDim, ...
+    // (every chunk that starts below tend starts below M)
+    const int stripe = (int)blockDim.x * G;
     int n0 = tstart + (int)threadIdx.x * G;
 
     // issue the first chunk's loads (counts and the lifetime factor at its
     // start) so their latency overlaps the staging
     float d[G];
     float E0 = 0.f;
-    if (n0 < M) E0 = __ldg(p.etab + (n0 >> 3));
-    if (MODE != kModel && n0 < M) {
+    if (n0 < tend) E0 = __ldg(p.etab + (n0 >> 3));
+    if (MODE != kModel && n0 < tend) {
         const float4* src = reinterpret_cast<const float4*>(hdata + n0);
         float4 a = __ldg(src), b = __ldg(src + 1);
         d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
@@ -1025,12 +1054,12 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         for (int a = 0; a < NACC; ++a) acc2[a] = make_float2(0.f, 0.f);
         G2Carry<NOSC> carry;
         carry.valid = false;
-        for (int c = 0; c < p.chunks; ++c) {
+        for (; n0 < tend; n0 += stripe) {
             // the next chunk's loads are in flight while this one is evaluated
             const int n1 = n0 + stripe;
             float dn[G];
             float En = 0.f;
-            if (c + 1 < p.chunks && n1 < M) {
+            if (n1 < tend) {
                 const float4* src = reinterpret_cast<const float4*>(hdata + n1);
                 float4 a = __ldg(src), b = __ldg(src + 1);
                 dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
@@ -1040,25 +1069,22 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 #pragma unroll
                 for (int g = 0; g < G; ++g) dn[g] = 0.f;
             }
-            if (n0 < M)
-                eval_pair<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc2, bad,
-                                                      &carry);
+            eval_pair<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc2, bad, &carry);
 #pragma unroll
             for (int g = 0; g < G; ++g) d[g] = dn[g];
             E0 = En;
-            n0 = n1;
         }
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = acc2[a].x + acc2[a].y;
     } else {
         GqCarry<NOSC> carry;
         carry.valid = false;
-        for (int c = 0; c < p.chunks; ++c) {
+        for (; n0 < tend; n0 += stripe) {
             // the next chunk's loads are in flight while this one is evaluated
             const int n1 = n0 + stripe;
             float dn[G];
             float En = 0.f;
-            if (c + 1 < p.chunks && n1 < M) {
+            if (n1 < tend) {
                 En = __ldg(p.etab + (n1 >> 3));
                 if (MODE != kModel) {
                     const float4* src = reinterpret_cast<const float4*>(hdata + n1);
@@ -1067,24 +1093,25 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
                     dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
                 }
             }
-            if (MODE == kModel || !(c + 1 < p.chunks && n1 < M)) {
+            if (MODE == kModel || !(n1 < tend)) {
 #pragma unroll
                 for (int g = 0; g < G; ++g) dn[g] = 0.f;
             }
-            if (n0 < M)
-                eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc, bad,
-                                                       MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
+            eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc, bad,
+                                                   MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
 #pragma unroll
             for (int g = 0; g < G; ++g) d[g] = dn[g];
             E0 = En;
-            n0 = n1;
         }
     }
+    // the next grid in the stream may begin its launch
+    asm volatile("griddepcontrol.launch_dependents;");
     if (MODE == kModel) return;
 
     // ---- block: FP32 warp sums scaled by the histogram's role factors, as
-    // fixed-point integers summed over the warps, one fixed-point add per
-    // accumulator into the histogram's totals ----
+    // fixed-point integers (one thread per warp and accumulator) summed over
+    // the warps, one fixed-point add per accumulator into the histogram's
+    // totals ----
     warp_sum<NACC>(acc);
     if (lane == 0) {
 #pragma unroll
@@ -1093,27 +1120,31 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     const int any_bad = __syncthreads_or(bad);
     {
         unsigned flag = (threadIdx.x == 0 && any_bad) ? 1u : 0u;
-        for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
+        for (int q = threadIdx.x; q < nwarps * NACC; q += blockDim.x) {
+            const int w = q / NACC, a = q - w * NACC;
             const float f = (MODE >= kGrad && a > 0) ? acc_factor<NE, NG, NS, KT, MODE>(hc, a) : 1.f;
+            if (!fix_of(red[w][a] * f, xred[w][a])) flag |= 2u;
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
             __int128 X = 0;
-            for (int w = 0; w < nwarps; ++w) {
-                __int128 x;
-                if (!fix_of(red[w][a] * f, x)) flag |= 2u;
-                X += x;
-            }
+            for (int w = 0; w < nwarps; ++w) X += xred[w][a];
             fix_add(p.facc + ((size_t)k * NACC + a) * 3, X);
         }
         if (flag) atomicOr(p.flags, flag);
     }
-    __threadfence();
+    // the barrier orders every thread's adds before thread 0's fence (fences
+    // are cumulative), which orders them before its ticket; the last block's
+    // thread 0 fences again before the block reads what the others added
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         const unsigned prev = atomicAdd(p.global_count, 1u);
         s_last = (prev == gridDim.x - 1u);
+        if (s_last) __threadfence();
     }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
 
     // ---- last block: per-histogram integer totals (their limbs zeroed for the
     // next launch), then theta via the CSR map, summed as integers; every load
@@ -1127,16 +1158,32 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         cptr = tbl;
         csrc = tbl + p.n_out + 1;
     }
-#pragma unroll 2
-    for (int i = threadIdx.x; i < p.K * NACC; i += blockDim.x) {
-        unsigned long long* l = p.facc + (size_t)i * 3;
-        const unsigned long long l0 = __ldcg(l), l1 = __ldcg(l + 1), l2 = __ldcg(l + 2);
-        hsum[i] = fix_total(l0, l1, l2);
-        l[0] = 0ull;
-        l[1] = 0ull;
-        l[2] = 0ull;
+    {
+        // up to four totals a thread with every load in flight before any store
+        const int n_tot = p.K * NACC;
+        unsigned long long lv[4][3];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = threadIdx.x + u * blockDim.x;
+            if (i < n_tot) {
+                const unsigned long long* l = p.facc + (size_t)i * 3;
+                lv[u][0] = __ldcg(l);
+                lv[u][1] = __ldcg(l + 1);
+                lv[u][2] = __ldcg(l + 2);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = threadIdx.x + u * blockDim.x;
+            if (i < n_tot) hsum[i] = fix_total(lv[u][0], lv[u][1], lv[u][2]);
+        }
+        for (int i = threadIdx.x + 4 * blockDim.x; i < n_tot; i += blockDim.x) {
+            const unsigned long long* l = p.facc + (size_t)i * 3;
+            hsum[i] = fix_total(__ldcg(l), __ldcg(l + 1), __ldcg(l + 2));
+        }
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < p.K * NACC * 3; i += blockDim.x) p.facc[i] = 0ull;
     const bool overflow = (fl & 2u) != 0u;
     double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
     for (int o = threadIdx.x; o < p.n_out; o += blockDim.x) {
@@ -1193,8 +1240,17 @@ cudaError_t launch_one(int threads, int n_tiles, cudaStream_t stream, const Eval
         return cudaFuncSetAttribute(eval_kernel<NE, NG, NS, KT, MODE>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, avail);
     }
-    eval_kernel<NE, NG, NS, KT, MODE><<<n_tiles, threads, smem, stream>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_tiles);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, eval_kernel<NE, NG, NS, KT, MODE>, p);
 }
 
 }  // namespace musr

@@ -548,6 +548,81 @@ extern "C" int musr_fit(musr_run run, int obj, double* theta, const uint8_t* fre
     return st;
 }
 
+// Fits whose objective is evaluated by the caller (musr_fit_eval): the same
+// Levenberg-Marquardt and BFGS steppers as musr_fit, with every evaluation a
+// call of `eval`.  A histogram-sharded run evaluates its shard on each GPU
+// and combines the shards' sums before returning them, so every rank takes
+// the same steps.
+extern "C" int musr_fit_eval(int32_t n_params, int64_t n_bins_total, musr_eval_fn eval, void* user,
+                             double* theta, const uint8_t* free_mask, const musr_fit_opts* opts,
+                             musr_fit_result* out) {
+    if (n_params <= 0 || !eval || !theta || !out) return MUSR_EINVAL;
+    musr_fit_opts o;
+    memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.max_iter <= 0) o.max_iter = 500;
+    if (!(o.edm_tol > 0.0)) o.edm_tol = 1e-8;
+    if (!(o.mu0 > 0.0)) o.mu0 = 1e-3;
+    if (o.method != MUSR_FIT_LM && o.method != MUSR_FIT_BFGS) return o.method == MUSR_FIT_BFGS_FD ? MUSR_ENOTSUP
+                                                                                                : MUSR_EINVAL;
+    for (int j = 0; j < n_params; ++j)
+        if (!std::isfinite(theta[j])) return MUSR_ENONFINITE;
+    const int P = n_params;
+    std::vector<int> fidx;
+    for (int j = 0; j < P; ++j)
+        if (!free_mask || free_mask[j]) fidx.push_back(j);
+    int evals = 0;
+    // value (+ gradient, + GN matrix) at th; a domain error reads as value +inf
+    auto call = [&](const double* th, int mode, double* f, double* g, double* H) -> int {
+        ++evals;
+        const int st = eval(user, mode, th, f, g, H);
+        if (st == MUSR_EDOMAIN) *f = INFINITY;
+        if (st == MUSR_OK && !std::isfinite(*f)) return MUSR_ENONFINITE;
+        return st;
+    };
+    musr_fit_result r = *out;
+    r.n_free = (int32_t)fidx.size();
+    r.ndf = (double)(n_bins_total - (int64_t)fidx.size());
+    int st;
+    if (o.method == MUSR_FIT_LM) {
+        LmStepper lm;
+        lm.init(P, fidx, o, theta);
+        double f;
+        st = call(theta, MUSR_VALUE_GRAD_GN, &f, lm.g.data(), lm.H.data());
+        if (st == MUSR_OK) {
+            lm.start(f);
+            while (lm.next()) {
+                double ft;
+                const int s2 = call(lm.trial.data(), MUSR_VALUE_GRAD_GN, &ft, lm.gt.data(), lm.Ht.data());
+                if (s2 != MUSR_OK && s2 != MUSR_EDOMAIN && s2 != MUSR_ENONFINITE) {
+                    st = s2;
+                    break;
+                }
+                lm.observe(s2, ft);
+            }
+            if (st == MUSR_OK) {
+                lm.finish(theta, &r);
+                st = lm.result;
+            }
+        }
+    } else {
+        std::vector<double> H((size_t)P * P);
+        auto value_grad = [&](const double* th, double* f, double* g) -> int {
+            return call(th, MUSR_VALUE_GRAD, f, g, nullptr);
+        };
+        auto start = [&](const double* th, double* f, double* g, double* hd) -> int {
+            const int s0 = call(th, MUSR_VALUE_GRAD_GN, f, g, H.data());
+            for (int j = 0; j < P; ++j) hd[j] = H[(size_t)j * P + j];
+            return s0;
+        };
+        st = fit_bfgs_generic(P, theta, fidx, o, false, value_grad, start, &r);
+    }
+    r.n_evals = evals;
+    r.status = st;
+    *out = r;
+    return st;
+}
+
 extern "C" int musr_fit_multistart(musr_run run, int obj, const double* starts, int32_t n_starts,
                                    const uint8_t* free_mask, const musr_fit_opts* opts, double* theta_out,
                                    musr_fit_result* out) {

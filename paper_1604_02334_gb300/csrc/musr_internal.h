@@ -34,6 +34,7 @@ struct OscConst {
     // rotation over 2 bins; qs2 = 2^(-4 b stripe) - 1
     float q2, cm1_2, sn_2, qs2;
     unsigned long long ph0, step;  // phase at bin 0 and per bin, 64-bit fixed-point turns
+    unsigned long long step_s;     // phase advance over one stripe (a thread's next chunk)
 };
 
 struct HistConst {
@@ -158,6 +159,7 @@ struct EvalParams {
     const int32_t* hist_nbins;    // [K]
     const int32_t* tile_hist;     // [n_tiles]
     const int32_t* tile_start;    // [n_tiles] first bin of the tile
+    const int32_t* tile_end;      // [n_tiles] bin past the tile (a multiple of 8, or the padded length)
     const int32_t* role_theta;    // [K][kMaxRoles][2] theta indices (or -1) per role
     const double* theta;          // [P] on the device (device calls)
     RunConst rc;
@@ -168,7 +170,6 @@ struct EvalParams {
     __int128* hist_sum;           // [K][nacc] integer totals (when they do not fit in shared memory)
     unsigned* global_count;       // [1]   (self-resetting)
     unsigned* flags;              // [1]   (self-resetting)
-    int chunks;                   // stripes of blockDim x 8 bins per tile
     const int32_t* csr_ptr;       // [n_out + 1]
     const int32_t* csr_src;       // sources: k * nacc + acc
     int n_out;
@@ -182,11 +183,12 @@ struct EvalParams {
     int theta_inline_n;           // > 0: theta_inline holds theta (host calls)
     double theta_inline[kInlineParams];
     // Equal-length histograms (the common layout): tile b belongs to histogram
-    // b / uni_tph and starts at min((b mod uni_tph) uni_tile_bins, uni_nbins
-    // rounded up to 8); histogram k starts at float k * uni_stride.  The tile
-    // and histogram tables are then not read, which takes two dependent
-    // memory round trips off the start of every block.  0: use the tables.
-    int uni_tph, uni_tile_bins, uni_nbins;
+    // k = b / uni_tph and covers chunks [j C / uni_tph, (j + 1) C / uni_tph)
+    // of it, j = b mod uni_tph, C = uni_chunks (8-bin chunks per histogram);
+    // histogram k starts at float k * uni_stride.  The tile and histogram
+    // tables are then not read, which takes two dependent memory round trips
+    // off the start of every block.  0: use the tables.
+    int uni_tph, uni_chunks, uni_nbins;
     int64_t uni_stride;
     // role -> theta rows of the first kInlineRoleHist histograms (when K fits),
     // so staging waits for theta alone

@@ -56,7 +56,7 @@ struct NaPlan {
     int64_t hist_off[kNaMaxHist];
     int32_t hist_nbins[kNaMaxHist];
     int32_t role_theta[kNaMaxHist * kMaxRoles * 2];
-    int32_t tile_hist[kNaMaxTiles], tile_start[kNaMaxTiles];
+    int32_t tile_hist[kNaMaxTiles], tile_start[kNaMaxTiles], tile_end[kNaMaxTiles];
     int32_t csr_ptr[kNaMaxParams + 2];
     int32_t csr_src[kNaMaxHist * (1 + 2 * kMaxRoles)];
     int32_t csr_cnt[kNaMaxParams + 2];
@@ -114,6 +114,7 @@ int plan_call(const musr_run_desc* d, int mode, int sms, NaPlan& pl) {
         for (int64_t j = 0; j < nt; ++j) {
             pl.tile_hist[pl.n_tiles] = k;
             pl.tile_start[pl.n_tiles] = (int32_t)std::min<int64_t>(j * pl.tile_bins, round_up(M, 8));
+            pl.tile_end[pl.n_tiles] = (int32_t)std::min<int64_t>((j + 1) * pl.tile_bins, round_up(M, 8));
             ++pl.n_tiles;
         }
     }
@@ -208,6 +209,7 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     const size_t o_nb = take(sizeof(int32_t) * pl.K);
     const size_t o_th = take(sizeof(int32_t) * pl.n_tiles);
     const size_t o_ts = take(sizeof(int32_t) * pl.n_tiles);
+    const size_t o_te = take(sizeof(int32_t) * pl.n_tiles);
     const size_t o_rt = take(sizeof(int32_t) * pl.K * kMaxRoles * 2);
     const size_t o_cp = take(sizeof(int32_t) * (pl.n_out + 1));
     const size_t o_cs = take(sizeof(int32_t) * (pl.n_src + 1));
@@ -231,6 +233,7 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     up(o_nb, pl.hist_nbins, sizeof(int32_t) * pl.K);
     up(o_th, pl.tile_hist, sizeof(int32_t) * pl.n_tiles);
     up(o_ts, pl.tile_start, sizeof(int32_t) * pl.n_tiles);
+    up(o_te, pl.tile_end, sizeof(int32_t) * pl.n_tiles);
     up(o_rt, pl.role_theta, sizeof(int32_t) * pl.K * kMaxRoles * 2);
     up(o_cp, pl.csr_ptr, sizeof(int32_t) * (pl.n_out + 1));
     up(o_cs, pl.csr_src, sizeof(int32_t) * pl.n_src);
@@ -255,6 +258,7 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.hist_nbins = reinterpret_cast<const int32_t*>(base + o_nb);
     p.tile_hist = reinterpret_cast<const int32_t*>(base + o_th);
     p.tile_start = reinterpret_cast<const int32_t*>(base + o_ts);
+    p.tile_end = reinterpret_cast<const int32_t*>(base + o_te);
     p.role_theta = reinterpret_cast<const int32_t*>(base + o_rt);
     p.theta = theta_dev;
     p.t0 = desc->t0_us;
@@ -269,7 +273,6 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.hist_sum = reinterpret_cast<__int128*>(base + o_hsum);
     p.global_count = reinterpret_cast<unsigned*>(base + o_cnt);
     p.flags = reinterpret_cast<unsigned*>(base + o_cnt) + 1;
-    p.chunks = 1;
     p.preload = 0;
     p.csr_ptr = reinterpret_cast<const int32_t*>(base + o_cp);
     p.csr_src = reinterpret_cast<const int32_t*>(base + o_cs);

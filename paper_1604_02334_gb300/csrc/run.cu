@@ -215,21 +215,37 @@ int musr_run_s::plan(const musr_run_desc* d) {
     return MUSR_OK;
 }
 
-// Tiles of `chunks` stripes of t x 8 bins, each within one histogram.
-void musr_run_s::build_tiles(Tiling& T, int t, int chunks) const {
+std::vector<int64_t> musr_run_s::tiles_per_hist(int t, int64_t target) const {
+    int64_t total = 0;
+    for (int k = 0; k < K; ++k) total += (n_bins[k] + kBinsPerThread - 1) / kBinsPerThread;
+    std::vector<int64_t> tph(K, 1);
+    if (total == 0) return tph;
+    for (int k = 0; k < K; ++k) {
+        const int64_t ck = (n_bins[k] + kBinsPerThread - 1) / kBinsPerThread;
+        const int64_t share = ck * target / total;              // proportional, rounded down
+        tph[k] = std::max<int64_t>(1, std::min(share, ck / t));  // >= one chunk per thread
+    }
+    return tph;
+}
+
+// Tiles of near-equal chunk ranges, tph[k] of them over histogram k.
+void musr_run_s::build_tiles(Tiling& T, int t, const std::vector<int64_t>& tph) const {
     T.threads = t;
-    T.chunks = chunks;
-    T.tile_bins = t * kBinsPerThread * chunks;
     T.tile_hist.clear();
     T.tile_start.clear();
+    T.tile_end.clear();
+    bool uniform = K > 0;
     for (int k = 0; k < K; ++k) {
-        const int64_t nt = std::max<int64_t>(1, (n_bins[k] + T.tile_bins - 1) / T.tile_bins);
-        for (int64_t j = 0; j < nt; ++j) {
+        const int64_t ck = (n_bins[k] + kBinsPerThread - 1) / kBinsPerThread;
+        for (int64_t j = 0; j < tph[k]; ++j) {
             T.tile_hist.push_back(k);
-            T.tile_start.push_back((int32_t)std::min<int64_t>(j * T.tile_bins, round_up(n_bins[k], 8)));
+            T.tile_start.push_back((int32_t)(j * ck / tph[k] * kBinsPerThread));
+            T.tile_end.push_back((int32_t)((j + 1) * ck / tph[k] * kBinsPerThread));
         }
+        if (n_bins[k] != n_bins[0] || tph[k] != tph[0]) uniform = false;
     }
     T.n_tiles = (int)T.tile_hist.size();
+    T.uni_tph = uniform ? (int)tph[0] : 0;
 }
 
 // Dynamic shared memory of the objective kernel's tail for a mode: the
@@ -303,10 +319,12 @@ int musr_run_s::allocate() {
         n_out[m] = (int)ptr[m].size() - 1;
         n_src[m] = (int)src[m].size();
     }
-    // per-mode tiling: among block sizes and stripes per tile, the one whose
-    // busiest SM holds the fewest bins, the blocks of a wave being spread
-    // evenly over the SMs (resident count from the kernel's occupancy), plus a
-    // cost per wave for the blocks' fixed work (staging, reduction)
+    // per-mode tiling: for each block size, one wave of resident blocks
+    // (resident count from the kernel's occupancy; more waves only for runs
+    // beyond 8 chunks a thread) as tiles of near-equal chunk ranges spread over
+    // the histograms in proportion to their bins; the block size whose busiest
+    // SM holds the fewest bins wins, with a cost per wave for the blocks' fixed
+    // work (staging, reduction)
     int dev_sms = 152;
     cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, device);
     for (int m = 0; m < 4; ++m) {
@@ -319,7 +337,8 @@ int musr_run_s::allocate() {
         // latency chains run side by side
         if (total_bins >= (int64_t)2 * dev_sms * kMaxThreads * kBinsPerThread)
             while (t_min < kMaxThreads && t_min < 32 * (2 + 2 * sig.n_osc())) t_min <<= 1;
-        int best_t = kMaxThreads, best_c = 1;
+        int best_t = kMaxThreads;
+        std::vector<int64_t> best_tph;
         int64_t best_cost = INT64_MAX;
         for (int t = kMaxThreads; t >= t_min; t >>= 1) {
             int per_sm = 0;
@@ -329,20 +348,29 @@ int musr_run_s::allocate() {
             q.status_out = reinterpret_cast<int32_t*>(&per_sm);
             if (launch_eval(sig, m, t, -1, stream, q) != cudaSuccess || per_sm < 1) per_sm = 1;
             const int64_t slots = (int64_t)per_sm * dev_sms;
-            for (int c = 1; c <= 8; ++c) {
-                const int64_t tile_bins = (int64_t)t * kBinsPerThread * c;
-                int64_t n = 0;
-                for (int k = 0; k < K; ++k) n += std::max<int64_t>(1, (n_bins[k] + tile_bins - 1) / tile_bins);
-                const int64_t waves = (n + slots - 1) / slots;
-                const int64_t cost = (n + dev_sms - 1) / dev_sms * tile_bins + kWaveCostBins * waves;
-                if (cost < best_cost) {
-                    best_cost = cost;
-                    best_t = t;
-                    best_c = c;
-                }
+            // one wave of tiles, or several when a run is too large for a wave
+            // of tiles of at most 8 chunks a thread
+            int64_t total = 0;
+            for (int k = 0; k < K; ++k) total += (n_bins[k] + kBinsPerThread - 1) / kBinsPerThread;
+            const int64_t waves = std::max<int64_t>(1, (total + slots * t * 8 - 1) / (slots * t * 8));
+            const std::vector<int64_t> tph = tiles_per_hist(t, slots * waves);
+            int64_t n = 0, max_chunks = 0;
+            for (int k = 0; k < K; ++k) {
+                const int64_t ck = (n_bins[k] + kBinsPerThread - 1) / kBinsPerThread;
+                n += tph[k];
+                max_chunks = std::max(max_chunks, (ck + tph[k] - 1) / tph[k]);
+            }
+            // the busiest SM's bins (its blocks' chunks, spread over its warps)
+            const int64_t per_sm_tiles = (n + dev_sms - 1) / dev_sms;
+            const int64_t cost = per_sm_tiles * max_chunks * kBinsPerThread + kWaveCostBins * ((n + slots - 1) / slots);
+            if (cost < best_cost) {
+                best_cost = cost;
+                best_t = t;
+                best_tph = tph;
             }
         }
-        build_tiles(tl[m], best_t, best_c);
+        build_tiles(tl[m], best_t, best_tph);
+
         if (m < 3) smem_bytes[m] = tail_smem(m, &hsum_in_smem[m], &csr_in_smem[m]);
     }
     const int n_out_max = n_out[Pk <= kMaxGnParams ? kGN : kGrad];
@@ -351,10 +379,11 @@ int musr_run_s::allocate() {
     const size_t o_hoff = A.take<int64_t>(K + 1);
     const size_t o_moff = A.take<int64_t>(K + 1);
     const size_t o_nb = A.take<int32_t>(K + 1);
-    size_t o_th[4], o_ts[4];
+    size_t o_th[4], o_ts[4], o_te[4];
     for (int m = 0; m < 4; ++m) {
         o_th[m] = A.take<int32_t>(tl[m].n_tiles + 1);
         o_ts[m] = A.take<int32_t>(tl[m].n_tiles + 1);
+        o_te[m] = A.take<int32_t>(tl[m].n_tiles + 1);
     }
     const size_t o_rt = A.take<int32_t>(role_theta.size() + 1);
     const size_t o_map = A.take<int32_t>(map.size() + 1);  // raw map rows (user theories)
@@ -386,6 +415,7 @@ int musr_run_s::allocate() {
     for (int m = 0; m < 4; ++m) {
         tl[m].d_tile_hist = reinterpret_cast<int32_t*>(b + o_th[m]);
         tl[m].d_tile_start = reinterpret_cast<int32_t*>(b + o_ts[m]);
+        tl[m].d_tile_end = reinterpret_cast<int32_t*>(b + o_te[m]);
     }
     d_role_theta = reinterpret_cast<int32_t*>(b + o_rt);
     d_map = reinterpret_cast<int32_t*>(b + o_map);
@@ -431,6 +461,7 @@ int musr_run_s::allocate() {
         if (T.n_tiles == 0) continue;  // a mode without a tiling (Gauss-Newton beyond kMaxGnParams)
         up(T.d_tile_hist, T.tile_hist.data(), sizeof(int32_t) * T.n_tiles);
         up(T.d_tile_start, T.tile_start.data(), sizeof(int32_t) * T.n_tiles);
+        up(T.d_tile_end, T.tile_end.data(), sizeof(int32_t) * T.n_tiles);
     }
     up(d_role_theta, role_theta.data(), sizeof(int32_t) * role_theta.size());
     up(d_map, map.data(), sizeof(int32_t) * map.size());
@@ -525,6 +556,7 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     const Tiling& T = tl[mode];
     p.tile_hist = T.d_tile_hist;
     p.tile_start = T.d_tile_start;
+    p.tile_end = T.d_tile_end;
     p.role_theta = d_role_theta;
     p.theta = theta_dev;
     p.t0 = t0;
@@ -539,7 +571,6 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.hist_sum = d_hist_sum;
     p.global_count = d_counters;
     p.flags = d_counters + 1;
-    p.chunks = T.chunks;
     const int m = mode == kModel ? kValue : mode;
     p.csr_ptr = d_csr_ptr[m];
     p.csr_src = d_csr_src[m];
@@ -552,11 +583,9 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
                 T.threads > 32 * (2 + 2 * sig.n_osc());  // warps beyond the staging ones exist
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
     // equal-length histograms: tiles and offsets by arithmetic (see EvalParams)
-    bool uniform = K > 0 && (int64_t)T.n_tiles % K == 0;
-    for (int kk = 1; kk < K && uniform; ++kk) uniform = n_bins[kk] == n_bins[0];
-    if (uniform && n_bins[0] + (int64_t)T.tile_bins < (int64_t)1 << 30) {
-        p.uni_tph = T.n_tiles / K;
-        p.uni_tile_bins = T.tile_bins;
+    if (T.uni_tph > 0 && n_bins[0] + kBinsPerThread * (int64_t)T.threads < (int64_t)1 << 30) {
+        p.uni_tph = T.uni_tph;
+        p.uni_chunks = (int)((n_bins[0] + kBinsPerThread - 1) / kBinsPerThread);
         p.uni_nbins = (int)n_bins[0];
         p.uni_stride = round_up(n_bins[0], 8);
     }

@@ -70,13 +70,14 @@ struct musr_run_s {
     musr::Signature sig;
     int R = 0;
     std::vector<int32_t> role_theta;  // [K][kMaxRoles][2]
-    // tiling, per mode (value, grad, GN, model): tiles of `chunks` stripes of
-    // threads x 8 bins of one histogram, sized so a launch is one wave of
-    // resident blocks
+    // tiling, per mode (value, grad, GN, model): tiles are ranges of 8-bin
+    // chunks of one histogram (histogram k split into tph[k] near-equal
+    // ranges), sized so a launch is about one wave of resident blocks with an
+    // even share of bins per SM
     struct Tiling {
-        int threads = 256, chunks = 1, tile_bins = 2048, n_tiles = 0;
-        std::vector<int32_t> tile_hist, tile_start;
-        int32_t *d_tile_hist = nullptr, *d_tile_start = nullptr;
+        int threads = 256, n_tiles = 0, uni_tph = 0;  // uni_tph: tiles per histogram when all are equal
+        std::vector<int32_t> tile_hist, tile_start, tile_end;
+        int32_t *d_tile_hist = nullptr, *d_tile_start = nullptr, *d_tile_end = nullptr;
     };
     Tiling tl[4];
     std::vector<int64_t> hist_off, model_off;
@@ -120,7 +121,10 @@ struct musr_run_s {
     int fd_batch_vec = 0;
 
     int plan(const musr_run_desc* d);
-    void build_tiles(Tiling& t, int threads, int chunks) const;
+    // tiles per histogram for a target tile count (>= 1 each, about
+    // proportional to its chunks, each tile at least one chunk per thread)
+    std::vector<int64_t> tiles_per_hist(int threads, int64_t target) const;
+    void build_tiles(Tiling& t, int threads, const std::vector<int64_t>& tph) const;
     int tail_smem(int mode, int* hsum_smem, int* csr_smem) const;
     void build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const;
     int allocate();
