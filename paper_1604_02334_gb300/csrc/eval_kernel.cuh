@@ -335,6 +335,69 @@ struct GqCarry {
     bool valid;
 };
 
+// ---- packed FP32 pairs (sm_100 FFMA2 / FMUL2 / FADD2): two values per instruction ----
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
+// Gauss-Newton accumulators of one thread, packed: the gradient sums
+// g[r] += w' x[r] as pairs g2[i] = (g[2i], g[2i+1]), and the upper triangle
+// h[r1][r2] += (wh x[r1]) x[r2], r2 >= r1, row by row: entries from an even
+// column in adjacent pairs (one FFMA2 against the aligned pair
+// (x[c], x[c+1])), the diagonal of an odd row and the last entry of a row
+// of odd length singly.  gn_scatter writes them in the standard layout.
+constexpr int gn_pairs(int R) {
+    int n = 0;
+    for (int r1 = 0; r1 < R; ++r1) n += (R - (r1 + (r1 & 1))) / 2;
+    return n;
+}
+constexpr int gn_singles(int R) {
+    int n = 0;
+    for (int r1 = 0; r1 < R; ++r1) n += (r1 & 1) + ((R - (r1 + (r1 & 1))) & 1);
+    return n;
+}
+template <int R>
+struct GnAcc {
+    static constexpr int RX = (R + 1) / 2;
+    static constexpr int NP = gn_pairs(R);
+    static constexpr int NSG = gn_singles(R);
+    float2 g2[RX];
+    float2 p[NP > 0 ? NP : 1];
+    float s[NSG > 0 ? NSG : 1];
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < RX; ++i) g2[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) p[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < NSG; ++i) s[i] = 0.f;
+    }
+};
+
+// acc[1 + r] = g[r]; acc[1 + R + ...] = the triangle row by row.
+template <int R, int NACC>
+__device__ __forceinline__ void gn_scatter(const GnAcc<R>& G, float (&acc)[NACC]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[1 + r] = (r & 1) ? G.g2[r >> 1].y : G.g2[r >> 1].x;
+    int a = 1 + R, pi = 0, si = 0;
+#pragma unroll
+    for (int r1 = 0; r1 < R; ++r1) {
+        int c = r1;
+        if (c & 1) {
+            acc[a++] = G.s[si++];
+            ++c;
+        }
+#pragma unroll
+        for (; c + 1 < R; c += 2) {
+            acc[a++] = G.p[pi].x;
+            acc[a++] = G.p[pi].y;
+            ++pi;
+        }
+        if (c < R) acc[a++] = G.s[si++];
+    }
+}
+
 // The lifetime factor at any bin n0 from the run's table of chunk starts,
 // stepped by the per-bin recurrence over the n0 mod 8 bins past the start.
 __device__ __forceinline__ float lifetime_from_table(const float* etab, int n0, float qE) {
@@ -348,7 +411,8 @@ template <int NE, int NG, int NS, int KT, int MODE, int NACC, bool FULL>
 __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int M,
                                                 const float (&d)[kBinsPerThread], float E0, int obj, float dtf,
                                                 float t0f, float (&acc)[NACC], bool& bad,
-                                                float* model_dst, GqCarry<NE + NG + NS>* carry) {
+                                                float* model_dst, GqCarry<NE + NG + NS>* carry,
+                                                GnAcc<2 + 4 * (NE + NG + NS) + NS + 2 * KT>* gn) {
     constexpr int NOSC = NE + NG + NS;
     constexpr int R = 2 + 4 * NOSC + NS + 2 * KT;
     constexpr int CS = NE + NG;    // index of the stretched line (when NS)
@@ -541,16 +605,33 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
                     x[RK] = GE;
                     x[RK + 1] = tt * (xk - 3.f) * e23;
                 }
+                // x as aligned pairs (x[R] = 0 when R is odd)
+                constexpr int RX = (R + 1) / 2;
+                float2 xp[RX];
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[1 + r] = fmaf(wq, x[r], acc[1 + r]);
-                int a = 1 + R;
+                for (int i = 0; i < RX; ++i) xp[i] = make_float2(x[2 * i], 2 * i + 1 < R ? x[2 * i + 1] : 0.f);
+                const float2 wq2 = bc2(wq);
+#pragma unroll
+                for (int i = 0; i < RX; ++i) gn->g2[i] = fma2(wq2, xp[i], gn->g2[i]);
+                int pi = 0, si = 0;
 #pragma unroll
                 for (int r1 = 0; r1 < R; ++r1) {
                     const float qv = wh * x[r1];
+                    const float2 q2 = bc2(qv);
+                    int c = r1;
+                    if (c & 1) {
+                        gn->s[si] = fmaf(qv, x[c], gn->s[si]);
+                        ++si;
+                        ++c;
+                    }
 #pragma unroll
-                    for (int r2 = r1; r2 < R; ++r2) {
-                        acc[a] = fmaf(qv, x[r2], acc[a]);
-                        ++a;
+                    for (; c + 1 < R; c += 2) {
+                        gn->p[pi] = fma2(q2, xp[c >> 1], gn->p[pi]);
+                        ++pi;
+                    }
+                    if (c < R) {
+                        gn->s[si] = fmaf(qv, x[c], gn->s[si]);
+                        ++si;
                     }
                 }
             }
@@ -582,13 +663,14 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
 template <int NE, int NG, int NS, int KT, int MODE, int NACC>
 __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M, const float (&d)[kBinsPerThread],
                                            float E0, int obj, float dtf, float t0f, float (&acc)[NACC], bool& bad,
-                                           float* model_dst, GqCarry<NE + NG + NS>* carry = nullptr) {
+                                           float* model_dst, GqCarry<NE + NG + NS>* carry = nullptr,
+                                           GnAcc<2 + 4 * (NE + NG + NS) + NS + 2 * KT>* gn = nullptr) {
     if (n0 + kBinsPerThread <= M)
         eval_chunk_body<NE, NG, NS, KT, MODE, NACC, true>(hc, n0, M, d, E0, obj, dtf, t0f, acc, bad, model_dst,
-                                                          carry);
+                                                          carry, gn);
     else
         eval_chunk_body<NE, NG, NS, KT, MODE, NACC, false>(hc, n0, M, d, E0, obj, dtf, t0f, acc, bad, model_dst,
-                                                           carry);
+                                                           carry, gn);
 }
 
 // ---- packed FP32 pairs: two bins per instruction (FFMA2 / FMUL2 / FADD2) ----
@@ -600,10 +682,6 @@ __device__ __forceinline__ void eval_chunk(const HistConst& hc, int n0, int M, c
 // bins (the 2-bin constants staged with the 1-bin ones); lane y is seeded
 // from lane x by one 1-bin step.  The arithmetic per bin is that of
 // eval_chunk_body, in half the instructions.
-__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 
 // What a thread carries from one chunk to its next, one stripe further, so
 // the next chunk's seeds need no multiplication or series: the fixed-point
@@ -1079,6 +1157,8 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     } else {
         GqCarry<NOSC> carry;
         carry.valid = false;
+        GnAcc<R> gnacc;
+        gnacc.zero();
         for (; n0 < tend; n0 += stripe) {
             // the next chunk's loads are in flight while this one is evaluated
             const int n1 = n0 + stripe;
@@ -1098,11 +1178,13 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
                 for (int g = 0; g < G; ++g) dn[g] = 0.f;
             }
             eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, (float)p.dt, (float)p.t0, acc, bad,
-                                                   MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry);
+                                                   MODE == kModel ? p.model_out + p.model_off[k] : nullptr, &carry,
+                                                   &gnacc);
 #pragma unroll
             for (int g = 0; g < G; ++g) d[g] = dn[g];
             E0 = En;
         }
+        if constexpr (MODE == kGN) gn_scatter(gnacc, acc);
     }
     // the next grid in the stream may begin its launch
     asm volatile("griddepcontrol.launch_dependents;");

@@ -39,6 +39,38 @@ using namespace musr;
 
 namespace {
 
+// Cholesky factor A = L L^T of an n x n SPD matrix in place (L in the lower
+// triangle); false if A is not positive definite.
+bool cholesky_factor(std::vector<double>& A, int n) {
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        if (!(s > 0.0)) return false;
+        const double l = sqrt(s);
+        A[j * n + j] = l;
+        for (int i = j + 1; i < n; ++i) {
+            double v = A[i * n + j];
+            for (int k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
+            A[i * n + j] = v / l;
+        }
+    }
+    return true;
+}
+
+// Solve L L^T x = b with the factor of cholesky_factor (b overwritten).
+void cholesky_back(const std::vector<double>& A, std::vector<double>& b, int n) {
+    for (int i = 0; i < n; ++i) {
+        double v = b[i];
+        for (int k = 0; k < i; ++k) v -= A[i * n + k] * b[k];
+        b[i] = v / A[i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double v = b[i];
+        for (int k = i + 1; k < n; ++k) v -= A[k * n + i] * b[k];
+        b[i] = v / A[i * n + i];
+    }
+}
+
 // Cholesky solve of the n x n SPD system A x = b (A overwritten).
 bool cholesky_solve(std::vector<double>& A, std::vector<double>& b, int n) {
     for (int j = 0; j < n; ++j) {
@@ -240,12 +272,13 @@ struct LmStepper {
         out->mu = mu;
         out->iters = it;
         if (out->cov) {
+            // covariance 2 H^-1 over the free block: one factorisation, nf solves
+            for (int a = 0; a < nf; ++a)
+                for (int e = 0; e < nf; ++e) A[(size_t)a * nf + e] = H[(size_t)fidx[a] * P + fidx[e]];
+            const bool ok = cholesky_factor(A, nf);
             for (int c = 0; c < nf; ++c) {
-                for (int a = 0; a < nf; ++a) {
-                    for (int e = 0; e < nf; ++e) A[(size_t)a * nf + e] = H[(size_t)fidx[a] * P + fidx[e]];
-                    b[a] = a == c ? 2.0 : 0.0;
-                }
-                const bool ok = cholesky_solve(A, b, nf);
+                for (int a = 0; a < nf; ++a) b[a] = a == c ? 2.0 : 0.0;
+                if (ok) cholesky_back(A, b, nf);
                 for (int a = 0; a < nf; ++a) out->cov[(size_t)a * nf + c] = ok ? b[a] : NAN;
             }
         }

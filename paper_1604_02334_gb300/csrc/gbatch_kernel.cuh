@@ -122,6 +122,8 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
         {
             GqCarry<NOSC> carry;
             carry.valid = false;
+            GnAcc<R> gnacc;
+            gnacc.zero();
             for (int row = 0; row < item.rows; ++row) {
                 const int n1 = n0 + stripe;
                 float dn[G];
@@ -137,12 +139,14 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
                     for (int g = 0; g < G; ++g) dn[g] = 0.f;
                 }
                 if (n0 < M)
-                    eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, dtf, t0f, acc, bad, nullptr, &carry);
+                    eval_chunk<NE, NG, NS, KT, MODE, NACC>(hc, n0, M, d, E0, p.obj, dtf, t0f, acc, bad, nullptr, &carry,
+                                                           &gnacc);
 #pragma unroll
                 for (int g = 0; g < G; ++g) d[g] = dn[g];
                 E0 = En;
                 n0 = n1;
             }
+            if constexpr (MODE == kGN) gn_scatter(gnacc, acc);
         }
         warp_sum<NACC>(acc);
         if (lane == 0) {
