@@ -10,16 +10,16 @@
  *
  * over every bin of every histogram, for a parameter vector theta addressed
  * through a per-histogram map (Sec. 4.1 Eq. 2; the parameter / map arrays of
- * Sec. 4.2.1, Listing 3).  A_k(t) is a sum of the predefined components of
- * Sec. 4.2.1 Listing 2 and Sec. 4.3 Eq. 5:
+ * Sec. 4.2.1).  A_k(t) is a sum of components built from the predefined muSR
+ * relaxation functions of Sec. 4.2.1 and the precession of Sec. 4.3 Eq. 5:
  *
  *   MUSR_TF_EXP          a exp(-lambda t)        cos(2 pi gamma (B + B2) t + phi)
  *   MUSR_TF_GAUSS        a exp(-(sigma t)^2 / 2) cos(2 pi gamma (B + B2) t + phi)
  *   MUSR_KT_STATIC_GAUSS a [1/3 + 2/3 (1 - (D t)^2) exp(-(D t)^2 / 2)]
  *   MUSR_TF_STRETCHED    a ge(t, lambda, beta)   cos(2 pi gamma (B + B2) t + phi),
  *                        ge = exp(-(lambda t)^beta) where lambda t > 0, 1 elsewhere
- *                        (the stretched exponential "ge" of Listing 2; the
- *                        listing's pow of a negative base is read as 1)
+ *                        (the stretched exponential; a negative base has no
+ *                        real power, so lambda t <= 0 is read as 1)
  *
  * Conventions shared by every entry point:
  *   - Every function returns MUSR_OK (0) or a negative status; none aborts.

@@ -11,8 +11,8 @@
  *                    t = n * dt  (n = 0, 1, 2, ...; a start offset t0 is
  *                    allowed, t = t0 + n * dt, with t0 = 0 reproducing Eq. 1)
  *   Sec. 4.1, Eq. 2  per-histogram parameter set {N0, Nbkg, p}; the map array
- *                    of Sec. 4.2.1 (Listing 3) gives the indirect addressing
- *                    from a histogram's slots to the global parameter vector.
+ *                    of Sec. 4.2.1 gives the indirect addressing from a
+ *                    histogram's slots to the global parameter vector.
  *   Sec. 4.1, Eq. 3  chi2 = sum_j sum_n (d - N)^2 / d_err^2, d_err^2 = d;
  *                    reading: d_err^2 = max(d, 1) so that empty bins are
  *                    defined.
@@ -20,17 +20,20 @@
  *                    log term sits inside the bracket (Poisson deviance,
  *                    -2 ln of the likelihood ratio), it is minimised, and a
  *                    bin with d = 0 contributes 2N.
- *   Sec. 4.2.1, Listing 2 predefined functions:
- *                    se(t, l)  = exp(-l t)
- *                    ge(t, l, b) = exp(-(l t)^b); reading: 1 where l t <= 0
- *                    (the listing's pow of a negative base has no real value)
- *                    sg(t, s)  = exp(-(s t)^2 / 2)
- *                    stg(t, s) = 1/3 + 2/3 (1 - (s t)^2) exp(-(s t)^2 / 2)
- *                    (the listing's integer 1/3 and 2/3 are read as the real
- *                    fractions of the static Gaussian Kubo-Toyabe function)
- *   Sec. 4.3, Eq. 5  A = A0 sg(t, sigma) cos(gamma_mu B t + phi); the cosine
- *                    "tf" of Listing 3 is cos(2 pi gamma B t + phi) with gamma
- *                    in MHz/G, t in us, phi in radians.
+ *   Sec. 4.2.1       theories are built from predefined relaxation functions
+ *                    common in muSR (the exponential and Gaussian ones among
+ *                    them); the four used here, from their standard
+ *                    definitions, lambda and sigma rates in 1/us:
+ *                    exponential          exp(-lambda t)
+ *                    Gaussian             exp(-(sigma t)^2 / 2)
+ *                    static Gaussian Kubo-Toyabe (zero field)
+ *                                         1/3 + 2/3 (1 - (sigma t)^2) exp(-(sigma t)^2 / 2)
+ *                    stretched exponential exp(-(lambda t)^beta); reading: 1
+ *                                         where lambda t <= 0 (a negative
+ *                                         base has no real power)
+ *   Sec. 4.3, Eq. 5  A = A0 exp(-(sigma t)^2 / 2) cos(gamma_mu B t + phi);
+ *                    the precession factor is cos(2 pi gamma B t + phi) with
+ *                    gamma in MHz/G, t in us, phi in radians.
  *
  * Component kinds (columns are indices into the histogram's map row; a map
  * entry of -1 stands for the constant 0):
@@ -149,24 +152,28 @@ static int check_layout(const orc_layout* L) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Listing 2 predefined functions, written out                               */
+/* Relaxation functions of the component kinds (Sec. 4.2.1, Eq. 5), in the  */
+/* order of the kinds                                                        */
 /* ------------------------------------------------------------------------ */
-static double fn_se(double t, double lambda) { return exp(-lambda * t); }
+/* TF_EXP: exponential relaxation */
+static double relax_exponential(double t, double lambda) { return exp(-lambda * t); }
 
-/* l t <= 0 gives 1: the power of a negative base is undefined for real b */
-static double fn_ge(double t, double lambda, double beta) {
-    double x = lambda * t;
-    return x > 0.0 ? exp(-pow(x, beta)) : 1.0;
-}
-
-static double fn_sg(double t, double sigma) {
+/* TF_GAUSS: Gaussian relaxation (Eq. 5) */
+static double relax_gaussian(double t, double sigma) {
     double st = sigma * t;
     return exp(-0.5 * st * st);
 }
 
-static double fn_stg(double t, double sigma) {
+/* KT_SG: static Gaussian Kubo-Toyabe function in zero field; -> 1/3 at large t */
+static double kubo_toyabe_static_gaussian(double t, double sigma) {
     double x = (sigma * t) * (sigma * t);
     return 1.0 / 3.0 + (2.0 / 3.0) * (1.0 - x) * exp(-0.5 * x);
+}
+
+/* TF_GE: stretched exponential; l t <= 0 gives 1 (a negative base has no real power) */
+static double relax_stretched(double t, double lambda, double beta) {
+    double x = lambda * t;
+    return x > 0.0 ? exp(-pow(x, beta)) : 1.0;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -191,7 +198,7 @@ static double theory_bin(const orc_layout* L, const double* theta, int k, double
         double a = map_value(L, theta, k, d[1]);
         double rate = map_value(L, theta, k, d[2]);
         if (kind == ORC_KT_SG) {
-            double g = fn_stg(t, rate);
+            double g = kubo_toyabe_static_gaussian(t, rate);
             asym += a * g;
             if (dA) {
                 if (d[1] >= 0) dA[d[1]] += g;
@@ -209,17 +216,17 @@ static double theory_bin(const orc_layout* L, const double* theta, int k, double
         double cs = cos(arg), sn = sin(arg);
         double env, denv_drate, denv_dbeta = 0.0;
         if (kind == ORC_TF_EXP) {
-            env = fn_se(t, rate);
+            env = relax_exponential(t, rate);
             denv_drate = -t * env;
         } else if (kind == ORC_TF_GAUSS) {
-            env = fn_sg(t, rate);
+            env = relax_gaussian(t, rate);
             denv_drate = -rate * t * t * env;
         } else {
             /* d/dl exp(-(l t)^b) = -b t (l t)^(b-1) exp(-(l t)^b);
                d/db exp(-(l t)^b) = -(l t)^b ln(l t) exp(-(l t)^b); both 0 where l t <= 0 */
             double beta = map_value(L, theta, k, d[6]);
             double x = rate * t;
-            env = fn_ge(t, rate, beta);
+            env = relax_stretched(t, rate, beta);
             denv_drate = x > 0.0 ? -beta * t * pow(x, beta - 1.0) * env : 0.0;
             denv_dbeta = x > 0.0 ? -pow(x, beta) * log(x) * env : 0.0;
         }

@@ -4,8 +4,10 @@ never does and this module imports nothing of it).
 
 Sec. 4.2.1 of the paper: the asymmetry A_k(t) of a histogram is a C
 expression over t (us), the parameter array p, the histogram's map row m and
-a function array f, using the predefined muSR functions of the paper's
-listing (se, ge, sg, stg) and tf, plus the C math functions.  This module
+a function array f, using the predefined muSR functions of the
+user-function language (se, ge, sg, stg, tf: exponential, stretched
+exponential, Gaussian and static Gaussian Kubo-Toyabe relaxation, precession),
+written from their definitions, plus the C math functions.  This module
 evaluates such an expression directly from its syntax tree with numpy, in
 FP64, vectorised over t, keeping C's typing of literals (an int / int
 division truncates toward zero, as in the compiled kernel), and forms

@@ -214,7 +214,9 @@ struct TT {
     double x;
     __device__ operator real() const { return f; }
 };
-// predefined functions (Listing 2 of the paper, written from their definitions)
+// the predefined muSR functions of the user-function language (Sec. 4.2.1),
+// from their definitions: se exponential, ge stretched exponential (1 where
+// lambda t <= 0), sg Gaussian, stg static Gaussian Kubo-Toyabe
 template <class L> __device__ __forceinline__ auto se(TT t, L lambda) { return exp(-(lambda * (real)t)); }
 template <class L, class B> __device__ __forceinline__ auto ge(TT t, L lambda, B beta) {
     const auto x = lambda * (real)t;

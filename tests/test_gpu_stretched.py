@@ -1,5 +1,5 @@
 """GPU parity of the stretched precession line, a exp(-(lambda t)^beta)
-cos(2 pi gamma (B + B2) t + phi) (the "ge" function of Sec. 4.2.1, Listing 2),
+cos(2 pi gamma (B + B2) t + phi) (the stretched exponential of Sec. 4.2.1),
 built into the FP32 objective / adjoint kernels, against the FP64 oracle.
 
 Tolerances are those of the other lines: objective relative 1e-6, gradient

@@ -72,7 +72,7 @@ def test_lifetime_and_background():
 
 def test_kubo_toyabe_special_values():
     """Static Gaussian KT: G(0) = 1, G(t -> inf) = 1/3, minimum at Delta t = sqrt(3)
-    with value 1/3 - (4/3) e^{-3/2} (Listing 2 stg with real-valued 1/3, 2/3)."""
+    with value 1/3 - (4/3) e^{-3/2} (the Kubo-Toyabe function with real-valued 1/3, 2/3)."""
     lay = unit_signal_layout(W.KT_STATIC_GAUSS, n_bins=200001, dt=1e-4)
     delta = 0.9
     theta = np.array([1.0, 0.0, 1.0, delta, 0.0, 0.0])
@@ -104,7 +104,7 @@ def test_precession_special_points(kind):
 
 def test_relaxation_envelopes():
     """At cos = 1 points (phi = 0, t = m T): exponential envelope e^{-lambda t},
-    Gaussian envelope e^{-(sigma t)^2 / 2} (Listing 2 se and sg)."""
+    Gaussian envelope e^{-(sigma t)^2 / 2} (Sec. 4.2.1 relaxation functions, Eq. 5)."""
     B = 100.0
     period = 1.0 / (W.GAMMA_MU_MHZ_PER_G * B)
     n_per = 500
@@ -142,7 +142,7 @@ def test_precession_frequency_by_fft():
 
 
 def test_mapped_multi_detector_matches_single_histograms():
-    """Map indirection (Eq. 2, Listing 3): each histogram of a 3-detector run equals
+    """Map indirection (Eq. 2, the map array of Sec. 4.2.1): each histogram of a 3-detector run equals
     a standalone single-histogram run with its own N0, bkg, phase and the shared rest."""
     lay = W.multi_detector_layout(3, [700, 500, 900], window_us=5.0)
     lay.comp = lay.comp[:1].copy()  # TF_EXP line only, so the single layout can express it

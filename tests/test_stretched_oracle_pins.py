@@ -1,13 +1,14 @@
 """Pins of the FP64 oracle's stretched precession line, a ge(t, lambda, beta)
-cos(2 pi gamma (B + B2) t + phi) component (the stretched exponential "ge" of
-Sec. 4.2.1, Listing 2), against facts fixed by mathematics:
+cos(2 pi gamma (B + B2) t + phi) component (the stretched exponential among
+the predefined relaxation functions of Sec. 4.2.1), against facts fixed by
+mathematics:
 
-  * beta = 1 is the exponential line (Listing 2 "se"), beta = 2 with
-    lambda = sigma / sqrt(2) the Gaussian line ("sg"), bit for bit up to
+  * beta = 1 is the exponential line, beta = 2 with
+    lambda = sigma / sqrt(2) the Gaussian line, bit for bit up to
     rounding, values and derivatives;
   * ge(1/lambda) = 1/e for every beta, ge(2/lambda) = exp(-2^beta);
-  * lambda t <= 0 gives ge = 1 (the reading of the listing's pow of a
-    negative base);
+  * lambda t <= 0 gives ge = 1 (the reading for a negative base, which has
+    no real power);
   * the closed-form beta derivative at beta = 1, the analytic gradient against
     central differences of the objective, the Gauss-Newton matrix against the
     exact Hessian at zero residual;
