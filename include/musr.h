@@ -305,10 +305,12 @@ typedef struct {
     double fd_rel_h;  /* MUSR_FIT_BFGS_FD steps: > 0 second-order central
                          differences with a fixed relative step
                          fd_rel_h * max(|theta_j|, 1); <= 0 (default)
-                         fourth-order central differences with a step of each
-                         parameter's standard error, from two passes of second
-                         differences at the start (the FP32 value noise
-                         enters the gradient divided by the step) */
+                         fourth-order central differences with a step of two
+                         standard errors of each parameter, from two passes
+                         of second differences at the start (the FP32 value
+                         noise enters the gradient divided by the step); a
+                         step whose stencil meets a non-finite value is
+                         quartered (up to three times) */
 } musr_fit_opts;
 
 typedef struct {

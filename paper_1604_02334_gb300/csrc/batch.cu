@@ -583,51 +583,72 @@ int musr_chi2_batch(const musr_run* runs, int32_t n_runs, int obj, const double*
 namespace musr {
 
 // Central-difference gradient over the free parameters from one batched launch
-// per 128 vectors: theta and theta +- h_j e_j, h_j = rel_h max(|theta_j|, 1).
-int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
-                      const double* h_abs, int order, double* value, double* grad, double* hdiag) {
+// per kBatchMaxVec vectors: theta and theta +- h_j e_j (and +- 2 h_j e_j for
+// order 4).  A parameter whose stencil meets a non-finite value (a deviance
+// step past N = 0) has its step quartered, up to three times; h_abs keeps
+// the reduced steps.  The launches use one fixed shape (no autotuning), so
+// a fit's differences, and so its path, are the same in every process.
+int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx, double* h_abs,
+                      int order, double* value, double* grad, double* hdiag) {
     const int P = run->P;
     const int nf = (int)fidx.size();
-    // vector 0 is theta; then per free parameter +h, -h (and +2h, -2h for order 4)
     const int per = order == 4 ? 4 : 2;
-    const int nv_total = 1 + per * nf;
     if (!run->fd_batch) {
-        int32_t mv = std::min(nv_total, kBatchMaxVec);
+        int32_t mv = std::min(1 + 4 * nf, kBatchMaxVec);  // room for either order
         musr_run r = run;
         int st = musr_batch_create(&r, 1, &mv, &run->fd_batch);
         if (st != MUSR_OK) return st;
+        run->fd_batch->tuned = true;  // the default shape, in every process
         run->fd_batch_vec = mv;
     }
     musr_batch B = run->fd_batch;
     const int cap = run->fd_batch_vec;
-    std::vector<double> vecs((size_t)nv_total * P), vals(nv_total);
-    for (int v = 0; v < nv_total; ++v) memcpy(vecs.data() + (size_t)v * P, theta, sizeof(double) * P);
     static const double kOffsets[4] = {1.0, -1.0, 2.0, -2.0};
-    for (int a = 0; a < nf; ++a)
-        for (int u = 0; u < per; ++u) vecs[(size_t)(1 + per * a + u) * P + fidx[a]] += kOffsets[u] * h_abs[a];
-    for (int v0 = 0; v0 < nv_total; v0 += cap) {
-        const int32_t nv = std::min(cap, nv_total - v0);
-        int st = musr_batch_eval(B, obj, vecs.data() + (size_t)v0 * P, &nv, vals.data() + v0);
-        if (st != MUSR_OK) return st;
-    }
-    *value = vals[0];
-    if (!isfinite(vals[0])) return MUSR_EDOMAIN;
     memset(grad, 0, sizeof(double) * P);
-    for (int a = 0; a < nf; ++a) {
-        const double* f = vals.data() + 1 + per * a;  // f(+h), f(-h) [, f(+2h), f(-2h)]
-        for (int u = 0; u < per; ++u)
-            if (!isfinite(f[u])) return MUSR_EDOMAIN;
-        const double h = h_abs[a];
-        if (order == 4) {
-            // fourth-order central differences: truncation error O(h^4)
-            grad[fidx[a]] = (8.0 * (f[0] - f[1]) - (f[2] - f[3])) / (12.0 * h);
-            if (hdiag) hdiag[fidx[a]] = (16.0 * (f[0] + f[1]) - (f[2] + f[3]) - 30.0 * vals[0]) / (12.0 * h * h);
-        } else {
-            grad[fidx[a]] = (f[0] - f[1]) / (2.0 * h);
-            if (hdiag) hdiag[fidx[a]] = (f[0] - 2.0 * vals[0] + f[1]) / (h * h);
+    std::vector<int> todo(nf);
+    for (int a = 0; a < nf; ++a) todo[a] = a;
+    for (int attempt = 0; attempt < 4 && !todo.empty(); ++attempt) {
+        // vector 0 is theta (first attempt); then per parameter to do +h, -h [, +2h, -2h]
+        const int first = attempt == 0 ? 1 : 0;
+        const int nv_total = first + per * (int)todo.size();
+        std::vector<double> vecs((size_t)nv_total * P), vals(nv_total);
+        for (int v = 0; v < nv_total; ++v) memcpy(vecs.data() + (size_t)v * P, theta, sizeof(double) * P);
+        for (size_t i = 0; i < todo.size(); ++i)
+            for (int u = 0; u < per; ++u)
+                vecs[(size_t)(first + per * i + u) * P + fidx[todo[i]]] += kOffsets[u] * h_abs[todo[i]];
+        for (int v0 = 0; v0 < nv_total; v0 += cap) {
+            const int32_t nv = std::min(cap, nv_total - v0);
+            int st = musr_batch_eval(B, obj, vecs.data() + (size_t)v0 * P, &nv, vals.data() + v0);
+            if (st != MUSR_OK) return st;
         }
+        if (first) {
+            *value = vals[0];
+            if (!isfinite(vals[0])) return MUSR_EDOMAIN;
+        }
+        std::vector<int> again;
+        for (size_t i = 0; i < todo.size(); ++i) {
+            const int a = todo[i];
+            const double* f = vals.data() + first + per * i;  // f(+h), f(-h) [, f(+2h), f(-2h)]
+            bool ok = true;
+            for (int u = 0; u < per; ++u) ok = ok && isfinite(f[u]);
+            if (!ok) {
+                h_abs[a] *= 0.25;
+                again.push_back(a);
+                continue;
+            }
+            const double h = h_abs[a];
+            if (order == 4) {
+                // fourth-order central differences: truncation error O(h^4)
+                grad[fidx[a]] = (8.0 * (f[0] - f[1]) - (f[2] - f[3])) / (12.0 * h);
+                if (hdiag) hdiag[fidx[a]] = (16.0 * (f[0] + f[1]) - (f[2] + f[3]) - 30.0 * *value) / (12.0 * h * h);
+            } else {
+                grad[fidx[a]] = (f[0] - f[1]) / (2.0 * h);
+                if (hdiag) hdiag[fidx[a]] = (f[0] - 2.0 * *value + f[1]) / (h * h);
+            }
+        }
+        todo.swap(again);
     }
-    return MUSR_OK;
+    return todo.empty() ? MUSR_OK : MUSR_EDOMAIN;
 }
 
 }  // namespace musr

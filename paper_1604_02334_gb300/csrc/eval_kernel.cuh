@@ -29,7 +29,7 @@
 //   * every block stages its histogram's constants itself, with few FP64
 //     instructions: double-float FP32 pairs where precision matters and
 //     integer fixed point for phases, spread over several warps so the
-//     dependency chains overlap (and with the first data loads in flight);
+//     dependency chains overlap (with the first data loads in flight);
 //   * the lifetime factor exp(-t/tau), which multiplies every bin, is seeded
 //     per chunk from a per-run table rounded once from FP64, so no coherent
 //     bias enters N (the gradient sums cancel ~100-fold and would amplify it);
@@ -280,26 +280,6 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
             const DF t0 = df_of(rc.t0);
             const DF x = df_add(df_mul(t0, it), df_mul(df_mul(s2, t0), DF{0.5f * t0.hi, 0.5f * t0.lo}));
             hc.kt_cenv = expf(-x.hi);
-        }
-    }
-}
-
-// Block-wide copy of n elements from global (L2) to shared memory with eight
-// loads in flight per thread: a plain loop would wait one L2 round trip per
-// element before issuing the next load.
-template <class T>
-__device__ __forceinline__ void copy_to_smem(T* dst, const T* src, int n) {
-    for (int base = threadIdx.x; base < n; base += 8 * blockDim.x) {
-        T v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = base + u * blockDim.x;
-            if (i < n) v[u] = __ldcg(src + i);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int i = base + u * blockDim.x;
-            if (i < n) dst[i] = v[u];
         }
     }
 }
@@ -1100,19 +1080,9 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     }
 
     // stage histogram k's constants: one part per warp, so the parts' latency
-    // chains overlap (theta is inline in the launch parameters for host calls);
-    // warps not staging preload the tail's CSR (only the last block will read
-    // it, but no block knows yet whether it is last)
-    __int128* hsum = p.hsum_in_smem ? reinterpret_cast<__int128*>(dyn_smem) : p.hist_sum;
-    int32_t* tbl = reinterpret_cast<int32_t*>(dyn_smem + (p.hsum_in_smem ? sizeof(__int128) * p.K * NACC : 0));
+    // chains overlap (theta is inline in the launch parameters for host calls)
     {
         constexpr int NPART = stage_parts<NE, NG, NS, KT>();
-        if (MODE != kModel && p.preload && (int)threadIdx.x >= 32 * NPART) {
-            const int n1 = p.n_out + 1, n2 = p.n_src;
-            const int stride = (int)blockDim.x - 32 * NPART;
-            for (int i = (int)threadIdx.x - 32 * NPART; i < n1 + n2; i += stride)
-                tbl[i] = i < n1 ? p.csr_ptr[i] : p.csr_src[i - n1];
-        }
         const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
         const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
@@ -1229,39 +1199,40 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     if (!s_last) return;
 
     // ---- last block: per-histogram integer totals (their limbs zeroed for the
-    // next launch), then theta via the CSR map, summed as integers; every load
-    // of the tail is issued before any result is needed ----
+    // next launch), then theta via the CSR map, summed as integers.  The CSR
+    // (into shared memory, when it fits) and the limbs come in batches of up
+    // to four elements a thread with the whole batch in flight: one L2 round
+    // trip for the common sizes ----
     const unsigned fl = *reinterpret_cast<volatile unsigned*>(p.flags);
-    const int32_t* cptr = p.preload ? tbl : p.csr_ptr;
-    const int32_t* csrc = p.preload ? tbl + p.n_out + 1 : p.csr_src;
-    if (!p.preload && p.csr_in_smem) {
-        copy_to_smem(tbl, p.csr_ptr, p.n_out + 1);
-        copy_to_smem(tbl + p.n_out + 1, p.csr_src, p.n_src);
-        cptr = tbl;
-        csrc = tbl + p.n_out + 1;
-    }
+    __int128* hsum = p.hsum_in_smem ? reinterpret_cast<__int128*>(dyn_smem) : p.hist_sum;
+    int32_t* tbl = reinterpret_cast<int32_t*>(dyn_smem + (p.hsum_in_smem ? sizeof(__int128) * p.K * NACC : 0));
+    const int n1 = p.n_out + 1;
+    const int32_t* cptr = p.csr_in_smem ? tbl : p.csr_ptr;
+    const int32_t* csrc = p.csr_in_smem ? tbl + n1 : p.csr_src;
     {
-        // up to four totals a thread with every load in flight before any store
         const int n_tot = p.K * NACC;
-        unsigned long long lv[4][3];
+        const int n_csr = p.csr_in_smem ? n1 + p.n_src : 0;
+        const int n_max = max(n_tot, n_csr);
+        for (int base = threadIdx.x; base < n_max; base += 4 * blockDim.x) {
+            int32_t cv[4];
+            unsigned long long lv[4][3];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = threadIdx.x + u * blockDim.x;
-            if (i < n_tot) {
-                const unsigned long long* l = p.facc + (size_t)i * 3;
-                lv[u][0] = __ldcg(l);
-                lv[u][1] = __ldcg(l + 1);
-                lv[u][2] = __ldcg(l + 2);
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + u * blockDim.x;
+                if (i < n_csr) cv[u] = __ldcg(i < n1 ? p.csr_ptr + i : p.csr_src + (i - n1));
+                if (i < n_tot) {
+                    const unsigned long long* l = p.facc + (size_t)i * 3;
+                    lv[u][0] = __ldcg(l);
+                    lv[u][1] = __ldcg(l + 1);
+                    lv[u][2] = __ldcg(l + 2);
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = threadIdx.x + u * blockDim.x;
-            if (i < n_tot) hsum[i] = fix_total(lv[u][0], lv[u][1], lv[u][2]);
-        }
-        for (int i = threadIdx.x + 4 * blockDim.x; i < n_tot; i += blockDim.x) {
-            const unsigned long long* l = p.facc + (size_t)i * 3;
-            hsum[i] = fix_total(__ldcg(l), __ldcg(l + 1), __ldcg(l + 2));
+            for (int u = 0; u < 4; ++u) {
+                const int i = base + u * blockDim.x;
+                if (i < n_csr) tbl[i] = cv[u];
+                if (i < n_tot) hsum[i] = fix_total(lv[u][0], lv[u][1], lv[u][2]);
+            }
         }
     }
     __syncthreads();

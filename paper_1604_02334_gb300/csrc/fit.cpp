@@ -31,8 +31,8 @@ musr_run gbatch_run(musr_gbatch b, int r);
 // Central differences of the objective along every free parameter fidx[a]
 // with absolute steps h_abs[a] (order 2: +-h; order 4: +-h, +-2h), in one
 // batched launch (batch.cu); hdiag (or NULL) receives the second differences.
-int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx,
-                      const double* h_abs, int order, double* value, double* grad, double* hdiag);
+int batch_fd_gradient(musr_run run, int obj, const double* theta, const std::vector<int>& fidx, double* h_abs,
+                      int order, double* value, double* grad, double* hdiag);
 }
 
 using namespace musr;
@@ -148,12 +148,15 @@ constexpr double kEdmResolution = 10.0;
 // Central-difference fits with automatic steps: fourth-order differences
 // with a step of kFdStepSigma standard errors along each free parameter (from
 // second differences at the start).  The FP32 value noise enters the gradient
-// divided by the step, so the step must be of the parameter's own scale, and
-// at that scale second-order differences would carry a truncation error of
-// ~1e-3 of the errors on correlated, curved directions; fourth-order ones
-// do not.  They stop after kFdStallSteps successive accepted steps that each
-// move every free parameter by less than kFdStallSigma of its standard error.
-constexpr double kFdStepSigma = 1.0;
+// divided by the step (a parameter's distance to the minimum is ~ noise /
+// (2 kFdStepSigma) of its error, noise = the value's rounding noise), so the
+// step must be of the parameter's own scale or larger; at that scale
+// second-order differences would carry a truncation error of ~1e-3 of the
+// errors on correlated, curved directions, fourth-order ones ~(h / L)^4 with
+// the curvature length L ~ 30 errors.  They stop after kFdStallSteps
+// successive accepted steps that each move every free parameter by less
+// than kFdStallSigma of its standard error.
+constexpr double kFdStepSigma = 2.0;
 constexpr double kFdStallSigma = 1e-4;
 constexpr int kFdStallSteps = 3;
 

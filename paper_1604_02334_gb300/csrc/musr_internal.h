@@ -175,7 +175,6 @@ struct EvalParams {
     int n_out;
     int n_src;                    // csr_src length
     int hsum_in_smem, csr_in_smem;
-    int preload;                  // 1: every block preloads the tail's CSR
     int smem_bytes;               // dynamic shared memory of the objective kernel
     double* out;                  // [n_out]
     int32_t* status_out;          // [1] or null

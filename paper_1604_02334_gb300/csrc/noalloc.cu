@@ -273,7 +273,6 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.hist_sum = reinterpret_cast<__int128*>(base + o_hsum);
     p.global_count = reinterpret_cast<unsigned*>(base + o_cnt);
     p.flags = reinterpret_cast<unsigned*>(base + o_cnt) + 1;
-    p.preload = 0;
     p.csr_ptr = reinterpret_cast<const int32_t*>(base + o_cp);
     p.csr_src = reinterpret_cast<const int32_t*>(base + o_cs);
     p.n_out = pl.n_out;

@@ -578,9 +578,6 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.n_src = n_src[m];
     p.hsum_in_smem = hsum_in_smem[m];
     p.csr_in_smem = csr_in_smem[m];
-    // a small CSR is preloaded by every block (overlapping its staging)
-    p.preload = mode != kModel && csr_in_smem[m] && (n_out[m] + 1 + n_src[m]) <= 1024 &&
-                T.threads > 32 * (2 + 2 * sig.n_osc());  // warps beyond the staging ones exist
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
     // equal-length histograms: tiles and offsets by arithmetic (see EvalParams)
     if (T.uni_tph > 0 && n_bins[0] + kBinsPerThread * (int64_t)T.threads < (int64_t)1 << 30) {
