@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchParams p)
             const int32_t* rt = R.role_theta + (size_t)k * kMaxRoles * 2;
             for (int q = threadIdx.x; q < V * NPART; q += blockDim.x) {
                 const int v = q / NPART, part = q % NPART;
-                stage_part<NE, NG, NS, KT>(part, rt, p.thetas + R.theta_off + (int64_t)v * R.P, R.rc, hcs[v]);
+                stage_part<NE, NG, NS, KT>(part, ThetaByRow{rt, p.thetas + R.theta_off + (int64_t)v * R.P}, R.rc, hcs[v]);
             }
         }
         for (int v = threadIdx.x; v < V; v += blockDim.x)

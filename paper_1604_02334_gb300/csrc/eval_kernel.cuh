@@ -69,13 +69,26 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
+// The theta entries of a histogram's roles, slot 2 r + j (j = 0, 1) of role
+// r, 0 where the map row has no entry: read through the row from theta ...
+struct ThetaByRow {
+    const int32_t* rt;
+    const double* theta;
+    __device__ __forceinline__ double operator()(int slot) const {
+        const int i = rt[slot];
+        return i >= 0 ? theta[i] : 0.0;
+    }
+};
+// ... or gathered beforehand (into shared memory).
+struct ThetaGathered {
+    const double* v;
+    __device__ __forceinline__ double operator()(int slot) const { return v[slot]; }
+};
+
 // Sum of the (up to two) theta entries a role reads (at most one FP64 add).
-__device__ __forceinline__ double role_value(const int32_t* rt, const double* theta, int r) {
-    const int i0 = rt[2 * r], i1 = rt[2 * r + 1];
-    double v = 0.0;
-    if (i0 >= 0) v += theta[i0];
-    if (i1 >= 0) v += theta[i1];
-    return v;
+template <class TH>
+__device__ __forceinline__ double role_value(const TH& th, int r) {
+    return th(2 * r) + th(2 * r + 1);
 }
 
 // ---- double-float (hi + lo) arithmetic on the FP32 pipe (Knuth TwoSum,
@@ -181,16 +194,15 @@ __host__ __device__ constexpr int stage_parts() {
 
 // stripe > 0: bins between a thread's consecutive chunks (for the Gaussian
 // ratio carried from chunk to chunk, see GqCarry); 0 when nothing is carried.
-template <int NE, int NG, int NS, int KT>
-__device__ void stage_part(int part, const int32_t* rt, const double* theta, const RunConst& rc,
-                           HistConst& hc, int stripe = 0) {
+template <int NE, int NG, int NS, int KT, class TH>
+__device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst& hc, int stripe = 0) {
     constexpr int NOSC = NE + NG + NS;
     const DF it = df_of(rc.inv_tau), dtL = df_of(rc.dt_log2e), dt = df_of(rc.dt);
     if (part == 0) {
-        const DF n0 = df_from(role_value(rt, theta, 0));
+        const DF n0 = df_from(role_value(th, 0));
         hc.n0 = n0.hi;
         hc.n0_lo = n0.lo;
-        hc.bkg = __double2float_rn(role_value(rt, theta, 1));
+        hc.bkg = __double2float_rn(role_value(th, 1));
         hc.qE = rc.qE;
         hc.qE2 = rc.qE * (2.f + rc.qE);
         hc.kfreq = rc.kfreq;
@@ -199,11 +211,11 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
         const int r = 2 + 4 * c;
         OscConst& o = hc.osc[c];
         if (part & 1) {  // envelope
-            const DF rate = df_from(role_value(rt, theta, r + 1));
-            o.amp = __double2float_rn(role_value(rt, theta, r));
+            const DF rate = df_from(role_value(th, r + 1));
+            o.amp = __double2float_rn(role_value(th, r));
             o.rate = rate.hi;
             if (c >= NE + NG) {  // exp(-(lambda t)^beta), evaluated per bin; the rotation alone is stepped
-                o.beta = __double2float_rn(role_value(rt, theta, 2 + 4 * NOSC));
+                o.beta = __double2float_rn(role_value(th, 2 + 4 * NOSC));
                 o.a_hi = o.a_lo = o.b_hi = o.b_lo = o.q = o.qs = o.q2 = o.qs2 = 0.f;
                 o.cenv = 1.f;
             } else if (c < NE) {  // exp(-(1/tau + lambda) t)
@@ -237,17 +249,11 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
                 }
             }
         } else {  // phase: sums of fixed-point products are exact mod 1 turn
-            const int i0 = rt[2 * (r + 2)], i1 = rt[2 * (r + 2) + 1], ip = rt[2 * (r + 3)];
-            unsigned long long step = 0ull, ph0 = 0ull;
-            if (i0 >= 0) {
-                step += fixmul(theta[i0], rc.turns_per_bin);
-                if (!rc.t0_zero) ph0 += fixmul(theta[i0], rc.turns_at_t0);
-            }
-            if (i1 >= 0) {
-                step += fixmul(theta[i1], rc.turns_per_bin);
-                if (!rc.t0_zero) ph0 += fixmul(theta[i1], rc.turns_at_t0);
-            }
-            if (ip >= 0) ph0 += fixmul(theta[ip], rc.inv_two_pi);
+            // an absent entry reads 0, whose fixed-point product is 0
+            const double f0 = th(2 * (r + 2)), f1 = th(2 * (r + 2) + 1), phi = th(2 * (r + 3));
+            unsigned long long step = fixmul(f0, rc.turns_per_bin) + fixmul(f1, rc.turns_per_bin);
+            unsigned long long ph0 = fixmul(phi, rc.inv_two_pi);
+            if (!rc.t0_zero) ph0 += fixmul(f0, rc.turns_at_t0) + fixmul(f1, rc.turns_at_t0);
             o.ph0 = ph0;
             o.step = step;
             o.step_s = step * (unsigned long long)stripe;  // mod 2^64: whole turns drop out
@@ -260,9 +266,9 @@ __device__ void stage_part(int part, const int32_t* rt, const double* theta, con
         }
     } else if (KT && part == 2 * NOSC + 1) {
         const int r = 2 + 4 * NOSC + NS;
-        const DF dl = df_from(role_value(rt, theta, r + 1));
+        const DF dl = df_from(role_value(th, r + 1));
         const DF s2 = df_mul(dl, dl);
-        hc.kt_amp = __double2float_rn(role_value(rt, theta, r));
+        hc.kt_amp = __double2float_rn(role_value(th, r));
         hc.kt_rate = dl.hi;
         const DF a = df_add(df_mul(it, dtL), df_mul(s2, df_of(rc.t0_dt_log2e)));
         const DF b = df_mul(s2, df_of(rc.half_dt2_log2e));
@@ -1064,8 +1070,19 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     const int stripe = (int)blockDim.x * G;
     int n0 = tstart + (int)threadIdx.x * G;
 
-    // issue the first chunk's loads (counts and the lifetime factor at its
-    // start) so their latency overlaps the staging
+    // the histogram's theta entries (one per role slot, warp 0) come first,
+    // alone: queued behind the block's data loads their round trip doubled.
+    // theta is inline in the launch parameters for host calls
+    __shared__ double s_th[2 * kMaxRoles];
+    if (threadIdx.x < 2 * kMaxRoles) {
+        const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
+        const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
+        s_th[threadIdx.x] = ThetaByRow{rt, theta}((int)threadIdx.x);
+    }
+    __syncthreads();
+
+    // then the first chunk's loads (counts and the lifetime factor at its
+    // start), whose latency overlaps the staging arithmetic
     float d[G];
     float E0 = 0.f;
     if (n0 < tend) E0 = __ldg(p.etab + (n0 >> 3));
@@ -1080,13 +1097,11 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     }
 
     // stage histogram k's constants: one part per warp, so the parts' latency
-    // chains overlap (theta is inline in the launch parameters for host calls)
+    // chains overlap
     {
         constexpr int NPART = stage_parts<NE, NG, NS, KT>();
-        const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
-        const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
-            if (lane == 0) stage_part<NE, NG, NS, KT>(part, rt, theta, p.rc, hc, (int)blockDim.x * G);
+            if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaGathered{s_th}, p.rc, hc, (int)blockDim.x * G);
     }
     __syncthreads();
 
@@ -1185,15 +1200,15 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         }
         if (flag) atomicOr(p.flags, flag);
     }
-    // the barrier orders every thread's adds before thread 0's fence (fences
-    // are cumulative), which orders them before its ticket; the last block's
-    // thread 0 fences again before the block reads what the others added
+    // the barrier orders every thread's adds before thread 0's ticket, a
+    // release (cumulative: it publishes what the barrier made thread 0
+    // observe) and, for the last block, an acquire of every other block's
+    // adds, which the second barrier passes on to the whole block
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(p.global_count, 1u);
+        unsigned prev;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(p.global_count) : "memory");
         s_last = (prev == gridDim.x - 1u);
-        if (s_last) __threadfence();
     }
     __syncthreads();
     if (!s_last) return;
@@ -1236,16 +1251,35 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         }
     }
     __syncthreads();
+    // every block has taken its ticket and set its flags, and every thread
+    // here has read the flags (the barrier performs its load): reset both for
+    // the next launch, and the limbs
+    if (threadIdx.x == 0) {
+        *p.global_count = 0u;
+        *p.flags = 0u;
+    }
     for (int i = threadIdx.x; i < p.K * NACC * 3; i += blockDim.x) p.facc[i] = 0ull;
     const bool overflow = (fl & 2u) != 0u;
     double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
     for (int o = threadIdx.x; o < p.n_out; o += blockDim.x) {
-        __int128 X = 0;
+        // integer sums are exact in any order: sixteen sources a step with all
+        // their loads in flight, into two accumulators
+        __int128 X0 = 0, X1 = 0;
+        int j = cptr[o];
         const int e = cptr[o + 1];
-#pragma unroll 4
-        for (int j = cptr[o]; j < e; ++j) X += hsum[csrc[j]];
+        for (; j + 16 <= e; j += 16) {
+            int32_t idx[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) idx[u] = csrc[j + u];
+#pragma unroll
+            for (int u = 0; u < 16; u += 2) {
+                X0 += hsum[idx[u]];
+                X1 += hsum[idx[u + 1]];
+            }
+        }
+        for (; j < e; ++j) X0 += hsum[csrc[j]];
         // NaN when a warp total was not representable (not finite, or >= 2^72)
-        const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll) : fix_to_double(X);
+        const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll) : fix_to_double(X0 + X1);
         p.out[o] = v;
         if (o == 0) out0 = v;
     }
@@ -1253,8 +1287,6 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     if (p.status_sys_fence) __threadfence_system();
     __syncthreads();
     if (threadIdx.x == 0) {
-        *p.global_count = 0u;
-        *p.flags = 0u;  // every block's flags arrived before its ticket
         unsigned f = fl & 1u;
         if (!isfinite(out0)) f |= 2u;
         if (p.status_out) {

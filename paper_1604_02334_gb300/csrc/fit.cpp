@@ -39,62 +39,86 @@ using namespace musr;
 
 namespace {
 
-// Cholesky factor A = L L^T of an n x n SPD matrix in place (L in the lower
-// triangle); false if A is not positive definite.
+// Dot product of x[0..m) and y[0..m) with four independent partial sums (the
+// multiply-add chains of a plain loop would wait on one another).
+inline double dot4(const double* x, const double* y, int m) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 4 <= m; k += 4) {
+        s0 += x[k] * y[k];
+        s1 += x[k + 1] * y[k + 1];
+        s2 += x[k + 2] * y[k + 2];
+        s3 += x[k + 3] * y[k + 3];
+    }
+    for (; k < m; ++k) s0 += x[k] * y[k];
+    return (s0 + s1) + (s2 + s3);
+}
+
+// Cholesky factor A = L L^T of an n x n SPD matrix in place (row-major; L in
+// the lower triangle, the strict upper triangle is left as it was); false if A
+// is not positive definite.  Right-looking: once column j is scaled, every
+// later row is updated by a contiguous multiply-add over its lower part (no
+// reduction chains, so the loops vectorise).
 bool cholesky_factor(std::vector<double>& A, int n) {
+    std::vector<double> c(n);
     for (int j = 0; j < n; ++j) {
-        double s = A[j * n + j];
-        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
+        double* Aj = A.data() + (size_t)j * n;
+        const double s = Aj[j];
         if (!(s > 0.0)) return false;
-        const double l = sqrt(s);
-        A[j * n + j] = l;
+        const double l = sqrt(s), il = 1.0 / l;
+        Aj[j] = l;
+        for (int k = j + 1; k < n; ++k) c[k] = (A[(size_t)k * n + j] *= il);
         for (int i = j + 1; i < n; ++i) {
-            double v = A[i * n + j];
-            for (int k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
-            A[i * n + j] = v / l;
+            double* Ai = A.data() + (size_t)i * n;
+            const double f = c[i];
+            for (int k = j + 1; k <= i; ++k) Ai[k] -= f * c[k];
         }
     }
     return true;
 }
 
-// Solve L L^T x = b with the factor of cholesky_factor (b overwritten).
+// Solve L L^T x = b with the factor of cholesky_factor (b overwritten):
+// forward by row dot products, backward by column updates.
 void cholesky_back(const std::vector<double>& A, std::vector<double>& b, int n) {
+    for (int i = 0; i < n; ++i) b[i] = (b[i] - dot4(A.data() + (size_t)i * n, b.data(), i)) / A[(size_t)i * n + i];
+    for (int i = n - 1; i >= 0; --i) {
+        const double xi = (b[i] /= A[(size_t)i * n + i]);
+        const double* Ai = A.data() + (size_t)i * n;
+        for (int k = 0; k < i; ++k) b[k] -= Ai[k] * xi;
+    }
+}
+
+// Solve L L^T X = B for the n x m right-hand sides B (row-major, n rows of m)
+// with the factor of cholesky_factor: every step updates whole rows of B.
+void cholesky_back_rows(const std::vector<double>& A, std::vector<double>& B, int n, int m) {
     for (int i = 0; i < n; ++i) {
-        double v = b[i];
-        for (int k = 0; k < i; ++k) v -= A[i * n + k] * b[k];
-        b[i] = v / A[i * n + i];
+        double* Bi = B.data() + (size_t)i * m;
+        const double* Ai = A.data() + (size_t)i * n;
+        for (int k = 0; k < i; ++k) {
+            const double f = Ai[k];
+            const double* Bk = B.data() + (size_t)k * m;
+            for (int c = 0; c < m; ++c) Bi[c] -= f * Bk[c];
+        }
+        const double il = 1.0 / Ai[i];
+        for (int c = 0; c < m; ++c) Bi[c] *= il;
     }
     for (int i = n - 1; i >= 0; --i) {
-        double v = b[i];
-        for (int k = i + 1; k < n; ++k) v -= A[k * n + i] * b[k];
-        b[i] = v / A[i * n + i];
+        double* Bi = B.data() + (size_t)i * m;
+        const double il = 1.0 / A[(size_t)i * n + i];
+        for (int c = 0; c < m; ++c) Bi[c] *= il;
+        const double* Ai = A.data() + (size_t)i * n;
+        for (int k = 0; k < i; ++k) {
+            const double f = Ai[k];
+            double* Bk = B.data() + (size_t)k * m;
+            for (int c = 0; c < m; ++c) Bk[c] -= f * Bi[c];
+        }
     }
 }
 
 // Cholesky solve of the n x n SPD system A x = b (A overwritten).
 bool cholesky_solve(std::vector<double>& A, std::vector<double>& b, int n) {
-    for (int j = 0; j < n; ++j) {
-        double s = A[j * n + j];
-        for (int k = 0; k < j; ++k) s -= A[j * n + k] * A[j * n + k];
-        if (!(s > 0.0)) return false;
-        const double l = sqrt(s);
-        A[j * n + j] = l;
-        for (int i = j + 1; i < n; ++i) {
-            double v = A[i * n + j];
-            for (int k = 0; k < j; ++k) v -= A[i * n + k] * A[j * n + k];
-            A[i * n + j] = v / l;
-        }
-    }
-    for (int i = 0; i < n; ++i) {
-        double v = b[i];
-        for (int k = 0; k < i; ++k) v -= A[i * n + k] * b[k];
-        b[i] = v / A[i * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {
-        double v = b[i];
-        for (int k = i + 1; k < n; ++k) v -= A[k * n + i] * b[k];
-        b[i] = v / A[i * n + i];
-    }
+    if (!cholesky_factor(A, n)) return false;
+    cholesky_back(A, b, n);
     return true;
 }
 
@@ -275,15 +299,15 @@ struct LmStepper {
         out->mu = mu;
         out->iters = it;
         if (out->cov) {
-            // covariance 2 H^-1 over the free block: one factorisation, nf solves
+            // covariance 2 H^-1 over the free block: one factorisation, the nf
+            // right-hand sides of 2 I solved together
             for (int a = 0; a < nf; ++a)
                 for (int e = 0; e < nf; ++e) A[(size_t)a * nf + e] = H[(size_t)fidx[a] * P + fidx[e]];
             const bool ok = cholesky_factor(A, nf);
-            for (int c = 0; c < nf; ++c) {
-                for (int a = 0; a < nf; ++a) b[a] = a == c ? 2.0 : 0.0;
-                if (ok) cholesky_back(A, b, nf);
-                for (int a = 0; a < nf; ++a) out->cov[(size_t)a * nf + c] = ok ? b[a] : NAN;
-            }
+            std::vector<double> X((size_t)nf * nf, 0.0);
+            for (int a = 0; a < nf; ++a) X[(size_t)a * nf + a] = 2.0;
+            if (ok) cholesky_back_rows(A, X, nf, nf);
+            for (size_t q = 0; q < X.size(); ++q) out->cov[q] = ok ? X[q] : NAN;
         }
     }
 };

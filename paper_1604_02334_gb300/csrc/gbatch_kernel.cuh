@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
             const int32_t* rt = Rr.role_theta + (size_t)k * kMaxRoles * 2;
             const double* theta = p.thetas + Rr.theta_off;
             for (int part = warp; part < NPART; part += nwarps)
-                if (lane == 0) stage_part<NE, NG, NS, KT>(part, rt, theta, Rr.rc, hc, stripe);
+                if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaByRow{rt, theta}, Rr.rc, hc, stripe);
         }
         __syncthreads();
 
