@@ -39,8 +39,8 @@ struct GPlan {
     int blocks = 0, n_items = 0;
     void* arena = nullptr;
     GRunRef* d_runs = nullptr;
-    GItem* d_items = nullptr;
-    int32_t *d_block_ptr = nullptr, *d_block_items = nullptr, *d_run_items = nullptr;
+    GWork* d_works = nullptr;
+    int32_t *d_block_ptr = nullptr, *d_run_items = nullptr;
     int32_t *d_hist_item_ptr = nullptr, *d_run_nitems = nullptr;
     double* d_partial = nullptr;
     unsigned *d_run_count = nullptr, *d_flags = nullptr;
@@ -151,10 +151,31 @@ int musr_gbatch_s::make_plan(int mode, const GShape& sh) {
         assign[l.second].push_back(i);
         heap.push({l.first + 1.0 + (double)items[i].rows, l.second});  // + staging cost of one row
     }
-    std::vector<int32_t> block_ptr(pl.blocks + 1, 0), block_items;
+    // the items as the blocks take them: one self-contained descriptor each
+    std::vector<int32_t> block_ptr(pl.blocks + 1, 0);
+    std::vector<GWork> works;
+    works.reserve(items.size());
     for (int b = 0; b < pl.blocks; ++b) {
-        block_items.insert(block_items.end(), assign[b].begin(), assign[b].end());
-        block_ptr[b + 1] = (int32_t)block_items.size();
+        for (int32_t i : assign[b]) {
+            const GItem& it = items[i];
+            const musr_run_s* run = runs[it.run];
+            GWork w;
+            memset(&w, 0, sizeof(w));
+            w.rc = run->rc;
+            w.hdata = run->d_data + run->hist_off[it.hist];
+            w.etab = run->d_etab;
+            w.theta_off = theta_off[it.run];
+            w.item = i;
+            w.run = it.run;
+            w.start = it.start;
+            w.rows = it.rows;
+            w.M = (int32_t)run->n_bins[it.hist];
+            w.dtf = (float)run->dt;
+            w.t0f = (float)run->t0;
+            memcpy(w.rt, run->role_theta.data() + (size_t)it.hist * kMaxRoles * 2, sizeof(w.rt));
+            works.push_back(w);
+        }
+        block_ptr[b + 1] = (int32_t)works.size();
     }
     const int nacc = nacc_of(mode, R);
     size_t sz = 0;
@@ -163,8 +184,8 @@ int musr_gbatch_s::make_plan(int mode, const GShape& sh) {
         sz += al256(bytes);
         return at;
     };
-    const size_t o_runs = take(sizeof(GRunRef) * refs.size()), o_items = take(sizeof(GItem) * items.size());
-    const size_t o_bp = take(sizeof(int32_t) * block_ptr.size()), o_bi = take(sizeof(int32_t) * block_items.size());
+    const size_t o_runs = take(sizeof(GRunRef) * refs.size()), o_works = take(sizeof(GWork) * works.size());
+    const size_t o_bp = take(sizeof(int32_t) * block_ptr.size());
     const size_t o_ri = take(sizeof(int32_t) * run_items.size()), o_hp = take(sizeof(int32_t) * hist_item_ptr.size());
     const size_t o_rn = take(sizeof(int32_t) * run_nitems.size());
     const size_t o_part = take(sizeof(double) * (size_t)pl.n_items * nacc);
@@ -175,9 +196,8 @@ int musr_gbatch_s::make_plan(int mode, const GShape& sh) {
     }
     char* a = static_cast<char*>(pl.arena);
     pl.d_runs = reinterpret_cast<GRunRef*>(a + o_runs);
-    pl.d_items = reinterpret_cast<GItem*>(a + o_items);
+    pl.d_works = reinterpret_cast<GWork*>(a + o_works);
     pl.d_block_ptr = reinterpret_cast<int32_t*>(a + o_bp);
-    pl.d_block_items = reinterpret_cast<int32_t*>(a + o_bi);
     pl.d_run_items = reinterpret_cast<int32_t*>(a + o_ri);
     pl.d_hist_item_ptr = reinterpret_cast<int32_t*>(a + o_hp);
     pl.d_run_nitems = reinterpret_cast<int32_t*>(a + o_rn);
@@ -189,9 +209,8 @@ int musr_gbatch_s::make_plan(int mode, const GShape& sh) {
         if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, stream);
     };
     up(pl.d_runs, refs.data(), sizeof(GRunRef) * refs.size());
-    up(pl.d_items, items.data(), sizeof(GItem) * items.size());
+    up(pl.d_works, works.data(), sizeof(GWork) * works.size());
     up(pl.d_block_ptr, block_ptr.data(), sizeof(int32_t) * block_ptr.size());
-    up(pl.d_block_items, block_items.data(), sizeof(int32_t) * block_items.size());
     up(pl.d_run_items, run_items.data(), sizeof(int32_t) * run_items.size());
     up(pl.d_hist_item_ptr, hist_item_ptr.data(), sizeof(int32_t) * hist_item_ptr.size());
     up(pl.d_run_nitems, run_nitems.data(), sizeof(int32_t) * run_nitems.size());
@@ -205,9 +224,8 @@ GParams musr_gbatch_s::params(int mode, int obj, const double* thetas, const uin
     GParams p;
     memset(&p, 0, sizeof(p));
     p.runs = pl.d_runs;
-    p.items = pl.d_items;
+    p.works = pl.d_works;
     p.block_ptr = pl.d_block_ptr;
-    p.block_items = pl.d_block_items;
     p.run_items = pl.d_run_items;
     p.hist_item_ptr = pl.d_hist_item_ptr;
     p.run_nitems = pl.d_run_nitems;

@@ -48,11 +48,25 @@ struct GItem {
     int32_t run, hist, start, rows;
 };
 
+// One item as the kernel takes it, in each block's schedule order: everything
+// its staging and rows need, so a block fetches an item with one contiguous
+// copy (issued while the previous item is evaluated) instead of a chain of
+// dependent loads through the run tables.
+struct __align__(16) GWork {
+    RunConst rc;
+    const float* hdata;  // the histogram's counts
+    const float* etab;   // the run's lifetime table
+    int64_t theta_off;   // the run's parameter vector in the launch's thetas
+    int32_t item, run, start, rows, M;
+    float dtf, t0f;
+    int32_t rt[2 * kMaxRoles];  // the histogram's role -> theta row
+};
+static_assert(sizeof(GWork) % 16 == 0, "GWork is copied in 16-byte pieces");
+
 struct GParams {
     const GRunRef* runs;
-    const GItem* items;
+    const GWork* works;  // by block: works[block_ptr[b] .. block_ptr[b + 1])
     const int32_t* block_ptr;
-    const int32_t* block_items;
     const int32_t* run_items;      // per run, its items by (histogram, first bin)
     const int32_t* hist_item_ptr;  // per run, K + 1 offsets into run_items
     const int32_t* run_nitems;
@@ -65,6 +79,18 @@ struct GParams {
     double* out;
     int32_t* status;  // per run
 };
+
+// Asynchronous global -> shared copies (completed by cp_async_wait_all in the
+// issuing thread; other threads see the data after a barrier that follows).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <int NE, int NG, int NS, int KT, int MODE>
 __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_kernel(const __grid_constant__ GParams p) {
@@ -82,21 +108,55 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
     const int nwarps = blockDim.x >> 5;
     const int stripe = blockDim.x * G;
 
-    for (int it = p.block_ptr[blockIdx.x]; it < p.block_ptr[blockIdx.x + 1]; ++it) {
-        const int item_idx = p.block_items[it];
-        const GItem item = p.items[item_idx];
-        if (p.active && !p.active[item.run]) continue;  // uniform over the block
-        const GRunRef& Rr = p.runs[item.run];
-        const int k = item.hist;
-        const int M = Rr.hist_nbins[k];
-        const float* hdata = Rr.data + Rr.hist_off[k];
-        int n0 = item.start + (int)threadIdx.x * G;
+    // item pipeline: wk / wth / wact hold item j's descriptor, theta entries
+    // and active flag in buffer (j - w0) & 1; item j + 1's descriptor is
+    // copied while item j's rows run, its theta entries while item j reduces
+    __shared__ GWork wk[2];
+    __shared__ double wth[2][2 * kMaxRoles];
+    __shared__ int wact[2];
+    constexpr int kWorkPieces = (int)(sizeof(GWork) / 16);
+    const int w0 = p.block_ptr[blockIdx.x], w1 = p.block_ptr[blockIdx.x + 1];
+    auto fetch_work = [&](int j, int buf) {
+        if ((int)threadIdx.x < kWorkPieces)
+            cp_async16(reinterpret_cast<uint4*>(&wk[buf]) + threadIdx.x,
+                       reinterpret_cast<const uint4*>(p.works + j) + threadIdx.x);
+    };
+    // after wk[buf] is complete and visible: its theta entries and active flag
+    auto fetch_theta = [&](int buf) {
+        const int t = (int)threadIdx.x;
+        if (t < 2 * kMaxRoles) {
+            const int i = wk[buf].rt[t];
+            if (i >= 0) cp_async8(&wth[buf][t], p.thetas + wk[buf].theta_off + i);
+            else wth[buf][t] = 0.0;
+        } else if (t == 2 * kMaxRoles) {
+            wact[buf] = p.active ? (int)p.active[wk[buf].run] : 1;
+        }
+    };
+    if (w0 < w1) {
+        fetch_work(w0, 0);
+        cp_async_wait_all();
+        __syncthreads();
+        fetch_theta(0);
+        cp_async_wait_all();
+    }
+
+    for (int it = w0; it < w1; ++it) {
+        const int cur = (it - w0) & 1, nxt = cur ^ 1;
+        cp_async_wait_all();  // this thread's copies of item it's theta entries
+        __syncthreads();  // item it's buffers complete; the previous item is done with hc / red / hsum
+        const GWork& W = wk[cur];
+        const bool act = wact[cur] != 0;  // uniform over the block
+        if (it + 1 < w1) fetch_work(it + 1, nxt);
+        const int item_idx = W.item, run = W.run;
+        const int M = W.M;
+        const float* hdata = W.hdata;
+        int n0 = W.start + (int)threadIdx.x * G;
 
         // first row's loads in flight while the constants are staged
         float d[G];
         float E0 = 0.f;
-        if (n0 < M) {
-            E0 = __ldg(Rr.etab + (n0 >> 3));
+        if (act && n0 < M) {
+            E0 = __ldg(W.etab + (n0 >> 3));
             const float4* src = reinterpret_cast<const float4*>(hdata + n0);
             const float4 a = __ldg(src), b = __ldg(src + 1);
             d[0] = a.x; d[1] = a.y; d[2] = a.z; d[3] = a.w;
@@ -105,12 +165,9 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
             for (int g = 0; g < G; ++g) d[g] = 0.f;
         }
-        __syncthreads();  // the previous item is done with hc / red / hsum
-        {
-            const int32_t* rt = Rr.role_theta + (size_t)k * kMaxRoles * 2;
-            const double* theta = p.thetas + Rr.theta_off;
+        if (act) {
             for (int part = warp; part < NPART; part += nwarps)
-                if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaByRow{rt, theta}, Rr.rc, hc, stripe);
+                if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaGathered{wth[cur]}, W.rc, hc, stripe);
         }
         __syncthreads();
 
@@ -118,22 +175,23 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
         bool bad = false;
-        const float dtf = (float)Rr.dt, t0f = (float)Rr.t0;
+        const float dtf = W.dtf, t0f = W.t0f;
+        const int rows = act ? W.rows : 0;
         {
             GqCarry<NOSC> carry;
             carry.valid = false;
             GnAcc<R> gnacc;
             gnacc.zero();
-            for (int row = 0; row < item.rows; ++row) {
+            for (int row = 0; row < rows; ++row) {
                 const int n1 = n0 + stripe;
                 float dn[G];
                 float En = 0.f;
-                if (row + 1 < item.rows && n1 < M) {
+                if (row + 1 < rows && n1 < M) {
                     const float4* src = reinterpret_cast<const float4*>(hdata + n1);
                     const float4 a = __ldg(src), b = __ldg(src + 1);
                     dn[0] = a.x; dn[1] = a.y; dn[2] = a.z; dn[3] = a.w;
                     dn[4] = b.x; dn[5] = b.y; dn[6] = b.z; dn[7] = b.w;
-                    En = __ldg(Rr.etab + (n1 >> 3));
+                    En = __ldg(W.etab + (n1 >> 3));
                 } else {
 #pragma unroll
                     for (int g = 0; g < G; ++g) dn[g] = 0.f;
@@ -148,28 +206,41 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
             }
             if constexpr (MODE == kGN) gn_scatter(gnacc, acc);
         }
+        // the next item's theta entries, once its descriptor is in (they
+        // arrive while this item reduces)
+        if (it + 1 < w1) {
+            cp_async_wait_all();
+            __syncthreads();
+            fetch_theta(nxt);
+        }
+        if (!act) continue;
         warp_sum<NACC>(acc);
         if (lane == 0) {
 #pragma unroll
             for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
         }
         const int any_bad = __syncthreads_or(bad);
-        if (threadIdx.x == 0 && any_bad) atomicOr(&p.flags[item.run], 1u);
+        if (threadIdx.x == 0 && any_bad) atomicOr(&p.flags[run], 1u);
         for (int a = threadIdx.x; a < NACC; a += blockDim.x) {
             double s = 0.0;
             for (int w = 0; w < nwarps; ++w) s += (double)red[w][a];
             // the histogram's role factor of this accumulator (see eval_chunk)
             p.partial[(size_t)item_idx * NACC + a] = a > 0 ? s * (double)acc_factor<NE, NG, NS, KT, MODE>(hc, a) : s;
         }
-        __threadfence();
+        // the barrier orders the block's partials before thread 0's ticket, a
+        // release (and, for the run's last item, an acquire of the others')
         __syncthreads();
         if (threadIdx.x == 0) {
-            const unsigned prev = atomicAdd(&p.run_count[item.run], 1u);
-            s_last = prev == (unsigned)p.run_nitems[item.run] - 1u;
+            unsigned prev;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                         : "=r"(prev)
+                         : "l"(p.run_count + run)
+                         : "memory");
+            s_last = prev == (unsigned)p.run_nitems[run] - 1u;
         }
         __syncthreads();
         if (!s_last) continue;
-        __threadfence();
+        const GRunRef& Rr = p.runs[run];
         // the run's last item: per-histogram sums in item order, then theta via the CSR
         const int32_t* hptr = p.hist_item_ptr + Rr.hist_ptr_off;
         for (int q = threadIdx.x; q < Rr.K * NACC; q += blockDim.x) {
@@ -198,10 +269,10 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            unsigned f = atomicExch(&p.flags[item.run], 0u);
+            unsigned f = atomicExch(&p.flags[run], 0u);
             if (!isfinite(out[0])) f |= 2u;
-            if (p.status) p.status[item.run] = (int32_t)f;
-            p.run_count[item.run] = 0u;
+            if (p.status) p.status[run] = (int32_t)f;
+            p.run_count[run] = 0u;
         }
     }
 }
