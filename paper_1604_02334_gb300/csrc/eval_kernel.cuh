@@ -1261,27 +1261,35 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     for (int i = threadIdx.x; i < p.K * NACC * 3; i += blockDim.x) p.facc[i] = 0ull;
     const bool overflow = (fl & 2u) != 0u;
     double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
-    for (int o = threadIdx.x; o < p.n_out; o += blockDim.x) {
-        // integer sums are exact in any order: sixteen sources a step with all
-        // their loads in flight, into two accumulators
-        __int128 X0 = 0, X1 = 0;
-        int j = cptr[o];
-        const int e = cptr[o + 1];
-        for (; j + 16 <= e; j += 16) {
-            int32_t idx[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) idx[u] = csrc[j + u];
-#pragma unroll
-            for (int u = 0; u < 16; u += 2) {
-                X0 += hsum[idx[u]];
-                X1 += hsum[idx[u + 1]];
-            }
+    // L = 1, 2 or 4 lanes an output (as many as one pass over the outputs
+    // allows), each summing every L-th of its sources (integer sums are exact
+    // in any order), their partial sums added across the L lanes
+    const int nl = (int)blockDim.x >= 4 * p.n_out ? 4 : (int)blockDim.x >= 2 * p.n_out ? 2 : 1;
+    const int lsh = nl >> 1;  // log2(nl)
+    for (int ob = 0; ob < p.n_out; ob += (int)blockDim.x >> lsh) {
+        const int o = ob + ((int)threadIdx.x >> lsh), q = (int)threadIdx.x & (nl - 1);
+        __int128 X = 0;
+        if (o < p.n_out) {
+            const int e = cptr[o + 1];
+#pragma unroll 4
+            for (int j = cptr[o] + q; j < e; j += nl) X += hsum[csrc[j]];
         }
-        for (; j < e; ++j) X0 += hsum[csrc[j]];
-        // NaN when a warp total was not representable (not finite, or >= 2^72)
-        const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll) : fix_to_double(X0 + X1);
-        p.out[o] = v;
-        if (o == 0) out0 = v;
+        unsigned long long lo = (unsigned long long)X;
+        long long hi = (long long)(X >> 64);
+        for (int m = 1; m < nl; m <<= 1) {
+            const unsigned long long lo2 = __shfl_xor_sync(0xffffffffu, lo, m);
+            const long long hi2 = __shfl_xor_sync(0xffffffffu, hi, m);
+            const unsigned long long sum = lo + lo2;
+            hi = hi + hi2 + (sum < lo ? 1ll : 0ll);
+            lo = sum;
+        }
+        if (o < p.n_out && q == 0) {
+            // NaN when a warp total was not representable (not finite, or >= 2^72)
+            const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll)
+                                      : fix_to_double(((__int128)hi << 64) | (__int128)lo);
+            p.out[o] = v;
+            if (o == 0) out0 = v;
+        }
     }
     // results in mapped host memory: visible to the host before the status that announces them
     if (p.status_sys_fence) __threadfence_system();
