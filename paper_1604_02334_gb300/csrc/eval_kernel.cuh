@@ -1246,19 +1246,25 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
             for (int u = 0; u < 4; ++u) {
                 const int i = base + u * blockDim.x;
                 if (i < n_csr) tbl[i] = cv[u];
-                if (i < n_tot) hsum[i] = fix_total(lv[u][0], lv[u][1], lv[u][2]);
+                if (i < n_tot) {
+                    hsum[i] = fix_total(lv[u][0], lv[u][1], lv[u][2]);
+                    // the limbs start from zero for the next launch
+                    unsigned long long* l = p.facc + (size_t)i * 3;
+                    l[0] = 0ull;
+                    l[1] = 0ull;
+                    l[2] = 0ull;
+                }
             }
         }
     }
     __syncthreads();
     // every block has taken its ticket and set its flags, and every thread
     // here has read the flags (the barrier performs its load): reset both for
-    // the next launch, and the limbs
+    // the next launch
     if (threadIdx.x == 0) {
         *p.global_count = 0u;
         *p.flags = 0u;
     }
-    for (int i = threadIdx.x; i < p.K * NACC * 3; i += blockDim.x) p.facc[i] = 0ull;
     const bool overflow = (fl & 2u) != 0u;
     double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
     // L = 1, 2 or 4 lanes an output (as many as one pass over the outputs
@@ -1268,8 +1274,17 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     const int lsh = nl >> 1;  // log2(nl)
     for (int ob = 0; ob < p.n_out; ob += (int)blockDim.x >> lsh) {
         const int o = ob + ((int)threadIdx.x >> lsh), q = (int)threadIdx.x & (nl - 1);
+        // Gauss-Newton entries: the map carries the sources of H[i][j], i <= j;
+        // the sum is stored at [i][j] and [j][i]
+        bool live = o < p.n_out;
+        int om = -1;
+        if (MODE == kGN && live && o > p.P) {
+            const int oh = o - 1 - p.P, i = oh / p.P, j = oh - i * p.P;
+            if (i > j) live = false;
+            else if (i < j) om = 1 + p.P + j * p.P + i;
+        }
         __int128 X = 0;
-        if (o < p.n_out) {
+        if (live) {
             const int e = cptr[o + 1];
 #pragma unroll 4
             for (int j = cptr[o] + q; j < e; j += nl) X += hsum[csrc[j]];
@@ -1283,11 +1298,12 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
             hi = hi + hi2 + (sum < lo ? 1ll : 0ll);
             lo = sum;
         }
-        if (o < p.n_out && q == 0) {
+        if (live && q == 0) {
             // NaN when a warp total was not representable (not finite, or >= 2^72)
             const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll)
                                       : fix_to_double(((__int128)hi << 64) | (__int128)lo);
             p.out[o] = v;
+            if (om >= 0) p.out[om] = v;
             if (o == 0) out0 = v;
         }
     }

@@ -262,10 +262,19 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
         __syncthreads();
         double* out = p.out + Rr.out_off;
         for (int o = threadIdx.x; o < Rr.n_out; o += blockDim.x) {
+            // Gauss-Newton entries: the map carries the sources of H[i][j],
+            // i <= j; the sum is stored at [i][j] and [j][i]
+            int om = -1;
+            if (MODE == kGN && o > Rr.P) {
+                const int oh = o - 1 - Rr.P, i = oh / Rr.P, j = oh - i * Rr.P;
+                if (i > j) continue;
+                if (i < j) om = 1 + Rr.P + j * Rr.P + i;
+            }
             double s = 0.0;
             const int e = Rr.csr_ptr[o + 1];
             for (int j = Rr.csr_ptr[o]; j < e; ++j) s += hsum[Rr.csr_src[j]];
             out[o] = s;
+            if (om >= 0) out[om] = s;
         }
         __syncthreads();
         if (threadIdx.x == 0) {

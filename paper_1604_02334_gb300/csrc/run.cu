@@ -274,6 +274,8 @@ void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int3
                     if (rt[2 * r + j] >= 0) e.push_back({1 + rt[2 * r + j], base + 1 + r});
         }
         if (mode == kGN) {
+            // H[i][j] and H[j][i] have the same sources: only entries with
+            // i <= j get them (the kernels store each sum at both places)
             int a = 1 + R;
             for (int r1 = 0; r1 < R; ++r1)
                 for (int r2 = r1; r2 < R; ++r2, ++a)
@@ -281,8 +283,8 @@ void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int3
                         for (int j2 = 0; j2 < 2; ++j2) {
                             const int i = rt[2 * r1 + j1], jj = rt[2 * r2 + j2];
                             if (i < 0 || jj < 0) continue;
-                            e.push_back({1 + Pk + (int64_t)i * Pk + jj, base + a});
-                            if (r1 != r2) e.push_back({1 + Pk + (int64_t)jj * Pk + i, base + a});
+                            if (i <= jj) e.push_back({1 + Pk + (int64_t)i * Pk + jj, base + a});
+                            if (r1 != r2 && jj <= i) e.push_back({1 + Pk + (int64_t)jj * Pk + i, base + a});
                         }
         }
     }
