@@ -1022,11 +1022,35 @@ __device__ __forceinline__ __int128 fix_total(unsigned long long l0, unsigned lo
     return (__int128)l0 + ((__int128)l1 << kFixLimbBits) + ((__int128)(long long)l2 << (2 * kFixLimbBits));
 }
 
-// X / 2^48 in FP64 (the one rounding of a sum).
+// X / 2^48 in FP64, rounded once to nearest (ties to even), assembled with
+// integer operations only: the FP64 pipe (conversions included) is narrow
+// on this GPU, and the tail converts thousands of sums at once.
+// |X| < 2^127, so the result is a normal double.
 __device__ __forceinline__ double fix_to_double(__int128 X) {
-    const long long hi = (long long)(X >> 64);
-    const unsigned long long lo = (unsigned long long)X;
-    return fma((double)hi, 65536.0, (double)lo * 3.5527136788005009e-15);  // hi 2^16 + lo 2^-48
+    if (X == 0) return 0.0;
+    const unsigned long long sign = X < 0 ? (1ull << 63) : 0ull;
+    const unsigned __int128 u = X < 0 ? (unsigned __int128)(-X) : (unsigned __int128)X;
+    const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);  // leading one
+    int e = msb - kFixFracBits;                                                     // result exponent
+    unsigned long long m;                                                           // 53-bit significand
+    if (msb <= 52) {
+        m = (unsigned long long)(u << (52 - msb));
+    } else {
+        const int sh = msb - 52;  // 1 .. 74 bits dropped
+        m = (unsigned long long)(u >> sh);
+        const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            ++m;
+            if (m >> 53) {  // carried into a new leading bit
+                m >>= 1;
+                ++e;
+            }
+        }
+    }
+    return __longlong_as_double(
+        (long long)(sign | ((unsigned long long)(e + 1023) << 52) | (m & ((1ull << 52) - 1ull))));
 }
 
 template <int NE, int NG, int NS, int KT, int MODE>
