@@ -1238,27 +1238,31 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     if (!s_last) return;
 
     // ---- last block: per-histogram integer totals (their limbs zeroed for the
-    // next launch), then theta via the CSR map, summed as integers.  The CSR
-    // (into shared memory, when it fits) and the limbs come in batches of up
-    // to four elements a thread with the whole batch in flight: one L2 round
-    // trip for the common sizes ----
+    // next launch), then theta via the map (CSR rows of sources; value and
+    // gradient: a row per output; Gauss-Newton: a row per output that has
+    // sources, whose output index the row table gives), summed as integers.
+    // The map (into shared memory, when it fits) and the limbs come in
+    // batches of up to eight elements a thread with the whole batch in flight ----
     const unsigned fl = *reinterpret_cast<volatile unsigned*>(p.flags);
     __int128* hsum = p.hsum_in_smem ? reinterpret_cast<__int128*>(dyn_smem) : p.hist_sum;
     int32_t* tbl = reinterpret_cast<int32_t*>(dyn_smem + (p.hsum_in_smem ? sizeof(__int128) * p.K * NACC : 0));
-    const int n1 = p.n_out + 1;
+    const int n_rows = p.csr_row ? p.n_rows : p.n_out;
+    const int n1 = n_rows + 1, n2 = n1 + p.n_src;
     const int32_t* cptr = p.csr_in_smem ? tbl : p.csr_ptr;
     const int32_t* csrc = p.csr_in_smem ? tbl + n1 : p.csr_src;
+    const int32_t* crow = p.csr_row ? (p.csr_in_smem ? tbl + n2 : p.csr_row) : nullptr;
     {
         const int n_tot = p.K * NACC;
-        const int n_csr = p.csr_in_smem ? n1 + p.n_src : 0;
+        const int n_csr = p.csr_in_smem ? n2 + (p.csr_row ? n_rows : 0) : 0;
         const int n_max = max(n_tot, n_csr);
-        for (int base = threadIdx.x; base < n_max; base += 4 * blockDim.x) {
-            int32_t cv[4];
-            unsigned long long lv[4][3];
+        for (int base = threadIdx.x; base < n_max; base += 8 * blockDim.x) {
+            int32_t cv[8];
+            unsigned long long lv[8][3];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const int i = base + u * blockDim.x;
-                if (i < n_csr) cv[u] = __ldcg(i < n1 ? p.csr_ptr + i : p.csr_src + (i - n1));
+                if (i < n_csr)
+                    cv[u] = __ldcg(i < n1 ? p.csr_ptr + i : i < n2 ? p.csr_src + (i - n1) : p.csr_row + (i - n2));
                 if (i < n_tot) {
                     const unsigned long long* l = p.facc + (size_t)i * 3;
                     lv[u][0] = __ldcg(l);
@@ -1267,7 +1271,7 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const int i = base + u * blockDim.x;
                 if (i < n_csr) tbl[i] = cv[u];
                 if (i < n_tot) {
@@ -1280,6 +1284,10 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
                 }
             }
         }
+        // outputs without a row are 0 (the run's own buffers already hold 0
+        // there); ordered before the rows' stores by the barrier below
+        if (p.csr_row && !p.out_zeroed)
+            for (int o = threadIdx.x; o < p.n_out; o += blockDim.x) p.out[o] = 0.0;
     }
     __syncthreads();
     // every block has taken its ticket and set its flags, and every thread
@@ -1291,27 +1299,19 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     }
     const bool overflow = (fl & 2u) != 0u;
     double out0 = 0.0;  // thread 0 keeps the objective: out may be host memory, slow to read back
-    // L = 1, 2 or 4 lanes an output (as many as one pass over the outputs
-    // allows), each summing every L-th of its sources (integer sums are exact
-    // in any order), their partial sums added across the L lanes
-    const int nl = (int)blockDim.x >= 4 * p.n_out ? 4 : (int)blockDim.x >= 2 * p.n_out ? 2 : 1;
+    // L = 1, 2 or 4 lanes a row (as many as one pass over the rows allows),
+    // each summing every L-th of its sources (integer sums are exact in any
+    // order), their partial sums added across the L lanes
+    const int nl = (int)blockDim.x >= 4 * n_rows ? 4 : (int)blockDim.x >= 2 * n_rows ? 2 : 1;
     const int lsh = nl >> 1;  // log2(nl)
-    for (int ob = 0; ob < p.n_out; ob += (int)blockDim.x >> lsh) {
-        const int o = ob + ((int)threadIdx.x >> lsh), q = (int)threadIdx.x & (nl - 1);
-        // Gauss-Newton entries: the map carries the sources of H[i][j], i <= j;
-        // the sum is stored at [i][j] and [j][i]
-        bool live = o < p.n_out;
-        int om = -1;
-        if (MODE == kGN && live && o > p.P) {
-            const int oh = o - 1 - p.P, i = oh / p.P, j = oh - i * p.P;
-            if (i > j) live = false;
-            else if (i < j) om = 1 + p.P + j * p.P + i;
-        }
+    for (int rb = 0; rb < n_rows; rb += (int)blockDim.x >> lsh) {
+        const int r = rb + ((int)threadIdx.x >> lsh), q = (int)threadIdx.x & (nl - 1);
+        const bool live = r < n_rows;
         __int128 X = 0;
         if (live) {
-            const int e = cptr[o + 1];
+            const int e = cptr[r + 1];
 #pragma unroll 4
-            for (int j = cptr[o] + q; j < e; j += nl) X += hsum[csrc[j]];
+            for (int j = cptr[r] + q; j < e; j += nl) X += hsum[csrc[j]];
         }
         unsigned long long lo = (unsigned long long)X;
         long long hi = (long long)(X >> 64);
@@ -1323,6 +1323,14 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
             lo = sum;
         }
         if (live && q == 0) {
+            const int o = crow ? crow[r] : r;
+            // Gauss-Newton entries: the rows carry H[i][j], i <= j; the sum is
+            // stored at [i][j] and [j][i]
+            int om = -1;
+            if (MODE == kGN && o > p.P) {
+                const int oh = o - 1 - p.P, i = oh / p.P, j = oh - i * p.P;
+                if (i < j) om = 1 + p.P + j * p.P + i;
+            }
             // NaN when a warp total was not representable (not finite, or >= 2^72)
             const double v = overflow ? __longlong_as_double(0x7ff8000000000000ll)
                                       : fix_to_double(((__int128)hi << 64) | (__int128)lo);

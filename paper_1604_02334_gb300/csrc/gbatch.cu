@@ -125,6 +125,8 @@ int musr_gbatch_s::make_plan(int mode, const GShape& sh) {
         Rr.role_theta = run->d_role_theta;
         Rr.csr_ptr = run->d_csr_ptr[mode];
         Rr.csr_src = run->d_csr_src[mode];
+        Rr.csr_row = run->d_csr_row[mode];
+        Rr.n_rows = run->n_rows[mode];
         Rr.rc = run->rc;
         Rr.etab = run->d_etab;
         Rr.t0 = run->t0;

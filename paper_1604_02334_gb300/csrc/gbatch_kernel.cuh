@@ -36,10 +36,11 @@ struct GRunRef {
     const int32_t* role_theta;
     const int32_t* csr_ptr;
     const int32_t* csr_src;
+    const int32_t* csr_row;  // Gauss-Newton: output index of each map row (null: row = output)
     const float* etab;  // lifetime factor at every chunk start
     RunConst rc;
     double t0, dt;
-    int32_t P, K, n_out;
+    int32_t P, K, n_out, n_rows;
     int64_t theta_off, out_off;
     int32_t hist_ptr_off;  // into hist_item_ptr: K + 1 offsets into run_items
 };
@@ -261,18 +262,25 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
         }
         __syncthreads();
         double* out = p.out + Rr.out_off;
-        for (int o = threadIdx.x; o < Rr.n_out; o += blockDim.x) {
-            // Gauss-Newton entries: the map carries the sources of H[i][j],
-            // i <= j; the sum is stored at [i][j] and [j][i]
+        if (Rr.csr_row) {
+            // outputs without a map row are 0 (the buffer's other layouts,
+            // of other modes, may have left anything there)
+            for (int o = threadIdx.x; o < Rr.n_out; o += blockDim.x) out[o] = 0.0;
+            __syncthreads();
+        }
+        const int n_rows = Rr.csr_row ? Rr.n_rows : Rr.n_out;
+        for (int r = threadIdx.x; r < n_rows; r += blockDim.x) {
+            const int o = Rr.csr_row ? Rr.csr_row[r] : r;
+            // Gauss-Newton entries: the rows carry H[i][j], i <= j; the sum is
+            // stored at [i][j] and [j][i]
             int om = -1;
             if (MODE == kGN && o > Rr.P) {
                 const int oh = o - 1 - Rr.P, i = oh / Rr.P, j = oh - i * Rr.P;
-                if (i > j) continue;
                 if (i < j) om = 1 + Rr.P + j * Rr.P + i;
             }
             double s = 0.0;
-            const int e = Rr.csr_ptr[o + 1];
-            for (int j = Rr.csr_ptr[o]; j < e; ++j) s += hsum[Rr.csr_src[j]];
+            const int e = Rr.csr_ptr[r + 1];
+            for (int j = Rr.csr_ptr[r]; j < e; ++j) s += hsum[Rr.csr_src[j]];
             out[o] = s;
             if (om >= 0) out[om] = s;
         }

@@ -174,6 +174,9 @@ struct EvalParams {
     const int32_t* csr_src;       // sources: k * nacc + acc
     int n_out;
     int n_src;                    // csr_src length
+    const int32_t* csr_row;       // [n_rows] output index of each map row, or null: row r is output r
+    int n_rows;                   // map rows (when csr_row is set)
+    int out_zeroed;               // 1: out holds 0 wherever the map has no row (else the kernel zeroes it)
     int hsum_in_smem, csr_in_smem;
     int smem_bytes;               // dynamic shared memory of the objective kernel
     double* out;                  // [n_out]

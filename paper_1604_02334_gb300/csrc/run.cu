@@ -252,15 +252,17 @@ void musr_run_s::build_tiles(Tiling& T, int t, const std::vector<int64_t>& tph) 
 // per-histogram totals and the CSR, each when it fits.
 int musr_run_s::tail_smem(int mode, int* hsum_smem, int* csr_smem) const {
     const int nacc = n_acc(mode, R);
+    const size_t csr_words = (size_t)n_rows[mode] + 1 + n_src[mode] + (mode == kGN ? n_rows[mode] : 0);
     const int hs = (size_t)K * nacc * 16 <= 64 * 1024;
-    const int cs = ((size_t)n_out[mode] + 1 + n_src[mode]) * 4 <= 64 * 1024;
+    const int cs = csr_words * 4 <= 64 * 1024;
     if (hsum_smem) *hsum_smem = hs;
     if (csr_smem) *csr_smem = cs;
-    return (int)(16 * (hs ? (size_t)K * nacc : 0) + 4 * (cs ? (size_t)n_out[mode] + 1 + n_src[mode] : 0));
+    return (int)(16 * (hs ? (size_t)K * nacc : 0) + 4 * (cs ? csr_words : 0));
 }
 
 // CSR of output entry -> (histogram, accumulator) sources for one mode.
-void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const {
+void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src,
+                            std::vector<int32_t>& rows) const {
     const int nacc = n_acc(mode, R);
     const int64_t n_out = 1 + (mode >= kGrad ? Pk : 0) + (mode == kGN ? (int64_t)Pk * Pk : 0);
     std::vector<std::pair<int64_t, int32_t>> e;
@@ -292,13 +294,26 @@ void musr_run_s::build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int3
                      [](const std::pair<int64_t, int32_t>& x, const std::pair<int64_t, int32_t>& y) {
                          return x.first < y.first;
                      });
-    ptr.assign(n_out + 1, 0);
     src.resize(e.size());
-    for (size_t i = 0; i < e.size(); ++i) {
-        ptr[e[i].first + 1]++;
-        src[i] = e[i].second;
+    for (size_t i = 0; i < e.size(); ++i) src[i] = e[i].second;
+    rows.clear();
+    if (mode != kGN) {
+        // one row per output
+        ptr.assign(n_out + 1, 0);
+        for (size_t i = 0; i < e.size(); ++i) ptr[e[i].first + 1]++;
+        for (int64_t o = 0; o < n_out; ++o) ptr[o + 1] += ptr[o];
+        return;
     }
-    for (int64_t o = 0; o < n_out; ++o) ptr[o + 1] += ptr[o];
+    // Gauss-Newton: one row per output that has sources (most of the P^2
+    // entries have none); rows[r] is its output index
+    ptr.assign(1, 0);
+    for (size_t i = 0; i < e.size(); ++i) {
+        if (i == 0 || e[i].first != e[i - 1].first) {
+            rows.push_back((int32_t)e[i].first);
+            ptr.push_back(ptr.back());
+        }
+        ptr.back()++;
+    }
 }
 
 // One device allocation holds every per-run array; pieces are 256-byte aligned.
@@ -314,11 +329,12 @@ struct Arena {
 
 int musr_run_s::allocate() {
     const int nacc_max = n_acc(Pk <= kMaxGnParams ? kGN : kGrad, R);
-    std::vector<int32_t> ptr[3], src[3];
+    std::vector<int32_t> ptr[3], src[3], rows[3];
     for (int m = 0; m < 3; ++m) {
         if (m == kGN && Pk > kMaxGnParams) continue;
-        build_csr(m, ptr[m], src[m]);
-        n_out[m] = (int)ptr[m].size() - 1;
+        build_csr(m, ptr[m], src[m], rows[m]);
+        n_out[m] = (int)(1 + (m >= kGrad ? Pk : 0) + (m == kGN ? (int64_t)Pk * Pk : 0));
+        n_rows[m] = (int)ptr[m].size() - 1;
         n_src[m] = (int)src[m].size();
     }
     // per-mode tiling: for each block size, one wave of resident blocks
@@ -393,10 +409,11 @@ int musr_run_s::allocate() {
     for (int k = 0; k < K; ++k) max_m = std::max(max_m, n_bins[k]);
     etab_len = lifetime_table_len(max_m);
     const size_t o_etab = A.take<float>((size_t)etab_len);
-    size_t o_ptr[3], o_src[3];
+    size_t o_ptr[3], o_src[3], o_row[3];
     for (int m = 0; m < 3; ++m) {
         o_ptr[m] = A.take<int32_t>(ptr[m].size() + 1);
         o_src[m] = A.take<int32_t>(src[m].size() + 1);
+        o_row[m] = A.take<int32_t>(rows[m].size() + 1);
     }
     const size_t o_facc = A.take<unsigned long long>((size_t)(K + 1) * nacc_max * 3);
     const size_t o_hsum = A.take<__int128>((size_t)(K + 1) * nacc_max);
@@ -425,6 +442,7 @@ int musr_run_s::allocate() {
     for (int m = 0; m < 3; ++m) {
         d_csr_ptr[m] = reinterpret_cast<int32_t*>(b + o_ptr[m]);
         d_csr_src[m] = reinterpret_cast<int32_t*>(b + o_src[m]);
+        d_csr_row[m] = rows[m].empty() ? nullptr : reinterpret_cast<int32_t*>(b + o_row[m]);
     }
     d_facc = reinterpret_cast<unsigned long long*>(b + o_facc);
     d_hist_sum = reinterpret_cast<__int128*>(b + o_hsum);
@@ -443,6 +461,8 @@ int musr_run_s::allocate() {
     }
     h_theta = static_cast<double*>(h_pinned);
     h_out = h_theta + Pk + 1;
+    // outputs the Gauss-Newton map never writes (entries without sources) stay 0
+    memset(h_out, 0, sizeof(double) * (n_out_max + 1));
     h_status = reinterpret_cast<int32_t*>(h_out + n_out_max + 1);
     if (cudaHostGetDevicePointer((void**)&hd_out, h_out, 0) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&hd_status, h_status, 0) != cudaSuccess)
@@ -471,6 +491,7 @@ int musr_run_s::allocate() {
     for (int m = 0; m < 3; ++m) {
         up(d_csr_ptr[m], ptr[m].data(), sizeof(int32_t) * ptr[m].size());
         up(d_csr_src[m], src[m].data(), sizeof(int32_t) * src[m].size());
+        if (d_csr_row[m]) up(d_csr_row[m], rows[m].data(), sizeof(int32_t) * rows[m].size());
     }
     // opt the kernels whose reduction tail needs > 48 KB of shared memory in
     for (int m = 0; m < 3 && e == cudaSuccess; ++m) {
@@ -482,6 +503,7 @@ int musr_run_s::allocate() {
     if (e == cudaSuccess)
         e = cudaMemsetAsync(d_facc, 0, sizeof(unsigned long long) * (size_t)(K + 1) * nacc_max * 3, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_data, 0, sizeof(float) * data_floats, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_out, 0, sizeof(double) * (n_out_max + 1), stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     return cuda_status(e);
 }
@@ -578,6 +600,10 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.csr_src = d_csr_src[m];
     p.n_out = n_out[m];
     p.n_src = n_src[m];
+    p.csr_row = d_csr_row[m];
+    p.n_rows = n_rows[m];
+    // the run's own output buffers hold 0 wherever the map writes nothing
+    p.out_zeroed = out_dev == d_out || out_dev == hd_out;
     p.hsum_in_smem = hsum_in_smem[m];
     p.csr_in_smem = csr_in_smem[m];
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];

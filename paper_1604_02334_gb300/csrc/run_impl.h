@@ -93,8 +93,12 @@ struct musr_run_s {
     int64_t etab_len = 0;
     int32_t* d_csr_ptr[3] = {nullptr, nullptr, nullptr};
     int32_t* d_csr_src[3] = {nullptr, nullptr, nullptr};
+    // Gauss-Newton: the map's rows are the outputs that have sources (their
+    // output index in d_csr_row); value and gradient: row = output, no table
+    int32_t* d_csr_row[3] = {nullptr, nullptr, nullptr};
     int n_out[3] = {0, 0, 0};
     int n_src[3] = {0, 0, 0};
+    int n_rows[3] = {0, 0, 0};
     // dynamic shared memory of the reduction tail per mode
     int hsum_in_smem[3] = {0, 0, 0}, csr_in_smem[3] = {0, 0, 0};
     int smem_bytes[3] = {0, 0, 0};
@@ -126,7 +130,7 @@ struct musr_run_s {
     std::vector<int64_t> tiles_per_hist(int threads, int64_t target) const;
     void build_tiles(Tiling& t, int threads, const std::vector<int64_t>& tph) const;
     int tail_smem(int mode, int* hsum_smem, int* csr_smem) const;
-    void build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src) const;
+    void build_csr(int mode, std::vector<int32_t>& ptr, std::vector<int32_t>& src, std::vector<int32_t>& rows) const;
     int allocate();
     int upload(int dtype, const void* data, int on_device);
     musr::EvalParams params(int obj, int mode, const double* theta_dev, double* out_dev,

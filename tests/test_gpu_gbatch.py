@@ -81,6 +81,33 @@ def test_gbatch_inactive_entries_and_device_entry(runs):
         r.close()
 
 
+def test_gbatch_gn_device_entry_into_a_nan_buffer(runs):
+    """The batched Gauss-Newton evaluation into a caller's buffer full of NaN:
+    every entry comes back, the entries without sources as 0, equal to the
+    host entry point's results."""
+    gruns = [Run(lay, d) for lay, d, _ in runs]
+    with GBatch(gruns, with_gn=True) as b:
+        thetas = [th for _, _, th in runs]
+        full, _ = b.eval(thetas, MUSR_CHI2, MUSR_VALUE_GRAD_GN)
+        flat = torch.tensor(np.concatenate(thetas), device="cuda")
+        sizes = b.out_sizes(MUSR_VALUE_GRAD_GN)
+        out = torch.full((int(np.sum(sizes)),), float("nan"), dtype=torch.float64, device="cuda")
+        b.eval_device(flat, out, MUSR_CHI2, MUSR_VALUE_GRAD_GN)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        off = 0
+        for e, n in enumerate(sizes):
+            P = len(full[e][1])
+            assert o[off] == full[e][0]
+            np.testing.assert_array_equal(o[off + 1:off + 1 + P], full[e][1])
+            H = o[off + 1 + P:off + n].reshape(P, P)
+            assert np.all(np.isfinite(H)) and np.array_equal(H, H.T)
+            np.testing.assert_array_equal(H, full[e][2])
+            off += n
+    for r in gruns:
+        r.close()
+
+
 def test_fit_batch_matches_single_fits_and_oracle(runs):
     """Lockstep LM fits of every run (the 16 x 65536 one included) converge
     (status MUSR_OK), equal the single fits, and lie within 1e-3 sigma of the

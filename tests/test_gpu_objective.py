@@ -209,14 +209,21 @@ def test_device_path_and_autograd(md_small):
         # device calls stage constants with FP32 functions, host calls in FP64
         assert rel_err(float(v.detach()), v_host) <= 1e-7
         assert grad_rel_err(ref[1:].cpu().numpy(), g_host) <= 1e-6
-        out = torch.empty(1 + lay.n_params + lay.n_params ** 2, dtype=torch.float64, device=dev)
+        # a caller's buffer full of NaN: the Gauss-Newton entries without
+        # sources must come back as 0, the others as the oracle's
+        P = lay.n_params
+        out = torch.full((1 + P + P ** 2,), float("nan"), dtype=torch.float64, device=dev)
         st = torch.zeros(1, dtype=torch.int32, device=dev)
         run.chi2_grad_device(t.detach(), out, MUSR_POISSON, 2, st)
         torch.cuda.synchronize()
-        rv, rg, rH = oracle.gradient(lay, d, th, oracle.POISSON)
+        rv, rg, rH = oracle.gradient(lay, d, th, oracle.POISSON, with_gn=True)
         o = out.cpu().numpy()
         assert rel_err(o[0], rv) <= 1e-6 and int(st.item()) == 0
-        assert grad_rel_err(o[1:1 + lay.n_params], rg) <= 1e-4
+        assert grad_rel_err(o[1:1 + P], rg) <= 1e-4
+        H = o[1 + P:].reshape(P, P)
+        assert np.all(np.isfinite(H))
+        assert np.array_equal(H, H.T)
+        assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
 
 
 def test_set_data_from_device_fp64(md_small):
