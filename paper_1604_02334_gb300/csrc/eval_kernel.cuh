@@ -299,6 +299,38 @@ __device__ __forceinline__ void warp_sum(float (&v)[NACC]) {
     }
 }
 
+// Reduce-scatter of N accumulators over the warp by recursive halving: at
+// step s every lane keeps half of its values (the upper half where bit s of
+// its lane index is set) and adds the partner's (lane ^ 2^s) copy of that
+// half, so the warp does ~N shuffles instead of the butterfly's 5 N.  On
+// return lane L holds the warp sums of accumulators j + (NP / 32) bitrev5(L),
+// j < NP / 32, in v[0 .. NP / 32) (NP = N rounded up to a multiple of 32;
+// the padding is zero).
+template <int N>
+struct WarpSplit {
+    static constexpr int NP = (N + 31) / 32 * 32;
+    static constexpr int PER = NP / 32;
+    float v[NP];
+};
+template <int N>
+__device__ __forceinline__ void warp_reduce_scatter(WarpSplit<N>& w, int lane) {
+    constexpr int NP = WarpSplit<N>::NP;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int M = NP >> s, H = M >> 1;
+        const bool up = (lane >> s) & 1;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            const float keep = up ? w.v[i + H] : w.v[i];
+            const float send = up ? w.v[i] : w.v[i + H];
+            w.v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 1 << s);
+        }
+    }
+}
+__device__ __forceinline__ int bitrev5(int x) {
+    return ((x & 1) << 4) | ((x & 2) << 2) | (x & 4) | ((x & 8) >> 2) | ((x & 16) >> 4);
+}
+
 // One thread's chunk of kBinsPerThread consecutive bins starting at bin n0 of a
 // histogram with M bins: theory (Eq. 1), objective term (Eq. 3 / Eq. 4) and,
 // by mode, the role partials accumulated into the gradient and GN matrix.
@@ -1203,10 +1235,22 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     // fixed-point integers (one thread per warp and accumulator) summed over
     // the warps, one fixed-point add per accumulator into the histogram's
     // totals ----
-    warp_sum<NACC>(acc);
-    if (lane == 0) {
+    if constexpr (NACC >= 32) {
+        // many accumulators (Gauss-Newton): reduce-scatter, each lane stores its share
+        WarpSplit<NACC> ws;
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
+        for (int a = 0; a < WarpSplit<NACC>::NP; ++a) ws.v[a] = a < NACC ? acc[a] : 0.f;
+        warp_reduce_scatter<NACC>(ws, lane);
+        const int a0 = WarpSplit<NACC>::PER * bitrev5(lane);
+#pragma unroll
+        for (int j = 0; j < WarpSplit<NACC>::PER; ++j)
+            if (a0 + j < NACC) red[warp][a0 + j] = ws.v[j];
+    } else {
+        warp_sum<NACC>(acc);
+        if (lane == 0) {
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
+        }
     }
     const int any_bad = __syncthreads_or(bad);
     {

@@ -215,10 +215,22 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
             fetch_theta(nxt);
         }
         if (!act) continue;
-        warp_sum<NACC>(acc);
-        if (lane == 0) {
+        if constexpr (NACC >= 32) {
+            // many accumulators (Gauss-Newton): reduce-scatter, each lane stores its share
+            WarpSplit<NACC> ws;
 #pragma unroll
-            for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
+            for (int a = 0; a < WarpSplit<NACC>::NP; ++a) ws.v[a] = a < NACC ? acc[a] : 0.f;
+            warp_reduce_scatter<NACC>(ws, lane);
+            const int a0 = WarpSplit<NACC>::PER * bitrev5(lane);
+#pragma unroll
+            for (int j = 0; j < WarpSplit<NACC>::PER; ++j)
+                if (a0 + j < NACC) red[warp][a0 + j] = ws.v[j];
+        } else {
+            warp_sum<NACC>(acc);
+            if (lane == 0) {
+#pragma unroll
+                for (int a = 0; a < NACC; ++a) red[warp][a] = acc[a];
+            }
         }
         const int any_bad = __syncthreads_or(bad);
         if (threadIdx.x == 0 && any_bad) atomicOr(&p.flags[run], 1u);
