@@ -133,11 +133,14 @@ struct Evaluator {
         buf.resize((size_t)run->n_out[mode] + 1);
         int32_t flags = 0;
         ++evals;
-        int st = run->eval_host(obj, mode, theta, buf.data(), &flags);
+        // results read straight from the run's pinned buffer where it holds them
+        // (no function array): one copy of the P x P matrix, not two
+        const double* o = buf.data();
+        int st = run->eval_host(obj, mode, theta, buf.data(), &flags, &o);
         if (st != MUSR_OK) return st;
-        *value = (flags & 1) ? INFINITY : buf[0];
-        if (grad && mode >= kGrad) memcpy(grad, buf.data() + 1, sizeof(double) * P);
-        if (gn && mode == kGN) memcpy(gn, buf.data() + 1 + P, sizeof(double) * P * P);
+        *value = (flags & 1) ? INFINITY : o[0];
+        if (grad && mode >= kGrad) memcpy(grad, o + 1, sizeof(double) * P);
+        if (gn && mode == kGN) memcpy(gn, o + 1 + P, sizeof(double) * P * P);
         if (flags & 1) return MUSR_EDOMAIN;
         return isfinite(*value) ? MUSR_OK : MUSR_ENONFINITE;
     }

@@ -653,7 +653,8 @@ int musr_run_s::extend_theta(const double* theta, double* ext, std::vector<std::
 // into mapped host memory.  With a function array the kernel works on the
 // Pk = P + F slots and the results are folded back onto theta by the chain
 // rule: g = g_p + J^T g_f, H = A^T H' A with A = [I; J].
-int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags) {
+int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags,
+                          const double** view) {
     if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
     if (mode < kValue || mode > kGN) return MUSR_EINVAL;
     if (mode == kGN && Pk > kMaxGnParams) return MUSR_ENOTSUP;
@@ -703,7 +704,8 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
     if (e != cudaSuccess) return cuda_status(e);
     *flags = __atomic_load_n(h_status, __ATOMIC_ACQUIRE);
     if (F == 0) {
-        memcpy(out_host, h_out, sizeof(double) * nuser);
+        if (view) *view = h_out;
+        else memcpy(out_host, h_out, sizeof(double) * nuser);
         return MUSR_OK;
     }
     out_host[0] = h_out[0];

@@ -141,6 +141,10 @@ struct musr_run_s {
     // function slots (jac[j][r] = d f_j / d theta[funcs[j].refs[r]])
     int extend_theta(const double* theta, double* ext, std::vector<std::vector<double>>* jac) const;
     // out_host: value (+ gradient, + Gauss-Newton matrix) over the P parameters
-    int eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags);
+    // view != null and no function array: the results are left in the run's
+    // pinned buffer, *view pointing at them (valid until the next call), and
+    // out_host is not written
+    int eval_host(int obj, int mode, const double* theta, double* out_host, int32_t* flags,
+                  const double** view = nullptr);
     ~musr_run_s();
 };
