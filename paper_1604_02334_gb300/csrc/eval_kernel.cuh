@@ -290,6 +290,18 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
     }
 }
 
+// Asynchronous global -> shared copies (completed by cp_async_wait_all in the
+// issuing thread; other threads see the data after a barrier that follows).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int NACC>
 __device__ __forceinline__ void warp_sum(float (&v)[NACC]) {
 #pragma unroll
@@ -1161,6 +1173,21 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
     }
     __syncthreads();
 
+    // the tail's map into shared memory (when it fits), copied while the bins
+    // are evaluated: only the last block reads it, but no block knows yet
+    // whether it is last, and the copies cost no registers
+    const int n_rows = p.csr_row ? p.n_rows : p.n_out;
+    const int cw1 = (n_rows + 1 + 3) >> 2, cw2 = (p.n_src + 3) >> 2;  // 16-byte pieces of pointers, sources
+    int32_t* tbl = reinterpret_cast<int32_t*>(dyn_smem + (p.hsum_in_smem ? sizeof(__int128) * p.K * NACC : 0));
+    if (MODE != kModel && p.csr_in_smem) {
+        const int cw3 = p.csr_row ? (n_rows + 3) >> 2 : 0;
+        for (int c = threadIdx.x; c < cw1 + cw2 + cw3; c += blockDim.x) {
+            if (c < cw1) cp_async16(tbl + 4 * c, p.csr_ptr + 4 * c);
+            else if (c < cw1 + cw2) cp_async16(tbl + 4 * c, p.csr_src + 4 * (c - cw1));
+            else cp_async16(tbl + 4 * c, p.csr_row + 4 * (c - cw1 - cw2));
+        }
+    }
+
     float acc[NACC];
 #pragma unroll
     for (int a = 0; a < NACC; ++a) acc[a] = 0.f;
@@ -1279,34 +1306,28 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
         s_last = (prev == gridDim.x - 1u);
     }
     __syncthreads();
+    cp_async_wait_all();  // this thread's map copies (long complete)
     if (!s_last) return;
 
     // ---- last block: per-histogram integer totals (their limbs zeroed for the
     // next launch), then theta via the map (CSR rows of sources; value and
     // gradient: a row per output; Gauss-Newton: a row per output that has
     // sources, whose output index the row table gives), summed as integers.
-    // The map (into shared memory, when it fits) and the limbs come in
-    // batches of up to eight elements a thread with the whole batch in flight ----
+    // The map is in shared memory already when it fits (copied during the
+    // bins); the limbs come in batches of up to eight totals a thread with the
+    // whole batch in flight ----
     const unsigned fl = *reinterpret_cast<volatile unsigned*>(p.flags);
     __int128* hsum = p.hsum_in_smem ? reinterpret_cast<__int128*>(dyn_smem) : p.hist_sum;
-    int32_t* tbl = reinterpret_cast<int32_t*>(dyn_smem + (p.hsum_in_smem ? sizeof(__int128) * p.K * NACC : 0));
-    const int n_rows = p.csr_row ? p.n_rows : p.n_out;
-    const int n1 = n_rows + 1, n2 = n1 + p.n_src;
     const int32_t* cptr = p.csr_in_smem ? tbl : p.csr_ptr;
-    const int32_t* csrc = p.csr_in_smem ? tbl + n1 : p.csr_src;
-    const int32_t* crow = p.csr_row ? (p.csr_in_smem ? tbl + n2 : p.csr_row) : nullptr;
+    const int32_t* csrc = p.csr_in_smem ? tbl + 4 * cw1 : p.csr_src;
+    const int32_t* crow = p.csr_row ? (p.csr_in_smem ? tbl + 4 * (cw1 + cw2) : p.csr_row) : nullptr;
     {
         const int n_tot = p.K * NACC;
-        const int n_csr = p.csr_in_smem ? n2 + (p.csr_row ? n_rows : 0) : 0;
-        const int n_max = max(n_tot, n_csr);
-        for (int base = threadIdx.x; base < n_max; base += 8 * blockDim.x) {
-            int32_t cv[8];
+        for (int base = threadIdx.x; base < n_tot; base += 8 * blockDim.x) {
             unsigned long long lv[8][3];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int i = base + u * blockDim.x;
-                if (i < n_csr)
-                    cv[u] = __ldcg(i < n1 ? p.csr_ptr + i : i < n2 ? p.csr_src + (i - n1) : p.csr_row + (i - n2));
                 if (i < n_tot) {
                     const unsigned long long* l = p.facc + (size_t)i * 3;
                     lv[u][0] = __ldcg(l);
@@ -1317,7 +1338,6 @@ __global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int i = base + u * blockDim.x;
-                if (i < n_csr) tbl[i] = cv[u];
                 if (i < n_tot) {
                     hsum[i] = fix_total(lv[u][0], lv[u][1], lv[u][2]);
                     // the limbs start from zero for the next launch

@@ -81,18 +81,6 @@ struct GParams {
     int32_t* status;  // per run
 };
 
-// Asynchronous global -> shared copies (completed by cp_async_wait_all in the
-// issuing thread; other threads see the data after a barrier that follows).
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 template <int NE, int NG, int NS, int KT, int MODE>
 __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_kernel(const __grid_constant__ GParams p) {
     constexpr int NOSC = NE + NG + NS;

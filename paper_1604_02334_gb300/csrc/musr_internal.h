@@ -206,6 +206,14 @@ struct EvalParams {
 static_assert(sizeof(EvalParams) <= 32000, "EvalParams exceeds the kernel parameter space");
 
 
+// 32-bit words of the objective kernel's map in shared memory: row pointers
+// (n_rows + 1), sources, and the row -> output table when there is one, each
+// array starting on a 16-byte boundary (the kernel copies them with cp.async).
+inline size_t csr_smem_words(int64_t n_rows, int64_t n_src, bool row_table) {
+    auto r4 = [](int64_t n) { return (size_t)((n + 3) / 4 * 4); };
+    return r4(n_rows + 1) + r4(n_src) + (row_table ? r4(n_rows) : 0);
+}
+
 // Launch the objective kernel for a signature / mode (eval_*.cu).
 cudaError_t launch_eval(const Signature& sig, int mode, int threads, int n_tiles,
                         cudaStream_t stream, const EvalParams& p);

@@ -279,7 +279,7 @@ extern "C" int musr_chi2_grad_noalloc(const musr_run_desc* desc, int obj, int mo
     p.n_src = pl.n_src;
     p.hsum_in_smem = 1;  // K <= 64 and nacc <= 13: at most 13 KB
     p.csr_in_smem = 1;   // at most ~7 KB
-    p.smem_bytes = (int)(16 * (size_t)pl.K * nacc + 4 * ((size_t)pl.n_out + 1 + pl.n_src));
+    p.smem_bytes = (int)(16 * (size_t)pl.K * nacc + 4 * csr_smem_words(pl.n_out, pl.n_src, false));
     p.out = out_dev;
     p.status_out = status_dev;
     p.etab = etab;

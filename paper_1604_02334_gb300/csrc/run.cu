@@ -252,7 +252,7 @@ void musr_run_s::build_tiles(Tiling& T, int t, const std::vector<int64_t>& tph) 
 // per-histogram totals and the CSR, each when it fits.
 int musr_run_s::tail_smem(int mode, int* hsum_smem, int* csr_smem) const {
     const int nacc = n_acc(mode, R);
-    const size_t csr_words = (size_t)n_rows[mode] + 1 + n_src[mode] + (mode == kGN ? n_rows[mode] : 0);
+    const size_t csr_words = csr_smem_words(n_rows[mode], n_src[mode], mode == kGN);
     const int hs = (size_t)K * nacc * 16 <= 64 * 1024;
     const int cs = csr_words * 4 <= 64 * 1024;
     if (hsum_smem) *hsum_smem = hs;
