@@ -1098,15 +1098,16 @@ __device__ __forceinline__ double fix_to_double(__int128 X) {
 }
 
 template <int NE, int NG, int NS, int KT, int MODE>
-__global__ void __launch_bounds__(kMaxThreads) eval_kernel(const __grid_constant__ EvalParams p) {
+__global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eval_kernel(const __grid_constant__ EvalParams p) {
     constexpr int NOSC = NE + NG + NS;
     constexpr int R = 2 + 4 * NOSC + NS + 2 * KT;
     constexpr int NACC = MODE == kValue ? 1 : MODE == kGrad ? 1 + R : MODE == kGN ? 1 + R + R * (R + 1) / 2 : 1;
     constexpr int G = kBinsPerThread;
 
     __shared__ HistConst hc;
-    __shared__ float red[kMaxWarps][NACC];
-    __shared__ __align__(16) __int128 xred[kMaxWarps][NACC];
+    constexpr int KW = MODE == kGN ? kMaxWarpsGn : kMaxWarps;
+    __shared__ float red[KW][NACC];
+    __shared__ __align__(16) __int128 xred[KW][NACC];
     __shared__ int s_last;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
 

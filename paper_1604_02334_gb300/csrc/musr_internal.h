@@ -15,6 +15,10 @@ constexpr int kMaxRoles = 2 + 4 * kMaxOsc + 1 + 2; // N0, bkg, 4 per line, stret
 constexpr int kBinsPerThread = 8;                  // consecutive bins per thread (2 x float4)
 constexpr int kMaxThreads = 256;                   // block size upper bound
 constexpr int kMaxWarps = kMaxThreads / 32;
+// the objective kernel's Gauss-Newton mode may also run 384-thread blocks:
+// at ~170 registers a thread only 256 fit otherwise, 8 warps an SM
+constexpr int kMaxThreadsGn = 384;
+constexpr int kMaxWarpsGn = kMaxThreadsGn / 32;
 constexpr int kInlineParams = 256;                 // theta passed inside the launch parameters
 constexpr int kInlineRoleHist = 32;                // role-map rows passed inside the launch parameters
 

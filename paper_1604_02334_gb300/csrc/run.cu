@@ -358,7 +358,11 @@ int musr_run_s::allocate() {
         int best_t = kMaxThreads;
         std::vector<int64_t> best_tph;
         int64_t best_cost = INT64_MAX;
-        for (int t = kMaxThreads; t >= t_min; t >>= 1) {
+        // block sizes 256, 128, ..., t_min; the Gauss-Newton mode tries 384 first
+        std::vector<int> sizes;
+        if (m == kGN) sizes.push_back(kMaxThreadsGn);
+        for (int t = kMaxThreads; t >= t_min; t >>= 1) sizes.push_back(t);
+        for (const int t : sizes) {
             int per_sm = 0;
             EvalParams q;
             memset(&q, 0, sizeof(q));
