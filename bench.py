@@ -715,8 +715,15 @@ def run_ours(args):
     torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
 
+    # a step: one chi2 + gradient evaluation queued with its theta by value
+    # (the library's queued entry), results into device memory; the rows are
+    # sliced beforehand so that the host keeps ahead of the GPU
+    th_rows = [np.ascontiguousarray(t) for t in thetas]
+    th_rows_t = [thetas_t[i] for i in range(n_vec)]
+    out_rows = [outs[i] for i in range(n_vec)]
+
     def step(i):
-        runs[i % N_RUNS].chi2_grad_device(thetas_t[i], outs[i], MUSR_CHI2, MUSR_VALUE_GRAD, stream=sptr)
+        runs[i % N_RUNS].chi2_grad_async(th_rows[i], out_rows[i], MUSR_CHI2, MUSR_VALUE_GRAD, stream=sptr)
 
     for i in range(args.warmup):
         step(i)
@@ -748,6 +755,20 @@ def run_ours(args):
     mean_ms = 1e3 * t_total / args.steps
     # the same evaluation one launch at a time, L2 flushed before each, events around the launch alone
     flushed_us = _flushed_us(run, thetas_t, outs[0], MUSR_CHI2, MUSR_VALUE_GRAD, flush, stream)
+    # the same steps through the device-theta entry (theta read from device
+    # memory after the previous kernel completes: no overlap between steps)
+    def step_dev(i):
+        runs[i % N_RUNS].chi2_grad_device(th_rows_t[i], out_rows[i], MUSR_CHI2, MUSR_VALUE_GRAD, stream=sptr)
+
+    for i in range(args.warmup):
+        step_dev(i)
+    torch.cuda.synchronize()
+    e_start.record(stream)
+    for j in range(args.steps):
+        step_dev(args.warmup + j)
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    device_theta_us = 1e3 * e_start.elapsed_time(e_end) / args.steps
 
     # end to end through the C ABI with host buffers: per step, upload the
     # histograms from pinned memory, evaluate chi2 + gradient, read them back
@@ -804,6 +825,7 @@ def run_ours(args):
         "e2e": _short(e2e),
         "gpu_launches": args.steps,  # one objective kernel launch per step
         "flushed_step_us": _r(flushed_us),
+        "device_theta_step_us": _r(device_theta_us),
         "pipe_rates_per_s": _short(peaks["rates"]),
     }
     details = {"wall_s": wall}

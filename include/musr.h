@@ -182,6 +182,20 @@ int musr_chi2_grad(musr_run run, int obj, const double* theta, double* value, do
 int musr_chi2_grad_device(musr_run run, int obj, int mode, const double* theta_dev,
                           double* out_dev, int32_t* status_dev, void* stream);
 
+/* Queued variant: theta[P] is a HOST FP64 vector, read during the call and
+ * passed by value inside the launch (the caller may reuse it on return);
+ * out_dev / status_dev / stream as for musr_chi2_grad_device, results in
+ * stream order.  Because theta cannot change after the call, a queued
+ * evaluation's parameter staging and bin loop (Eq. 1, Eq. 3 / Eq. 4 and their
+ * adjoint) may run while the previous kernel in the stream finishes; its
+ * additions into the run's reduction buffers and its results wait for that
+ * kernel.  MUSR_ENONFINITE for non-finite theta, MUSR_ENOTSUP with a
+ * function array or more than 256 parameters.  Evaluations of one run queued
+ * on different streams must be ordered by the caller (one reduction buffer
+ * per run). */
+int musr_chi2_grad_async(musr_run run, int obj, int mode, const double* theta, double* out_dev,
+                         int32_t* status_dev, void* stream);
+
 /* Model N for every bin (FP32, histogram-major, total_bins values) into a
  * host (out_on_device == 0) or device buffer. */
 int musr_model(musr_run run, const double* theta, float* out, int32_t out_on_device);

@@ -115,6 +115,7 @@ SIGNATURES = {
     "musr_chi2": (ctypes.c_int, [_run, ctypes.c_int, _dp, _dp]),
     "musr_chi2_grad": (ctypes.c_int, [_run, ctypes.c_int, _dp, _dp, _dp, _dp]),
     "musr_chi2_grad_device": (ctypes.c_int, [_run, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "musr_chi2_grad_async": (ctypes.c_int, [_run, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp]),
     "musr_model": (ctypes.c_int, [_run, _dp, _vp, ctypes.c_int32]),
     "musr_chi2_batch": (ctypes.c_int, [ctypes.POINTER(_run), ctypes.c_int32, ctypes.c_int, _dp,
                                        _i32p, _dp]),

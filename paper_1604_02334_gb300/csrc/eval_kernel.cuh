@@ -1114,9 +1114,16 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = blockDim.x >> 5;
     // programmatic dependent launch: this grid may be scheduled while the
-    // previous one in the stream finishes; nothing it wrote is read before
-    // the previous grid has completed
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    // previous one in the stream finishes.  Nothing that grid may write is
+    // read before it has completed (griddepcontrol.wait); what is read earlier
+    // is immutable (pre_wait, see EvalParams).  Every thread waits before the
+    // block's first global write.
+    const int pre_wait = MODE == kModel ? 0 : p.pre_wait;
+    if (pre_wait == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
+    // the next grid in the stream may be launched at once: its blocks take SM
+    // slots as this grid's blocks leave them (every kernel of this library
+    // waits before it touches what this grid writes)
+    asm volatile("griddepcontrol.launch_dependents;");
     const int tile = blockIdx.x;
     int k, M, tstart, tend;
     const float* hdata;
@@ -1141,12 +1148,15 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
 
     // the histogram's theta entries (one per role slot, warp 0) come first,
     // alone: queued behind the block's data loads their round trip doubled.
-    // theta is inline in the launch parameters for host calls
+    // theta is inline in the launch parameters for host calls; the role rows
+    // are immutable, theta in device memory is read after the wait
     __shared__ double s_th[2 * kMaxRoles];
     if (threadIdx.x < 2 * kMaxRoles) {
         const double* theta = p.theta_inline_n ? p.theta_inline : p.theta;
         const int32_t* rt = (p.rt_inline ? p.rt_rows : p.role_theta) + (size_t)k * kMaxRoles * 2;
-        s_th[threadIdx.x] = ThetaByRow{rt, theta}((int)threadIdx.x);
+        const int i = rt[threadIdx.x];
+        if (pre_wait == 1) asm volatile("griddepcontrol.wait;" ::: "memory");
+        s_th[threadIdx.x] = i >= 0 ? theta[i] : 0.0;
     }
     __syncthreads();
 
@@ -1255,8 +1265,6 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
         }
         if constexpr (MODE == kGN) gn_scatter(gnacc, acc);
     }
-    // the next grid in the stream may begin its launch
-    asm volatile("griddepcontrol.launch_dependents;");
     if (MODE == kModel) return;
 
     // ---- block: FP32 warp sums scaled by the histogram's role factors, as
@@ -1281,6 +1289,9 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
         }
     }
     const int any_bad = __syncthreads_or(bad);
+    // the previous grid has completed (its limbs and counters reset, its
+    // output written) before this block adds anything
+    if (pre_wait != 0) asm volatile("griddepcontrol.wait;" ::: "memory");
     {
         unsigned flag = (threadIdx.x == 0 && any_bad) ? 1u : 0u;
         for (int q = threadIdx.x; q < nwarps * NACC; q += blockDim.x) {

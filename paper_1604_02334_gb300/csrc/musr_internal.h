@@ -188,6 +188,15 @@ struct EvalParams {
     int status_sys_fence;         // 1: out / status_out are mapped host memory the host polls
     int theta_inline_n;           // > 0: theta_inline holds theta (host calls)
     double theta_inline[kInlineParams];
+    // What a block may read before the grid-dependency wait of programmatic
+    // dependent launch (the previous kernel in the stream may still run):
+    //   0  nothing (the wait comes first)
+    //   1  the run's tables, counts and lifetime factors (written only by
+    //      calls that synchronise before returning); theta after the wait
+    //   2  those and theta (inline): staging and the whole bin loop run before
+    //      the wait, which then precedes the block's first global write
+    // Never 2 in kModel, whose bin loop writes the model.
+    int pre_wait;
     // Equal-length histograms (the common layout): tile b belongs to histogram
     // k = b / uni_tph and covers chunks [j C / uni_tph, (j + 1) C / uni_tph)
     // of it, j = b mod uni_tph, C = uni_chunks (8-bin chunks per histogram);

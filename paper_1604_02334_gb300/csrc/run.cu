@@ -626,6 +626,10 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.status_out = status_dev;
     p.model_off = d_model_off;
     p.etab = d_etab;
+    // the run's counts, tables and lifetime factors change only in calls
+    // that synchronise before returning: a block may read them before its
+    // grid-dependency wait (theta in device memory only after it)
+    p.pre_wait = 1;
     return p;
 }
 
@@ -684,6 +688,7 @@ int musr_run_s::eval_host(int obj, int mode, const double* theta, double* out_ho
     if (Pk <= kInlineParams) {
         p.theta_inline_n = Pk;
         memcpy(p.theta_inline, th, sizeof(double) * Pk);
+        p.pre_wait = 2;
     } else {
         memcpy(h_theta, th, sizeof(double) * Pk);
         e = cudaMemcpyAsync(d_theta, h_theta, sizeof(double) * Pk, cudaMemcpyHostToDevice, stream);
@@ -856,6 +861,31 @@ int musr_chi2_grad_device(musr_run run, int obj, int mode, const double* theta_d
         return cuda_status(e);
     }
     return run->launch(obj, mode, theta_dev, out_dev, status_dev, st, nullptr);
+}
+
+int musr_chi2_grad_async(musr_run run, int obj, int mode, const double* theta, double* out_dev,
+                         int32_t* status_dev, void* stream) {
+    if (!run || !theta || !out_dev) return MUSR_EINVAL;
+    if (obj != MUSR_CHI2 && obj != MUSR_POISSON) return MUSR_EINVAL;
+    if (mode < MUSR_VALUE || mode > MUSR_VALUE_GRAD_GN) return MUSR_EINVAL;
+    if (run->F > 0 || run->Pk > kInlineParams) return MUSR_ENOTSUP;
+    if (mode == kGN && run->Pk > kMaxGnParams) return MUSR_ENOTSUP;
+    for (int j = 0; j < run->P; ++j)
+        if (!isfinite(theta[j])) return MUSR_ENONFINITE;
+    DeviceGuard g(run->device);
+    cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : run->stream;
+    if (run->K == 0) {
+        cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * run->n_out[mode], st);
+        if (e == cudaSuccess && status_dev) e = cudaMemsetAsync(status_dev, 0, sizeof(int32_t), st);
+        return cuda_status(e);
+    }
+    // theta by value in the launch parameters: immutable, so the whole bin
+    // loop may precede the grid-dependency wait
+    EvalParams p = run->params(obj, mode, nullptr, out_dev, status_dev);
+    p.theta_inline_n = run->Pk;
+    memcpy(p.theta_inline, theta, sizeof(double) * run->Pk);
+    p.pre_wait = 2;
+    return cuda_status(launch_eval(run->sig, mode, run->tl[mode].threads, run->tl[mode].n_tiles, st, p));
 }
 
 int musr_model(musr_run run, const double* theta, float* out, int32_t out_on_device) {

@@ -43,12 +43,31 @@ def test_gradient_workload_32x131072(obj, oobj):
     with Run(lay, d.astype(np.float32)) as run:
         v, g, _ = run.chi2_grad(th, obj)
         vh, gh, H = run.chi2_grad(th, obj, gn=True)
+        # queued host-theta evaluations back to back (as the benchmark times
+        # them: each one's bin loop may overlap the previous one's reduction),
+        # the measured theta between perturbed ones, against the device entry
+        P = lay.n_params
+        ths = [W.perturb(theta, lay.free, 0.01, W.rng(seed + 40 + j)) for j in range(5)]
+        ths[2] = th
+        out = torch.full((5, 1 + P), float("nan"), dtype=torch.float64, device="cuda:0")
+        ref = torch.full((5, 1 + P), float("nan"), dtype=torch.float64, device="cuda:0")
+        st = torch.full((5,), -1, dtype=torch.int32, device="cuda:0")
+        for j in range(5):
+            run.chi2_grad_async(ths[j], out[j], obj, MUSR_VALUE_GRAD, st[j:j + 1])
+        torch.cuda.synchronize()
+        for j in range(5):
+            run.chi2_grad_device(torch.tensor(ths[j], device="cuda:0"), ref[j], obj, MUSR_VALUE_GRAD)
+        torch.cuda.synchronize()
+        qa = out.cpu().numpy()
+        assert np.array_equal(qa, ref.cpu().numpy()) and not st.any().item()
     rv, rg, rH = oracle.gradient(lay, d, th, oobj, with_gn=True)
     assert rel_err(v, rv) <= 1e-6
     assert grad_rel_err(g, rg) <= 1e-4
     assert rel_err(vh, rv) <= 1e-6
     assert grad_rel_err(gh, rg) <= 1e-4
     assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
+    assert rel_err(qa[2, 0], rv) <= 1e-6
+    assert grad_rel_err(qa[2, 1:], rg) <= 1e-4
 
 
 @pytest.mark.parametrize("M", [W.SWEEP_BINS[0], W.SWEEP_BINS[-1]])

@@ -226,6 +226,65 @@ def test_device_path_and_autograd(md_small):
         assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
 
 
+def test_async_entry_queued_back_to_back(md_small):
+    """Host-theta evaluations queued back to back on one stream, each one's
+    staging and bin loop free to run while the previous kernel finishes:
+    every result equals, bit for bit, the device entry's at the same theta
+    (modes and objectives mixed, device-entry calls interleaved), the
+    Gauss-Newton entries without sources come back 0 in a NaN buffer, and the
+    results match the oracle."""
+    torch = pytest.importorskip("torch")
+    lay, theta, th, d = md_small
+    P = lay.n_params
+    n = 1 + P + P * P
+    J = 24
+    dev = torch.device("cuda:0")
+    ths = [W.perturb(theta, lay.free, 0.01, W.rng(300 + j)) for j in range(J)]
+    cases = [((MUSR_CHI2, MUSR_POISSON)[j % 2], j % 3) for j in range(J)]
+    width = [1, 1 + P, n]
+    with Run(lay, d) as run:
+        s = torch.cuda.Stream(device=dev)
+        ths_t = [torch.tensor(t, dtype=torch.float64, device=dev) for t in ths]
+        ref = torch.full((J, n), float("nan"), dtype=torch.float64, device=dev)
+        for j, (obj, mode) in enumerate(cases):
+            run.chi2_grad_device(ths_t[j], ref[j], obj, mode, stream=s.cuda_stream)
+        s.synchronize()
+        out = torch.full((J, n), float("nan"), dtype=torch.float64, device=dev)
+        st = torch.full((J,), -1, dtype=torch.int32, device=dev)
+        mixed = torch.full((J, n), float("nan"), dtype=torch.float64, device=dev)
+        for j, (obj, mode) in enumerate(cases):
+            run.chi2_grad_async(ths[j], out[j], obj, mode, st[j:j + 1], stream=s.cuda_stream)
+            if j % 5 == 0:  # a device-entry call between queued ones
+                run.chi2_grad_device(ths_t[j], mixed[j], obj, mode, stream=s.cuda_stream)
+        s.synchronize()
+        o, r, m = out.cpu().numpy(), ref.cpu().numpy(), mixed.cpu().numpy()
+        assert not st.any().item()
+        for j, (obj, mode) in enumerate(cases):
+            w = width[mode]
+            assert np.array_equal(o[j, :w], r[j, :w]), j
+            assert np.all(np.isnan(o[j, w:]))
+            if j % 5 == 0:
+                assert np.array_equal(m[j, :w], r[j, :w]), j
+        for j in (0, 1, 2, 5):
+            obj, mode = cases[j]
+            rv, rg, rH = oracle.gradient(lay, d, ths[j], (oracle.CHI2, oracle.POISSON)[j % 2], with_gn=True)
+            assert rel_err(o[j, 0], rv) <= 1e-6
+            if mode >= 1:
+                assert grad_rel_err(o[j, 1:1 + P], rg) <= 1e-4
+            if mode == 2:
+                H = o[j, 1 + P:].reshape(P, P)
+                assert np.array_equal(H, H.T)
+                assert np.linalg.norm(H - rH) <= 1e-4 * np.linalg.norm(rH)
+        # host-side checks: nothing is launched
+        bad = ths[0].copy()
+        bad[0] = np.nan
+        with pytest.raises(_lib.MusrError) as ei:
+            run.chi2_grad_async(bad, out[0], MUSR_CHI2, 1)
+        assert ei.value.code == _lib.MUSR_ENONFINITE
+        with pytest.raises(ValueError):
+            run.chi2_grad_async(ths[0][:-1], out[0], MUSR_CHI2, 1)
+
+
 def test_set_data_from_device_fp64(md_small):
     torch = pytest.importorskip("torch")
     lay, theta, th, d = md_small
