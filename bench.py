@@ -744,6 +744,7 @@ def run_ours(args):
     e_start.record(stream)
     for j in range(args.steps):
         step(args.warmup + j)
+    enqueue = time.perf_counter() - wall0
     e_end.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -826,6 +827,7 @@ def run_ours(args):
         "gpu_launches": args.steps,  # one objective kernel launch per step
         "flushed_step_us": _r(flushed_us),
         "device_theta_step_us": _r(device_theta_us),
+        "host_enqueue_us_per_step": _r(1e6 * enqueue / args.steps),
         "pipe_rates_per_s": _short(peaks["rates"]),
     }
     details = {"wall_s": wall}

@@ -184,15 +184,16 @@ class Run:
                         stream=None):
         """theta: host FP64 vector [P], passed by value (reusable on return);
         out_dev: CUDA FP64 tensor, 1 (+P (+P*P)) long; queued on the stream."""
+        # plain integers for the pointers: this call is made once per queued
+        # evaluation and its host cost bounds the queue's rate
         th = np.ascontiguousarray(theta, dtype=np.float64)
         if th.shape != (self.P,):
             raise ValueError(f"theta must hold {self.P} values")
-        st = ctypes.c_void_p(int(stream)) if stream is not None else _torch_stream_ptr()
-        check(_lib.load().musr_chi2_grad_async(
-            self.handle, int(obj), int(mode), th.ctypes.data_as(ctypes.c_void_p),
-            ctypes.c_void_p(out_dev.data_ptr()),
-            ctypes.c_void_p(status_dev.data_ptr()) if status_dev is not None else None, st),
-            "musr_chi2_grad_async")
+        st = int(stream) if stream is not None else _torch_stream_ptr()
+        rc = _lib.load().musr_chi2_grad_async(self.handle, int(obj), int(mode), th.ctypes.data, out_dev.data_ptr(),
+                                             status_dev.data_ptr() if status_dev is not None else None, st)
+        if rc:
+            check(rc, "musr_chi2_grad_async")
 
     # -- synthetic data ------------------------------------------------------
     def generate(self, thetas_dev, rebin, seed, out_dev, sample_offset=0, log1p_out=False,
