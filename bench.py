@@ -425,6 +425,24 @@ def _b2b_us(run, thetas_t, out, obj, mode, stream, steps=50):
     return 1e3 * e0.elapsed_time(e1) / steps
 
 
+def _queued_us(run, thetas, out, obj, mode, stream, steps=50):
+    """Microseconds per evaluation queued back to back through the host-theta
+    entry (theta by value: each evaluation's bin loop may overlap the previous
+    one's reduction), CUDA events around all of them."""
+    import torch
+    rows = [np.ascontiguousarray(t) for t in thetas]
+    n = len(rows)
+    for j in range(5):
+        run.chi2_grad_async(rows[j % n], out, obj, mode, stream=stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for j in range(steps):
+        run.chi2_grad_async(rows[j % n], out, obj, mode, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / steps
+
+
 def other_configs(rank, peaks, flush, stream):
     """The remaining workloads of the measurement plan, each a small extra:
     the 16 x 65536 workload (chi2 + gradient, Gauss-Newton, value, deviance;
@@ -452,10 +470,13 @@ def other_configs(rank, peaks, flush, stream):
         t_dev = _flushed_us(run, ths, out, MUSR_POISSON, MUSR_VALUE_GRAD, flush, stream)
         t_b2b = _b2b_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD, stream)
         t_b2b_gn = _b2b_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD_GN, stream)
+        t_q = _queued_us(run, ths.cpu().numpy(), out, MUSR_CHI2, MUSR_VALUE_GRAD, stream)
+        t_q_gn = _queued_us(run, ths.cpu().numpy(), out, MUSR_CHI2, MUSR_VALUE_GRAD_GN, stream)
     rl = roofline(lay.total_bins, t_grad * 1e-6, peaks, ALG_FP32_FLOP_PER_BIN, ALG_SFU_PER_BIN, ALG_BYTES_PER_BIN)
     res["cfg_16x65536"] = {"chi2_grad_us": t_grad, "bin_evals_per_s": lay.total_bins / (t_grad * 1e-6),
                            "frac": rl["frac"], "pipe": rl["pipe"], "gn_us": t_gn, "value_us": t_val,
-                           "deviance_grad_us": t_dev, "chi2_grad_us_b2b_l2": t_b2b, "gn_us_b2b_l2": t_b2b_gn}
+                           "deviance_grad_us": t_dev, "chi2_grad_us_b2b_l2": t_b2b, "gn_us_b2b_l2": t_b2b_gn,
+                           "chi2_grad_us_queued_l2": t_q, "gn_us_queued_l2": t_q_gn}
     # Gauss-Newton mode on the headline shape (what every LM iteration evaluates)
     lay, theta, seed = W.config_gradient()
     with Run(lay) as m:
@@ -467,6 +488,8 @@ def other_configs(rank, peaks, flush, stream):
     data = W.poisson_counts(mean, seed + rank)
     with Run(lay, torch.tensor(data, dtype=torch.float32, device=dev)) as run:
         res["cfg_32x131072_gn_us"] = _flushed_us(run, ths, out, MUSR_CHI2, MUSR_VALUE_GRAD_GN, flush, stream)
+        res["cfg_32x131072_gn_us_queued_l2"] = _queued_us(run, ths.cpu().numpy(), out, MUSR_CHI2,
+                                                          MUSR_VALUE_GRAD_GN, stream)
         starts = [W.perturb(theta, lay.free, 0.01, g) for _ in range(5)]
         res["cfg_32x131072_fits"] = {
             "lm_adjoint_gn": _fit_rate(run, starts, MUSR_CHI2, lay.free, MUSR_FIT_LM),
@@ -837,8 +860,10 @@ def run_ours(args):
         line["cfg_16x65536"] = _short(
             {"chi2_grad_us_flushed": c2["chi2_grad_us"], "chi2_grad_us_b2b_l2": c2["chi2_grad_us_b2b_l2"],
              "gn_us_flushed": c2["gn_us"], "gn_us_b2b_l2": c2["gn_us_b2b_l2"], "value_us_flushed": c2["value_us"],
-             "deviance_grad_us_flushed": c2["deviance_grad_us"]})
+             "deviance_grad_us_flushed": c2["deviance_grad_us"], "chi2_grad_us_queued_l2": c2["chi2_grad_us_queued_l2"],
+             "gn_us_queued_l2": c2["gn_us_queued_l2"]})
         line["cfg_32x131072_gn_us"] = _r(others["cfg_32x131072_gn_us"])
+        line["cfg_32x131072_gn_us_queued_l2"] = _r(others["cfg_32x131072_gn_us_queued_l2"])
         f4 = others["cfg_32x131072_fits"]
         line["cfg_32x131072_fits_per_s"] = _short({k: v["fits_per_s"] for k, v in f4.items()})
     if batched:

@@ -194,6 +194,15 @@ __host__ __device__ constexpr int stage_parts() {
 
 // stripe > 0: bins between a thread's consecutive chunks (for the Gaussian
 // ratio carried from chunk to chunk, see GqCarry); 0 when nothing is carried.
+// Out-of-line copies of the staging's functions: the staging runs once per
+// block, and an inlined copy at every call site multiplies the prologue's
+// code, which a block fetches cold while the other block on its SM runs the
+// bin loop.
+static __device__ __noinline__ float stage_expm1(float x) { return step_expm1(x); }
+static __device__ __noinline__ float stage_sinpi(float x) { return step_sinpi(x); }
+static __device__ __noinline__ unsigned long long stage_fixmul(double x, ulonglong2 c) { return fixmul(x, c); }
+static __device__ __noinline__ float stage_exp(float x) { return expf(x); }
+
 template <int NE, int NG, int NS, int KT, class TH>
 __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst& hc, int stripe = 0) {
     constexpr int NOSC = NE + NG + NS;
@@ -224,10 +233,10 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
                 o.a_hi = a.hi;
                 o.a_lo = a.lo;
                 o.b_hi = o.b_lo = 0.f;
-                o.q = step_expm1(-df_mul(rtot, dt).hi);
+                o.q = stage_expm1(-df_mul(rtot, dt).hi);
                 o.q2 = o.q * (2.f + o.q);
                 o.qs = o.qs2 = 0.f;
-                o.cenv = rc.t0_zero ? 1.f : expf(-df_mul(rtot, df_of(rc.t0)).hi);
+                o.cenv = rc.t0_zero ? 1.f : stage_exp(-df_mul(rtot, df_of(rc.t0)).hi);
             } else {  // exp(-t/tau - sigma^2 t^2 / 2), t = t0 + n dt
                 const DF s2 = df_mul(rate, rate);
                 const DF a = df_add(df_mul(it, dtL), df_mul(s2, df_of(rc.t0_dt_log2e)));
@@ -236,33 +245,33 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
                 o.a_lo = a.lo;
                 o.b_hi = b.hi;
                 o.b_lo = b.lo;
-                o.q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));  // 2^(-2 b) - 1
-                o.qs = step_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
-                o.q2 = step_expm1(-5.54517744447956247532f * (b.hi + b.lo));  // 2^(-8 b) - 1
-                o.qs2 = step_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
+                o.q = stage_expm1(-1.38629436111989061883f * (b.hi + b.lo));  // 2^(-2 b) - 1
+                o.qs = stage_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
+                o.q2 = stage_expm1(-5.54517744447956247532f * (b.hi + b.lo));  // 2^(-8 b) - 1
+                o.qs2 = stage_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
                 if (rc.t0_zero) {
                     o.cenv = 1.f;
                 } else {
                     const DF t0 = df_of(rc.t0);
                     const DF x = df_add(df_mul(t0, it), df_mul(df_mul(s2, t0), DF{0.5f * t0.hi, 0.5f * t0.lo}));
-                    o.cenv = expf(-x.hi);
+                    o.cenv = stage_exp(-x.hi);
                 }
             }
         } else {  // phase: sums of fixed-point products are exact mod 1 turn
             // an absent entry reads 0, whose fixed-point product is 0
             const double f0 = th(2 * (r + 2)), f1 = th(2 * (r + 2) + 1), phi = th(2 * (r + 3));
-            unsigned long long step = fixmul(f0, rc.turns_per_bin) + fixmul(f1, rc.turns_per_bin);
-            unsigned long long ph0 = fixmul(phi, rc.inv_two_pi);
-            if (!rc.t0_zero) ph0 += fixmul(f0, rc.turns_at_t0) + fixmul(f1, rc.turns_at_t0);
+            unsigned long long step = stage_fixmul(f0, rc.turns_per_bin) + stage_fixmul(f1, rc.turns_per_bin);
+            unsigned long long ph0 = stage_fixmul(phi, rc.inv_two_pi);
+            if (!rc.t0_zero) ph0 += stage_fixmul(f0, rc.turns_at_t0) + stage_fixmul(f1, rc.turns_at_t0);
             o.ph0 = ph0;
             o.step = step;
             o.step_s = step * (unsigned long long)stripe;  // mod 2^64: whole turns drop out
             const float red = (float)(long long)step * 5.42101086242752217e-20f;  // turns in [-1/2, 1/2)
-            const float sh = step_sinpi(red);
+            const float sh = stage_sinpi(red);
             o.cm1 = -2.f * sh * sh;        // cos(step) - 1
-            o.sn = step_sinpi(2.f * red);  // sin(step)
+            o.sn = stage_sinpi(2.f * red);  // sin(step)
             o.cm1_2 = -2.f * o.sn * o.sn;  // cos(2 step) - 1
-            o.sn_2 = step_sinpi(4.f * red);
+            o.sn_2 = stage_sinpi(4.f * red);
         }
     } else if (KT && part == 2 * NOSC + 1) {
         const int r = 2 + 4 * NOSC + NS;
@@ -276,16 +285,16 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
         hc.kt_a_lo = a.lo;
         hc.kt_b_hi = b.hi;
         hc.kt_b_lo = b.lo;
-        hc.kt_q = step_expm1(-1.38629436111989061883f * (b.hi + b.lo));
-        hc.kt_qs = step_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
-        hc.kt_q2 = step_expm1(-5.54517744447956247532f * (b.hi + b.lo));
-        hc.kt_qs2 = step_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
+        hc.kt_q = stage_expm1(-1.38629436111989061883f * (b.hi + b.lo));
+        hc.kt_qs = stage_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
+        hc.kt_q2 = stage_expm1(-5.54517744447956247532f * (b.hi + b.lo));
+        hc.kt_qs2 = stage_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
         if (rc.t0_zero) {
             hc.kt_cenv = 1.f;
         } else {
             const DF t0 = df_of(rc.t0);
             const DF x = df_add(df_mul(t0, it), df_mul(df_mul(s2, t0), DF{0.5f * t0.hi, 0.5f * t0.lo}));
-            hc.kt_cenv = expf(-x.hi);
+            hc.kt_cenv = stage_exp(-x.hi);
         }
     }
 }
@@ -436,6 +445,34 @@ __device__ __forceinline__ float lifetime_from_table(const float* etab, int n0, 
     return E;
 }
 
+// 2-bin ratio minus 1 of a Gaussian envelope exp2(-(a n + b n^2)) at bin n:
+// 2^(-(2 a + 4 b (n + 1))) - 1.
+__device__ __forceinline__ float gauss_ratio2(float a_hi, float a_lo, float b_hi, float b_lo, int n) {
+    const float k4 = 4.f * (float)(n + 1);
+    return step_expm1(-0.693147180559945309f * fmaf(k4, b_hi, fmaf(k4, b_lo, 2.f * (a_hi + a_lo))));
+}
+
+// First-chunk seeds of a Gaussian ratio recurrence (a Gaussian envelope or
+// the Kubo-Toyabe term), exp2(-(a n + b n^2)) at bin n0: the 1-bin ratio
+// minus 1, 2^(-(a + b (2 n0 + 1))) - 1, and the 2-bin ratios at n0 and n0 + 1.
+// Out of line: a thread that carries the ratios from chunk to chunk computes
+// them once, and inlined copies would enlarge the bin loop's code.
+struct GaussSeed {
+    float q1, r0, r1;
+};
+static __device__ __noinline__ float gauss_seed1(float a_hi, float a_lo, float b_hi, float b_lo, int n0) {
+    const float k1 = fmaf(2.f, (float)n0, 1.f);
+    return step_expm1(-0.693147180559945309f * fmaf(k1, b_hi, fmaf(k1, b_lo, a_hi + a_lo)));
+}
+static __device__ __noinline__ GaussSeed gauss_seed(float a_hi, float a_lo, float b_hi, float b_lo, int n0) {
+    const float k1 = fmaf(2.f, (float)n0, 1.f);
+    GaussSeed g;
+    g.q1 = step_expm1(-0.693147180559945309f * fmaf(k1, b_hi, fmaf(k1, b_lo, a_hi + a_lo)));
+    g.r0 = gauss_ratio2(a_hi, a_lo, b_hi, b_lo, n0);
+    g.r1 = gauss_ratio2(a_hi, a_lo, b_hi, b_lo, n0 + 1);
+    return g;
+}
+
 // E0: the lifetime factor exp(-t/tau) at bin n0 (from the run's lifetime table)
 template <int NE, int NG, int NS, int KT, int MODE, int NACC, bool FULL>
 __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int M,
@@ -475,6 +512,8 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
             env = o.cenv * ex2_approx(-fmaf(nn0, o.b_hi, fmaf(nf0, o.a_hi, fmaf(nn0, o.b_lo, nf0 * o.a_lo))));
             if (carry && carry->valid) {
                 gq[c] = carry->gq[c];
+            } else if (carry) {  // once per thread: out of line
+                gq[c] = gauss_seed1(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0);
             } else {
                 gq[c] = step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
             }
@@ -499,6 +538,8 @@ __device__ __forceinline__ void eval_chunk_body(const HistConst& hc, int n0, int
               ex2_approx(-fmaf(nn0, hc.kt_b_hi, fmaf(nf0, hc.kt_a_hi, fmaf(nn0, hc.kt_b_lo, nf0 * hc.kt_a_lo))));
         if (carry && carry->valid) {
             gqk = carry->gqk;
+        } else if (carry) {  // once per thread: out of line
+            gqk = gauss_seed1(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0);
         } else {
             gqk = step_expm1(-0.693147180559945309f *
                              fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
@@ -729,12 +770,6 @@ struct G2Carry {
     bool valid;
 };
 
-// 2-bin ratio minus 1 of a Gaussian envelope exp2(-(a n + b n^2)) at bin n:
-// 2^(-(2 a + 4 b (n + 1))) - 1.
-__device__ __forceinline__ float gauss_ratio2(float a_hi, float a_lo, float b_hi, float b_lo, int n) {
-    const float k4 = 4.f * (float)(n + 1);
-    return step_expm1(-0.693147180559945309f * fmaf(k4, b_hi, fmaf(k4, b_lo, 2.f * (a_hi + a_lo))));
-}
 
 // One chunk of 8 bins starting at n0 (a multiple of 8) in packed lanes:
 // MODE kValue or kGrad.  d holds the chunk's counts, E0 the lifetime factor at
@@ -758,7 +793,6 @@ __device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int 
     const float2 qE2 = bc2(hc.qE2);
     float2 C[NOSC > 0 ? NOSC : 1], Sn[NOSC > 0 ? NOSC : 1], g2[NOSC > 0 ? NOSC : 1];
     float2 stA[NOSC > 0 ? NOSC : 1], stB[NOSC > 0 ? NOSC : 1], nstB[NOSC > 0 ? NOSC : 1];
-    const float k1 = fmaf(2.f, nf0, 1.f);  // 2 n0 + 1
     const float nn0 = nf0 * nf0;
     const bool carried = carry && carry->valid;
 #pragma unroll
@@ -787,17 +821,17 @@ __device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int 
         } else {
             env = o.cenv * ex2_approx(-fmaf(nn0, o.b_hi, fmaf(nf0, o.a_hi, fmaf(nn0, o.b_lo, nf0 * o.a_lo))));
             // 1-bin ratio at n0 (lane y's seed), then both lanes' 2-bin ratios
-            const float gq1 =
-                carried ? carry->gq1[c]
-                        : step_expm1(-0.693147180559945309f * fmaf(k1, o.b_hi, fmaf(k1, o.b_lo, o.a_hi + o.a_lo)));
-            if (carry) carry->gq1[c] = fmaf(gq1, o.qs, gq1 + o.qs);
-            envy = fmaf(env, gq1, env);
+            float gq1;
             if (carried) {
+                gq1 = carry->gq1[c];
                 g2[c] = carry->g2[c];
             } else {
-                g2[c] = make_float2(gauss_ratio2(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0),
-                                    gauss_ratio2(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0 + 1));
+                const GaussSeed sd = gauss_seed(o.a_hi, o.a_lo, o.b_hi, o.b_lo, n0);
+                gq1 = sd.q1;
+                g2[c] = make_float2(sd.r0, sd.r1);
             }
+            if (carry) carry->gq1[c] = fmaf(gq1, o.qs, gq1 + o.qs);
+            envy = fmaf(env, gq1, env);
             if (carry) carry->g2[c] = fma2(g2[c], bc2(o.qs2), add2(g2[c], bc2(o.qs2)));
             stA[c] = bc2(o.cm1_2);
             stB[c] = bc2(o.sn_2);
@@ -812,18 +846,17 @@ __device__ __forceinline__ void eval_pair_body(const HistConst& hc, int n0, int 
     if (KT) {
         const float ex = 0.666666667f * hc.kt_cenv *
                          ex2_approx(-fmaf(nn0, hc.kt_b_hi, fmaf(nf0, hc.kt_a_hi, fmaf(nn0, hc.kt_b_lo, nf0 * hc.kt_a_lo))));
-        const float gq1 =
-            carried ? carry->gqk1
-                    : step_expm1(-0.693147180559945309f *
-                                 fmaf(k1, hc.kt_b_hi, fmaf(k1, hc.kt_b_lo, hc.kt_a_hi + hc.kt_a_lo)));
-        if (carry) carry->gqk1 = fmaf(gq1, hc.kt_qs, gq1 + hc.kt_qs);
-        e23 = make_float2(ex, fmaf(ex, gq1, ex));
+        float gq1;
         if (carried) {
+            gq1 = carry->gqk1;
             g2k = carry->g2k;
         } else {
-            g2k = make_float2(gauss_ratio2(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0),
-                              gauss_ratio2(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0 + 1));
+            const GaussSeed sd = gauss_seed(hc.kt_a_hi, hc.kt_a_lo, hc.kt_b_hi, hc.kt_b_lo, n0);
+            gq1 = sd.q1;
+            g2k = make_float2(sd.r0, sd.r1);
         }
+        if (carry) carry->gqk1 = fmaf(gq1, hc.kt_qs, gq1 + hc.kt_qs);
+        e23 = make_float2(ex, fmaf(ex, gq1, ex));
         if (carry) carry->g2k = fma2(g2k, bc2(hc.kt_qs2), add2(g2k, bc2(hc.kt_qs2)));
         const float r2 = hc.kt_rate * hc.kt_rate;
         kr2 = bc2(r2);
