@@ -192,8 +192,6 @@ __host__ __device__ constexpr int stage_parts() {
     return 2 + 2 * (NE + NG + NS);
 }
 
-// stripe > 0: bins between a thread's consecutive chunks (for the Gaussian
-// ratio carried from chunk to chunk, see GqCarry); 0 when nothing is carried.
 // Out-of-line copies of the staging's functions: the staging runs once per
 // block, and an inlined copy at every call site multiplies the prologue's
 // code, which a block fetches cold while the other block on its SM runs the
@@ -203,8 +201,70 @@ static __device__ __noinline__ float stage_sinpi(float x) { return step_sinpi(x)
 static __device__ __noinline__ unsigned long long stage_fixmul(double x, ulonglong2 c) { return fixmul(x, c); }
 static __device__ __noinline__ float stage_exp(float x) { return expf(x); }
 
+// N independent evaluations of a staging function: by one thread in turn
+// (lane < 0), or by the lanes of a warp at once, lane j evaluating the j-th
+// (every lane of the warp takes part, and every lane receives all N results).
+// Both ways evaluate the same function on the same arguments.
+template <int N>
+__device__ __forceinline__ void stage_expm1_n(const float (&x)[N], float (&y)[N], int lane) {
+    if (lane < 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) y[j] = stage_expm1(x[j]);
+        return;
+    }
+    float xi = x[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+        if (lane == j) xi = x[j];
+    const float yi = stage_expm1(xi);
+#pragma unroll
+    for (int j = 0; j < N; ++j) y[j] = __shfl_sync(0xffffffffu, yi, j);
+}
+template <int N>
+__device__ __forceinline__ void stage_sinpi_n(const float (&x)[N], float (&y)[N], int lane) {
+    if (lane < 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) y[j] = stage_sinpi(x[j]);
+        return;
+    }
+    float xi = x[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+        if (lane == j) xi = x[j];
+    const float yi = stage_sinpi(xi);
+#pragma unroll
+    for (int j = 0; j < N; ++j) y[j] = __shfl_sync(0xffffffffu, yi, j);
+}
+// the first n of N products (all N by a warp: the lanes beyond n cost nothing)
+template <int N>
+__device__ __forceinline__ void stage_fixmul_n(const double (&x)[N], const ulonglong2 (&c)[N],
+                                               unsigned long long (&y)[N], int n, int lane) {
+    if (lane < 0) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) y[j] = j < n ? stage_fixmul(x[j], c[j]) : 0ull;
+        return;
+    }
+    double xi = x[0];
+    ulonglong2 ci = c[0];
+#pragma unroll
+    for (int j = 1; j < N; ++j)
+        if (lane == j) {
+            xi = x[j];
+            ci = c[j];
+        }
+    const unsigned long long yi = stage_fixmul(xi, ci);
+#pragma unroll
+    for (int j = 0; j < N; ++j) y[j] = j < n ? __shfl_sync(0xffffffffu, yi, j) : 0ull;
+}
+
+// stripe > 0: bins between a thread's consecutive chunks (for the Gaussian
+// ratio carried from chunk to chunk, see GqCarry); 0 when nothing is carried.
+// lane < 0: one thread stages the part; lane >= 0: all 32 lanes of a warp
+// call with the same part and their lane index, and share its independent
+// function evaluations (every lane stores the same values).
 template <int NE, int NG, int NS, int KT, class TH>
-__device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst& hc, int stripe = 0) {
+__device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst& hc, int stripe = 0,
+                           int lane = -1) {
     constexpr int NOSC = NE + NG + NS;
     const DF it = df_of(rc.inv_tau), dtL = df_of(rc.dt_log2e), dt = df_of(rc.dt);
     if (part == 0) {
@@ -245,10 +305,17 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
                 o.a_lo = a.lo;
                 o.b_hi = b.hi;
                 o.b_lo = b.lo;
-                o.q = stage_expm1(-1.38629436111989061883f * (b.hi + b.lo));  // 2^(-2 b) - 1
-                o.qs = stage_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
-                o.q2 = stage_expm1(-5.54517744447956247532f * (b.hi + b.lo));  // 2^(-8 b) - 1
-                o.qs2 = stage_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
+                // 2^(-2 b) - 1, its change over a stripe, 2^(-8 b) - 1, the 2-bin change over a stripe
+                const float xq[4] = {-1.38629436111989061883f * (b.hi + b.lo),
+                                     -1.38629436111989061883f * (float)stripe * (b.hi + b.lo),
+                                     -5.54517744447956247532f * (b.hi + b.lo),
+                                     -2.77258872223978123767f * (float)stripe * (b.hi + b.lo)};
+                float yq[4];
+                stage_expm1_n<4>(xq, yq, lane);
+                o.q = yq[0];
+                o.qs = yq[1];
+                o.q2 = yq[2];
+                o.qs2 = yq[3];
                 if (rc.t0_zero) {
                     o.cenv = 1.f;
                 } else {
@@ -260,18 +327,24 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
         } else {  // phase: sums of fixed-point products are exact mod 1 turn
             // an absent entry reads 0, whose fixed-point product is 0
             const double f0 = th(2 * (r + 2)), f1 = th(2 * (r + 2) + 1), phi = th(2 * (r + 3));
-            unsigned long long step = stage_fixmul(f0, rc.turns_per_bin) + stage_fixmul(f1, rc.turns_per_bin);
-            unsigned long long ph0 = stage_fixmul(phi, rc.inv_two_pi);
-            if (!rc.t0_zero) ph0 += stage_fixmul(f0, rc.turns_at_t0) + stage_fixmul(f1, rc.turns_at_t0);
+            const double xf[5] = {f0, f1, phi, f0, f1};
+            const ulonglong2 cf[5] = {rc.turns_per_bin, rc.turns_per_bin, rc.inv_two_pi, rc.turns_at_t0,
+                                      rc.turns_at_t0};
+            unsigned long long yf[5];
+            stage_fixmul_n<5>(xf, cf, yf, rc.t0_zero ? 3 : 5, lane);
+            const unsigned long long step = yf[0] + yf[1];
+            const unsigned long long ph0 = yf[2] + (yf[3] + yf[4]);
             o.ph0 = ph0;
             o.step = step;
             o.step_s = step * (unsigned long long)stripe;  // mod 2^64: whole turns drop out
             const float red = (float)(long long)step * 5.42101086242752217e-20f;  // turns in [-1/2, 1/2)
-            const float sh = stage_sinpi(red);
-            o.cm1 = -2.f * sh * sh;        // cos(step) - 1
-            o.sn = stage_sinpi(2.f * red);  // sin(step)
-            o.cm1_2 = -2.f * o.sn * o.sn;  // cos(2 step) - 1
-            o.sn_2 = stage_sinpi(4.f * red);
+            const float xs[3] = {red, 2.f * red, 4.f * red};
+            float ys[3];
+            stage_sinpi_n<3>(xs, ys, lane);
+            o.cm1 = -2.f * ys[0] * ys[0];    // cos(step) - 1
+            o.sn = ys[1];                    // sin(step)
+            o.cm1_2 = -2.f * ys[1] * ys[1];  // cos(2 step) - 1
+            o.sn_2 = ys[2];
         }
     } else if (KT && part == 2 * NOSC + 1) {
         const int r = 2 + 4 * NOSC + NS;
@@ -285,10 +358,16 @@ __device__ void stage_part(int part, const TH& th, const RunConst& rc, HistConst
         hc.kt_a_lo = a.lo;
         hc.kt_b_hi = b.hi;
         hc.kt_b_lo = b.lo;
-        hc.kt_q = stage_expm1(-1.38629436111989061883f * (b.hi + b.lo));
-        hc.kt_qs = stage_expm1(-1.38629436111989061883f * (float)stripe * (b.hi + b.lo));
-        hc.kt_q2 = stage_expm1(-5.54517744447956247532f * (b.hi + b.lo));
-        hc.kt_qs2 = stage_expm1(-2.77258872223978123767f * (float)stripe * (b.hi + b.lo));
+        const float xq[4] = {-1.38629436111989061883f * (b.hi + b.lo),
+                             -1.38629436111989061883f * (float)stripe * (b.hi + b.lo),
+                             -5.54517744447956247532f * (b.hi + b.lo),
+                             -2.77258872223978123767f * (float)stripe * (b.hi + b.lo)};
+        float yq[4];
+        stage_expm1_n<4>(xq, yq, lane);
+        hc.kt_q = yq[0];
+        hc.kt_qs = yq[1];
+        hc.kt_q2 = yq[2];
+        hc.kt_qs2 = yq[3];
         if (rc.t0_zero) {
             hc.kt_cenv = 1.f;
         } else {
@@ -1209,11 +1288,12 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
     }
 
     // stage histogram k's constants: one part per warp, so the parts' latency
-    // chains overlap
+    // chains overlap, and a part's independent function evaluations spread
+    // over the warp's lanes
     {
         constexpr int NPART = stage_parts<NE, NG, NS, KT>();
         for (int part = warp; part < NPART; part += nwarps)
-            if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaGathered{s_th}, p.rc, hc, (int)blockDim.x * G);
+            stage_part<NE, NG, NS, KT>(part, ThetaGathered{s_th}, p.rc, hc, (int)blockDim.x * G, lane);
     }
     __syncthreads();
 
