@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kMaxThreads, MODE == kGrad ? 3 : 1) gbatch_ker
         }
         if (act) {
             for (int part = warp; part < NPART; part += nwarps)
-                if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaGathered{wth[cur]}, W.rc, hc, stripe);
+                stage_part<NE, NG, NS, KT>(part, ThetaGathered{wth[cur]}, W.rc, hc, stripe, lane);
         }
         __syncthreads();
 

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kMaxThreads) generate_kernel(const __grid_cons
         const double* theta = p.thetas + s * p.P;
         const int32_t* rt = p.role_theta + (size_t)k * kMaxRoles * 2;
         for (int part = warp; part < NPART; part += nwarps)
-            if (lane == 0) stage_part<NE, NG, NS, KT>(part, ThetaByRow{rt, theta}, p.rc, hc);
+            stage_part<NE, NG, NS, KT>(part, ThetaByRow{rt, theta}, p.rc, hc, 0, lane);
     }
     __syncthreads();
     const int M = p.hist_nbins[k];
