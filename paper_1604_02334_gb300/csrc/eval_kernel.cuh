@@ -1230,7 +1230,14 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
     // read before it has completed (griddepcontrol.wait); what is read earlier
     // is immutable (pre_wait, see EvalParams).  Every thread waits before the
     // block's first global write.
+    // the tile's launch parameters are read together, ahead of the wait (a
+    // launch's parameters never change): their first reads miss the constant
+    // cache, and one miss after another would add up
     const int pre_wait = MODE == kModel ? 0 : p.pre_wait;
+    const unsigned uni_tph = (unsigned)p.uni_tph, uni_chunks = (unsigned)p.uni_chunks;
+    const int uni_nbins = p.uni_nbins;
+    const int64_t uni_stride = p.uni_stride;
+    const float* const data = p.data;
     if (pre_wait == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
     // the next grid in the stream may be launched at once: its blocks take SM
     // slots as this grid's blocks leave them (every kernel of this library
@@ -1239,13 +1246,15 @@ __global__ void __launch_bounds__(MODE == kGN ? kMaxThreadsGn : kMaxThreads) eva
     const int tile = blockIdx.x;
     int k, M, tstart, tend;
     const float* hdata;
-    if (p.uni_tph > 0) {
-        k = tile / p.uni_tph;
-        M = p.uni_nbins;
-        const int64_t j = tile - k * p.uni_tph;
-        tstart = (int)(j * p.uni_chunks / p.uni_tph) * G;
-        tend = (int)((j + 1) * p.uni_chunks / p.uni_tph) * G;
-        hdata = p.data + (int64_t)k * p.uni_stride;
+    if (uni_tph > 0) {
+        // chunk range [j C / T, (j + 1) C / T) in 32-bit arithmetic: the host
+        // sets this form only when C T < 2^32
+        const unsigned kk = (unsigned)tile / uni_tph, j = (unsigned)tile - kk * uni_tph;
+        k = (int)kk;
+        M = uni_nbins;
+        tstart = (int)(j * uni_chunks / uni_tph) * G;
+        tend = (int)((j + 1) * uni_chunks / uni_tph) * G;
+        hdata = data + (int64_t)k * uni_stride;
     } else {
         k = p.tile_hist[tile];
         M = p.hist_nbins[k];

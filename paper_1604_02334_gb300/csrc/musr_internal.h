@@ -202,7 +202,8 @@ struct EvalParams {
     // of it, j = b mod uni_tph, C = uni_chunks (8-bin chunks per histogram);
     // histogram k starts at float k * uni_stride.  The tile and histogram
     // tables are then not read, which takes two dependent memory round trips
-    // off the start of every block.  0: use the tables.
+    // off the start of every block.  0: use the tables.  Set only when
+    // C * uni_tph < 2^32 (the kernel divides in 32-bit arithmetic).
     int uni_tph, uni_chunks, uni_nbins;
     int64_t uni_stride;
     // role -> theta rows of the first kInlineRoleHist histograms (when K fits),

@@ -612,7 +612,8 @@ EvalParams musr_run_s::params(int obj, int mode, const double* theta_dev, double
     p.csr_in_smem = csr_in_smem[m];
     p.smem_bytes = mode == kModel ? 0 : smem_bytes[m];
     // equal-length histograms: tiles and offsets by arithmetic (see EvalParams)
-    if (T.uni_tph > 0 && n_bins[0] + kBinsPerThread * (int64_t)T.threads < (int64_t)1 << 30) {
+    if (T.uni_tph > 0 && n_bins[0] + kBinsPerThread * (int64_t)T.threads < (int64_t)1 << 30 &&
+        (n_bins[0] + kBinsPerThread - 1) / kBinsPerThread * (int64_t)T.uni_tph < (int64_t)1 << 32) {
         p.uni_tph = T.uni_tph;
         p.uni_chunks = (int)((n_bins[0] + kBinsPerThread - 1) / kBinsPerThread);
         p.uni_nbins = (int)n_bins[0];
