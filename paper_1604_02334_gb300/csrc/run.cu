@@ -392,6 +392,17 @@ int musr_run_s::allocate() {
             }
         }
         build_tiles(tl[m], best_t, best_tph);
+        // Queued evaluations overlap one another, so their rate is set by the
+        // SM time their blocks hold, not by one launch's busiest SM: they take
+        // the fewest tiles whose threads get no more chunks each (every tile
+        // fewer is one staging and one reduction fewer).  One launch alone is
+        // better served by more, shorter tiles, which spread the bins over
+        // more SMs.
+        if (tl[m].uni_tph > 0) {
+            const int64_t ck = (n_bins[0] + kBinsPerThread - 1) / kBinsPerThread, t = tl[m].threads;
+            const int64_t per_thread = ((ck + tl[m].uni_tph - 1) / tl[m].uni_tph + t - 1) / t;
+            tl[m].uni_tph_queued = (int)std::max<int64_t>(1, (ck + per_thread * t - 1) / (per_thread * t));
+        }
 
         if (m < 3) smem_bytes[m] = tail_smem(m, &hsum_in_smem[m], &csr_in_smem[m]);
     }
@@ -886,7 +897,12 @@ int musr_chi2_grad_async(musr_run run, int obj, int mode, const double* theta, d
     p.theta_inline_n = run->Pk;
     memcpy(p.theta_inline, theta, sizeof(double) * run->Pk);
     p.pre_wait = 2;
-    return cuda_status(launch_eval(run->sig, mode, run->tl[mode].threads, run->tl[mode].n_tiles, st, p));
+    int n_tiles = run->tl[mode].n_tiles;
+    if (p.uni_tph > 0 && run->tl[mode].uni_tph_queued > 0) {  // equal histograms: the queued tiling
+        p.uni_tph = run->tl[mode].uni_tph_queued;
+        n_tiles = run->K * p.uni_tph;
+    }
+    return cuda_status(launch_eval(run->sig, mode, run->tl[mode].threads, n_tiles, st, p));
 }
 
 int musr_model(musr_run run, const double* theta, float* out, int32_t out_on_device) {

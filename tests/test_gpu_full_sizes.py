@@ -44,8 +44,10 @@ def test_gradient_workload_32x131072(obj, oobj):
         v, g, _ = run.chi2_grad(th, obj)
         vh, gh, H = run.chi2_grad(th, obj, gn=True)
         # queued host-theta evaluations back to back (as the benchmark times
-        # them: each one's bin loop may overlap the previous one's reduction),
-        # the measured theta between perturbed ones, against the device entry
+        # them: each one's bin loop may overlap the previous one's reduction,
+        # in the queued tiling), the measured theta between perturbed ones,
+        # against the device entry (FP32 lane sums round differently between
+        # tilings: value 1e-6, gradient 1e-5) and the oracle
         P = lay.n_params
         ths = [W.perturb(theta, lay.free, 0.01, W.rng(seed + 40 + j)) for j in range(5)]
         ths[2] = th
@@ -58,8 +60,11 @@ def test_gradient_workload_32x131072(obj, oobj):
         for j in range(5):
             run.chi2_grad_device(torch.tensor(ths[j], device="cuda:0"), ref[j], obj, MUSR_VALUE_GRAD)
         torch.cuda.synchronize()
-        qa = out.cpu().numpy()
-        assert np.array_equal(qa, ref.cpu().numpy()) and not st.any().item()
+        qa, qr = out.cpu().numpy(), ref.cpu().numpy()
+        assert not st.any().item()
+        for j in range(5):
+            assert rel_err(qa[j, 0], qr[j, 0]) <= 1e-6
+            assert grad_rel_err(qa[j, 1:], qr[j, 1:]) <= 1e-5
     rv, rg, rH = oracle.gradient(lay, d, th, oobj, with_gn=True)
     assert rel_err(v, rv) <= 1e-6
     assert grad_rel_err(g, rg) <= 1e-4
