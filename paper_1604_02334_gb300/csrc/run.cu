@@ -356,6 +356,7 @@ int musr_run_s::allocate() {
         if (total_bins >= (int64_t)2 * dev_sms * kMaxThreads * kBinsPerThread)
             while (t_min < kMaxThreads && t_min < 32 * (2 + 2 * sig.n_osc())) t_min <<= 1;
         int best_t = kMaxThreads;
+        int64_t best_slots = 1;
         std::vector<int64_t> best_tph;
         int64_t best_cost = INT64_MAX;
         // block sizes 256, 128, ..., t_min; the Gauss-Newton mode tries 384 first
@@ -389,19 +390,26 @@ int musr_run_s::allocate() {
                 best_cost = cost;
                 best_t = t;
                 best_tph = tph;
+                best_slots = slots;
             }
         }
         build_tiles(tl[m], best_t, best_tph);
         // Queued evaluations overlap one another, so their rate is set by the
-        // SM time their blocks hold, not by one launch's busiest SM: they take
-        // the fewest tiles whose threads get no more chunks each (every tile
-        // fewer is one staging and one reduction fewer).  One launch alone is
-        // better served by more, shorter tiles, which spread the bins over
-        // more SMs.
+        // SM time their blocks hold, not by one launch's busiest SM: every
+        // tile fewer is one staging and one reduction fewer, and the next
+        // evaluations' blocks fill the slots a launch leaves free.  When the
+        // planner's tiles fit in one wave they take tiles of twice the chunks
+        // a thread (up to 16), else as many chunks a thread (measured: longer
+        // blocks lengthen the chain of dependent reductions once a launch
+        // spans waves), in the fewest tiles that give no thread more.  One
+        // launch alone is better served by the planner's tiles, which spread
+        // the bins over more SMs.
         if (tl[m].uni_tph > 0) {
             const int64_t ck = (n_bins[0] + kBinsPerThread - 1) / kBinsPerThread, t = tl[m].threads;
             const int64_t per_thread = ((ck + tl[m].uni_tph - 1) / tl[m].uni_tph + t - 1) / t;
-            tl[m].uni_tph_queued = (int)std::max<int64_t>(1, (ck + per_thread * t - 1) / (per_thread * t));
+            const bool one_wave = tl[m].n_tiles <= best_slots;
+            const int64_t pq = one_wave && per_thread <= 8 ? 2 * per_thread : per_thread;
+            tl[m].uni_tph_queued = (int)std::max<int64_t>(1, (ck + pq * t - 1) / (pq * t));
         }
 
         if (m < 3) smem_bytes[m] = tail_smem(m, &hsum_in_smem[m], &csr_in_smem[m]);

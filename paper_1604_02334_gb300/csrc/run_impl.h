@@ -77,7 +77,7 @@ struct musr_run_s {
     struct Tiling {
         int threads = 256, n_tiles = 0, uni_tph = 0;  // uni_tph: tiles per histogram when all are equal
         // tiles per histogram for queued evaluations (equal histograms only,
-        // else 0): the fewest that give no thread more chunks than uni_tph does
+        // else 0): fewer, longer tiles than uni_tph (see the planner)
         int uni_tph_queued = 0;
         std::vector<int32_t> tile_hist, tile_start, tile_end;
         int32_t *d_tile_hist = nullptr, *d_tile_start = nullptr, *d_tile_end = nullptr;
