@@ -189,10 +189,13 @@ int musr_chi2_grad_device(musr_run run, int obj, int mode, const double* theta_d
  * evaluation's parameter staging and bin loop (Eq. 1, Eq. 3 / Eq. 4 and their
  * adjoint) may run while the previous kernel in the stream finishes; its
  * additions into the run's reduction buffers and its results wait for that
- * kernel.  MUSR_ENONFINITE for non-finite theta, MUSR_ENOTSUP with a
- * function array or more than 256 parameters.  Evaluations of one run queued
- * on different streams must be ordered by the caller (one reduction buffer
- * per run). */
+ * kernel.  Runs of equal-length histograms are split into fewer, longer
+ * blocks here than in the other entries (queued launches overlap, so fewer
+ * blocks cost less), so results agree with theirs to FP32 rounding, not bit
+ * for bit; repeated queued calls are bitwise equal.  MUSR_ENONFINITE for
+ * non-finite theta, MUSR_ENOTSUP with a function array or more than 256
+ * parameters.  Evaluations of one run queued on different streams must be
+ * ordered by the caller (one reduction buffer per run). */
 int musr_chi2_grad_async(musr_run run, int obj, int mode, const double* theta, double* out_dev,
                          int32_t* status_dev, void* stream);
 
