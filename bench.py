@@ -843,6 +843,7 @@ def run_ours(args):
                    "l2": f"inputs larger than L2: {N_RUNS} independent runs of the workload "
                          f"({N_RUNS * lay.total_bins * 4 / 1e6:.0f} MB of counts) cycled step by step, "
                          "launches back to back",
+                   "entry": "musr_chi2_grad_async: theta by value, results in device memory, evaluations queued",
                    "parallelism": f"replicas x{world}"},
         "roofline": rl,
         "clocks": clk,
